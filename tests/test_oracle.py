@@ -1,0 +1,332 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks an oracle function against something other than itself: a value the
+paper prints, a closed form, an invariant, a library routine or brute force on a tiny
+case.  None of these tests touches the CUDA library.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_20491_b300 import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+# ------------------------------------------------------------ inputs -----
+
+def test_splitmix64_published_outputs():
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64_seed0.json")))
+    want = [int(h, 16) for h in g["outputs_hex"]]
+    assert [S.splitmix64_scalar(g["seed"], k) for k in range(3)] == want
+    got = [int(v) for v in S.splitmix64(g["seed"], np.arange(3))]
+    assert got == want
+
+
+def test_splitmix64_vector_matches_scalar():
+    ks = np.array([0, 1, 2, 17, 12345, 2**40 + 3], dtype=np.uint64)
+    for seed in (0, 1, 4, 2**63 + 5):
+        v = S.splitmix64(seed, ks)
+        assert [int(x) for x in v] == [S.splitmix64_scalar(seed, int(k)) for k in ks]
+
+
+def test_generators_order_independent_and_distributed():
+    a = S.uniform(0, 1000)
+    b = S.uniform(0, 10)
+    assert np.array_equal(a[:10], b)
+    assert a.min() >= -1 and a.max() < 1 and abs(a.mean()) < 0.1
+    z = S.normal(2, 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    c = S.complex_normal(3, 100000)
+    assert abs(c[0::2].std() - 1) < 0.02 and abs(c[1::2].std() - 1) < 0.02
+    assert abs(np.corrcoef(c[0::2], c[1::2])[0, 1]) < 0.02
+
+
+# -------------------------------------------------- 1D operator, plan -----
+
+@pytest.mark.parametrize("n,L", [(5, 1.0), (32, 8.0), (100, 3.0), (255, 8.0)])
+def test_dirichlet_laplacian_eigenvalues_closed_form(n, L):
+    """V1 = 0: eigenvalues of h^-2 tridiag(-1,2,-1) are 4/h^2 sin^2(j pi / (2(n+1)))."""
+    P = O.plan([n], [L], [np.zeros(n)])
+    h = 2 * L / (n + 1)
+    j = np.arange(1, n + 1)
+    exact = 4.0 / h**2 * np.sin(j * math.pi / (2 * (n + 1))) ** 2
+    # a backward-stable eigensolver is accurate to O(eps ||H||) in absolute terms
+    assert np.max(np.abs(P.lam[0] - exact)) < 1e-13 * exact.max()
+
+
+@pytest.mark.parametrize("n", [7, 40])
+def test_dirichlet_laplacian_eigenvectors_closed_form(n):
+    """Eigenvector j is +-sqrt(2/(n+1)) sin(i j pi/(n+1)), i = 1..n."""
+    P = O.plan([n], [2.0], [np.zeros(n)])
+    i = np.arange(1, n + 1)
+    for j in range(1, n + 1):
+        v = math.sqrt(2.0 / (n + 1)) * np.sin(i * j * math.pi / (n + 1))
+        s = P.S[0][:, j - 1]
+        assert min(np.max(np.abs(s - v)), np.max(np.abs(s + v))) < 1e-13
+
+
+def test_operator_1d_matches_definition():
+    n, L = 6, 2.0
+    f = np.arange(n, dtype=float) ** 2
+    H = O.operator_1d(n, L, f)
+    h = 2 * L / (n + 1)
+    want = (2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)) / h**2 + np.diag(f)
+    assert np.array_equal(H, want)
+    assert np.allclose(O.grid(n, L), -L + h * np.arange(1, n + 1), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [8, 64, 200])
+def test_jacobi_reconstruction_orthogonality_and_library(n):
+    f = S.harmonic([n], [8.0], [1.3])[0]
+    H = O.operator_1d(n, 8.0, f)
+    lam, Q = O.jacobi_eigh(H)
+    assert np.max(np.abs(Q.T @ Q - np.eye(n))) < 1e-13
+    assert np.max(np.abs(Q @ np.diag(lam) @ Q.T - H)) < 1e-12 * np.abs(H).max()
+    assert np.all(np.diff(lam) >= 0)  # ascending (coarse symmetric grids give near-equal pairs)
+    ref = np.linalg.eigvalsh(H)
+    assert np.max(np.abs(lam - ref)) < 1e-12 * np.abs(ref).max()
+
+
+def test_jacobi_random_symmetric_vs_library():
+    A = S.normal(11, 30 * 30).reshape(30, 30)
+    A = A + A.T
+    lam, Q = O.jacobi_eigh(A)
+    assert np.max(np.abs(lam - np.linalg.eigvalsh(A))) < 1e-12
+    assert np.max(np.abs(Q @ np.diag(lam) @ Q.T - A)) < 1e-12
+
+
+# ------------------------------------------------------- dense checks -----
+
+@pytest.mark.parametrize("n", [(3, 4), (4, 3, 2), (2, 3, 2, 2)])
+def test_dense_operator_is_kronecker_sum(n):
+    """eq. general_system: A = sum_k I (x) .. (x) H_k (x) .. (x) I with axis 1 fastest,
+    i.e. H_1 is the right-most Kronecker factor."""
+    L = [1.0 + 0.5 * k for k in range(len(n))]
+    f = [S.uniform(7 + k, nk, 0, 3) for k, nk in enumerate(n)]
+    P = O.Plan(tuple(n), tuple(L), f)
+    A = O.dense_operator(P, sigma=0.25)
+    N = int(np.prod(n))
+    want = 0.25 * np.eye(N)
+    for k in range(len(n)):
+        Hk = O.operator_1d(n[k], L[k], f[k])
+        term = np.ones((1, 1))
+        for j in reversed(range(len(n))):
+            term = np.kron(term, Hk if j == k else np.eye(n[j]))
+        want += term
+    assert np.array_equal(A, want)
+
+
+def test_lu_solve_vs_library():
+    A = S.normal(5, 50 * 50).reshape(50, 50) + 3 * np.eye(50)
+    b = S.normal(6, 50)
+    assert rel(O.lu_solve(A, b), np.linalg.solve(A, b)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [(4, 4, 4), (6, 6, 6), (8, 8, 8), (10, 10, 10), (4, 6), (10, 8), (5, 8, 6)])
+def test_apply_inverse_vs_dense_lu(n):
+    """O2a vs O2b: the 4-step tensor solve equals LU of the assembled Kronecker sum."""
+    L = (8.0,) * len(n)
+    f = S.harmonic(n, L, (1.0, 1.3, 0.7)[: len(n)])
+    P = O.plan(n, L, f)
+    b = S.uniform(0, P.N)
+    u = O.apply_inverse(P, 1.0, b)
+    x = O.lu_solve(O.dense_operator(P, 1.0), b)
+    assert rel(u, x) < 1e-13
+
+
+def test_manufactured_solution_reproduces_table_accuracy_gh200():
+    """Q^1 FP64 3D row of Table accuracy_gh200: relative l2 error 3.66e-6 at n = 1099 on
+    [-1,1]^3 with eq. test_potential and u* = sin(pi x) sin(2 pi y) sin(3 pi z).
+    The error follows C h^2 + O(h^4); C is Richardson-extrapolated from n = 63, 127 and
+    the prediction at n = 1099 must round to the printed value."""
+    g = json.load(open(os.path.join(GOLDEN, "table_accuracy_gh200_q1.json")))
+    consts = []
+    for n in (63, 127):
+        x = S.nodes(n, 1.0)
+        f = [1600 * np.sin(math.pi / 4 * x) ** 2 + c * x**2 for c in (1, 2, 3)]
+        P = O.plan((n,) * 3, (1.0,) * 3, f)
+        X, Y, Z = x[None, None, :], x[None, :, None], x[:, None, None]
+        us = np.sin(math.pi * X) * np.sin(2 * math.pi * Y) * np.sin(3 * math.pi * Z)
+        V = 1600 * (np.sin(math.pi / 4 * X) ** 2 + np.sin(math.pi / 4 * Y) ** 2 + np.sin(math.pi / 4 * Z) ** 2) \
+            + X**2 + 2 * Y**2 + 3 * Z**2
+        rhs = ((14 * math.pi**2 + V) * us).reshape(-1)       # -Lap u* = 14 pi^2 u*
+        u = O.apply_inverse(P, 0.0, rhs)
+        consts.append(rel(u, us.reshape(-1)) * (n + 1) ** 2)
+    c_inf = consts[1] + (consts[1] - consts[0]) / 3.0
+    pred = c_inf / (g["n"] + 1) ** 2
+    assert round(pred, 8) == pytest.approx(g["rel_l2_err"], abs=5e-9), pred
+
+
+def test_harmonic_ground_energy_tends_to_d():
+    """V1 = sum x_k^2 on [-8,8]^d: lambda_min -> d (1D oscillator ground energy 1 per axis)
+    with an O(h^2) error: the error falls by ~4x per halving of h."""
+    errs = []
+    for n in (31, 63, 127, 255):
+        f = S.harmonic([n], [8.0], [1.0])[0]
+        lam, _ = O.jacobi_eigh(O.operator_1d(n, 8.0, f))
+        errs.append(abs(3 * lam[0] - 3.0))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.9 < r < 4.1 for r in ratios), ratios
+    assert errs[-1] < 2e-3
+
+
+# ------------------------------------------------------------- exp -------
+
+def _small_plan(n, seed=0):
+    L = (8.0,) * len(n)
+    return O.plan(n, L, S.harmonic(n, L, (1.0, 1.3, 0.7, 0.9)[: len(n)]))
+
+
+@pytest.mark.parametrize("n", [(6, 6, 6), (5, 4, 6), (6, 6)])
+def test_apply_exp_vs_dense_exponential(n):
+    P = _small_plan(n)
+    psi = S.complex_normal(3, P.N)
+    got = O.apply_exp(P, 0.01, psi)
+    H = O.dense_operator(P, 0.0)
+    assert rel(got, O.dense_exp(H, 0.01, psi)) < 1e-12
+    # the dense exponential itself against scipy's expm on the assembled matrix
+    import scipy.linalg
+    E = scipy.linalg.expm(-1j * 0.01 * H)
+    want = E @ (psi[0::2] + 1j * psi[1::2])
+    assert rel(got[0::2] + 1j * got[1::2], want) < 1e-11
+
+
+def test_exp_unitary_group_and_eigenphase():
+    P = _small_plan((12, 10, 9))
+    psi = S.complex_normal(3, P.N)
+    a = O.apply_exp(P, 0.03, psi)
+    assert abs(np.linalg.norm(a) / np.linalg.norm(psi) - 1) < 1e-14
+    back = O.apply_exp(P, -0.03, a)
+    assert rel(back, psi) < 1e-13
+    twice = O.apply_exp(P, 0.03, a)
+    assert rel(twice, O.apply_exp(P, 0.06, psi)) < 1e-13
+    # the ground eigenvector picks up exactly the phase e^{-i tau lambda_min}
+    g = np.einsum("i,j,k->kji", P.S[0][:, 0], P.S[1][:, 0], P.S[2][:, 0]).reshape(-1)
+    lam0 = sum(l[0] for l in P.lam)
+    z = np.zeros(2 * P.N)
+    z[0::2] = g
+    out = O.apply_exp(P, 0.7, z)
+    want = np.exp(-1j * 0.7 * lam0) * g
+    assert np.max(np.abs(out[0::2] + 1j * out[1::2] - want)) < 1e-13
+
+
+# ------------------------------------------------------------- PCG -------
+
+def test_pcg_v2_zero_one_iteration():
+    P = _small_plan((16, 16, 16))
+    b = S.uniform(0, P.N)
+    x, it, r = O.pcg(P, b, sigma=1.0, tol=1e-12)
+    assert it == 1 and r < 1e-13
+
+
+def test_pcg_constant_v2_one_iteration_with_shifted_preconditioner():
+    P = _small_plan((12, 16, 8))
+    b = S.uniform(1, P.N)
+    V2 = np.full(P.N, 2.5)
+    x, it, r = O.pcg(P, b, sigma=1.0, sigma_P=3.5, V2=V2, tol=1e-12)
+    assert it == 1 and r < 1e-13
+
+
+@pytest.mark.parametrize("n", [(6, 6, 6), (8, 7, 6)])
+def test_pcg_vs_dense_lu(n):
+    P = _small_plan(n)
+    b = S.uniform(2, P.N)
+    V2 = S.uniform(3, P.N, 0.0, 5.0)
+    x, it, r = O.pcg(P, b, sigma=0.5, V2=V2, tol=1e-13)
+    assert it > 1 and r < 1e-12
+    want = np.linalg.solve(O.dense_operator(P, 0.5, V2), b)
+    assert rel(x, want) < 1e-12
+
+
+def test_pcg_iterations_mesh_independent_for_bounded_v2():
+    """Theorem pcg: with bounded V2, the preconditioned operator's condition number is
+    bounded independently of h, so the iteration count stays (roughly) constant."""
+    its = []
+    for n in (16, 32, 64):
+        n3 = (n, n, n)
+        L = (8.0,) * 3
+        P = O.plan(n3, L, S.harmonic(n3, L, (1, 1, 1)))
+        V2 = S.v2_cos_bumps(n3, L, seed=1) + 5.0
+        b = S.uniform(0, P.N)
+        _, it, r = O.pcg(P, b, sigma=0.0, V2=V2, tol=1e-10)
+        assert it > 0 and r < 1e-9
+        its.append(it)
+    assert max(its) - min(its) <= 3, its
+
+
+# ---------------------------------------------------- inverse iteration ---
+
+def test_inverse_iteration_separable_one_step():
+    P = _small_plan((10, 12, 9))
+    lam_exact = sum(l[0] for l in P.lam)
+    u, lam, it, _ = O.inverse_iteration(P, shift=lam_exact - 1.0, V2=np.zeros(P.N))
+    assert it == 1
+    assert abs(lam - lam_exact) / lam_exact < 1e-14
+
+
+@pytest.mark.parametrize("n", [(6, 6, 6), (8, 8, 8)])
+def test_inverse_iteration_vs_dense_eigensolver(n):
+    L = (8.0,) * 3
+    P = O.plan(n, L, S.harmonic(n, L, (1, 1, 1)))
+    V2 = S.v2_cos_bumps(n, L, seed=1)
+    s = sum(l[0] for l in P.lam) + V2.min() - 1.0
+    u, lam, it, _ = O.inverse_iteration(P, shift=s, V2=V2, pcg_tol=1e-12)
+    ev, evec = np.linalg.eigh(O.dense_operator(P, 0.0, V2))
+    assert it > 0
+    assert abs(lam - ev[0]) / abs(ev[0]) < 1e-11
+    g = evec[:, 0] * np.sign(evec[:, 0].sum())
+    assert np.linalg.norm(u - g) < 1e-5  # eigenvector error ~ sqrt of the eigenvalue tolerance
+
+
+# ------------------------------------------------------------ Strang -----
+
+def test_strang_v2_zero_is_exact_propagator():
+    P = _small_plan((8, 9, 7))
+    psi = S.complex_normal(3, P.N)
+    a = O.strang(P, np.zeros(P.N), 0.02, 5, psi)
+    b = O.apply_exp(P, 0.1, psi)
+    assert rel(a, b) < 1e-13
+
+
+def test_strang_separable_v2_second_order_and_norm():
+    """Separable V2 = sum g_k(x_k): the exact answer is the exact propagator of the plan
+    with V1 + V2; Strang's global error falls 4x per halving of dt (order 2.00)."""
+    n = (10, 9, 8)
+    L = (4.0,) * 3
+    f = S.harmonic(n, L, (1, 1, 1))
+    g = [np.cos(S.nodes(nk, Lk)) * 3.0 for nk, Lk in zip(n, L)]
+    P = O.plan(n, L, f)
+    Pfull = O.plan(n, L, [a + b for a, b in zip(f, g)])
+    V2 = (g[0][None, None, :] + g[1][None, :, None] + g[2][:, None, None]).reshape(-1)
+    psi = S.sine_state(n, L)
+    T = 0.2
+    exact = O.apply_exp(Pfull, T, psi)
+    errs = []
+    for steps in (10, 20, 40):
+        out = O.strang(P, V2, T / steps, steps, psi)
+        assert abs(np.linalg.norm(out) - 1.0) < steps * 1e-14  # rounding random walk
+        errs.append(np.linalg.norm(out - exact))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.95 < r < 2.05 for r in rates), rates
+
+
+def test_strang_converges_to_dense_exponential_of_full_h():
+    n = (5, 5, 4)
+    L = (3.0,) * 3
+    P = O.plan(n, L, S.harmonic(n, L, (1, 1, 1)))
+    V2 = S.v2_soft_coulomb((5, 5, 4), L, dim=1)  # three 1D particles: a non-separable V2
+    psi = S.complex_normal(9, P.N)
+    H = O.dense_operator(P, 0.0, V2)
+    want = O.dense_exp(H, 0.1, psi)
+    e1 = rel(O.strang(P, V2, 0.01, 10, psi), want)
+    e2 = rel(O.strang(P, V2, 0.005, 20, psi), want)
+    assert e1 < 1e-3 and 3.8 < e1 / e2 < 4.2
