@@ -1,0 +1,181 @@
+/*
+ * tschrod.h -- C ABI of the B300 (sm_103a) tensor-product solver for the
+ * Schroedinger operator  H = -Delta + V1 (+ V2)  on the box [-L_1,L_1] x ... x [-L_d,L_d]
+ * with homogeneous Dirichlet conditions, discretised by Q^1 spectral elements
+ * (second-order central differences), with a separable potential
+ *     V1(x) = f_1(x_1) + ... + f_d(x_d).
+ *
+ * Method (Sec. 2.1, eqs. general_system, tensor_system, eigen_decomp): per axis k the
+ * 1D operator H_k = h_k^-2 tridiag(-1,2,-1) + diag f_k(x_{k,i}) is eigendecomposed once,
+ * H_k = S_k diag(lambda_k) S_k^T (plan creation; S_k orthogonal because the Q^1 mass
+ * matrix is h I).  Every apply then runs d mode-k contractions with S_k^T (forward
+ * transform), a pointwise scale of coefficient (i_1..i_d) by a function of
+ * Lambda = lambda_1[i_1] + ... + lambda_d[i_d], and d mode-k contractions with S_k
+ * (backward transform).
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: axis k has n_k interior nodes x_{k,i} = -L_k + i h_k, i = 1..n_k,
+ *     h_k = 2 L_k / (n_k + 1).
+ *   - Layout: a grid function is the vector vec(U) with axis 1 fastest, i.e. element
+ *     (i_1, ..., i_d) (0-based) sits at i_1 + n_1 (i_2 + n_2 (i_3 + ...)).
+ *     N = n_1 n_2 ... n_d.  Complex data are interleaved (re, im) pairs:
+ *     TS_C128 = 2 doubles per element, TS_C64 = 2 floats per element.
+ *   - Every array argument is caller-owned DEVICE memory on the plan's device unless
+ *     stated otherwise, aligned to at least 16 bytes.  The library never frees it.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls enqueue
+ *     their work on it and return without waiting, except those that return host
+ *     scalars (iterations, residuals, eigenvalues), which synchronise that stream.
+ *   - Scratch memory (a few N-sized buffers) comes from the stream-ordered CUDA memory
+ *     pool of the plan's device (cudaMallocAsync / cudaFreeAsync on `stream`).
+ *   - A plan is immutable once created; several host threads may use one plan at once
+ *     on different streams.
+ *   - Errors are returned as a ts_status, never by aborting; ts_last_error() gives a
+ *     thread-local message for the last failing call of the calling thread.
+ */
+#ifndef TSCHROD_H
+#define TSCHROD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TS_MAX_DIM 12
+
+typedef enum {
+  TS_OK = 0,
+  TS_ERR_INVALID_ARG = 1,   /* a pointer, size or enum is out of range                */
+  TS_ERR_NO_MEMORY = 2,     /* a device allocation failed                             */
+  TS_ERR_CUDA = 3,          /* a CUDA runtime/library call failed                     */
+  TS_ERR_NOT_CONVERGED = 4, /* an iteration hit its cap; the best iterate is written  */
+  TS_ERR_UNSUPPORTED = 5,   /* valid request that this build/plan cannot serve        */
+  TS_ERR_TIMEOUT = 6        /* a bounded device-side wait ran out                     */
+} ts_status;
+
+/* Arithmetic of the mode-k contractions (the eigendecompositions, the eigenvalue sums,
+ * PCG scalars and inner products are always FP64). */
+typedef enum {
+  TS_FP64 = 0,   /* plain FP64 (FFMA64) contractions                                      */
+  TS_BF16X3 = 1, /* 2-term bf16 splits of data and S_k, 3 products, FP32 accumulate (tcgen05) */
+  TS_BF16X6 = 2, /* 3-term bf16 splits, 6 products, FP32 accumulate (tcgen05)              */
+  TS_TF32X3 = 3, /* 2-term tf32 splits, 3 products (reserved)                              */
+  TS_FP16X3 = 4  /* 2-term fp16 splits with scaling (reserved)                             */
+} ts_precision;
+
+typedef enum { TS_R64 = 0, TS_C128 = 1, TS_C64 = 2 } ts_dtype;
+
+typedef struct ts_plan ts_plan;
+
+/* Problem description.  All pointers are HOST memory, read during ts_plan_create only. */
+typedef struct {
+  int d;                   /* dimension, 1 <= d <= TS_MAX_DIM                          */
+  const int* n;            /* n[k] interior nodes on axis k, 1 <= n[k] <= 4096          */
+  const double* L;         /* L[k] > 0: axis k spans [-L[k], L[k]]                     */
+  const double* const* f;  /* f[k][i] = f_k(x_{k,i+1}), i = 0..n[k]-1 (V1 samples)      */
+  int bc;                  /* boundary condition: 0 = homogeneous Dirichlet (only one) */
+} ts_plan_desc;
+
+/*
+ * Step 1 of Sec. 2.1 (eq. eigen_decomp): assemble H_k = h_k^-2 tridiag(-1,2,-1) + diag f_k
+ * for every axis, eigendecompose each in FP64 on the GPU (axes with identical (n, L, f)
+ * share one decomposition) and keep S_k, S_k^T, lambda_k and, for every precision bit
+ * set in precision_mask (bit p = 1u << ts_precision p; TS_FP64 is always built), the
+ * split low-precision copies of S_k resident on the current device.  The work runs on
+ * `stream` and is complete when the call returns.  *out receives the plan; on error it
+ * is set to NULL.
+ */
+ts_status ts_plan_create(const ts_plan_desc* desc, unsigned precision_mask, void* stream,
+                         ts_plan** out);
+
+/* Frees the plan's device tables.  NULL is accepted.  No call may be using the plan. */
+ts_status ts_plan_destroy(ts_plan* plan);
+
+/* Copies lambda_axis (ascending, n[axis] doubles) into HOST memory lambda_host. */
+ts_status ts_plan_eigs(const ts_plan* plan, int axis, double* lambda_host);
+
+/* Copies S_axis (row-major n x n, column j = eigenvector of lambda_j) into HOST memory. */
+ts_status ts_plan_eigvecs(const ts_plan* plan, int axis, double* S_host);
+
+/* Plan geometry: *d, n[0..d-1] (n may be NULL) and *N (may be NULL). */
+ts_status ts_plan_shape(const ts_plan* plan, int* d, int* n, long long* N);
+
+/* Bytes of device memory the plan's tables hold. */
+ts_status ts_plan_bytes(const ts_plan* plan, long long* bytes);
+
+/*
+ * u = (-Delta_h + V1 + sigma)^{-1} b   (steps 2-4 of Sec. 2.1; direct solve).
+ * b, u: N doubles (real, FP64).  b and u may alias.  sigma must keep the operator
+ * nonsingular (sigma != -lambda_min sum); the call does not check definiteness.
+ * prec selects the contraction arithmetic (TS_FP64, TS_BF16X3, TS_BF16X6); a split
+ * precision needs its bit in the plan's precision_mask and every n_k a multiple of 8.
+ */
+ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, double* u,
+                           ts_precision prec, void* stream);
+
+/*
+ * psi_out = e^{-i tau (-Delta_h + V1)} psi_in   (exact propagator, eq. exact_prop):
+ * forward transform, multiply coefficient (i_1..i_d) by e^{-i tau Lambda}, backward
+ * transform.  dtype TS_C128 (2N doubles) or TS_C64 (2N floats); psi_in and psi_out may
+ * alias.  prec as for ts_apply_inverse (TS_C64 data with TS_FP64 arithmetic is allowed).
+ */
+ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void* psi_out,
+                       ts_dtype dtype, ts_precision prec, void* stream);
+
+/*
+ * y = (-Delta_h + V1 + V2 + sigma) x by the 2d+1 point stencil of eq. general_system
+ * (zero Dirichlet ghosts).  V2: N doubles or NULL.  x, y: N doubles, must not alias.
+ */
+ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2,
+                            const double* x, double* y, void* stream);
+
+/*
+ * Preconditioned CG (Sec. 3.2) for (-Delta_h + V1 + V2 + sigma) x = b with the
+ * preconditioner P = (-Delta_h + V1 + sigma_P)^{-1} applied in precision `precond`.
+ * The recurrence uses the flexible (Polak-Ribiere) beta = -alpha (z_{k+1}, q_k)/(z_k, r_k),
+ * which equals the standard beta when P is applied exactly.  All inner products and
+ * vector updates are FP64 with deterministic reductions.
+ * x: in = initial guess, out = iterate.  Stops when ||r_k||_2 / ||b||_2 < tol on the
+ * recurrence residual, or after maxit iterations (then TS_ERR_NOT_CONVERGED, x holds
+ * the last iterate).  *iters (may be NULL) = iterations taken; *relres (may be NULL) =
+ * TRUE relative residual ||b - A x|| / ||b|| recomputed at exit.  Synchronises stream.
+ */
+ts_status ts_pcg(const ts_plan* plan, double sigma, double sigma_P, const double* V2,
+                 const double* b, double* x, double tol, int maxit, ts_precision precond,
+                 int* iters, double* relres, void* stream);
+
+/*
+ * Shifted inverse iteration (Sec. 4.1, Sec. 5.3.1) for the smallest eigenpair of
+ * H = -Delta_h + V1 + V2 with shift s (H - s must be positive definite):
+ *   u_0 = product of the per-axis ground eigenvectors (if init_from_plan != 0, else
+ *         the caller's u), lambda_0 = (u_0, H u_0);
+ *   repeat  solve (H - s) w = u_k by ts_pcg (sigma = sigma_P = -s, tolerance pcg_tol,
+ *           warm start w_0 = u_k / (lambda_k - s));  u_{k+1} = w / ||w||;
+ *           lambda_{k+1} = (u_{k+1}, H u_{k+1})
+ *   until |lambda_{k+1} - lambda_k| / |lambda_{k+1}| < tol_lambda or maxit.
+ * u: N doubles (in/out).  The sign is fixed so that sum(u) > 0.  *lambda, *outer_iters,
+ * *pcg_iters may be NULL.  Synchronises stream.
+ */
+ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* V2, double* u,
+                               int init_from_plan, double tol_lambda, int maxit, double pcg_tol,
+                               int pcg_maxit, ts_precision precond, double* lambda,
+                               int* outer_iters, long long* pcg_iters, void* stream);
+
+/*
+ * nsteps Strang steps (Sec. 5.1, Remark cost_naive_merged with M = 1) of
+ * i d psi/dt = (A + B) psi, A = -Delta_h + V1 (exact propagator), B = diag(V2):
+ *     psi <- e^{-i V2 dt/2} e^{-i A dt} e^{-i V2 dt/2} psi.
+ * The half steps of adjacent steps are merged into one e^{-i V2 dt} factor.
+ * V2: N doubles (device).  psi: TS_C128 or TS_C64, updated in place.
+ */
+ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double* V2, void* psi,
+                        ts_dtype dtype, ts_precision prec, void* stream);
+
+/* Thread-local message of the calling thread's last failing call ("" if none). */
+const char* ts_last_error(void);
+
+/* Library build string (compile flags, architecture). */
+const char* ts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSCHROD_H */

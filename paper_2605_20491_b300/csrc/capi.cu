@@ -1,0 +1,204 @@
+// extern "C" entry points of include/tschrod.h: argument validation, device selection
+// and error reporting around the drivers.
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+#include "mixed.cuh"
+#include "pointwise.cuh"
+#include "solvers.cuh"
+
+namespace ts {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+void plan_free(ts_plan* p);
+ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, ts_plan** out);
+
+namespace {
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+ts_status check_prec(const ts_plan* p, ts_precision prec) {
+  if ((int)prec < 0 || (int)prec >= NPREC) {
+    set_error("invalid precision %d", (int)prec);
+    return TS_ERR_INVALID_ARG;
+  }
+  if (prec == TS_FP64) return TS_OK;
+  if (!(p->precision_mask & (1u << prec))) {
+    set_error("precision %d was not requested in the plan's precision_mask", (int)prec);
+    return TS_ERR_UNSUPPORTED;
+  }
+  return TS_OK;
+}
+
+}  // namespace
+}  // namespace ts
+
+using namespace ts;
+
+#define TS_API_BEGIN(plan)                                       \
+  clear_error();                                                 \
+  if (!(plan)) {                                                 \
+    set_error("plan is NULL");                                   \
+    return TS_ERR_INVALID_ARG;                                   \
+  }                                                              \
+  DeviceGuard _guard((plan)->device);                            \
+  if (!_guard.ok) {                                              \
+    set_error("cannot select device %d", (plan)->device);        \
+    return TS_ERR_CUDA;                                          \
+  }
+
+extern "C" {
+
+const char* ts_last_error(void) { return g_err; }
+
+const char* ts_version(void) {
+  return "tschrod 0.1 (sm_103a; FP64 SIMT, bf16 split tcgen05, small-n fused kernels)";
+}
+
+ts_status ts_plan_create(const ts_plan_desc* desc, unsigned precision_mask, void* stream, ts_plan** out) {
+  clear_error();
+  if (!out) {
+    set_error("out is NULL");
+    return TS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  TS_REQUIRE(desc, "desc is NULL");
+  TS_REQUIRE(desc->d >= 1 && desc->d <= TS_MAX_DIM, "d = %d out of range [1, %d]", desc->d, TS_MAX_DIM);
+  TS_REQUIRE(desc->n && desc->L && desc->f, "desc->n, desc->L and desc->f must be non-NULL");
+  TS_REQUIRE(desc->bc == 0, "only homogeneous Dirichlet (bc = 0) is supported");
+  TS_REQUIRE(precision_mask < (1u << NPREC), "precision_mask 0x%x has unknown bits", precision_mask);
+  long long N = 1;
+  for (int k = 0; k < desc->d; ++k) {
+    TS_REQUIRE(desc->n[k] >= 1 && desc->n[k] <= 4096, "n[%d] = %d out of range [1, 4096]", k, desc->n[k]);
+    TS_REQUIRE(desc->L[k] > 0.0, "L[%d] must be positive", k);
+    TS_REQUIRE(desc->f[k], "f[%d] is NULL", k);
+    N *= desc->n[k];
+    TS_REQUIRE(N <= (1LL << 40), "grid too large");
+  }
+  return plan_create(desc, precision_mask, (cudaStream_t)stream, out);
+}
+
+ts_status ts_plan_destroy(ts_plan* plan) {
+  clear_error();
+  if (!plan) return TS_OK;
+  DeviceGuard g(plan->device);
+  plan_free(plan);
+  return TS_OK;
+}
+
+ts_status ts_plan_eigs(const ts_plan* plan, int axis, double* lambda_host) {
+  clear_error();
+  TS_REQUIRE(plan && lambda_host, "NULL argument");
+  TS_REQUIRE(axis >= 0 && axis < plan->d, "axis %d out of range", axis);
+  std::memcpy(lambda_host, plan->lam_host[axis].data(), sizeof(double) * plan->n[axis]);
+  return TS_OK;
+}
+
+ts_status ts_plan_eigvecs(const ts_plan* plan, int axis, double* S_host) {
+  clear_error();
+  TS_REQUIRE(plan && S_host, "NULL argument");
+  TS_REQUIRE(axis >= 0 && axis < plan->d, "axis %d out of range", axis);
+  std::memcpy(S_host, plan->S_host[axis].data(), sizeof(double) * plan->n[axis] * plan->n[axis]);
+  return TS_OK;
+}
+
+ts_status ts_plan_shape(const ts_plan* plan, int* d, int* n, long long* N) {
+  clear_error();
+  TS_REQUIRE(plan, "plan is NULL");
+  if (d) *d = plan->d;
+  if (n)
+    for (int k = 0; k < plan->d; ++k) n[k] = plan->n[k];
+  if (N) *N = plan->N;
+  return TS_OK;
+}
+
+ts_status ts_plan_bytes(const ts_plan* plan, long long* bytes) {
+  clear_error();
+  TS_REQUIRE(plan && bytes, "NULL argument");
+  *bytes = plan->bytes;
+  return TS_OK;
+}
+
+ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, double* u, ts_precision prec,
+                           void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(b && u, "b and u must be non-NULL");
+  TS_TRY(check_prec(plan, prec));
+  return apply_inverse_impl(plan, sigma, b, u, prec, (cudaStream_t)stream);
+}
+
+ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void* psi_out, ts_dtype dtype,
+                       ts_precision prec, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(psi_in && psi_out, "psi_in and psi_out must be non-NULL");
+  TS_REQUIRE(dtype == TS_C128 || dtype == TS_C64, "dtype must be TS_C128 or TS_C64");
+  TS_TRY(check_prec(plan, prec));
+  return apply_exp_impl(plan, tau, psi_in, psi_out, dtype, prec, (cudaStream_t)stream);
+}
+
+ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2, const double* x, double* y,
+                            void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(x && y && x != y, "x and y must be non-NULL and distinct");
+  double* partial = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  TS_TRY(scratch_alloc((void**)&partial, sizeof(double) * 2 * RED_BLOCKS, s));
+  ts_status st = stencil_apply(plan, V2, sigma, x, y, partial, nullptr, s);
+  scratch_free(partial, s);
+  return st;
+}
+
+ts_status ts_pcg(const ts_plan* plan, double sigma, double sigma_P, const double* V2, const double* b, double* x,
+                 double tol, int maxit, ts_precision precond, int* iters, double* relres, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(b && x && b != x, "b and x must be non-NULL and distinct");
+  TS_REQUIRE(tol > 0.0 && maxit >= 0, "tol must be > 0 and maxit >= 0");
+  TS_TRY(check_prec(plan, precond));
+  return pcg_impl(plan, sigma, sigma_P, V2, b, x, tol, maxit, precond, iters, relres, (cudaStream_t)stream);
+}
+
+ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* V2, double* u, int init_from_plan,
+                               double tol_lambda, int maxit, double pcg_tol, int pcg_maxit, ts_precision precond,
+                               double* lambda, int* outer_iters, long long* pcg_iters, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(u, "u must be non-NULL");
+  TS_REQUIRE(tol_lambda > 0.0 && pcg_tol > 0.0 && maxit >= 1 && pcg_maxit >= 1, "bad tolerances or caps");
+  TS_TRY(check_prec(plan, precond));
+  return inverse_iteration_impl(plan, shift, V2, u, init_from_plan, tol_lambda, maxit, pcg_tol, pcg_maxit, precond,
+                                lambda, outer_iters, pcg_iters, (cudaStream_t)stream);
+}
+
+ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double* V2, void* psi, ts_dtype dtype,
+                        ts_precision prec, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(V2 && psi, "V2 and psi must be non-NULL");
+  TS_REQUIRE(dtype == TS_C128 || dtype == TS_C64, "dtype must be TS_C128 or TS_C64");
+  TS_REQUIRE(nsteps >= 0, "nsteps must be >= 0");
+  TS_TRY(check_prec(plan, prec));
+  return split_step_impl(plan, dt, nsteps, V2, psi, dtype, prec, (cudaStream_t)stream);
+}
+
+}  // extern "C"

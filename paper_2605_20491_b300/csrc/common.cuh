@@ -1,0 +1,110 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/tschrod.h"
+
+namespace ts {
+
+constexpr int MAXD = TS_MAX_DIM;
+constexpr int NPREC = 5;
+constexpr int MAX_PLANES = 3;
+
+// Thread-local error message of the last failing call.
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define TS_CHECK_CUDA(call)                                                               \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) {                                                              \
+      ::ts::set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #call,                  \
+                      cudaGetErrorString(_e));                                            \
+      return _e == cudaErrorMemoryAllocation ? TS_ERR_NO_MEMORY : TS_ERR_CUDA;            \
+    }                                                                                     \
+  } while (0)
+
+#define TS_TRY(expr)                       \
+  do {                                     \
+    ts_status _s = (expr);                 \
+    if (_s != TS_OK) return _s;            \
+  } while (0)
+
+#define TS_REQUIRE(cond, ...)              \
+  do {                                     \
+    if (!(cond)) {                         \
+      ::ts::set_error(__VA_ARGS__);        \
+      return TS_ERR_INVALID_ARG;           \
+    }                                      \
+  } while (0)
+
+// Per-axis parameters passed by value to pointwise kernels.
+struct AxisParams {
+  int d;
+  int n[MAXD];
+  long long stride[MAXD];   // stride of axis k in vec() order
+  double ih2[MAXD];         // 1 / h_k^2
+  const double* tab[MAXD];  // per-axis table (eigenvalues or potential samples), n[k] entries
+};
+
+}  // namespace ts
+
+// The plan: per-axis device tables.  Axes with identical (n, L, f) share storage.
+struct ts_plan {
+  int device = 0;
+  int d = 0;
+  int n[TS_MAX_DIM] = {};
+  double L[TS_MAX_DIM] = {};
+  long long N = 0;
+  int nmax = 0;
+  unsigned precision_mask = 1u;
+  // FP64 tables (device).  S: row-major S[i][j] (column j = eigenvector j); St = S^T.
+  double* S[TS_MAX_DIM] = {};
+  double* St[TS_MAX_DIM] = {};
+  double* lam[TS_MAX_DIM] = {};
+  double* f[TS_MAX_DIM] = {};
+  // Split bf16 planes (device), [prec][axis][plane]: row-major n x n copies of S^T
+  // (forward operand, "Bf") and S (backward operand, "Bb"), K (contracted index)
+  // contiguous in both.
+  __nv_bfloat16* Bf[ts::NPREC][TS_MAX_DIM][ts::MAX_PLANES] = {};
+  __nv_bfloat16* Bb[ts::NPREC][TS_MAX_DIM][ts::MAX_PLANES] = {};
+  // Host copies.
+  std::vector<double> lam_host[TS_MAX_DIM];
+  std::vector<double> S_host[TS_MAX_DIM];
+  // Ownership: which axis owns each shared table (owner[k] == k owns it).
+  int owner[TS_MAX_DIM] = {};
+  long long bytes = 0;
+};
+
+namespace ts {
+
+// Device-side helpers implemented in the .cu files.
+AxisParams axis_params(const ts_plan* p, bool eig_tables);
+
+// Scratch allocation from the stream-ordered pool.
+ts_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t s);
+void scratch_free(void* ptr, cudaStream_t s);
+
+// FP64 contraction pass (rotating form): see mode_fp64.cu.
+ts_status rot_pass_fp64(const double* X, double* Y, const double* B, long long R, int n, int ncomp,
+                        cudaStream_t s);
+// Pointwise kernels: see pointwise.cu.
+ts_status scale_inverse_fp64(const ts_plan* p, double sigma, double* X, cudaStream_t s);
+ts_status scale_exp_c128(const ts_plan* p, double tau, double* X, cudaStream_t s);
+ts_status phase_v2_c128(long long N, const double* V2, double theta_scale, double* psi, cudaStream_t s);
+ts_status phase_v2_c64(long long N, const double* V2, double theta_scale, float* psi, cudaStream_t s);
+ts_status convert_c64_to_c128(long long N, const float* in, double* out, cudaStream_t s);
+ts_status convert_c128_to_c64(long long N, const double* in, float* out, cudaStream_t s);
+
+// Drivers: see apply.cu.
+ts_status apply_inverse_impl(const ts_plan* p, double sigma, const double* b, double* u,
+                             ts_precision prec, cudaStream_t s);
+ts_status apply_exp_impl(const ts_plan* p, double tau, const void* in, void* out, ts_dtype dt,
+                         ts_precision prec, cudaStream_t s);
+
+}  // namespace ts

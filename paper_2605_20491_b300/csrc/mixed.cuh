@@ -1,0 +1,20 @@
+// Split-precision (tensor-core) apply: see mixed.cu.
+#pragma once
+#include "common.cuh"
+
+namespace ts {
+
+enum class MixedOp { Inverse = 0, Exp = 1 };
+
+// Number of bf16 planes per value for a split precision (0 if not a bf16 split).
+int bf16_planes(ts_precision prec);
+
+// Mixed-precision apply: op Inverse (real FP64 in/out, param = sigma) or Exp (complex
+// in/out of dtype dt, param = tau).
+ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
+                      ts_dtype dt, cudaStream_t s);
+
+// Build the split planes of S_k^T and S_k for precision `prec` (plan creation).
+ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s);
+
+}  // namespace ts

@@ -1,0 +1,371 @@
+// Pointwise kernels of the solver: the eigenvalue scale (step 3 of Sec. 2.1), the
+// propagator phase e^{-i tau Lambda} (eq. exact_prop), the potential phase e^{-i V2 theta}
+// of the Strang step (Sec. 5.1), the 2d+1 point operator of eq. general_system, the
+// PCG vector updates (Sec. 3.2) and deterministic FP64 reductions.
+//
+// All kernels are HBM-bound streams; they use grid-stride loops over a fixed grid of
+// (148 SMs x 4) CTAs so that reductions see a fixed partition of the index space and
+// return bit-identical sums on every call (two-level reduction: per-CTA partials in a
+// fixed order, then one CTA sums the partials in a fixed order).
+#include "common.cuh"
+#include "pointwise.cuh"
+
+namespace ts {
+
+AxisParams axis_params(const ts_plan* p, bool eig_tables) {
+  AxisParams a{};
+  a.d = p->d;
+  long long st = 1;
+  for (int k = 0; k < p->d; ++k) {
+    a.n[k] = p->n[k];
+    a.stride[k] = st;
+    st *= p->n[k];
+    double h = 2.0 * p->L[k] / (p->n[k] + 1);
+    a.ih2[k] = 1.0 / (h * h);
+    a.tab[k] = eig_tables ? p->lam[k] : p->f[k];
+  }
+  return a;
+}
+
+namespace {
+
+__device__ __forceinline__ double lambda_sum(const AxisParams& a, long long idx) {
+  double s = 0.0;
+  for (int k = 0; k < a.d; ++k) {
+    long long q = idx / a.n[k];
+    int i = (int)(idx - q * a.n[k]);
+    s += a.tab[k][i];
+    idx = q;
+  }
+  return s;
+}
+
+__global__ void k_scale_inverse(AxisParams a, double sigma, double* X, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    X[i] = X[i] / (lambda_sum(a, i) + sigma);
+}
+
+__global__ void k_scale_exp(AxisParams a, double tau, double* X, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s, c;
+    sincos(tau * lambda_sum(a, i), &s, &c);
+    double re = X[2 * i], im = X[2 * i + 1];
+    X[2 * i] = re * c + im * s;
+    X[2 * i + 1] = im * c - re * s;
+  }
+}
+
+__global__ void k_phase_c128(const double* V2, double th, double* psi, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s, c;
+    sincos(th * V2[i], &s, &c);
+    double re = psi[2 * i], im = psi[2 * i + 1];
+    psi[2 * i] = re * c + im * s;
+    psi[2 * i + 1] = im * c - re * s;
+  }
+}
+
+__global__ void k_phase_c64(const double* V2, double th, float* psi, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s, c;
+    sincos(th * V2[i], &s, &c);
+    float2 v = reinterpret_cast<float2*>(psi)[i];
+    float re = v.x, im = v.y;
+    reinterpret_cast<float2*>(psi)[i] = make_float2((float)(re * c + im * s), (float)(im * c - re * s));
+  }
+}
+
+__global__ void k_c64_to_c128(const float* in, double* out, long long n2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+__global__ void k_c128_to_c64(const double* in, float* out, long long n2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// ---------------------------------------------------------------- reductions ---
+
+// Block-wide sum in a fixed order: warp shuffles then one warp over the warp sums.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) ws[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (l < (int)(blockDim.x >> 5)) ? ws[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// y = (A + V2 + sigma) x (mode 0), or y = b - (A + V2 + sigma) x (mode 1), with the
+// 2d+1 point stencil; partial[blk*2 + 0] = sum of x.y (mode 0) or y.y (mode 1),
+// partial[blk*2 + 1] = b.b (mode 1) or 0.
+template <int MODE>
+__global__ void k_stencil(AxisParams a, const double* __restrict__ V2, double sigma,
+                          const double* __restrict__ x, const double* __restrict__ b,
+                          double* __restrict__ y, long long N, double* partial) {
+  double acc0 = 0.0, acc1 = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double xc = x[idx];
+    double v = sigma + (V2 ? V2[idx] : 0.0);
+    double lap = 0.0;
+    long long r = idx;
+    for (int k = 0; k < a.d; ++k) {
+      long long q = r / a.n[k];
+      int i = (int)(r - q * a.n[k]);
+      r = q;
+      double left = i > 0 ? x[idx - a.stride[k]] : 0.0;
+      double right = i + 1 < a.n[k] ? x[idx + a.stride[k]] : 0.0;
+      lap += a.ih2[k] * (2.0 * xc - left - right);
+      v += a.tab[k][i];
+    }
+    double ax = lap + v * xc;
+    if (MODE == 0) {
+      y[idx] = ax;
+      acc0 += xc * ax;
+    } else {
+      double bi = b[idx];
+      double ri = bi - ax;
+      y[idx] = ri;
+      acc0 += ri * ri;
+      acc1 += bi * bi;
+    }
+  }
+  double s0 = block_sum(acc0);
+  double s1 = block_sum(acc1);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// partial sums of (a.b) and (c.d) (c, d may be NULL).
+__global__ void k_dot2(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                       const double* __restrict__ d, long long N, double* partial) {
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    s0 += b ? a[i] * b[i] : a[i];
+    if (c) s1 += c[i] * d[i];
+  }
+  s0 = block_sum(s0);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// Sum the partials in a fixed order; out[0], out[1] = the two sums.
+__global__ void k_sum_partials(const double* partial, int nblk, double* out) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    s0 += partial[2 * i];
+    s1 += partial[2 * i + 1];
+  }
+  s0 = block_sum(s0);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    out[0] = s0;
+    out[1] = s1;
+  }
+}
+
+// PCG step: alpha = rz / pq; x += alpha p; r -= alpha q; partial r.r; alpha -> *alpha_out.
+__global__ void k_pcg_xr(const double* rz, const double* pq, double* alpha_out, double* __restrict__ x,
+                         double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q,
+                         long long N, double* partial) {
+  double alpha = rz[0] / pq[0];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = acc;
+    partial[2 * blockIdx.x + 1] = 0.0;
+    if (blockIdx.x == 0) *alpha_out = alpha;
+  }
+}
+
+// p = z + beta p with the flexible beta = -alpha (z_{k+1}.q_k) / (z_k.r_k); first: p = z.
+__global__ void k_pcg_p(const double* alpha, const double* zq, const double* rz_old, int first,
+                        double* __restrict__ p, const double* __restrict__ z, long long N) {
+  double beta = first ? 0.0 : -alpha[0] * zq[0] / rz_old[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+}
+
+__global__ void k_copy_scalar(const double* src, double* dst) { *dst = *src; }
+
+// u = prod_k g_k[i_k] where g_k = row 0 of S_k^T (the ground eigenvector of axis k).
+__global__ void k_tensor_ground(AxisParams a, double* u, long long N) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx;
+    double v = 1.0;
+    for (int k = 0; k < a.d; ++k) {
+      long long q = r / a.n[k];
+      int i = (int)(r - q * a.n[k]);
+      r = q;
+      v *= a.tab[k][i];
+    }
+    u[idx] = v;
+  }
+}
+
+__global__ void k_axpby(double a, const double* x, double b, double* y, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_scale_by_scalar(const double* num, const double* den, double* y, const double* x, long long N) {
+  // y = x * (num[0] / den[0]) -- den may be NULL (then y = x / sqrt(num[0]))
+  double f = den ? num[0] / den[0] : 1.0 / sqrt(num[0]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] * f;
+}
+
+}  // namespace
+
+int red_blocks() { return RED_BLOCKS; }
+
+static inline unsigned grid_for(long long N) {
+  long long g = (N + 255) / 256;
+  return (unsigned)(g < RED_BLOCKS ? (g < 1 ? 1 : g) : RED_BLOCKS);
+}
+
+ts_status scale_inverse_fp64(const ts_plan* p, double sigma, double* X, cudaStream_t s) {
+  k_scale_inverse<<<grid_for(p->N), 256, 0, s>>>(axis_params(p, true), sigma, X, p->N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status scale_exp_c128(const ts_plan* p, double tau, double* X, cudaStream_t s) {
+  k_scale_exp<<<grid_for(p->N), 256, 0, s>>>(axis_params(p, true), tau, X, p->N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status phase_v2_c128(long long N, const double* V2, double th, double* psi, cudaStream_t s) {
+  k_phase_c128<<<grid_for(N), 256, 0, s>>>(V2, th, psi, N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status phase_v2_c64(long long N, const double* V2, double th, float* psi, cudaStream_t s) {
+  k_phase_c64<<<grid_for(N), 256, 0, s>>>(V2, th, psi, N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status convert_c64_to_c128(long long N, const float* in, double* out, cudaStream_t s) {
+  k_c64_to_c128<<<grid_for(2 * N), 256, 0, s>>>(in, out, 2 * N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status convert_c128_to_c64(long long N, const double* in, float* out, cudaStream_t s) {
+  k_c128_to_c64<<<grid_for(2 * N), 256, 0, s>>>(in, out, 2 * N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
+                        double* partial, double* out2, cudaStream_t s) {
+  unsigned g = grid_for(p->N);
+  k_stencil<0><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, nullptr, y, p->N, partial);
+  TS_CHECK_CUDA(cudaGetLastError());
+  if (out2) {
+    k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
+    TS_CHECK_CUDA(cudaGetLastError());
+  }
+  return TS_OK;
+}
+
+ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, const double* x, const double* b,
+                           double* r, double* partial, double* out2, cudaStream_t s) {
+  unsigned g = grid_for(p->N);
+  k_stencil<1><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, r, p->N, partial);
+  TS_CHECK_CUDA(cudaGetLastError());
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
+               double* out2, cudaStream_t s) {
+  unsigned g = grid_for(N);
+  k_dot2<<<g, 256, 0, s>>>(a, b, c, d, N, partial);
+  TS_CHECK_CUDA(cudaGetLastError());
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status pcg_update_xr(const double* rz, const double* pq, double* alpha_out, double* x, double* r,
+                        const double* p, const double* q, long long N, double* partial, double* out2,
+                        cudaStream_t s) {
+  unsigned g = grid_for(N);
+  k_pcg_xr<<<g, 256, 0, s>>>(rz, pq, alpha_out, x, r, p, q, N, partial);
+  TS_CHECK_CUDA(cudaGetLastError());
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status pcg_update_p(const double* alpha, const double* zq, const double* rz_old, int first, double* p,
+                       const double* z, long long N, cudaStream_t s) {
+  k_pcg_p<<<grid_for(N), 256, 0, s>>>(alpha, zq, rz_old, first, p, z, N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status copy_scalar(const double* src, double* dst, cudaStream_t s) {
+  k_copy_scalar<<<1, 1, 0, s>>>(src, dst);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status tensor_ground(const ts_plan* p, double* u, cudaStream_t s) {
+  AxisParams a = axis_params(p, true);
+  for (int k = 0; k < p->d; ++k) a.tab[k] = p->St[k];
+  k_tensor_ground<<<grid_for(p->N), 256, 0, s>>>(a, u, p->N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status axpby(long long N, double a, const double* x, double b, double* y, cudaStream_t s) {
+  k_axpby<<<grid_for(N), 256, 0, s>>>(a, x, b, y, N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status scale_by_device_ratio(long long N, const double* num, const double* den, const double* x, double* y,
+                                cudaStream_t s) {
+  k_scale_by_scalar<<<grid_for(N), 256, 0, s>>>(num, den, y, x, N);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+}  // namespace ts

@@ -1,0 +1,37 @@
+// Declarations of the pointwise / reduction kernels in pointwise.cu.
+#pragma once
+#include "common.cuh"
+
+namespace ts {
+
+// Fixed reduction grid: 148 SMs x 4 CTAs of 256 threads.  Partial buffers hold
+// 2 doubles per CTA.
+constexpr int RED_BLOCKS = 148 * 4;
+int red_blocks();
+
+// y = (A + V2 + sigma) x; if out2 != NULL, out2[0] = x.y (partials in `partial`).
+ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
+                        double* partial, double* out2, cudaStream_t s);
+// r = b - (A + V2 + sigma) x; out2[0] = r.r, out2[1] = b.b.
+ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, const double* x, const double* b,
+                           double* r, double* partial, double* out2, cudaStream_t s);
+// out2[0] = a.b (b == NULL: sum of a), out2[1] = c.d (c, d may be NULL).
+ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
+               double* out2, cudaStream_t s);
+// alpha = rz/pq (-> *alpha_out); x += alpha p; r -= alpha q; out2[0] = r.r.
+ts_status pcg_update_xr(const double* rz, const double* pq, double* alpha_out, double* x, double* r,
+                        const double* p, const double* q, long long N, double* partial, double* out2,
+                        cudaStream_t s);
+// p = z + beta p, beta = -alpha zq / rz_old (first: p = z).
+ts_status pcg_update_p(const double* alpha, const double* zq, const double* rz_old, int first, double* p,
+                       const double* z, long long N, cudaStream_t s);
+ts_status copy_scalar(const double* src, double* dst, cudaStream_t s);
+// u = tensor product of the per-axis ground eigenvectors (column 0 of each S_k).
+ts_status tensor_ground(const ts_plan* p, double* u, cudaStream_t s);
+// y = a x + b y (x may alias y).
+ts_status axpby(long long N, double a, const double* x, double b, double* y, cudaStream_t s);
+// y = x * num/den (den != NULL) or y = x / sqrt(num) (den == NULL); num, den device scalars.
+ts_status scale_by_device_ratio(long long N, const double* num, const double* den, const double* x, double* y,
+                                cudaStream_t s);
+
+}  // namespace ts

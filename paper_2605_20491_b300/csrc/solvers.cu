@@ -1,0 +1,185 @@
+// Iterative drivers built on the tensor-product apply:
+//   pcg_impl              -- PCG with P = (-Delta+V1+sigma_P)^{-1}            (Sec. 3.2)
+//   inverse_iteration_impl -- shifted inverse iteration, warm-started PCG      (Sec. 4.1, 5.3.1)
+//   split_step_impl       -- Strang e^{-iV2 dt/2} e^{-iA dt} e^{-iV2 dt/2}, A = -Delta+V1
+//                            with adjacent half steps merged                  (Sec. 5.1)
+// Every vector update and inner product is FP64 on the device; scalars live in device
+// memory and only the residual norm / eigenvalue crosses to the host once per iteration
+// for the stopping test.
+#include <cmath>
+
+#include "common.cuh"
+#include "mixed.cuh"
+#include "pointwise.cuh"
+#include "solvers.cuh"
+
+namespace ts {
+
+namespace {
+
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (void* p : ptrs) scratch_free(p, s);
+  }
+  ts_status get(double** out, size_t count) {
+    void* p = nullptr;
+    TS_TRY(scratch_alloc(&p, sizeof(double) * count, s));
+    ptrs.push_back(p);
+    *out = (double*)p;
+    return TS_OK;
+  }
+};
+
+ts_status read_scalars(const double* dev, double* host, int count, cudaStream_t s) {
+  TS_CHECK_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+  TS_CHECK_CUDA(cudaStreamSynchronize(s));
+  return TS_OK;
+}
+
+}  // namespace
+
+ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double* V2, const double* b, double* x,
+                   double tol, int maxit, ts_precision prec, int* iters_out, double* relres_out, cudaStream_t s) {
+  const long long N = p->N;
+  Scratch sc_mem(s);
+  double *r, *z, *pv, *q, *partial, *sc;
+  TS_TRY(sc_mem.get(&r, N));
+  TS_TRY(sc_mem.get(&z, N));
+  TS_TRY(sc_mem.get(&pv, N));
+  TS_TRY(sc_mem.get(&q, N));
+  TS_TRY(sc_mem.get(&partial, 2 * RED_BLOCKS));
+  TS_TRY(sc_mem.get(&sc, 16));
+  double h[2];
+  // r = b - A x;  sc[0] = r.r, sc[1] = b.b
+  TS_TRY(stencil_residual(p, V2, sigma, x, b, r, partial, sc + 0, s));
+  TS_TRY(read_scalars(sc, h, 2, s));
+  double bnorm = std::sqrt(h[1]);
+  if (bnorm == 0.0) bnorm = 1.0;
+  int it = 0;
+  bool converged = std::sqrt(h[0]) / bnorm < tol;
+  if (!converged) {
+    TS_TRY(apply_inverse_impl(p, sigma_P, r, z, prec, s));           // z = P r
+    TS_TRY(dot2(N, r, z, nullptr, nullptr, partial, sc + 2, s));     // sc[2] = r.z
+    TS_TRY(pcg_update_p(nullptr, nullptr, nullptr, 1, pv, z, N, s)); // p = z
+  }
+  while (!converged && it < maxit) {
+    TS_TRY(stencil_apply(p, V2, sigma, pv, q, partial, sc + 4, s));                     // q = A p; sc[4] = p.q
+    TS_TRY(pcg_update_xr(sc + 2, sc + 4, sc + 6, x, r, pv, q, N, partial, sc + 8, s));  // sc[6] = alpha, sc[8] = r.r
+    ++it;
+    TS_TRY(read_scalars(sc + 8, h, 1, s));
+    if (!std::isfinite(h[0])) {
+      set_error("PCG breakdown: non-finite residual at iteration %d", it);
+      if (iters_out) *iters_out = it;
+      return TS_ERR_NOT_CONVERGED;
+    }
+    if (std::sqrt(h[0]) / bnorm < tol) {
+      converged = true;
+      break;
+    }
+    TS_TRY(apply_inverse_impl(p, sigma_P, r, z, prec, s));          // z = P r
+    TS_TRY(dot2(N, r, z, z, q, partial, sc + 10, s));               // sc[10] = r.z, sc[11] = z.q
+    TS_TRY(pcg_update_p(sc + 6, sc + 11, sc + 2, 0, pv, z, N, s));  // p = z + beta p
+    TS_TRY(copy_scalar(sc + 10, sc + 2, s));
+  }
+  // true residual at exit
+  TS_TRY(stencil_residual(p, V2, sigma, x, b, r, partial, sc + 12, s));
+  TS_TRY(read_scalars(sc + 12, h, 1, s));
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = std::sqrt(h[0]) / bnorm;
+  if (!converged) {
+    set_error("PCG did not reach tol %.3e in %d iterations", tol, maxit);
+    return TS_ERR_NOT_CONVERGED;
+  }
+  return TS_OK;
+}
+
+ts_status inverse_iteration_impl(const ts_plan* p, double shift, const double* V2, double* u, int init_from_plan,
+                                 double tol_lambda, int maxit, double pcg_tol, int pcg_maxit, ts_precision prec,
+                                 double* lambda_out, int* outer_out, long long* pcg_out, cudaStream_t s) {
+  const long long N = p->N;
+  Scratch sc_mem(s);
+  double *w, *Hu, *partial, *sc;
+  TS_TRY(sc_mem.get(&w, N));
+  TS_TRY(sc_mem.get(&Hu, N));
+  TS_TRY(sc_mem.get(&partial, 2 * RED_BLOCKS));
+  TS_TRY(sc_mem.get(&sc, 8));
+  if (init_from_plan) TS_TRY(tensor_ground(p, u, s));
+  // u <- u / ||u||; lambda = (u, H u)
+  TS_TRY(dot2(N, u, u, nullptr, nullptr, partial, sc, s));
+  TS_TRY(scale_by_device_ratio(N, sc, nullptr, u, u, s));
+  TS_TRY(stencil_apply(p, V2, 0.0, u, Hu, partial, sc + 2, s));
+  double h[2];
+  TS_TRY(read_scalars(sc + 2, h, 1, s));
+  double lambda = h[0];
+  long long pcg_total = 0;
+  int it = 0;
+  bool converged = false;
+  ts_status st = TS_OK;
+  while (it < maxit) {
+    double den = lambda - shift;
+    if (!(den > 0.0)) {
+      set_error("inverse iteration: Rayleigh quotient %.6e is not above the shift %.6e", lambda, shift);
+      return TS_ERR_INVALID_ARG;
+    }
+    TS_TRY(axpby(N, 1.0 / den, u, 0.0, w, s));  // warm start w0 = u / (lambda - s)
+    int pit = 0;
+    st = pcg_impl(p, -shift, -shift, V2, u, w, pcg_tol, pcg_maxit, prec, &pit, nullptr, s);
+    pcg_total += pit;
+    if (st != TS_OK && st != TS_ERR_NOT_CONVERGED) return st;
+    TS_TRY(dot2(N, w, w, nullptr, nullptr, partial, sc, s));
+    TS_TRY(scale_by_device_ratio(N, sc, nullptr, w, u, s));  // u = w / ||w||
+    TS_TRY(stencil_apply(p, V2, 0.0, u, Hu, partial, sc + 2, s));
+    TS_TRY(read_scalars(sc + 2, h, 1, s));
+    ++it;
+    double change = std::fabs(h[0] - lambda) / std::fabs(h[0]);
+    lambda = h[0];
+    if (change < tol_lambda) {
+      converged = true;
+      break;
+    }
+  }
+  // sign: sum(u) > 0
+  TS_TRY(dot2(N, u, nullptr, nullptr, nullptr, partial, sc + 4, s));
+  TS_TRY(read_scalars(sc + 4, h, 1, s));
+  if (h[0] < 0.0) TS_TRY(axpby(N, -1.0, u, 0.0, u, s));
+  if (lambda_out) *lambda_out = lambda;
+  if (outer_out) *outer_out = it;
+  if (pcg_out) *pcg_out = pcg_total;
+  TS_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (!converged) {
+    set_error("inverse iteration did not reach |dlambda|/|lambda| < %.3e in %d iterations", tol_lambda, maxit);
+    return TS_ERR_NOT_CONVERGED;
+  }
+  return TS_OK;
+}
+
+ts_status split_step_impl(const ts_plan* p, double dt, int nsteps, const double* V2, void* psi, ts_dtype dtype,
+                          ts_precision prec, cudaStream_t s) {
+  if (nsteps <= 0) return TS_OK;
+  const long long N = p->N;
+  if (prec == TS_FP64 && dtype == TS_C64) {
+    // FP64 arithmetic on complex64 data: widen once, run in complex128, narrow once.
+    Scratch sc_mem(s);
+    double* w;
+    TS_TRY(sc_mem.get(&w, 2 * N));
+    TS_TRY(convert_c64_to_c128(N, (const float*)psi, w, s));
+    TS_TRY(split_step_impl(p, dt, nsteps, V2, w, TS_C128, prec, s));
+    TS_TRY(convert_c128_to_c64(N, w, (float*)psi, s));
+    return TS_OK;
+  }
+  auto phase = [&](double theta) -> ts_status {
+    if (dtype == TS_C128) return phase_v2_c128(N, V2, theta, (double*)psi, s);
+    return phase_v2_c64(N, V2, theta, (float*)psi, s);
+  };
+  TS_TRY(phase(0.5 * dt));
+  for (int k = 0; k < nsteps; ++k) {
+    TS_TRY(apply_exp_impl(p, dt, psi, psi, dtype, prec, s));
+    TS_TRY(phase(k == nsteps - 1 ? 0.5 * dt : dt));  // merged half steps between steps
+  }
+  return TS_OK;
+}
+
+}  // namespace ts

@@ -1,0 +1,209 @@
+"""Python binding of the C ABI in include/tschrod.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but
+convert arguments: device arrays are torch tensors (their ``data_ptr()`` is passed),
+streams are ``torch.cuda.Stream`` objects (or None for the current stream), and a
+non-TS_OK status raises ``TsError`` carrying ``ts_last_error()``.  All computation runs
+in the library's CUDA kernels; if the library cannot be loaded, importing this module
+fails loudly -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtschrod.so")
+
+TS_OK, TS_ERR_INVALID_ARG, TS_ERR_NO_MEMORY, TS_ERR_CUDA, TS_ERR_NOT_CONVERGED, TS_ERR_UNSUPPORTED, \
+    TS_ERR_TIMEOUT = range(7)
+STATUS_NAMES = ["TS_OK", "TS_ERR_INVALID_ARG", "TS_ERR_NO_MEMORY", "TS_ERR_CUDA", "TS_ERR_NOT_CONVERGED",
+                "TS_ERR_UNSUPPORTED", "TS_ERR_TIMEOUT"]
+TS_FP64, TS_BF16X3, TS_BF16X6, TS_TF32X3, TS_FP16X3 = range(5)
+TS_R64, TS_C128, TS_C64 = range(3)
+TS_MAX_DIM = 12
+
+#: Every extern "C" symbol that include/tschrod.h declares.
+EXPORTS = [
+    "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
+    "ts_apply_inverse", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
+    "ts_last_error", "ts_version",
+]
+
+
+class TsError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class _Desc(C.Structure):
+    _fields_ = [("d", C.c_int), ("n", C.POINTER(C.c_int)), ("L", C.POINTER(C.c_double)),
+                ("f", C.POINTER(C.POINTER(C.c_double))), ("bc", C.c_int)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libtschrod.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError(f"{LIB_PATH} is missing: run `python -m paper_2605_20491_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.c_double, C.c_int
+    L.ts_plan_create.argtypes = [C.POINTER(_Desc), C.c_uint, vp, C.POINTER(vp)]
+    L.ts_plan_destroy.argtypes = [vp]
+    L.ts_plan_eigs.argtypes = [vp, ip, vp]
+    L.ts_plan_eigvecs.argtypes = [vp, ip, vp]
+    L.ts_plan_shape.argtypes = [vp, C.POINTER(ip), vp, C.POINTER(C.c_longlong)]
+    L.ts_plan_bytes.argtypes = [vp, C.POINTER(C.c_longlong)]
+    L.ts_apply_inverse.argtypes = [vp, dp, vp, vp, ip, vp]
+    L.ts_apply_exp.argtypes = [vp, dp, vp, vp, ip, ip, vp]
+    L.ts_apply_operator.argtypes = [vp, dp, vp, vp, vp, vp]
+    L.ts_pcg.argtypes = [vp, dp, dp, vp, vp, vp, dp, ip, ip, C.POINTER(ip), C.POINTER(dp), vp]
+    L.ts_inverse_iteration.argtypes = [vp, dp, vp, vp, ip, dp, ip, dp, ip, ip, C.POINTER(dp), C.POINTER(ip),
+                                       C.POINTER(C.c_longlong), vp]
+    L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
+    L.ts_last_error.restype = C.c_char_p
+    L.ts_last_error.argtypes = []
+    L.ts_version.restype = C.c_char_p
+    L.ts_version.argtypes = []
+    for name in EXPORTS:
+        if name not in ("ts_last_error", "ts_version"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def ts_last_error() -> str:
+    return lib().ts_last_error().decode()
+
+
+def ts_version() -> str:
+    return lib().ts_version().decode()
+
+
+def _check(status: int, where: str, allow=()):
+    if status != TS_OK and status not in allow:
+        raise TsError(status, where, ts_last_error())
+    return status
+
+
+def _ptr(t) -> C.c_void_p | None:
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p | None:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Owning handle of a ts_plan (freed by ts_plan_destroy on close / garbage collection)."""
+
+    def __init__(self, handle: int, n, L):
+        self.handle = C.c_void_p(handle)
+        self.n = tuple(n)
+        self.L = tuple(L)
+        self.N = int(np.prod(self.n))
+
+    @property
+    def d(self) -> int:
+        return len(self.n)
+
+    def close(self):
+        if self.handle:
+            ts_plan_destroy(self)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ts_plan_create(n, L, f, precision_mask: int = 0, stream=None, bc: int = 0) -> Plan:
+    d = len(n)
+    f_arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in f]
+    n_arr = (C.c_int * d)(*[int(v) for v in n])
+    L_arr = (C.c_double * d)(*[float(v) for v in L])
+    f_ptrs = (C.POINTER(C.c_double) * d)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in f_arrs])
+    desc = _Desc(d, n_arr, L_arr, f_ptrs, bc)
+    out = C.c_void_p()
+    _check(lib().ts_plan_create(C.byref(desc), precision_mask, _stream(stream), C.byref(out)), "ts_plan_create")
+    return Plan(out.value, n, L)
+
+
+def ts_plan_destroy(plan: Plan):
+    _check(lib().ts_plan_destroy(plan.handle), "ts_plan_destroy")
+
+
+def ts_plan_eigs(plan: Plan, axis: int) -> np.ndarray:
+    out = np.empty(plan.n[axis])
+    _check(lib().ts_plan_eigs(plan.handle, axis, out.ctypes.data), "ts_plan_eigs")
+    return out
+
+
+def ts_plan_eigvecs(plan: Plan, axis: int) -> np.ndarray:
+    out = np.empty((plan.n[axis], plan.n[axis]))
+    _check(lib().ts_plan_eigvecs(plan.handle, axis, out.ctypes.data), "ts_plan_eigvecs")
+    return out
+
+
+def ts_plan_bytes(plan: Plan) -> int:
+    v = C.c_longlong()
+    _check(lib().ts_plan_bytes(plan.handle, C.byref(v)), "ts_plan_bytes")
+    return v.value
+
+
+def ts_apply_inverse(plan: Plan, sigma: float, b, u, prec: int = TS_FP64, stream=None):
+    _check(lib().ts_apply_inverse(plan.handle, sigma, _ptr(b), _ptr(u), prec, _stream(stream)), "ts_apply_inverse")
+
+
+def ts_apply_exp(plan: Plan, tau: float, psi_in, psi_out, dtype: int, prec: int = TS_FP64, stream=None):
+    _check(lib().ts_apply_exp(plan.handle, tau, _ptr(psi_in), _ptr(psi_out), dtype, prec, _stream(stream)),
+           "ts_apply_exp")
+
+
+def ts_apply_operator(plan: Plan, sigma: float, V2, x, y, stream=None):
+    _check(lib().ts_apply_operator(plan.handle, sigma, _ptr(V2), _ptr(x), _ptr(y), _stream(stream)),
+           "ts_apply_operator")
+
+
+def ts_pcg(plan: Plan, sigma: float, sigma_P: float, V2, b, x, tol: float, maxit: int, precond: int = TS_FP64,
+           stream=None, allow_not_converged: bool = False):
+    """Returns (status, iterations, true relative residual)."""
+    it = C.c_int(0)
+    rel = C.c_double(0.0)
+    st = lib().ts_pcg(plan.handle, sigma, sigma_P, _ptr(V2), _ptr(b), _ptr(x), tol, maxit, precond,
+                      C.byref(it), C.byref(rel), _stream(stream))
+    _check(st, "ts_pcg", allow=(TS_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return st, it.value, rel.value
+
+
+def ts_inverse_iteration(plan: Plan, shift: float, V2, u, init_from_plan: bool = True, tol_lambda: float = 1e-12,
+                         maxit: int = 200, pcg_tol: float = 1e-10, pcg_maxit: int = 500, precond: int = TS_FP64,
+                         stream=None):
+    """Returns (lambda, outer iterations, total PCG iterations)."""
+    lam = C.c_double(0.0)
+    outer = C.c_int(0)
+    tot = C.c_longlong(0)
+    _check(lib().ts_inverse_iteration(plan.handle, shift, _ptr(V2), _ptr(u), int(init_from_plan), tol_lambda, maxit,
+                                      pcg_tol, pcg_maxit, precond, C.byref(lam), C.byref(outer), C.byref(tot),
+                                      _stream(stream)), "ts_inverse_iteration")
+    return lam.value, outer.value, tot.value
+
+
+def ts_split_step(plan: Plan, dt: float, nsteps: int, V2, psi, dtype: int, prec: int = TS_FP64, stream=None):
+    _check(lib().ts_split_step(plan.handle, dt, nsteps, _ptr(V2), _ptr(psi), dtype, prec, _stream(stream)),
+           "ts_split_step")
