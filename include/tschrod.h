@@ -169,6 +169,14 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
 ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double* V2, void* psi,
                         ts_dtype dtype, ts_precision prec, void* stream);
 
+/*
+ * Device-side failure check (no counterpart in the paper).  The tensor-core kernels never
+ * wait without a bound: a wait that runs out (about 2 s) sets a device flag and the kernel
+ * returns.  This call synchronises `stream`, returns TS_ERR_TIMEOUT if the flag was set
+ * since the previous call (and clears it), else TS_OK.
+ */
+ts_status ts_device_status(void* stream);
+
 /* Thread-local message of the calling thread's last failing call ("" if none). */
 const char* ts_last_error(void);
 

@@ -191,6 +191,17 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
                                 lambda, outer_iters, pcg_iters, (cudaStream_t)stream);
 }
 
+ts_status ts_device_status(void* stream) {
+  clear_error();
+  int flag = 0;
+  TS_TRY(mixed_error_flag(&flag, true, (cudaStream_t)stream));
+  if (flag != 0) {
+    set_error("a bounded device-side wait ran out (code %d)", flag);
+    return TS_ERR_TIMEOUT;
+  }
+  return TS_OK;
+}
+
 ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double* V2, void* psi, ts_dtype dtype,
                         ts_precision prec, void* stream) {
   TS_API_BEGIN(plan);

@@ -68,11 +68,11 @@ struct ts_plan {
   double* St[TS_MAX_DIM] = {};
   double* lam[TS_MAX_DIM] = {};
   double* f[TS_MAX_DIM] = {};
-  // Split bf16 planes (device), [prec][axis][plane]: row-major n x n copies of S^T
-  // (forward operand, "Bf") and S (backward operand, "Bb"), K (contracted index)
-  // contiguous in both.
-  __nv_bfloat16* Bf[ts::NPREC][TS_MAX_DIM][ts::MAX_PLANES] = {};
-  __nv_bfloat16* Bb[ts::NPREC][TS_MAX_DIM][ts::MAX_PLANES] = {};
+  // Split bf16 planes (device), [prec][axis] -> [plane][n][n]: row-major copies of
+  // S^T (forward operand, "Bf") and S (backward operand, "Bb"), so that the contracted
+  // index is contiguous in both (K-major tensor-core operands).
+  __nv_bfloat16* Bf[ts::NPREC][TS_MAX_DIM] = {};
+  __nv_bfloat16* Bb[ts::NPREC][TS_MAX_DIM] = {};
   // Host copies.
   std::vector<double> lam_host[TS_MAX_DIM];
   std::vector<double> S_host[TS_MAX_DIM];

@@ -1,5 +1,35 @@
-// Split-precision apply on the tensor cores (placeholder until the tcgen05 path lands).
+// Split-precision mode-k contraction on the 5th-generation tensor cores (tcgen05).
+//
+// Every contraction of the apply (steps 2 and 4 of Sec. 2.1) is the rotating-form GEMM
+//     D[r][j] = sum_i X[r][i] B[j][i],   output stored transposed, Y[r + R j]
+// (B[j][i] = S_k[i][j] forward, S_k[j][i] backward).  The data X and the tables B are
+// carried as NP bf16 "planes" whose sum reproduces the value (x = x_0 + x_1 (+ x_2), each
+// plane the bf16 rounding of what the previous planes leave), following the multi-term
+// bf16 products of Henry, Tang & Heinecke (2019):
+//     NP = 2 (TS_BF16X3): x0 b0 + x0 b1 + x1 b0                          (~16 bits)
+//     NP = 3 (TS_BF16X6): x0 b0 + x0 b1 + x1 b0 + x1 b1 + x0 b2 + x2 b0  (~24 bits)
+// All products of one output tile accumulate in one FP32 accumulator in tensor memory.
+//
+// Kernel structure (one 128 x BN output tile per CTA, 128 threads):
+//   warp 0 lane 0  -- TMA producer: for each 64-wide K chunk, loads the X planes
+//                     (128 x 64 bf16 boxes, 128-byte swizzle) and the B planes
+//                     (BN x 64 boxes) into an NS-stage shared-memory ring;
+//   warp 1 lane 0  -- MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16) for
+//                     every (plane pair, K step), accumulating in TMEM; commits free the
+//                     ring slots and finally signal the epilogue;
+//   all 4 warps    -- epilogue: tcgen05.ld of the accumulator rows (warp w owns TMEM
+//                     lanes 32w..32w+31 = rows), optional fused pointwise step 3
+//                     (1/(Lambda + sigma) or e^{-i tau Lambda}, Lambda from per-axis
+//                     tables), then either the NP bf16 planes of the next pass or the
+//                     final FP64 / complex128 / complex64 result, stored transposed.
+// Complex data is planar inside the pipeline (re and im planes); a complex tile keeps
+// two accumulators (re, im) that share every B tile, so the phase multiply can mix them.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+
 #include "mixed.cuh"
+#include "tc_ptx.cuh"
 
 namespace ts {
 
@@ -9,15 +39,472 @@ int bf16_planes(ts_precision prec) {
   return 0;
 }
 
-ts_status build_split_tables(ts_plan*, ts_precision prec, cudaStream_t) {
-  set_error("precision %d is not available in this build", (int)prec);
-  return TS_ERR_UNSUPPORTED;
+namespace {
+
+__device__ int g_tc_error = 0;
+
+constexpr int BM = 128;             // rows per tile = TMEM lanes
+constexpr int BK = 64;              // bf16 elements per K chunk (one 128-byte swizzle row)
+constexpr int UMMA_K = 16;          // K of one tcgen05.mma kind::f16
+constexpr int MAX_STAGES = 8;
+constexpr int SMEM_LIMIT = 232448;  // 227 KB opt-in shared memory per CTA
+
+struct EpiParams {
+  int out_mode;    // 0: bf16 planes, 1: FP64 real, 2: complex128, 3: complex64
+  int scale_mode;  // 0: none, 1: inverse 1/(Lambda + sigma), 2: phase e^{-i tau Lambda}
+  long long R;     // rows of the pass
+  int n;           // contracted (= output column) extent
+  long long N;     // elements per plane (R * n)
+  void* out;
+  int nstages;
+  int bn;
+  double sigma;
+  int rd;                     // row axes for the scale (d - 1)
+  int rn[MAXD];               // their sizes, fastest first
+  const double* rlam[MAXD];   // their eigenvalues (scale_mode 1)
+  const double2* rph[MAXD];   // their phase tables (scale_mode 2)
+  const double* clam;         // eigenvalues of the contracted axis
+  const double2* cph;         // phase table of the contracted axis
+};
+
+template <int NP>
+struct Products;
+template <>
+struct Products<2> {
+  static constexpr int count = 3;
+  __device__ static int a(int q) { return q == 2 ? 1 : 0; }
+  __device__ static int b(int q) { return q == 1 ? 1 : 0; }
+};
+template <>
+struct Products<3> {
+  static constexpr int count = 6;
+  // (0,0) (0,1) (1,0) (1,1) (0,2) (2,0)
+  __device__ static int a(int q) { return q == 2 || q == 3 ? 1 : (q == 5 ? 2 : 0); }
+  __device__ static int b(int q) { return q == 1 || q == 3 ? 1 : (q == 4 ? 2 : 0); }
+};
+
+template <int NP>
+__device__ __forceinline__ void split_store(float v, __nv_bfloat16* base, long long plane_stride, long long idx) {
+  __nv_bfloat16 h = __float2bfloat16_rn(v);
+  base[idx] = h;
+  float rres = v - __bfloat162float(h);
+  __nv_bfloat16 m = __float2bfloat16_rn(rres);
+  base[plane_stride + idx] = m;
+  if (NP == 3) {
+    float r2 = rres - __bfloat162float(m);
+    base[2 * plane_stride + idx] = __float2bfloat16_rn(r2);
+  }
 }
 
-ts_status mixed_apply(const ts_plan*, ts_precision prec, MixedOp, double, const void*, void*, ts_dtype,
-                      cudaStream_t) {
-  set_error("precision %d is not available in this build", (int)prec);
-  return TS_ERR_UNSUPPORTED;
+template <int NP, int NACC>
+__global__ void __launch_bounds__(128, 1)
+    k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const EpiParams ep) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int BN = ep.bn;
+  const int NS = ep.nstages;
+  const uint32_t A_TILE = BM * BK * 2;
+  const uint32_t B_TILE = (uint32_t)BN * BK * 2;
+  const uint32_t A_STAGE = NACC * NP * A_TILE;
+  const uint32_t STAGE = A_STAGE + NP * B_TILE;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + (size_t)NS * A_STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NS * STAGE);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + MAX_STAGES;
+  uint64_t* accb = bars + 2 * MAX_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAX_STAGES + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long m0 = (long long)blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int nk = (ep.n + BK - 1) / BK;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(NACC * BN)) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(accb, 1);
+    tc::fence_barrier_init();
+    tc::fence_proxy_async();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, ncols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % NS, round = kc / NS;
+      if (round > 0) tc::mbar_wait(&empty[s], (round - 1) & 1, &g_tc_error, 1);
+      tc::mbar_arrive_expect_tx(&full[s], STAGE);
+      for (int c = 0; c < NACC; ++c)
+        for (int p = 0; p < NP; ++p)
+          tc::tma_load_3d(sA + (size_t)s * A_STAGE + (c * NP + p) * A_TILE, &tmA, kc * BK, (int)m0, c * NP + p,
+                          &full[s]);
+      for (int p = 0; p < NP; ++p)
+        tc::tma_load_3d(sB + (size_t)s * NP * B_TILE + p * B_TILE, &tmB, kc * BK, n0, p, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % NS, round = kc / NS;
+      tc::mbar_wait(&full[s], round & 1, &g_tc_error, 2);
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_u32(sA + (size_t)s * A_STAGE);
+      const uint32_t b0 = tc::smem_u32(sB + (size_t)s * NP * B_TILE);
+#pragma unroll
+      for (int ks = 0; ks < BK / UMMA_K; ++ks) {
+#pragma unroll
+        for (int q = 0; q < Products<NP>::count; ++q) {
+          const uint64_t bdesc = tc::desc_sw128(b0 + Products<NP>::b(q) * B_TILE + ks * 32);
+#pragma unroll
+          for (int c = 0; c < NACC; ++c) {
+            const uint64_t adesc = tc::desc_sw128(a0 + (c * NP + Products<NP>::a(q)) * A_TILE + ks * 32);
+            tc::mma_bf16(tmem + (uint32_t)(c * BN), adesc, bdesc, idesc, (kc | ks | q) != 0);
+          }
+        }
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(accb);
+  }
+  __syncwarp();
+
+  // ---------------- epilogue (all four warps)
+  tc::mbar_wait(accb, 0, &g_tc_error, 3);
+  __syncwarp();
+  tc::tc_fence_after();
+
+  const long long r = m0 + warp * 32 + lane;
+  const bool row_ok = r < ep.R;
+  float rowsum = 0.f;
+  float2 rowph = make_float2(1.f, 0.f);
+  if (ep.scale_mode != 0 && row_ok) {
+    long long q = r;
+    double s = ep.sigma;
+    double pr = 1.0, pi = 0.0;
+    for (int k = 0; k < ep.rd; ++k) {
+      long long qq = q / ep.rn[k];
+      int i = (int)(q - qq * ep.rn[k]);
+      q = qq;
+      if (ep.scale_mode == 1) {
+        s += ep.rlam[k][i];
+      } else {
+        double2 ph = ep.rph[k][i];
+        double tr = pr * ph.x - pi * ph.y;
+        pi = pr * ph.y + pi * ph.x;
+        pr = tr;
+      }
+    }
+    rowsum = (float)s;
+    rowph = make_float2((float)pr, (float)pi);
+  }
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int col0 = 0; col0 < BN; col0 += 16) {
+    uint32_t v[NACC][16];
+#pragma unroll
+    for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
+    tc::tmem_ld_wait();
+    if (!row_ok) continue;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int j = n0 + col0 + i;
+      if (j >= ep.n) break;
+      float val[NACC];
+#pragma unroll
+      for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
+      if (ep.scale_mode == 1) {
+        val[0] = val[0] * (1.0f / (rowsum + (float)ep.clam[j]));
+      } else if (ep.scale_mode == 2 && NACC == 2) {
+        const double2 cp = ep.cph[j];
+        const float cx = (float)cp.x, cy = (float)cp.y;
+        const float phx = rowph.x * cx - rowph.y * cy;
+        const float phy = rowph.x * cy + rowph.y * cx;
+        const float re = val[0] * phx - val[NACC - 1] * phy;
+        const float im = val[0] * phy + val[NACC - 1] * phx;
+        val[0] = re;
+        val[NACC - 1] = im;
+      }
+      const long long idx = r + ep.R * (long long)j;
+      if (ep.out_mode == 0) {
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
+#pragma unroll
+        for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
+      } else if (ep.out_mode == 1) {
+        reinterpret_cast<double*>(ep.out)[idx] = (double)val[0];
+      } else if (ep.out_mode == 2) {
+        reinterpret_cast<double2*>(ep.out)[idx] = make_double2((double)val[0], (double)val[NACC - 1]);
+      } else {
+        reinterpret_cast<float2*>(ep.out)[idx] = make_float2(val[0], val[NACC - 1]);
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ------------------------------------------------------------ pointwise ----
+
+// FP64 / complex input -> planar bf16 planes [c][p][N]; x rounded to FP32 first (the
+// planes carry at most 24 bits), then split exactly in FP32.
+template <int NP, int MODE>  // MODE 0: real FP64, 1: complex128, 2: complex64
+__global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N) {
+  const int NC = MODE == 0 ? 1 : 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    float v[2];
+    if (MODE == 0) {
+      v[0] = (float)reinterpret_cast<const double*>(in)[i];
+    } else if (MODE == 1) {
+      double2 z = reinterpret_cast<const double2*>(in)[i];
+      v[0] = (float)z.x;
+      v[1] = (float)z.y;
+    } else {
+      float2 z = reinterpret_cast<const float2*>(in)[i];
+      v[0] = z.x;
+      v[1] = z.y;
+    }
+    for (int c = 0; c < NC; ++c) split_store<NP>(v[c], planes + (long long)c * NP * N, N, i);
+  }
+}
+
+// FP64 table -> NP bf16 planes (FP64 arithmetic; tables are tiny).
+__global__ void k_split_table(const double* src, __nv_bfloat16* dst, long long count, int np) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    double x = src[i];
+    for (int p = 0; p < np; ++p) {
+      __nv_bfloat16 h = __double2bfloat16(x);
+      dst[p * count + i] = h;
+      x -= (double)__bfloat162float(h);
+    }
+  }
+}
+
+// ph[i] = e^{-i tau lambda_i} = (cos(tau lambda_i), -sin(tau lambda_i)), FP64.
+__global__ void k_phase_table(const double* lam, double tau, double2* ph, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double s, c;
+    sincos(tau * lam[i], &s, &c);
+    ph[i] = make_double2(c, -s);
+  }
+}
+
+// ------------------------------------------------------------ host side ----
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3D bf16 tensor map over planes [planes][rows][cols] (cols contiguous), box
+// {64 cols, box_rows rows, 1 plane}, 128-byte swizzle, zero fill out of bounds.
+ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long rows, int planes, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is unavailable");
+    return TS_ERR_CUDA;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(cols * 2), (cuuint64_t)(cols * rows * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for cols=%lld rows=%lld planes=%d", (int)r, cols, rows, planes);
+    return TS_ERR_CUDA;
+  }
+  return TS_OK;
+}
+
+template <int NP, int NACC>
+ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
+                      cudaStream_t s) {
+  const int bn_cap = NACC == 1 ? 256 : 128;
+  int bn = ((n + 15) / 16) * 16;
+  if (bn > bn_cap) bn = bn_cap;
+  const int stage = NACC * NP * BM * BK * 2 + NP * bn * BK * 2;
+  const int reserve = 1024 + 8 * (2 * MAX_STAGES + 2);
+  int ns = (SMEM_LIMIT - reserve) / stage;
+  if (ns > MAX_STAGES) ns = MAX_STAGES;
+  if (ns < 1) {
+    set_error("tile does not fit in shared memory");
+    return TS_ERR_UNSUPPORTED;
+  }
+  const int smem = ns * stage + reserve;
+  CUtensorMap ma, mb;
+  TS_TRY(make_map(&ma, A, n, R, NACC * NP, BM));
+  TS_TRY(make_map(&mb, B, n, n, NP, bn));
+  ep.R = R;
+  ep.n = n;
+  ep.N = R * n;
+  ep.bn = bn;
+  ep.nstages = ns;
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)((R + BM - 1) / BM), (unsigned)((n + bn - 1) / bn));
+  k_rot_tc<NP, NACC><<<grid, 128, smem, s>>>(ma, mb, ep);
+  TS_CHECK_CUDA(cudaGetLastError());
+  return TS_OK;
+}
+
+ts_status pass(int np, int nacc, const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n,
+               const EpiParams& ep, cudaStream_t s) {
+  if (np == 2 && nacc == 1) return launch_pass<2, 1>(A, B, R, n, ep, s);
+  if (np == 2 && nacc == 2) return launch_pass<2, 2>(A, B, R, n, ep, s);
+  if (np == 3 && nacc == 1) return launch_pass<3, 1>(A, B, R, n, ep, s);
+  return launch_pass<3, 2>(A, B, R, n, ep, s);
+}
+
+unsigned grid_1d(long long N) {
+  long long g = (N + 255) / 256;
+  if (g > 148 * 8) g = 148 * 8;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s) {
+  const int np = bf16_planes(prec);
+  if (np == 0) {
+    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X3, TS_BF16X6)", (int)prec);
+    return TS_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < p->d; ++k) {
+    if (p->owner[k] != k) {
+      p->Bf[prec][k] = p->Bf[prec][p->owner[k]];
+      p->Bb[prec][k] = p->Bb[prec][p->owner[k]];
+      continue;
+    }
+    const long long cnt = (long long)p->n[k] * p->n[k];
+    TS_CHECK_CUDA(cudaMalloc(&p->Bf[prec][k], sizeof(__nv_bfloat16) * np * cnt));
+    TS_CHECK_CUDA(cudaMalloc(&p->Bb[prec][k], sizeof(__nv_bfloat16) * np * cnt));
+    p->bytes += 2LL * np * cnt * (long long)sizeof(__nv_bfloat16);
+    // Forward operand B[j][i] = S[i][j] is the row-major S^T; backward B[i][j] = S[i][j].
+    k_split_table<<<grid_1d(cnt), 256, 0, s>>>(p->St[k], p->Bf[prec][k], cnt, np);
+    k_split_table<<<grid_1d(cnt), 256, 0, s>>>(p->S[k], p->Bb[prec][k], cnt, np);
+    TS_CHECK_CUDA(cudaGetLastError());
+  }
+  return TS_OK;
+}
+
+ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
+                      ts_dtype dt, cudaStream_t s) {
+  const int np = bf16_planes(prec);
+  if (np == 0) {
+    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X3, TS_BF16X6)", (int)prec);
+    return TS_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < p->d; ++k) {
+    if (p->n[k] % 8 != 0 || p->N / p->n[k] >= (1LL << 31)) {
+      set_error("split-precision path needs every n_k to be a multiple of 8 and N/n_k < 2^31 (axis %d: n = %d)", k,
+                p->n[k]);
+      return TS_ERR_UNSUPPORTED;
+    }
+  }
+  const int nc = op == MixedOp::Exp ? 2 : 1;
+  const long long N = p->N;
+  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)nc * np * N;
+  void *w0 = nullptr, *w1 = nullptr, *tabs = nullptr;
+  TS_TRY(scratch_alloc(&w0, plane_bytes, s));
+  ts_status st = scratch_alloc(&w1, plane_bytes, s);
+  int tab_off[MAXD] = {};
+  if (st == TS_OK && op == MixedOp::Exp) {
+    int tot = 0;
+    for (int k = 0; k < p->d; ++k) {
+      tab_off[k] = tot;
+      tot += p->n[k];
+    }
+    st = scratch_alloc(&tabs, sizeof(double2) * tot, s);
+    for (int k = 0; k < p->d && st == TS_OK; ++k) {
+      k_phase_table<<<(p->n[k] + 127) / 128, 128, 0, s>>>(p->lam[k], param, (double2*)tabs + tab_off[k], p->n[k]);
+      if (cudaGetLastError() != cudaSuccess) {
+        set_error("phase table launch failed");
+        st = TS_ERR_CUDA;
+      }
+    }
+  }
+  __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
+  if (st == TS_OK) {
+    if (dt == TS_R64)
+      np == 2 ? k_split_input<2, 0><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N)
+              : k_split_input<3, 0><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N);
+    else if (dt == TS_C128)
+      np == 2 ? k_split_input<2, 1><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N)
+              : k_split_input<3, 1><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N);
+    else
+      np == 2 ? k_split_input<2, 2><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N)
+              : k_split_input<3, 2><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N);
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("split launch failed");
+      st = TS_ERR_CUDA;
+    }
+  }
+  const int d = p->d;
+  for (int t = 0; t < 2 * d && st == TS_OK; ++t) {
+    const int k = t % d;
+    const bool fwd = t < d;
+    const bool last = t == 2 * d - 1;
+    EpiParams ep{};
+    ep.out_mode = last ? (dt == TS_R64 ? 1 : (dt == TS_C128 ? 2 : 3)) : 0;
+    ep.out = last ? out : (void*)buf[(t + 1) & 1];
+    ep.scale_mode = 0;
+    if (t == d - 1) {
+      ep.scale_mode = op == MixedOp::Inverse ? 1 : 2;
+      ep.sigma = op == MixedOp::Inverse ? param : 0.0;
+      ep.rd = d - 1;
+      for (int q = 0; q < d - 1; ++q) {
+        ep.rn[q] = p->n[q];
+        ep.rlam[q] = p->lam[q];
+        ep.rph[q] = tabs ? (const double2*)tabs + tab_off[q] : nullptr;
+      }
+      ep.clam = p->lam[k];
+      ep.cph = tabs ? (const double2*)tabs + tab_off[k] : nullptr;
+    }
+    const __nv_bfloat16* B = fwd ? p->Bf[prec][k] : p->Bb[prec][k];
+    st = pass(np, nc, buf[t & 1], B, N / p->n[k], p->n[k], ep, s);
+  }
+  scratch_free(w0, s);
+  scratch_free(w1, s);
+  scratch_free(tabs, s);
+  return st;
+}
+
+ts_status mixed_error_flag(int* host_flag, bool reset, cudaStream_t s) {
+  TS_CHECK_CUDA(cudaMemcpyFromSymbolAsync(host_flag, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  TS_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (reset) {
+    int zero = 0;
+    TS_CHECK_CUDA(cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+  }
+  return TS_OK;
 }
 
 }  // namespace ts

@@ -14,6 +14,10 @@ int bf16_planes(ts_precision prec);
 ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
                       ts_dtype dt, cudaStream_t s);
 
+// Reads (and optionally clears) the flag that bounded device-side waits of the
+// tensor-core kernels set when they time out.  Synchronises s.
+ts_status mixed_error_flag(int* host_flag, bool reset, cudaStream_t s);
+
 // Build the split planes of S_k^T and S_k for precision `prec` (plan creation).
 ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s);
 

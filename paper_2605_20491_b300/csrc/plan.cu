@@ -94,11 +94,10 @@ void plan_free(ts_plan* p) {
     cudaFree(p->S[k]);
     cudaFree(p->St[k]);
     cudaFree(p->lam[k]);
-    for (int q = 0; q < NPREC; ++q)
-      for (int pl = 0; pl < MAX_PLANES; ++pl) {
-        cudaFree(p->Bf[q][k][pl]);
-        cudaFree(p->Bb[q][k][pl]);
-      }
+    for (int q = 0; q < NPREC; ++q) {
+      cudaFree(p->Bf[q][k]);
+      cudaFree(p->Bb[q][k]);
+    }
   }
   for (int k = 0; k < p->d; ++k) cudaFree(p->f[k]);  // potential samples are per axis
   delete p;

@@ -29,7 +29,7 @@ TS_MAX_DIM = 12
 EXPORTS = [
     "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
     "ts_apply_inverse", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
-    "ts_last_error", "ts_version",
+    "ts_device_status", "ts_last_error", "ts_version",
 ]
 
 
@@ -69,6 +69,7 @@ def lib() -> C.CDLL:
     L.ts_inverse_iteration.argtypes = [vp, dp, vp, vp, ip, dp, ip, dp, ip, ip, C.POINTER(dp), C.POINTER(ip),
                                        C.POINTER(C.c_longlong), vp]
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
+    L.ts_device_status.argtypes = [vp]
     L.ts_last_error.restype = C.c_char_p
     L.ts_last_error.argtypes = []
     L.ts_version.restype = C.c_char_p
@@ -202,6 +203,10 @@ def ts_inverse_iteration(plan: Plan, shift: float, V2, u, init_from_plan: bool =
                                       pcg_tol, pcg_maxit, precond, C.byref(lam), C.byref(outer), C.byref(tot),
                                       _stream(stream)), "ts_inverse_iteration")
     return lam.value, outer.value, tot.value
+
+
+def ts_device_status(stream=None):
+    _check(lib().ts_device_status(_stream(stream)), "ts_device_status")
 
 
 def ts_split_step(plan: Plan, dt: float, nsteps: int, V2, psi, dtype: int, prec: int = TS_FP64, stream=None):

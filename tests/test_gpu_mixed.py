@@ -1,0 +1,78 @@
+"""Parity of the split-precision (tcgen05) path with the CPU oracle, through the C ABI.
+
+Shapes cover a ragged M tail (R not a multiple of 128), K tails (n not a multiple of 64),
+N tails (n > 256 and not a multiple of the N tile) and several tiles per pass.
+
+Tolerances (relative l2 against the FP64 oracle), from the arithmetic: a 2-term bf16
+split carries 16 bits (unit 2^-17 per value and per table entry), so each pass adds
+O(2^-16) relative error; 2d passes stay below 5e-5 (BF16X3, measured about 1e-5).  A
+3-term split carries 24 bits, so the FP32 accumulation inside the tensor core
+(O(sqrt(n) 2^-24) per pass) dominates: below 1e-5 for 2d passes (BF16X6, measured
+2e-6 to 4e-6).  Complex64 output adds one FP32 rounding."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_20491_b300 import synth as S
+from gpu_util import dev, harmonic_case, host, plans, rel
+
+pytestmark = pytest.mark.gpu
+TOL = {1: 5e-5, 2: 1e-5}   # TS_BF16X3, TS_BF16X6
+MASK = (1 << 1) | (1 << 2)
+
+SHAPES = [(64, 64, 64), (40, 24, 8), (128, 96, 40), (264, 16), (8, 8, 8, 8, 8), (32, 32, 32)]
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch  # noqa: F401
+    from paper_2605_20491_b300 import tschrod
+    return tschrod
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n", SHAPES)
+def test_inverse_mixed_vs_oracle(T, n, prec):
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)
+    b = S.normal(2, Po.N)
+    u = dev(np.zeros(Po.N))
+    T.ts_apply_inverse(P, 0.5, dev(b), u, prec)
+    T.ts_device_status()
+    err = rel(host(u), O.apply_inverse(Po, 0.5, b))
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n", [(64, 48, 32), (40, 24, 8), (16, 16, 16, 16), (272, 8)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_exp_mixed_vs_oracle(T, n, prec, dtype):
+    L, f = harmonic_case(n, L=4.0)
+    P, Po = plans(n, L, f, MASK)
+    psi = S.complex_normal(3, Po.N)
+    if dtype == "c128":
+        out = dev(np.zeros(2 * Po.N))
+        T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C128, prec)
+        tol = TOL[prec]
+    else:
+        psi = psi.astype(np.float32)
+        out = dev(np.zeros(2 * Po.N, dtype=np.float32))
+        T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C64, prec)
+        tol = max(TOL[prec], 1e-6)
+    T.ts_device_status()
+    err = rel(host(out), O.apply_exp(Po, 0.01, psi.astype(np.float64)))
+    assert err < tol, err
+
+
+def test_mixed_rejects_unsupported(T):
+    n = (12, 16)
+    L, f = harmonic_case(n)
+    P, _ = plans(n, L, f, MASK)
+    b = dev(np.ones(P.N))
+    with pytest.raises(T.TsError) as e:
+        T.ts_apply_inverse(P, 1.0, b, b, T.TS_BF16X3)
+    assert e.value.status == T.TS_ERR_UNSUPPORTED
+    P2, _ = plans((16, 16), L, [f[1], f[1]], 0)
+    with pytest.raises(T.TsError) as e:
+        T.ts_apply_inverse(P2, 1.0, b[:256], b[:256], T.TS_BF16X3)
+    assert e.value.status == T.TS_ERR_UNSUPPORTED
