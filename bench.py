@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark of the tensor-product direct solve of -Delta + V1 on one B300 per rank.
+
+Workload (the 3D single large apply): n = 512 per axis (1.34e8 DoF) on [-8,8]^3,
+homogeneous Dirichlet, V1 = sum (omega_k x_k)^2 with omega = (1, 1.3, 0.7), shift
+sigma = 0.5, right-hand side iid N(0,1) (SplitMix64, seed 2).
+
+One step = one solve of (-Delta_h + V1 + sigma) u = b to relative error <= 1e-10: PCG
+(V2 = 0, i.e. iterative refinement accelerated by CG) with the split-precision BF16X3
+tensor-core inverse as the preconditioner and FP64 residuals, from a zero initial guess.
+`value` is GDoF/s = N / step time (summed over ranks).  The same JSON line also carries
+the plain FP64 apply and a single unrefined BF16X3 apply, each with its error against the
+FP64 apply, so the FP64-vs-mixed comparison is in one place.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain C, FP64, all host cores) on a bounded sample
+of the same workload; multi-GPU launches run one independent replica per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_20491_b300 import synth  # noqa: E402
+
+WORKLOAD = "3d_n512_apply"
+METRIC = "GDoF/s of (-Delta+V1)^-1 apply, FP64 vs mixed at stated err; p50/p99 latency"
+UNIT = "GDoF/s"
+# PCG tolerance on the relative residual: the largest of 1e-11, 1e-12, 1e-13 whose solve
+# stays within 1e-10 relative error of the FP64 direct solve at this size (measured).
+PCG_TOL = 1e-12
+ERR_TARGET = 1e-10
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def cpu_oracle_sample(target_seconds: float = 15.0):
+    """Time the CPU oracle (FP64, all host cores) on a bounded sample of the workload: the
+    same operator family on a 3D n = 192 grid; the oracle's cost per DoF grows like n, so the
+    rate is scaled by 192/512 to the full n = 512 workload."""
+    import oracle as O
+    n_s = 192
+    w = synth.WORKLOADS[WORKLOAD]
+    n = (n_s,) * 3
+    f = synth.harmonic(n, w["L"], w["omega"])
+    P = O.plan(n, w["L"], f)
+    b = synth.normal(w["seed"], P.N)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.apply_inverse(P, w["sigma"], b)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > target_seconds or reps >= 3:
+            break
+    per = el / reps
+    rate = P.N / per / 1e9 * (n_s / 512.0)
+    return {"value": rate, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"oracle FP64 4-step apply (plain C loops, OpenMP) on 3D n={n_s} ({P.N} DoF), "
+                      f"{reps} run(s) of {per:.2f} s each; rate scaled by {n_s}/512 to n=512 "
+                      f"(oracle cost per DoF grows like n)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    w = synth.WORKLOADS[WORKLOAD]
+    n_s = 160
+    n = (n_s,) * 3
+    P = O.plan(n, w["L"], synth.harmonic(n, w["L"], w["omega"]))
+    b = synth.normal(w["seed"], P.N)
+    for _ in range(args.warmup):
+        O.apply_inverse(P, w["sigma"], b)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.apply_inverse(P, w["sigma"], b)
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = P.N / (ms * 1e-3) / 1e9 * (n_s / 512.0)
+    sample = (f"oracle FP64 4-step apply on 3D n={n_s} ({P.N} DoF) per step; rate scaled by {n_s}/512 "
+              f"to the n=512 workload (oracle cost per DoF grows like n)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": [512, 512, 512], "sample_n": n_s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2605_20491_b300 import tschrod as T
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = synth.WORKLOADS[WORKLOAD]
+    n, L = w["n"], w["L"]
+    f = synth.harmonic(n, L, w["omega"])
+    mask = (1 << T.TS_BF16X3)
+    P = T.ts_plan_create(n, L, f, mask)
+    N = P.N
+    sigma = w["sigma"]
+    b_host = torch.from_numpy(synth.normal(w["seed"], N)).pin_memory()
+    b = b_host.cuda()
+    x = torch.zeros_like(b)
+    u64 = torch.empty_like(b)
+    stream = torch.cuda.current_stream()
+
+    # FP64 direct apply (plain form) and its time.
+    T.ts_apply_inverse(P, sigma, b, u64, T.TS_FP64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    T.ts_apply_inverse(P, sigma, b, u64, T.TS_FP64)
+    e1.record()
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    nrm = u64.norm().item()
+
+    # One unrefined split-precision apply and its error.
+    um = torch.empty_like(b)
+    for _ in range(3):
+        T.ts_apply_inverse(P, sigma, b, um, T.TS_BF16X3)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        T.ts_apply_inverse(P, sigma, b, um, T.TS_BF16X3)
+    e1.record()
+    torch.cuda.synchronize()
+    mixed1_ms = e0.elapsed_time(e1) / 5
+    mixed1_err = ((um - u64).norm() / nrm).item()
+    del um
+
+    iters = []
+
+    def step():
+        x.zero_()
+        st, it, rel = T.ts_pcg(P, sigma, sigma, None, b, x, PCG_TOL, 20, T.TS_BF16X3)
+        iters.append(it)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    err = ((x - u64).norm() / nrm).item()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = T.ts_launch_count()
+    T.ts_profile_begin()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    tc_launches, tc_ms, tc_flops, tc_bytes = T.ts_profile_end(T.PROF_TC_PASS)
+    launches = T.ts_launch_count() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    value = world * N / (ms * 1e-3) / 1e9
+
+    # End to end through the public API with host buffers: H2D of b, solve, D2H of u.
+    u_host = torch.empty_like(b_host).pin_memory()
+    bd = torch.empty_like(b)
+
+    def e2e_step():
+        bd.copy_(b_host, non_blocking=True)
+        x.zero_()
+        T.ts_pcg(P, sigma, sigma, None, bd, x, PCG_TOL, 20, T.TS_BF16X3)
+        u_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    n_e2e = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) / n_e2e * 1e3
+    e2e_err = float(np.linalg.norm(u_host.numpy() - u64.cpu().numpy()) / nrm)
+
+    peaks, peaks_src = load_peaks()
+    avg_launch_ms = tc_ms / max(1, tc_launches)
+    achieved = (tc_flops / max(1, tc_launches)) / (avg_launch_ms * 1e-3) / 1e12 if tc_launches else None
+    peak = peaks["bf16_tflops_sustained"]
+    roofline = {"bound": "tensor", "kernel": "k_rot_tc (BF16X3 split pass)", "achieved": achieved, "peak": peak,
+                "peak_kind": f"bf16 dense sustained ({peaks_src})", "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": TRAFFIC_PER_LAUNCH,
+                "algorithmic_flops_per_launch": tc_flops / max(1, tc_launches),
+                "algorithmic_bytes_per_launch": tc_bytes / max(1, tc_launches),
+                "avg_launch_ms": avg_launch_ms, "launches": tc_launches,
+                "share_of_step": tc_ms / (ms * args.steps)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": list(n), "L": list(L), "omega": list(w["omega"]), "sigma": sigma,
+                       "rhs": "iid N(0,1), SplitMix64 seed 2", "precond": "BF16X3 split tcgen05",
+                       "pcg_tol": PCG_TOL, "l2": "inputs larger than L2 (1.07 GB per vector)",
+                       "parallelism": f"replicas x{world}"},
+            "err_vs_fp64": err, "err_target": ERR_TARGET, "pcg_iters": statistics.median(iters),
+            "fp64": {"ms": fp64_ms, "gdofs": N / (fp64_ms * 1e-3) / 1e9, "kernel": "k_rot_fp64 (FFMA64)"},
+            "mixed_single_apply": {"prec": "BF16X3", "ms": mixed1_ms, "gdofs": N / (mixed1_ms * 1e-3) / 1e9,
+                                   "err_vs_fp64": mixed1_err},
+            "speedup_vs_fp64": fp64_ms / ms,
+            "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N, "err_vs_fp64": e2e_err}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    T.ts_device_status()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture
+# summarised in profiles/; None until a capture of the current kernel exists.
+TRAFFIC_PER_LAUNCH = None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

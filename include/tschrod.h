@@ -170,6 +170,29 @@ ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double
                         ts_dtype dtype, ts_precision prec, void* stream);
 
 /*
+ * Tile configuration of the split-precision tensor-core contraction (no counterpart in
+ * the paper; set by the autotuner).  For real (complex_data = 0) or complex data and a
+ * contracted axis of length n (n = 0: the default for all lengths): K chunk bk (64 =
+ * 128-byte swizzled rows, 32 = 64-byte) and the cap bn_cap (multiple of 16, <= 256) on the
+ * N tile.  Process-wide; takes effect for calls issued afterwards.
+ */
+ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap);
+
+/*
+ * Runtime instrumentation (no counterpart in the paper).
+ * ts_launch_count: number of CUDA kernels the library has launched in this process.
+ * ts_profile_begin: start recording a CUDA event pair around every launch of the
+ *   contraction kernels (on the launching stream); clears earlier records.
+ * ts_profile_end: stop recording and sum the records of one kernel kind
+ *   (0 = split-precision tensor-core pass, 1 = FP64 pass, 2 = small-n fused pass):
+ *   launches, total device time in ms, algorithmic FLOPs and algorithmic HBM bytes.
+ *   Synchronises on the recorded events.  Any pointer may be NULL.
+ */
+long long ts_launch_count(void);
+ts_status ts_profile_begin(void);
+ts_status ts_profile_end(int kind, long long* launches, double* total_ms, double* flops, double* bytes);
+
+/*
  * Device-side failure check (no counterpart in the paper).  The tensor-core kernels never
  * wait without a bound: a wait that runs out (about 2 s) sets a device flag and the kernel
  * returns.  This call synchronises `stream`, returns TS_ERR_TIMEOUT if the flag was set

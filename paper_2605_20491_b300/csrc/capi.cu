@@ -191,6 +191,11 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
                                 lambda, outer_iters, pcg_iters, (cudaStream_t)stream);
 }
 
+ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap) {
+  clear_error();
+  return tc_config_set(complex_data, n, bk, bn_cap);
+}
+
 ts_status ts_device_status(void* stream) {
   clear_error();
   int flag = 0;

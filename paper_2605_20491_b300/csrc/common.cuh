@@ -29,6 +29,22 @@ void clear_error();
     }                                                                                     \
   } while (0)
 
+// Every kernel launch of the library goes through TS_LAUNCHED(count): it adds to the
+// process-wide launch counter (ts_launch_count) and checks the launch.
+void count_launches(int k);
+#define TS_LAUNCHED(k)                       \
+  do {                                       \
+    ::ts::count_launches(k);                 \
+    TS_CHECK_CUDA(cudaGetLastError());       \
+  } while (0)
+
+// Live per-kernel timing (ts_profile_begin / ts_profile_end): when enabled, the launch
+// sites of the contraction kernels bracket each launch with CUDA events on its stream.
+enum ProfKind { PROF_TC_PASS = 0, PROF_FP64_PASS = 1, PROF_SMALL_PASS = 2, PROF_NKINDS = 3 };
+bool prof_enabled();
+void prof_begin_launch(cudaStream_t s, void** token);
+void prof_end_launch(cudaStream_t s, void* token, int kind, double flops, double bytes);
+
 #define TS_TRY(expr)                       \
   do {                                     \
     ts_status _s = (expr);                 \

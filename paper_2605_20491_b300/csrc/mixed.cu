@@ -10,23 +10,29 @@
 //     NP = 3 (TS_BF16X6): x0 b0 + x0 b1 + x1 b0 + x1 b1 + x0 b2 + x2 b0  (~24 bits)
 // All products of one output tile accumulate in one FP32 accumulator in tensor memory.
 //
-// Kernel structure (one 128 x BN output tile per CTA, 128 threads):
-//   warp 0 lane 0  -- TMA producer: for each 64-wide K chunk, loads the X planes
-//                     (128 x 64 bf16 boxes, 128-byte swizzle) and the B planes
-//                     (BN x 64 boxes) into an NS-stage shared-memory ring;
+// Kernel structure: persistent (one CTA per SM, 192 threads), 128 x BN output tiles
+// handed out round-robin with the N tile fastest, so that the CTAs working on the same
+// 128 rows run together and share the X tile through L2:
+//   warp 0 lane 0  -- TMA producer: for each K chunk (BK = 64 with the 128-byte swizzle
+//                     or 32 with the 64-byte swizzle) loads the X planes (128 x BK bf16
+//                     boxes) and the B planes (BN x BK) into an NS-stage ring that runs
+//                     across tiles;
 //   warp 1 lane 0  -- MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16) for
-//                     every (plane pair, K step), accumulating in TMEM; commits free the
-//                     ring slots and finally signal the epilogue;
-//   all 4 warps    -- epilogue: tcgen05.ld of the accumulator rows (warp w owns TMEM
-//                     lanes 32w..32w+31 = rows), optional fused pointwise step 3
-//                     (1/(Lambda + sigma) or e^{-i tau Lambda}, Lambda from per-axis
-//                     tables), then either the NP bf16 planes of the next pass or the
-//                     final FP64 / complex128 / complex64 result, stored transposed.
+//                     every (plane pair, K step) into one of two TMEM accumulator buffers;
+//                     commits free the ring slots and hand the buffer to the epilogue;
+//   warps 2..5     -- epilogue, overlapped with the next tile's MMAs: tcgen05.ld of the
+//                     accumulator rows (warp w owns TMEM lanes 32 (w % 4) + 0..31),
+//                     optional fused pointwise step 3 (1/(Lambda + sigma) or
+//                     e^{-i tau Lambda}, Lambda from per-axis tables), then either the NP
+//                     bf16 planes of the next pass or the final FP64 / complex128 /
+//                     complex64 result, stored transposed.
 // Complex data is planar inside the pipeline (re and im planes); a complex tile keeps
 // two accumulators (re, im) that share every B tile, so the phase multiply can mix them.
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "mixed.cuh"
 #include "tc_ptx.cuh"
@@ -44,7 +50,6 @@ namespace {
 __device__ int g_tc_error = 0;
 
 constexpr int BM = 128;             // rows per tile = TMEM lanes
-constexpr int BK = 64;              // bf16 elements per K chunk (one 128-byte swizzle row)
 constexpr int UMMA_K = 16;          // K of one tcgen05.mma kind::f16
 constexpr int MAX_STAGES = 8;
 constexpr int SMEM_LIMIT = 232448;  // 227 KB opt-in shared memory per CTA
@@ -96,38 +101,45 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16* base, long l
   }
 }
 
-template <int NP, int NACC>
-__global__ void __launch_bounds__(128, 1)
+template <int NP, int NACC, int BKT>
+__global__ void __launch_bounds__(192, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const EpiParams ep) {
+  constexpr int SW = BKT * 2;  // bytes per smem row = swizzle width
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int BN = ep.bn;
   const int NS = ep.nstages;
-  const uint32_t A_TILE = BM * BK * 2;
-  const uint32_t B_TILE = (uint32_t)BN * BK * 2;
+  const uint32_t A_TILE = BM * BKT * 2;
+  const uint32_t B_TILE = (uint32_t)BN * BKT * 2;
   const uint32_t A_STAGE = NACC * NP * A_TILE;
-  const uint32_t STAGE = A_STAGE + NP * B_TILE;
+  const uint32_t B_STAGE = NP * B_TILE;
   uint8_t* sA = smem;
   uint8_t* sB = smem + (size_t)NS * A_STAGE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NS * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NS * (A_STAGE + B_STAGE));
   uint64_t* full = bars;
   uint64_t* empty = bars + MAX_STAGES;
-  uint64_t* accb = bars + 2 * MAX_STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAX_STAGES + 1);
+  uint64_t* accf = bars + 2 * MAX_STAGES;      // accumulator buffer b ready (MMA -> epilogue)
+  uint64_t* acce = bars + 2 * MAX_STAGES + 2;  // accumulator buffer b drained (epilogue -> MMA)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAX_STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long m0 = (long long)blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN;
-  const int nk = (ep.n + BK - 1) / BK;
+  const int nk = (ep.n + BKT - 1) / BKT;
+  const int mtiles = (int)((ep.R + BM - 1) / BM);
+  const int ntiles = (ep.n + BN - 1) / BN;
+  const int total = mtiles * ntiles;
+  const uint32_t acc_cols = NACC * BN;
   uint32_t ncols = 32;
-  while (ncols < (uint32_t)(NACC * BN)) ncols <<= 1;
+  while (ncols < 2 * acc_cols) ncols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 4);
+    }
     tc::fence_barrier_init();
     tc::fence_proxy_async();
     tc::prefetch_tmap(&tmA);
@@ -142,118 +154,145 @@ __global__ void __launch_bounds__(128, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % NS, round = kc / NS;
-      if (round > 0) tc::mbar_wait(&empty[s], (round - 1) & 1, &g_tc_error, 1);
-      tc::mbar_arrive_expect_tx(&full[s], STAGE);
-      for (int c = 0; c < NACC; ++c)
-        for (int p = 0; p < NP; ++p)
-          tc::tma_load_3d(sA + (size_t)s * A_STAGE + (c * NP + p) * A_TILE, &tmA, kc * BK, (int)m0, c * NP + p,
-                          &full[s]);
-      for (int p = 0; p < NP; ++p)
-        tc::tma_load_3d(sB + (size_t)s * NP * B_TILE + p * B_TILE, &tmB, kc * BK, n0, p, &full[s]);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: a ring of NS stages that runs across tiles
+      int it = 0;
+      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int m0 = (t / ntiles) * BM, n0 = (t % ntiles) * BN;
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int s = it % NS, round = it / NS;
+          if (round > 0) tc::mbar_wait(&empty[s], (round - 1) & 1, &g_tc_error, 1);
+          tc::mbar_arrive_expect_tx(&full[s], A_STAGE + B_STAGE);
+          for (int c = 0; c < NACC; ++c)
+            for (int p = 0; p < NP; ++p)
+              tc::tma_load_3d(sA + (size_t)s * A_STAGE + (c * NP + p) * A_TILE, &tmA, kc * BKT, m0, c * NP + p,
+                              &full[s]);
+          for (int p = 0; p < NP; ++p)
+            tc::tma_load_3d(sB + (size_t)s * B_STAGE + p * B_TILE, &tmB, kc * BKT, n0, p, &full[s]);
+        }
+      }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    const uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % NS, round = kc / NS;
-      tc::mbar_wait(&full[s], round & 1, &g_tc_error, 2);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      int it = 0, tl = 0;
+      for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+        const int ab = tl & 1, use = tl >> 1;
+        if (use > 0) tc::mbar_wait(&acce[ab], (use - 1) & 1, &g_tc_error, 4);
+        tc::tc_fence_after();
+        const uint32_t dbase = tmem + (uint32_t)(ab * acc_cols);
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int s = it % NS, round = it / NS;
+          tc::mbar_wait(&full[s], round & 1, &g_tc_error, 2);
+          tc::tc_fence_after();
+          const uint32_t a0 = tc::smem_u32(sA + (size_t)s * A_STAGE);
+          const uint32_t b0 = tc::smem_u32(sB + (size_t)s * B_STAGE);
+#pragma unroll
+          for (int ks = 0; ks < BKT / UMMA_K; ++ks) {
+#pragma unroll
+            for (int q = 0; q < Products<NP>::count; ++q) {
+              const uint64_t bdesc = tc::desc_sw<SW>(b0 + Products<NP>::b(q) * B_TILE + ks * 32);
+#pragma unroll
+              for (int c = 0; c < NACC; ++c) {
+                const uint64_t adesc = tc::desc_sw<SW>(a0 + (c * NP + Products<NP>::a(q)) * A_TILE + ks * 32);
+                tc::mma_bf16(dbase + (uint32_t)(c * BN), adesc, bdesc, idesc, (kc | ks | q) != 0);
+              }
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(&accf[ab]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5; warp w owns TMEM lanes 32 (w % 4) + 0..31
+    const int g = warp & 3;
+    int tl = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+      const int ab = tl & 1, use = tl >> 1;
+      const long long m0 = (long long)(t / ntiles) * BM;
+      const int n0 = (t % ntiles) * BN;
+      tc::mbar_wait(&accf[ab], use & 1, &g_tc_error, 3);
+      __syncwarp();
       tc::tc_fence_after();
-      const uint32_t a0 = tc::smem_u32(sA + (size_t)s * A_STAGE);
-      const uint32_t b0 = tc::smem_u32(sB + (size_t)s * NP * B_TILE);
+      const long long r = m0 + g * 32 + lane;
+      const bool row_ok = r < ep.R;
+      float rowsum = 0.f;
+      float2 rowph = make_float2(1.f, 0.f);
+      if (ep.scale_mode != 0 && row_ok) {
+        long long q = r;
+        double sacc = ep.sigma;
+        double pr = 1.0, pi = 0.0;
+        for (int k = 0; k < ep.rd; ++k) {
+          long long qq = q / ep.rn[k];
+          int i = (int)(q - qq * ep.rn[k]);
+          q = qq;
+          if (ep.scale_mode == 1) {
+            sacc += ep.rlam[k][i];
+          } else {
+            double2 ph = ep.rph[k][i];
+            double tr = pr * ph.x - pi * ph.y;
+            pi = pr * ph.y + pi * ph.x;
+            pr = tr;
+          }
+        }
+        rowsum = (float)sacc;
+        rowph = make_float2((float)pr, (float)pi);
+      }
+      const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
+      for (int col0 = 0; col0 < BN; col0 += 16) {
+        uint32_t v[NACC][16];
 #pragma unroll
-      for (int ks = 0; ks < BK / UMMA_K; ++ks) {
+        for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
+        tc::tmem_ld_wait();
+        if (!row_ok) continue;
 #pragma unroll
-        for (int q = 0; q < Products<NP>::count; ++q) {
-          const uint64_t bdesc = tc::desc_sw128(b0 + Products<NP>::b(q) * B_TILE + ks * 32);
+        for (int i = 0; i < 16; ++i) {
+          const int j = n0 + col0 + i;
+          if (j >= ep.n) break;
+          float val[NACC];
 #pragma unroll
-          for (int c = 0; c < NACC; ++c) {
-            const uint64_t adesc = tc::desc_sw128(a0 + (c * NP + Products<NP>::a(q)) * A_TILE + ks * 32);
-            tc::mma_bf16(tmem + (uint32_t)(c * BN), adesc, bdesc, idesc, (kc | ks | q) != 0);
+          for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
+          if (ep.scale_mode == 1) {
+            val[0] = val[0] * (1.0f / (rowsum + (float)ep.clam[j]));
+          } else if (ep.scale_mode == 2 && NACC == 2) {
+            const double2 cp = ep.cph[j];
+            const float cx = (float)cp.x, cy = (float)cp.y;
+            const float phx = rowph.x * cx - rowph.y * cy;
+            const float phy = rowph.x * cy + rowph.y * cx;
+            const float re = val[0] * phx - val[NACC - 1] * phy;
+            const float im = val[0] * phy + val[NACC - 1] * phx;
+            val[0] = re;
+            val[NACC - 1] = im;
+          }
+          const long long idx = r + ep.R * (long long)j;
+          if (ep.out_mode == 0) {
+            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
+#pragma unroll
+            for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
+          } else if (ep.out_mode == 1) {
+            reinterpret_cast<double*>(ep.out)[idx] = (double)val[0];
+          } else if (ep.out_mode == 2) {
+            reinterpret_cast<double2*>(ep.out)[idx] = make_double2((double)val[0], (double)val[NACC - 1]);
+          } else {
+            reinterpret_cast<float2*>(ep.out)[idx] = make_float2(val[0], val[NACC - 1]);
           }
         }
       }
-      tc::mma_commit(&empty[s]);
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[ab]);
     }
-    tc::mma_commit(accb);
   }
   __syncwarp();
-
-  // ---------------- epilogue (all four warps)
-  tc::mbar_wait(accb, 0, &g_tc_error, 3);
-  __syncwarp();
-  tc::tc_fence_after();
-
-  const long long r = m0 + warp * 32 + lane;
-  const bool row_ok = r < ep.R;
-  float rowsum = 0.f;
-  float2 rowph = make_float2(1.f, 0.f);
-  if (ep.scale_mode != 0 && row_ok) {
-    long long q = r;
-    double s = ep.sigma;
-    double pr = 1.0, pi = 0.0;
-    for (int k = 0; k < ep.rd; ++k) {
-      long long qq = q / ep.rn[k];
-      int i = (int)(q - qq * ep.rn[k]);
-      q = qq;
-      if (ep.scale_mode == 1) {
-        s += ep.rlam[k][i];
-      } else {
-        double2 ph = ep.rph[k][i];
-        double tr = pr * ph.x - pi * ph.y;
-        pi = pr * ph.y + pi * ph.x;
-        pr = tr;
-      }
-    }
-    rowsum = (float)s;
-    rowph = make_float2((float)pr, (float)pi);
-  }
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-  for (int col0 = 0; col0 < BN; col0 += 16) {
-    uint32_t v[NACC][16];
-#pragma unroll
-    for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
-    tc::tmem_ld_wait();
-    if (!row_ok) continue;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int j = n0 + col0 + i;
-      if (j >= ep.n) break;
-      float val[NACC];
-#pragma unroll
-      for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
-      if (ep.scale_mode == 1) {
-        val[0] = val[0] * (1.0f / (rowsum + (float)ep.clam[j]));
-      } else if (ep.scale_mode == 2 && NACC == 2) {
-        const double2 cp = ep.cph[j];
-        const float cx = (float)cp.x, cy = (float)cp.y;
-        const float phx = rowph.x * cx - rowph.y * cy;
-        const float phy = rowph.x * cy + rowph.y * cx;
-        const float re = val[0] * phx - val[NACC - 1] * phy;
-        const float im = val[0] * phy + val[NACC - 1] * phx;
-        val[0] = re;
-        val[NACC - 1] = im;
-      }
-      const long long idx = r + ep.R * (long long)j;
-      if (ep.out_mode == 0) {
-        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
-#pragma unroll
-        for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
-      } else if (ep.out_mode == 1) {
-        reinterpret_cast<double*>(ep.out)[idx] = (double)val[0];
-      } else if (ep.out_mode == 2) {
-        reinterpret_cast<double2*>(ep.out)[idx] = make_double2((double)val[0], (double)val[NACC - 1]);
-      } else {
-        reinterpret_cast<float2*>(ep.out)[idx] = make_float2(val[0], val[NACC - 1]);
-      }
-    }
-  }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, ncols);
+  }
 }
 
 // ------------------------------------------------------------ pointwise ----
@@ -320,8 +359,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 3D bf16 tensor map over planes [planes][rows][cols] (cols contiguous), box
-// {64 cols, box_rows rows, 1 plane}, 128-byte swizzle, zero fill out of bounds.
-ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long rows, int planes, int box_rows) {
+// {box_cols cols, box_rows rows, 1 plane}, swizzle = 2 * box_cols bytes (128 or 64),
+// zero fill out of bounds.
+ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long rows, int planes, int box_cols,
+                   int box_rows) {
   auto enc = get_encode();
   if (!enc) {
     set_error("cuTensorMapEncodeTiled is unavailable");
@@ -329,10 +370,12 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
   }
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(cols * 2), (cuuint64_t)(cols * rows * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d) for cols=%lld rows=%lld planes=%d", (int)r, cols, rows, planes);
@@ -341,24 +384,25 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
   return TS_OK;
 }
 
-template <int NP, int NACC>
-ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
-                      cudaStream_t s) {
-  const int bn_cap = NACC == 1 ? 256 : 128;
+int g_num_sms = 0;
+
+template <int NP, int NACC, int BKT>
+ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
+                        int bn_cap, cudaStream_t s) {
   int bn = ((n + 15) / 16) * 16;
   if (bn > bn_cap) bn = bn_cap;
-  const int stage = NACC * NP * BM * BK * 2 + NP * bn * BK * 2;
-  const int reserve = 1024 + 8 * (2 * MAX_STAGES + 2);
+  const int stage = NACC * NP * BM * BKT * 2 + NP * bn * BKT * 2;
+  const int reserve = 1024 + 8 * (2 * MAX_STAGES + 6);
   int ns = (SMEM_LIMIT - reserve) / stage;
   if (ns > MAX_STAGES) ns = MAX_STAGES;
-  if (ns < 1) {
+  if (ns < 2) {
     set_error("tile does not fit in shared memory");
     return TS_ERR_UNSUPPORTED;
   }
   const int smem = ns * stage + reserve;
   CUtensorMap ma, mb;
-  TS_TRY(make_map(&ma, A, n, R, NACC * NP, BM));
-  TS_TRY(make_map(&mb, B, n, n, NP, bn));
+  TS_TRY(make_map(&ma, A, n, R, NACC * NP, BKT, BM));
+  TS_TRY(make_map(&mb, B, n, n, NP, BKT, bn));
   ep.R = R;
   ep.n = n;
   ep.N = R * n;
@@ -366,13 +410,74 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
   ep.nstages = ns;
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
-    TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
+    TS_CHECK_CUDA(
+        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
     attr_set = true;
   }
-  dim3 grid((unsigned)((R + BM - 1) / BM), (unsigned)((n + bn - 1) / bn));
-  k_rot_tc<NP, NACC><<<grid, 128, smem, s>>>(ma, mb, ep);
-  TS_CHECK_CUDA(cudaGetLastError());
+  if (g_num_sms == 0) {
+    int dev = 0;
+    TS_CHECK_CUDA(cudaGetDevice(&dev));
+    TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long long tiles = ((R + BM - 1) / BM) * ((n + bn - 1) / bn);
+  TS_REQUIRE(tiles < (1LL << 31), "too many tiles");
+  const unsigned grid = (unsigned)(tiles < g_num_sms ? tiles : g_num_sms);
+  void* tok = nullptr;
+  if (prof_enabled()) prof_begin_launch(s, &tok);
+  k_rot_tc<NP, NACC, BKT><<<grid, 192, smem, s>>>(ma, mb, ep);
+  TS_LAUNCHED(1);
+  if (tok) {
+    const double flops = 2.0 * Products<NP>::count * NACC * (double)R * n * n;
+    const double bytes = (double)NACC * R * n * 2.0 * NP * (ep.out_mode == 0 ? 2.0 : 1.0) +
+                         (ep.out_mode == 1 ? 8.0 : ep.out_mode == 2 ? 16.0 : ep.out_mode == 3 ? 8.0 : 0.0) * R * n;
+    prof_end_launch(s, tok, PROF_TC_PASS, flops, bytes);
+  }
   return TS_OK;
+}
+
+// Tile configuration of one pass (the autotuner's search space): K chunk 64 (128-byte
+// swizzle) or 32 (64-byte swizzle), and the cap on the N tile.
+struct TcConfig {
+  int bk = 64;
+  int bn_cap = 256;
+};
+
+std::mutex g_cfg_mu;
+std::map<std::pair<int, int>, TcConfig> g_cfg;  // (nacc, n) -> config; n = 0 is the default
+
+TcConfig lookup_config(int nacc, int n) {
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  auto it = g_cfg.find({nacc, n});
+  if (it != g_cfg.end()) return it->second;
+  it = g_cfg.find({nacc, 0});
+  if (it != g_cfg.end()) return it->second;
+  TcConfig c;
+  c.bk = 64;
+  c.bn_cap = nacc == 1 ? 256 : 128;
+  return c;
+}
+
+template <int NP, int NACC>
+ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
+                      cudaStream_t s) {
+  TcConfig c = lookup_config(NACC, n);
+  if (2 * NACC * c.bn_cap > 512) c.bn_cap = 256 / NACC;  // two accumulator buffers must fit in TMEM
+  // Fall back to a narrower K chunk, then a narrower N tile, until two stages fit.
+  const int reserve = 1024 + 8 * (2 * MAX_STAGES + 6);
+  for (;;) {
+    int bn = ((n + 15) / 16) * 16;
+    if (bn > c.bn_cap) bn = c.bn_cap;
+    const int stage = NACC * NP * BM * c.bk * 2 + NP * bn * c.bk * 2;
+    if ((SMEM_LIMIT - reserve) / stage >= 2) break;
+    if (c.bk == 64)
+      c.bk = 32;
+    else if (c.bn_cap > 16)
+      c.bn_cap /= 2;
+    else
+      break;
+  }
+  if (c.bk == 32) return launch_pass_t<NP, NACC, 32>(A, B, R, n, ep, c.bn_cap, s);
+  return launch_pass_t<NP, NACC, 64>(A, B, R, n, ep, c.bn_cap, s);
 }
 
 ts_status pass(int np, int nacc, const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n,
@@ -410,7 +515,7 @@ ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s) {
     // Forward operand B[j][i] = S[i][j] is the row-major S^T; backward B[i][j] = S[i][j].
     k_split_table<<<grid_1d(cnt), 256, 0, s>>>(p->St[k], p->Bf[prec][k], cnt, np);
     k_split_table<<<grid_1d(cnt), 256, 0, s>>>(p->S[k], p->Bb[prec][k], cnt, np);
-    TS_CHECK_CUDA(cudaGetLastError());
+    TS_LAUNCHED(2);
   }
   return TS_OK;
 }
@@ -445,6 +550,7 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
     st = scratch_alloc(&tabs, sizeof(double2) * tot, s);
     for (int k = 0; k < p->d && st == TS_OK; ++k) {
       k_phase_table<<<(p->n[k] + 127) / 128, 128, 0, s>>>(p->lam[k], param, (double2*)tabs + tab_off[k], p->n[k]);
+      count_launches(1);
       if (cudaGetLastError() != cudaSuccess) {
         set_error("phase table launch failed");
         st = TS_ERR_CUDA;
@@ -462,6 +568,7 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
     else
       np == 2 ? k_split_input<2, 2><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N)
               : k_split_input<3, 2><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N);
+    count_launches(1);
     if (cudaGetLastError() != cudaSuccess) {
       set_error("split launch failed");
       st = TS_ERR_CUDA;
@@ -495,6 +602,19 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
   scratch_free(w1, s);
   scratch_free(tabs, s);
   return st;
+}
+
+ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap) {
+  if ((bk != 32 && bk != 64) || bn_cap < 16 || bn_cap > 256 || bn_cap % 16 != 0 || n < 0) {
+    set_error("invalid tensor-core tile configuration (bk %d, bn_cap %d)", bk, bn_cap);
+    return TS_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  TcConfig c;
+  c.bk = bk;
+  c.bn_cap = bn_cap;
+  g_cfg[{complex_data ? 2 : 1, n}] = c;
+  return TS_OK;
 }
 
 ts_status mixed_error_flag(int* host_flag, bool reset, cudaStream_t s) {

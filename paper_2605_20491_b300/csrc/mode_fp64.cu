@@ -99,8 +99,11 @@ ts_status launch(const double* X, double* Y, const double* B, long long R, int n
   long long gx = (M + BM - 1) / BM;
   TS_REQUIRE(gx < (1LL << 31), "rot_pass_fp64: grid too large (M=%lld)", M);
   dim3 grid((unsigned)gx, (unsigned)((n + BN - 1) / BN));
+  void* tok = nullptr;
+  if (prof_enabled()) prof_begin_launch(s, &tok);
   k_rot_fp64<BN, BK, NC><<<grid, 256, 0, s>>>(X, Y, B, R, n);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
+  if (tok) prof_end_launch(s, tok, PROF_FP64_PASS, 2.0 * (double)M * n * n, 16.0 * (double)M * n);
   return TS_OK;
 }
 

@@ -257,37 +257,37 @@ static inline unsigned grid_for(long long N) {
 
 ts_status scale_inverse_fp64(const ts_plan* p, double sigma, double* X, cudaStream_t s) {
   k_scale_inverse<<<grid_for(p->N), 256, 0, s>>>(axis_params(p, true), sigma, X, p->N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status scale_exp_c128(const ts_plan* p, double tau, double* X, cudaStream_t s) {
   k_scale_exp<<<grid_for(p->N), 256, 0, s>>>(axis_params(p, true), tau, X, p->N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status phase_v2_c128(long long N, const double* V2, double th, double* psi, cudaStream_t s) {
   k_phase_c128<<<grid_for(N), 256, 0, s>>>(V2, th, psi, N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status phase_v2_c64(long long N, const double* V2, double th, float* psi, cudaStream_t s) {
   k_phase_c64<<<grid_for(N), 256, 0, s>>>(V2, th, psi, N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status convert_c64_to_c128(long long N, const float* in, double* out, cudaStream_t s) {
   k_c64_to_c128<<<grid_for(2 * N), 256, 0, s>>>(in, out, 2 * N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status convert_c128_to_c64(long long N, const double* in, float* out, cudaStream_t s) {
   k_c128_to_c64<<<grid_for(2 * N), 256, 0, s>>>(in, out, 2 * N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
@@ -295,10 +295,10 @@ ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const 
                         double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
   k_stencil<0><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, nullptr, y, p->N, partial);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   if (out2) {
     k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
-    TS_CHECK_CUDA(cudaGetLastError());
+    TS_LAUNCHED(1);
   }
   return TS_OK;
 }
@@ -307,9 +307,9 @@ ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, con
                            double* r, double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
   k_stencil<1><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, r, p->N, partial);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
@@ -317,9 +317,9 @@ ts_status dot2(long long N, const double* a, const double* b, const double* c, c
                double* out2, cudaStream_t s) {
   unsigned g = grid_for(N);
   k_dot2<<<g, 256, 0, s>>>(a, b, c, d, N, partial);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
@@ -328,22 +328,22 @@ ts_status pcg_update_xr(const double* rz, const double* pq, double* alpha_out, d
                         cudaStream_t s) {
   unsigned g = grid_for(N);
   k_pcg_xr<<<g, 256, 0, s>>>(rz, pq, alpha_out, x, r, p, q, N, partial);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status pcg_update_p(const double* alpha, const double* zq, const double* rz_old, int first, double* p,
                        const double* z, long long N, cudaStream_t s) {
   k_pcg_p<<<grid_for(N), 256, 0, s>>>(alpha, zq, rz_old, first, p, z, N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status copy_scalar(const double* src, double* dst, cudaStream_t s) {
   k_copy_scalar<<<1, 1, 0, s>>>(src, dst);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
@@ -351,20 +351,20 @@ ts_status tensor_ground(const ts_plan* p, double* u, cudaStream_t s) {
   AxisParams a = axis_params(p, true);
   for (int k = 0; k < p->d; ++k) a.tab[k] = p->St[k];
   k_tensor_ground<<<grid_for(p->N), 256, 0, s>>>(a, u, p->N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status axpby(long long N, double a, const double* x, double b, double* y, cudaStream_t s) {
   k_axpby<<<grid_for(N), 256, 0, s>>>(a, x, b, y, N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 
 ts_status scale_by_device_ratio(long long N, const double* num, const double* den, const double* x, double* y,
                                 cudaStream_t s) {
   k_scale_by_scalar<<<grid_for(N), 256, 0, s>>>(num, den, y, x, N);
-  TS_CHECK_CUDA(cudaGetLastError());
+  TS_LAUNCHED(1);
   return TS_OK;
 }
 

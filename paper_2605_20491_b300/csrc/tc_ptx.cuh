@@ -30,6 +30,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
@@ -92,17 +96,20 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 // ------------------------------------------------------------ descriptors -----
 
-// Shared-memory matrix descriptor for a K-major operand tile stored with the 128-byte
-// swizzle (rows of 128 bytes, 8-row atoms of 1024 bytes): start address, leading byte
-// offset (unused for swizzled K-major, encoded 1), stride byte offset 1024 between
-// 8-row groups, descriptor version 1 (bits 46-47), layout type 2 = SWIZZLE_128B (bits 61-63).
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor for a K-major operand tile stored with a SW-byte
+// swizzle (SW = 128 or 64: rows of SW bytes, 8-row atoms of 8*SW bytes): start address,
+// leading byte offset (unused for swizzled K-major, encoded 1), stride byte offset 8*SW
+// between 8-row groups, descriptor version 1 (bits 46-47), layout type in bits 61-63
+// (2 = SWIZZLE_128B, 4 = SWIZZLE_64B).
+template <int SW>
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr) {
+  static_assert(SW == 128 || SW == 64, "swizzle");
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((8 * SW) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(SW == 128 ? 2 : 4) << 61;
   return d;
 }
 

@@ -29,7 +29,8 @@ TS_MAX_DIM = 12
 EXPORTS = [
     "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
     "ts_apply_inverse", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
-    "ts_device_status", "ts_last_error", "ts_version",
+    "ts_tc_config_set", "ts_device_status", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
+    "ts_last_error", "ts_version",
 ]
 
 
@@ -70,6 +71,10 @@ def lib() -> C.CDLL:
                                        C.POINTER(C.c_longlong), vp]
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
     L.ts_device_status.argtypes = [vp]
+    L.ts_tc_config_set.argtypes = [ip, ip, ip, ip]
+    L.ts_launch_count.argtypes = []
+    L.ts_profile_begin.argtypes = []
+    L.ts_profile_end.argtypes = [ip, C.POINTER(C.c_longlong), C.POINTER(dp), C.POINTER(dp), C.POINTER(dp)]
     L.ts_last_error.restype = C.c_char_p
     L.ts_last_error.argtypes = []
     L.ts_version.restype = C.c_char_p
@@ -77,6 +82,7 @@ def lib() -> C.CDLL:
     for name in EXPORTS:
         if name not in ("ts_last_error", "ts_version"):
             getattr(L, name).restype = C.c_int
+    L.ts_launch_count.restype = C.c_longlong
     _lib = L
     return L
 
@@ -203,6 +209,29 @@ def ts_inverse_iteration(plan: Plan, shift: float, V2, u, init_from_plan: bool =
                                       pcg_tol, pcg_maxit, precond, C.byref(lam), C.byref(outer), C.byref(tot),
                                       _stream(stream)), "ts_inverse_iteration")
     return lam.value, outer.value, tot.value
+
+
+def ts_tc_config_set(complex_data: bool, n: int, bk: int, bn_cap: int):
+    _check(lib().ts_tc_config_set(int(complex_data), n, bk, bn_cap), "ts_tc_config_set")
+
+
+def ts_launch_count() -> int:
+    return lib().ts_launch_count()
+
+
+def ts_profile_begin():
+    _check(lib().ts_profile_begin(), "ts_profile_begin")
+
+
+PROF_TC_PASS, PROF_FP64_PASS, PROF_SMALL_PASS = range(3)
+
+
+def ts_profile_end(kind: int):
+    """Returns (launches, total ms, algorithmic FLOPs, algorithmic bytes) for one kernel kind."""
+    n = C.c_longlong(0)
+    ms, fl, by = C.c_double(0), C.c_double(0), C.c_double(0)
+    _check(lib().ts_profile_end(kind, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)), "ts_profile_end")
+    return n.value, ms.value, fl.value, by.value
 
 
 def ts_device_status(stream=None):

@@ -14,7 +14,7 @@ def declared_symbols():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\*?\s*(ts_[a-z_0-9]+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^\s*[A-Za-z_][A-Za-z_0-9 \t]*[\s*]+(ts_[a-z_0-9]+)\s*\(", src, re.M))
     return names
 
 
