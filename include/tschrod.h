@@ -112,6 +112,20 @@ ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, d
                            ts_precision prec, void* stream);
 
 /*
+ * The direct solve of ts_apply_inverse carried to FP64 accuracy by mixed-precision
+ * iterative refinement (the split-precision inverse as preconditioner of the Richardson
+ * iteration, a special case of Sec. 3.2's PCG with V2 = 0):
+ *     u_0 = P b,   u_{k+1} = u_k + P (b - (-Delta_h + V1 + sigma) u_k),  k < refinements,
+ * P = (-Delta_h + V1 + sigma)^{-1} applied in precision prec, residuals in FP64 by the
+ * stencil of eq. general_system.  Each refinement multiplies the error by about the
+ * relative error of one split-precision apply (~1e-5 for TS_BF16X3), so two refinements
+ * reach FP64 rounding.  No host synchronisation.  b, u: N doubles, must not alias.
+ * prec = TS_FP64 performs the plain FP64 apply (refinements ignored).
+ */
+ts_status ts_solve_refined(const ts_plan* plan, double sigma, const double* b, double* u,
+                           ts_precision prec, int refinements, void* stream);
+
+/*
  * psi_out = e^{-i tau (-Delta_h + V1)} psi_in   (exact propagator, eq. exact_prop):
  * forward transform, multiply coefficient (i_1..i_d) by e^{-i tau Lambda}, backward
  * transform.  dtype TS_C128 (2N doubles) or TS_C64 (2N floats); psi_in and psi_out may

@@ -150,6 +150,16 @@ ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, d
   return apply_inverse_impl(plan, sigma, b, u, prec, (cudaStream_t)stream);
 }
 
+ts_status ts_solve_refined(const ts_plan* plan, double sigma, const double* b, double* u, ts_precision prec,
+                           int refinements, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(b && u && b != u, "b and u must be non-NULL and distinct");
+  TS_REQUIRE(refinements >= 0 && refinements <= 16, "refinements must be in [0, 16]");
+  TS_TRY(check_prec(plan, prec));
+  if (prec == TS_FP64) return apply_inverse_impl(plan, sigma, b, u, prec, (cudaStream_t)stream);
+  return mixed_refine(plan, prec, sigma, b, u, refinements, (cudaStream_t)stream);
+}
+
 ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void* psi_out, ts_dtype dtype,
                        ts_precision prec, void* stream) {
   TS_API_BEGIN(plan);

@@ -10,7 +10,7 @@
 //     NP = 3 (TS_BF16X6): x0 b0 + x0 b1 + x1 b0 + x1 b1 + x0 b2 + x2 b0  (~24 bits)
 // All products of one output tile accumulate in one FP32 accumulator in tensor memory.
 //
-// Kernel structure: persistent (one CTA per SM, 192 threads), 128 x BN output tiles
+// Kernel structure: persistent (one CTA per SM, 320 threads), 128 x BN output tiles
 // handed out round-robin with the N tile fastest, so that the CTAs working on the same
 // 128 rows run together and share the X tile through L2:
 //   warp 0 lane 0  -- TMA producer: for each K chunk (BK = 64 with the 128-byte swizzle
@@ -20,8 +20,9 @@
 //   warp 1 lane 0  -- MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16) for
 //                     every (plane pair, K step) into one of two TMEM accumulator buffers;
 //                     commits free the ring slots and hand the buffer to the epilogue;
-//   warps 2..5     -- epilogue, overlapped with the next tile's MMAs: tcgen05.ld of the
-//                     accumulator rows (warp w owns TMEM lanes 32 (w % 4) + 0..31),
+//   warps 2..9     -- epilogue, overlapped with the next tile's MMAs: tcgen05.ld of the
+//                     accumulator rows (warp w owns TMEM lanes 32 (w % 4) + 0..31 and
+//                     every other 16-column chunk),
 //                     optional fused pointwise step 3 (1/(Lambda + sigma) or
 //                     e^{-i tau Lambda}, Lambda from per-axis tables), then either the NP
 //                     bf16 planes of the next pass or the final FP64 / complex128 /
@@ -35,6 +36,8 @@
 #include <mutex>
 
 #include "mixed.cuh"
+#include "pointwise.cuh"
+#include "split.cuh"
 #include "tc_ptx.cuh"
 
 namespace ts {
@@ -55,7 +58,7 @@ constexpr int MAX_STAGES = 8;
 constexpr int SMEM_LIMIT = 232448;  // 227 KB opt-in shared memory per CTA
 
 struct EpiParams {
-  int out_mode;    // 0: bf16 planes, 1: FP64 real, 2: complex128, 3: complex64
+  int out_mode;    // 0: bf16 planes, 1: FP64 real, 2: complex128, 3: complex64, 4: FP64 real +=
   int scale_mode;  // 0: none, 1: inverse 1/(Lambda + sigma), 2: phase e^{-i tau Lambda}
   long long R;     // rows of the pass
   int n;           // contracted (= output column) extent
@@ -88,21 +91,24 @@ struct Products<3> {
   __device__ static int b(int q) { return q == 1 || q == 3 ? 1 : (q == 4 ? 2 : 0); }
 };
 
-template <int NP>
-__device__ __forceinline__ void split_store(float v, __nv_bfloat16* base, long long plane_stride, long long idx) {
-  __nv_bfloat16 h = __float2bfloat16_rn(v);
-  base[idx] = h;
-  float rres = v - __bfloat162float(h);
-  __nv_bfloat16 m = __float2bfloat16_rn(rres);
-  base[plane_stride + idx] = m;
-  if (NP == 3) {
-    float r2 = rres - __bfloat162float(m);
-    base[2 * plane_stride + idx] = __float2bfloat16_rn(r2);
-  }
+constexpr int EPI_WARPS = 8;                   // two warps per TMEM lane quarter
+constexpr int TC_THREADS = 32 * (2 + EPI_WARPS);
+
+// Exact float -> double conversion with integer instructions (sign, exponent rebias
+// +896, mantissa shift by 29): FP64-pipe conversions are scarce on this GPU.  Zero,
+// subnormal, infinite and NaN inputs take the ordinary conversion.
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)f;
+  const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                  ((unsigned long long)(e + 896u) << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
 }
 
-template <int NP, int NACC, int BKT>
-__global__ void __launch_bounds__(192, 1)
+template <int NP, int NACC, int BKT, bool PLANES_OUT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const EpiParams ep) {
   constexpr int SW = BKT * 2;  // bytes per smem row = swizzle width
   extern __shared__ uint8_t smem_raw[];
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&accf[b], 1);
-      tc::mbar_init(&acce[b], 4);
+      tc::mbar_init(&acce[b], EPI_WARPS);
     }
     tc::fence_barrier_init();
     tc::fence_proxy_async();
@@ -207,8 +213,10 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5; warp w owns TMEM lanes 32 (w % 4) + 0..31
+    // ---------------- epilogue: warps 2..9.  Warp w reads TMEM lanes 32 (w % 4) + 0..31
+    // (tile rows) and every other 16-column chunk (half (w - 2) / 4).
     const int g = warp & 3;
+    const int half = (warp - 2) >> 2;
     int tl = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
       const int ab = tl & 1, use = tl >> 1;
@@ -242,16 +250,19 @@ __global__ void __launch_bounds__(192, 1)
         rowph = make_float2((float)pr, (float)pi);
       }
       const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
-      for (int col0 = 0; col0 < BN; col0 += 16) {
+      for (int col0 = half * 16; col0 < BN; col0 += 32) {
         uint32_t v[NACC][16];
 #pragma unroll
         for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
         tc::tmem_ld_wait();
         if (!row_ok) continue;
+        const int jbase = n0 + col0;
+        const int jn = ep.n - jbase < 16 ? ep.n - jbase : 16;
+        long long idx = r + ep.R * (long long)jbase;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int j = n0 + col0 + i;
-          if (j >= ep.n) break;
+        for (int i = 0; i < 16; ++i, idx += ep.R) {
+          if (i >= jn) break;
+          const int j = jbase + i;
           float val[NACC];
 #pragma unroll
           for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
@@ -267,15 +278,16 @@ __global__ void __launch_bounds__(192, 1)
             val[0] = re;
             val[NACC - 1] = im;
           }
-          const long long idx = r + ep.R * (long long)j;
-          if (ep.out_mode == 0) {
+          if (PLANES_OUT) {
             __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
 #pragma unroll
             for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
           } else if (ep.out_mode == 1) {
-            reinterpret_cast<double*>(ep.out)[idx] = (double)val[0];
+            reinterpret_cast<double*>(ep.out)[idx] = f2d(val[0]);
+          } else if (ep.out_mode == 4) {
+            reinterpret_cast<double*>(ep.out)[idx] += f2d(val[0]);
           } else if (ep.out_mode == 2) {
-            reinterpret_cast<double2*>(ep.out)[idx] = make_double2((double)val[0], (double)val[NACC - 1]);
+            reinterpret_cast<double2*>(ep.out)[idx] = make_double2(f2d(val[0]), f2d(val[NACC - 1]));
           } else {
             reinterpret_cast<float2*>(ep.out)[idx] = make_float2(val[0], val[NACC - 1]);
           }
@@ -386,7 +398,7 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
 
 int g_num_sms = 0;
 
-template <int NP, int NACC, int BKT>
+template <int NP, int NACC, int BKT, bool PO>
 ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
                         int bn_cap, cudaStream_t s) {
   int bn = ((n + 15) / 16) * 16;
@@ -411,7 +423,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     TS_CHECK_CUDA(
-        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
+        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
     attr_set = true;
   }
   if (g_num_sms == 0) {
@@ -424,12 +436,13 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   const unsigned grid = (unsigned)(tiles < g_num_sms ? tiles : g_num_sms);
   void* tok = nullptr;
   if (prof_enabled()) prof_begin_launch(s, &tok);
-  k_rot_tc<NP, NACC, BKT><<<grid, 192, smem, s>>>(ma, mb, ep);
+  k_rot_tc<NP, NACC, BKT, PO><<<grid, TC_THREADS, smem, s>>>(ma, mb, ep);
   TS_LAUNCHED(1);
   if (tok) {
     const double flops = 2.0 * Products<NP>::count * NACC * (double)R * n * n;
     const double bytes = (double)NACC * R * n * 2.0 * NP * (ep.out_mode == 0 ? 2.0 : 1.0) +
-                         (ep.out_mode == 1 ? 8.0 : ep.out_mode == 2 ? 16.0 : ep.out_mode == 3 ? 8.0 : 0.0) * R * n;
+                         (ep.out_mode == 1 ? 8.0 : ep.out_mode == 2 ? 16.0 : ep.out_mode == 3 ? 8.0
+                                                 : ep.out_mode == 4 ? 16.0 : 0.0) * R * n;
     prof_end_launch(s, tok, PROF_TC_PASS, flops, bytes);
   }
   return TS_OK;
@@ -476,8 +489,12 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
     else
       break;
   }
-  if (c.bk == 32) return launch_pass_t<NP, NACC, 32>(A, B, R, n, ep, c.bn_cap, s);
-  return launch_pass_t<NP, NACC, 64>(A, B, R, n, ep, c.bn_cap, s);
+  if (ep.out_mode == 0) {
+    if (c.bk == 32) return launch_pass_t<NP, NACC, 32, true>(A, B, R, n, ep, c.bn_cap, s);
+    return launch_pass_t<NP, NACC, 64, true>(A, B, R, n, ep, c.bn_cap, s);
+  }
+  if (c.bk == 32) return launch_pass_t<NP, NACC, 32, false>(A, B, R, n, ep, c.bn_cap, s);
+  return launch_pass_t<NP, NACC, 64, false>(A, B, R, n, ep, c.bn_cap, s);
 }
 
 ts_status pass(int np, int nacc, const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n,
@@ -520,10 +537,10 @@ ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s) {
   return TS_OK;
 }
 
-ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
-                      ts_dtype dt, cudaStream_t s) {
-  const int np = bf16_planes(prec);
-  if (np == 0) {
+namespace {
+
+ts_status check_mixed(const ts_plan* p, ts_precision prec) {
+  if (bf16_planes(prec) == 0) {
     set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X3, TS_BF16X6)", (int)prec);
     return TS_ERR_UNSUPPORTED;
   }
@@ -534,6 +551,64 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
       return TS_ERR_UNSUPPORTED;
     }
   }
+  return TS_OK;
+}
+
+// The 2d contraction passes of one apply: planes in buf[0] -> ... -> `out` (out_mode of the
+// last pass: 1 FP64 store, 2 complex128, 3 complex64, 4 FP64 accumulate), with the
+// pointwise step fused into pass d-1.
+ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double param, __nv_bfloat16* const buf[2],
+                     const double2* tabs, const int* tab_off, void* out, int last_mode, cudaStream_t s) {
+  const int np = bf16_planes(prec);
+  const int nc = op == MixedOp::Exp ? 2 : 1;
+  const int d = p->d;
+  ts_status st = TS_OK;
+  for (int t = 0; t < 2 * d && st == TS_OK; ++t) {
+    const int k = t % d;
+    const bool fwd = t < d;
+    const bool last = t == 2 * d - 1;
+    EpiParams ep{};
+    ep.out_mode = last ? last_mode : 0;
+    ep.out = last ? out : (void*)buf[(t + 1) & 1];
+    ep.scale_mode = 0;
+    if (t == d - 1) {
+      ep.scale_mode = op == MixedOp::Inverse ? 1 : 2;
+      ep.sigma = op == MixedOp::Inverse ? param : 0.0;
+      ep.rd = d - 1;
+      for (int q = 0; q < d - 1; ++q) {
+        ep.rn[q] = p->n[q];
+        ep.rlam[q] = p->lam[q];
+        ep.rph[q] = tabs ? tabs + tab_off[q] : nullptr;
+      }
+      ep.clam = p->lam[k];
+      ep.cph = tabs ? tabs + tab_off[k] : nullptr;
+    }
+    const __nv_bfloat16* B = fwd ? p->Bf[prec][k] : p->Bb[prec][k];
+    st = pass(np, nc, buf[t & 1], B, p->N / p->n[k], p->n[k], ep, s);
+  }
+  return st;
+}
+
+ts_status split_input(int np, ts_dtype dt, const void* in, __nv_bfloat16* planes, long long N, cudaStream_t s) {
+  if (dt == TS_R64)
+    np == 2 ? k_split_input<2, 0><<<grid_1d(N), 256, 0, s>>>(in, planes, N)
+            : k_split_input<3, 0><<<grid_1d(N), 256, 0, s>>>(in, planes, N);
+  else if (dt == TS_C128)
+    np == 2 ? k_split_input<2, 1><<<grid_1d(N), 256, 0, s>>>(in, planes, N)
+            : k_split_input<3, 1><<<grid_1d(N), 256, 0, s>>>(in, planes, N);
+  else
+    np == 2 ? k_split_input<2, 2><<<grid_1d(N), 256, 0, s>>>(in, planes, N)
+            : k_split_input<3, 2><<<grid_1d(N), 256, 0, s>>>(in, planes, N);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
+}  // namespace
+
+ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
+                      ts_dtype dt, cudaStream_t s) {
+  TS_TRY(check_mixed(p, prec));
+  const int np = bf16_planes(prec);
   const int nc = op == MixedOp::Exp ? 2 : 1;
   const long long N = p->N;
   const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)nc * np * N;
@@ -558,49 +633,38 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
     }
   }
   __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
-  if (st == TS_OK) {
-    if (dt == TS_R64)
-      np == 2 ? k_split_input<2, 0><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N)
-              : k_split_input<3, 0><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N);
-    else if (dt == TS_C128)
-      np == 2 ? k_split_input<2, 1><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N)
-              : k_split_input<3, 1><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N);
-    else
-      np == 2 ? k_split_input<2, 2><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N)
-              : k_split_input<3, 2><<<grid_1d(N), 256, 0, s>>>(in, buf[0], N);
-    count_launches(1);
-    if (cudaGetLastError() != cudaSuccess) {
-      set_error("split launch failed");
-      st = TS_ERR_CUDA;
-    }
-  }
-  const int d = p->d;
-  for (int t = 0; t < 2 * d && st == TS_OK; ++t) {
-    const int k = t % d;
-    const bool fwd = t < d;
-    const bool last = t == 2 * d - 1;
-    EpiParams ep{};
-    ep.out_mode = last ? (dt == TS_R64 ? 1 : (dt == TS_C128 ? 2 : 3)) : 0;
-    ep.out = last ? out : (void*)buf[(t + 1) & 1];
-    ep.scale_mode = 0;
-    if (t == d - 1) {
-      ep.scale_mode = op == MixedOp::Inverse ? 1 : 2;
-      ep.sigma = op == MixedOp::Inverse ? param : 0.0;
-      ep.rd = d - 1;
-      for (int q = 0; q < d - 1; ++q) {
-        ep.rn[q] = p->n[q];
-        ep.rlam[q] = p->lam[q];
-        ep.rph[q] = tabs ? (const double2*)tabs + tab_off[q] : nullptr;
-      }
-      ep.clam = p->lam[k];
-      ep.cph = tabs ? (const double2*)tabs + tab_off[k] : nullptr;
-    }
-    const __nv_bfloat16* B = fwd ? p->Bf[prec][k] : p->Bb[prec][k];
-    st = pass(np, nc, buf[t & 1], B, N / p->n[k], p->n[k], ep, s);
-  }
+  if (st == TS_OK) st = split_input(np, dt, in, buf[0], N, s);
+  if (st == TS_OK)
+    st = run_passes(p, prec, op, param, buf, (const double2*)tabs, tab_off, out,
+                    dt == TS_R64 ? 1 : (dt == TS_C128 ? 2 : 3), s);
   scratch_free(w0, s);
   scratch_free(w1, s);
   scratch_free(tabs, s);
+  return st;
+}
+
+ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
+                       int refinements, cudaStream_t s) {
+  TS_TRY(check_mixed(p, prec));
+  const int np = bf16_planes(prec);
+  const long long N = p->N;
+  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)np * N;
+  void *w0 = nullptr, *w1 = nullptr, *partial = nullptr;
+  TS_TRY(scratch_alloc(&w0, plane_bytes, s));
+  ts_status st = scratch_alloc(&w1, plane_bytes, s);
+  if (st == TS_OK) st = scratch_alloc(&partial, sizeof(double) * 2 * RED_BLOCKS, s);
+  __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
+  // u_0 = P b
+  if (st == TS_OK) st = split_input(np, TS_R64, b, buf[0], N, s);
+  if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, u, 1, s);
+  // u_{k+1} = u_k + P (b - A u_k), residual in FP64, split straight into the planes
+  for (int it = 0; it < refinements && st == TS_OK; ++it) {
+    st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
+    if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, u, 4, s);
+  }
+  scratch_free(w0, s);
+  scratch_free(w1, s);
+  scratch_free(partial, s);
   return st;
 }
 

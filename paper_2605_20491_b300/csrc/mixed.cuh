@@ -14,6 +14,11 @@ int bf16_planes(ts_precision prec);
 ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
                       ts_dtype dt, cudaStream_t s);
 
+// Mixed-precision iterative refinement of the direct solve: u_0 = P b,
+// u_{k+1} = u_k + P (b - A u_k), P the split-precision inverse, residuals in FP64.
+ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
+                       int refinements, cudaStream_t s);
+
 // Reads (and optionally clears) the flag that bounded device-side waits of the
 // tensor-core kernels set when they time out.  Synchronises s.
 ts_status mixed_error_flag(int* host_flag, bool reset, cudaStream_t s);

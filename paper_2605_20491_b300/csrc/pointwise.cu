@@ -9,6 +9,7 @@
 // fixed order, then one CTA sums the partials in a fixed order).
 #include "common.cuh"
 #include "pointwise.cuh"
+#include "split.cuh"
 
 namespace ts {
 
@@ -109,41 +110,77 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;  // valid in thread 0
 }
 
-// y = (A + V2 + sigma) x (mode 0), or y = b - (A + V2 + sigma) x (mode 1), with the
-// 2d+1 point stencil; partial[blk*2 + 0] = sum of x.y (mode 0) or y.y (mode 1),
-// partial[blk*2 + 1] = b.b (mode 1) or 0.
-template <int MODE>
-__global__ void k_stencil(AxisParams a, const double* __restrict__ V2, double sigma,
-                          const double* __restrict__ x, const double* __restrict__ b,
-                          double* __restrict__ y, long long N, double* partial) {
+// The 2d+1 point operator of eq. general_system, A x = sum_k h_k^-2 (2x - x_{-e_k} - x_{+e_k})
+// + (sigma + V1 + V2) x with zero Dirichlet ghosts, in three forms:
+//   MODE 0: y = A x;                      partial sums of x.y
+//   MODE 1: y = b - A x;                  partial sums of y.y and b.b
+//   MODE 2: planes = split(b - A x);      partial sums of (b - A x)^2 and b.b
+// Work is mapped by grid rows (all axes but the first): a group of G lanes (G = n_1
+// rounded up to a power of two, at most 32) walks one row with unit stride, so the
+// multi-index of the row is decomposed once per row and every load is coalesced.
+template <int MODE, int NP>
+__global__ void k_stencil(AxisParams a, const double* __restrict__ V2, double sigma, const double* __restrict__ x,
+                          const double* __restrict__ b, double* __restrict__ y, __nv_bfloat16* __restrict__ planes,
+                          long long N, double* partial) {
+  // FP64 instructions are the scarce resource on this GPU (about two per clock per SM),
+  // so the operator is evaluated as  A x = diag x - sum_k h_k^-2 (x_{-e_k} + x_{+e_k})
+  // with diag = sigma + V1 + V2 + 2 sum_k h_k^-2 (the row part summed once per row):
+  // about 2 FP64 instructions per axis and element.
+  const int n0 = a.n[0];
+  int G = 1;
+  while (G < n0 && G < 32) G <<= 1;
+  const int rows_per_warp = 32 / G;
+  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
+  const long long R = N / n0;
+  const long long warps_total = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const double c0 = a.ih2[0];
   double acc0 = 0.0, acc1 = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-       idx += (long long)gridDim.x * blockDim.x) {
-    double xc = x[idx];
-    double v = sigma + (V2 ? V2[idx] : 0.0);
-    double lap = 0.0;
-    long long r = idx;
-    for (int k = 0; k < a.d; ++k) {
-      long long q = r / a.n[k];
-      int i = (int)(r - q * a.n[k]);
-      r = q;
-      double left = i > 0 ? x[idx - a.stride[k]] : 0.0;
-      double right = i + 1 < a.n[k] ? x[idx + a.stride[k]] : 0.0;
-      lap += a.ih2[k] * (2.0 * xc - left - right);
-      v += a.tab[k][i];
+  for (long long rb = wid * rows_per_warp; rb < R; rb += warps_total * rows_per_warp) {
+    const long long row = rb + sub;
+    if (row >= R) continue;
+    long long q = row;
+    double drow = sigma + 2.0 * c0;
+    unsigned lo_mask = 0, hi_mask = 0;
+    for (int k = 1; k < a.d; ++k) {
+      long long qq = q / a.n[k];
+      int i = (int)(q - qq * a.n[k]);
+      q = qq;
+      drow += a.tab[k][i] + 2.0 * a.ih2[k];
+      if (i == 0) lo_mask |= 1u << k;
+      if (i == a.n[k] - 1) hi_mask |= 1u << k;
     }
-    double ax = lap + v * xc;
-    if (MODE == 0) {
-      y[idx] = ax;
-      acc0 += xc * ax;
-    } else {
-      double bi = b[idx];
-      double ri = bi - ax;
-      y[idx] = ri;
-      acc0 += ri * ri;
-      acc1 += bi * bi;
+    const long long base = row * n0;
+    for (int i0 = gl; i0 < n0; i0 += G) {
+      const long long idx = base + i0;
+      const double xc = x[idx];
+      double diag = drow + a.tab[0][i0];
+      if (V2) diag += V2[idx];
+      const double l0 = i0 > 0 ? x[idx - 1] : 0.0;
+      const double r0 = i0 + 1 < n0 ? x[idx + 1] : 0.0;
+      // MODE 0: acc = A x;  MODE 1, 2: acc = b - A x
+      double acc = MODE == 0 ? diag * xc : fma(-diag, xc, b[idx]);
+      const double sgn = MODE == 0 ? -1.0 : 1.0;
+      acc = fma(sgn * c0, l0 + r0, acc);
+      for (int k = 1; k < a.d; ++k) {
+        const double left = ((lo_mask >> k) & 1u) ? 0.0 : x[idx - a.stride[k]];
+        const double right = ((hi_mask >> k) & 1u) ? 0.0 : x[idx + a.stride[k]];
+        acc = fma(sgn * a.ih2[k], left + right, acc);
+      }
+      if (MODE == 0) {
+        y[idx] = acc;
+        acc0 = fma(xc, acc, acc0);
+      } else if (MODE == 1) {
+        y[idx] = acc;
+        const double bi = b[idx];
+        acc0 = fma(acc, acc, acc0);
+        acc1 = fma(bi, bi, acc1);
+      } else {
+        split_store<NP>((float)acc, planes, N, idx);
+      }
     }
   }
+  if (MODE == 2) return;  // the refinement needs no norms
   double s0 = block_sum(acc0);
   double s1 = block_sum(acc1);
   if (threadIdx.x == 0) {
@@ -294,7 +331,7 @@ ts_status convert_c128_to_c64(long long N, const double* in, float* out, cudaStr
 ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
                         double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  k_stencil<0><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, nullptr, y, p->N, partial);
+  k_stencil<0, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, nullptr, y, nullptr, p->N, partial);
   TS_LAUNCHED(1);
   if (out2) {
     k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
@@ -306,9 +343,20 @@ ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const 
 ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, const double* x, const double* b,
                            double* r, double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  k_stencil<1><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, r, p->N, partial);
+  k_stencil<1, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, r, nullptr, p->N, partial);
   TS_LAUNCHED(1);
   k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
+ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigma, const double* x,
+                                 const double* b, __nv_bfloat16* planes, int np, double* partial, cudaStream_t s) {
+  unsigned g = grid_for(p->N);
+  if (np == 2)
+    k_stencil<2, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
+  else
+    k_stencil<2, 3><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
   TS_LAUNCHED(1);
   return TS_OK;
 }

@@ -15,6 +15,9 @@ ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const 
 // r = b - (A + V2 + sigma) x; out2[0] = r.r, out2[1] = b.b.
 ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, const double* x, const double* b,
                            double* r, double* partial, double* out2, cudaStream_t s);
+// planes (np bf16 planes of N values) = split(b - (A + V2 + sigma) x); partial sums only.
+ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigma, const double* x,
+                                 const double* b, __nv_bfloat16* planes, int np, double* partial, cudaStream_t s);
 // out2[0] = a.b (b == NULL: sum of a), out2[1] = c.d (c, d may be NULL).
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s);

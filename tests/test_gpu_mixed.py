@@ -76,3 +76,27 @@ def test_mixed_rejects_unsupported(T):
     with pytest.raises(T.TsError) as e:
         T.ts_apply_inverse(P2, 1.0, b[:256], b[:256], T.TS_BF16X3)
     assert e.value.status == T.TS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n", [(64, 64, 64), (128, 96, 40), (40, 24, 8), (16, 16, 16, 16)])
+def test_refined_solve_reaches_fp64_accuracy(T, n):
+    """Two refinements of the BF16X3 inverse reach FP64 rounding (< 1e-12 vs the oracle);
+    zero refinements is the single split-precision apply."""
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)
+    b = S.normal(2, Po.N)
+    want = O.apply_inverse(Po, 0.5, b)
+    bt = dev(b)
+    errs = []
+    for k in (0, 1, 2):
+        u = dev(np.zeros(Po.N))
+        T.ts_solve_refined(P, 0.5, bt, u, T.TS_BF16X3, k)
+        errs.append(rel(host(u), want))
+    assert errs[0] < TOL[1]
+    assert errs[1] < 1e-8
+    assert errs[2] < 1e-12, errs
+    u1 = dev(np.zeros(Po.N))
+    T.ts_apply_inverse(P, 0.5, bt, u1, T.TS_BF16X3)
+    u0 = dev(np.zeros(Po.N))
+    T.ts_solve_refined(P, 0.5, bt, u0, T.TS_BF16X3, 0)
+    assert np.array_equal(host(u0), host(u1))
