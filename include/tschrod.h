@@ -112,6 +112,24 @@ ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, d
                            ts_precision prec, void* stream);
 
 /*
+ * ts_apply_inverse without any device allocation (the paper has no counterpart: this is
+ * a library service).  For callers that must not allocate device memory while they run,
+ * e.g. an application that gives the whole device to its own allocator at start-up, or
+ * a latency-critical loop that cannot pay for cudaMalloc/cudaFree (cudaFree synchronises
+ * the device) or for growing a memory pool.  Same arguments and result as
+ * ts_apply_inverse (prec TS_FP64, TS_BF16X3 or TS_BF16X6; b and u may alias); the two
+ * intermediate buffers come from a fixed 32 MiB array inside the library, which every GPU
+ * that loads the library holds until the process exits.  Limit: 2 * N * 8 bytes (TS_FP64),
+ * 2 * N * 4 (TS_BF16X3) or 2 * N * 6 (TS_BF16X6) must fit in 32 MiB, i.e. N <= 2,097,152,
+ * 4,194,304 or 2,796,202; larger N returns TS_ERR_INVALID_ARG with the limit in the message.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it.  All calls share the array and it keeps the last call's contents; calls
+ * that overlap on the GPU (other streams or threads) race on it, so serialise them.
+ */
+ts_status ts_apply_inverse_noalloc(const ts_plan* plan, double sigma, const double* b, double* u,
+                                   ts_precision prec, void* stream);
+
+/*
  * The direct solve of ts_apply_inverse carried to FP64 accuracy by mixed-precision
  * iterative refinement (the split-precision inverse as preconditioner of the Richardson
  * iteration, a special case of Sec. 3.2's PCG with V2 = 0):

@@ -643,6 +643,14 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
   return st;
 }
 
+ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
+                                __nv_bfloat16* w0, __nv_bfloat16* w1, cudaStream_t s) {
+  TS_TRY(check_mixed(p, prec));
+  __nv_bfloat16* buf[2] = {w0, w1};
+  TS_TRY(split_input(bf16_planes(prec), TS_R64, b, buf[0], p->N, s));
+  return run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, u, 1, s);
+}
+
 ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
                        int refinements, cudaStream_t s) {
   TS_TRY(check_mixed(p, prec));

@@ -14,6 +14,11 @@ int bf16_planes(ts_precision prec);
 ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
                       ts_dtype dt, cudaStream_t s);
 
+// Split-precision inverse apply with caller-provided plane buffers w0, w1 of
+// bf16_planes(prec) * N bf16 each (no allocation).
+ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
+                                __nv_bfloat16* w0, __nv_bfloat16* w1, cudaStream_t s);
+
 // Mixed-precision iterative refinement of the direct solve: u_0 = P b,
 // u_{k+1} = u_k + P (b - A u_k), P the split-precision inverse, residuals in FP64.
 ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,

@@ -28,7 +28,7 @@ TS_MAX_DIM = 12
 #: Every extern "C" symbol that include/tschrod.h declares.
 EXPORTS = [
     "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
-    "ts_apply_inverse", "ts_solve_refined", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
+    "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
     "ts_tc_config_set", "ts_device_status", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
     "ts_last_error", "ts_version",
 ]
@@ -66,6 +66,7 @@ def lib() -> C.CDLL:
     L.ts_apply_inverse.argtypes = [vp, dp, vp, vp, ip, vp]
     L.ts_apply_exp.argtypes = [vp, dp, vp, vp, ip, ip, vp]
     L.ts_solve_refined.argtypes = [vp, dp, vp, vp, ip, ip, vp]
+    L.ts_apply_inverse_noalloc.argtypes = [vp, dp, vp, vp, ip, vp]
     L.ts_apply_operator.argtypes = [vp, dp, vp, vp, vp, vp]
     L.ts_pcg.argtypes = [vp, dp, dp, vp, vp, vp, dp, ip, ip, C.POINTER(ip), C.POINTER(dp), vp]
     L.ts_inverse_iteration.argtypes = [vp, dp, vp, vp, ip, dp, ip, dp, ip, ip, C.POINTER(dp), C.POINTER(ip),
@@ -176,6 +177,13 @@ def ts_plan_bytes(plan: Plan) -> int:
 
 def ts_apply_inverse(plan: Plan, sigma: float, b, u, prec: int = TS_FP64, stream=None):
     _check(lib().ts_apply_inverse(plan.handle, sigma, _ptr(b), _ptr(u), prec, _stream(stream)), "ts_apply_inverse")
+
+
+def ts_apply_inverse_noalloc(plan: Plan, sigma: float, b, u, prec: int = TS_FP64, stream=None):
+    """ts_apply_inverse with its work buffers in a fixed 32 MiB array inside the library,
+    for callers that must not allocate device memory (see include/tschrod.h)."""
+    _check(lib().ts_apply_inverse_noalloc(plan.handle, sigma, _ptr(b), _ptr(u), prec, _stream(stream)),
+           "ts_apply_inverse_noalloc")
 
 
 def ts_solve_refined(plan: Plan, sigma: float, b, u, prec: int = TS_BF16X3, refinements: int = 2, stream=None):
