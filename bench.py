@@ -166,6 +166,23 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """Small fixed case for profiler captures (a few GB on the device): the refined solve
+    of the n = 512 workload only, warmup + steps times, nothing else."""
+    import torch
+    from paper_2605_20491_b300 import tschrod as T
+    w = synth.WORKLOADS[WORKLOAD]
+    P = T.ts_plan_create(w["n"], w["L"], synth.harmonic(w["n"], w["L"], w["omega"]), (1 << T.TS_BF16X3))
+    b = torch.from_numpy(synth.normal(w["seed"], P.N)).cuda()
+    x = torch.empty_like(b)
+    for _ in range(args.warmup + args.steps):
+        T.ts_solve_refined(P, w["sigma"], b, x, T.TS_BF16X3, REFINEMENTS)
+    torch.cuda.synchronize()
+    T.ts_device_status()
+    print("profile case done", flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2605_20491_b300 import tschrod as T
@@ -333,7 +350,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run only the refined solve (for ncu captures); prints no JSON line")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

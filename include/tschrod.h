@@ -210,6 +210,81 @@ ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double
  */
 ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap);
 
+/* ------------------------------------------------------------------ serving ----- */
+/*
+ * Continuous-batching request server (no counterpart in the paper; it serves the paper's
+ * three operations to many independent callers).  A scheduler thread admits queued
+ * requests while fewer than max_inflight are on the GPU and their scratch fits
+ * memory_budget_bytes, looks each grid's plan up in a cache keyed by (n_k, L_k, f_k)
+ * (building it on a miss), captures every round of admitted inverse / exp requests into
+ * one CUDA graph with one stream per request (their kernels overlap), and runs PCG
+ * requests (which read one scalar back per iteration) on pooled host threads with their
+ * own streams.  Results are bitwise the same alone and in a mix.  in / out / V2 are
+ * caller-owned device arrays that must stay valid until ts_server_wait returns.
+ */
+typedef enum { TS_REQ_INVERSE = 0, TS_REQ_EXP = 1, TS_REQ_PCG = 2 } ts_request_kind;
+
+typedef struct {
+  int kind;            /* ts_request_kind                                                 */
+  ts_plan_desc grid;   /* grid and V1 samples (host memory, copied at submit)             */
+  double sigma;        /* inverse: shift; PCG: shift of the system and of P (sigma_P)     */
+  double tau;          /* exp: time                                                       */
+  const double* V2;    /* PCG: N doubles on the device, or NULL                           */
+  double tol;          /* PCG: relative residual tolerance                                */
+  int maxit;           /* PCG: iteration cap                                              */
+  const void* in;      /* device: b (inverse, PCG) or psi_in (exp)                        */
+  void* out;           /* device: u, x (PCG; initial guess on entry) or psi_out           */
+  ts_dtype dtype;      /* TS_R64 for inverse / PCG; TS_C128 or TS_C64 for exp             */
+  ts_precision prec;   /* contraction precision (PCG: of the preconditioner)              */
+} ts_request;
+
+typedef struct {
+  long long memory_budget_bytes; /* scratch budget (<= 0: half the free device memory)   */
+  int max_inflight;              /* requests on the GPU at once (<= 0: 8)                */
+  int max_batch;                 /* requests per captured graph (<= 0: max_inflight)     */
+  int plan_cache_entries;        /* cached plans (<= 0: 64)                              */
+} ts_server_config;
+
+typedef struct {
+  long long completed;
+  double p50_ms, p99_ms, max_ms;   /* latency from submit to completion                 */
+  double makespan_ms;              /* first submit to last completion                   */
+  double gdofs;                    /* sum of N over completed requests / makespan       */
+  long long plan_hits, plan_misses;
+  long long batches, graph_requests;
+  long long peak_scratch_bytes;
+} ts_serving_stats;
+
+typedef struct ts_server ts_server;
+
+/* Start a server on the current device. */
+ts_status ts_server_create(const ts_server_config* cfg, ts_server** out);
+/* Queue a request; *ticket identifies it.  Non-blocking. */
+ts_status ts_server_submit(ts_server* server, const ts_request* req, long long* ticket);
+/* Block until the request finishes; *result = its status (the message is in
+ * ts_last_error), *latency_ms, *iterations (PCG).  Each ticket may be waited once. */
+ts_status ts_server_wait(ts_server* server, long long ticket, ts_status* result, double* latency_ms,
+                         int* iterations);
+/* Block until every submitted request has finished. */
+ts_status ts_server_drain(ts_server* server);
+/* Latency percentiles, throughput, plan-cache and batching counters since the last reset. */
+ts_status ts_server_stats(ts_server* server, ts_serving_stats* stats);
+ts_status ts_server_reset_stats(ts_server* server);
+/* Finish all queued work, then free the server, its streams and its cached plans. */
+ts_status ts_server_destroy(ts_server* server);
+
+/*
+ * Autotuner of the split-precision contraction (no counterpart in the paper).  For every
+ * distinct axis length n of the plan and the data kind (dtype TS_R64: real data of
+ * ts_apply_inverse; TS_C128: complex data of ts_apply_exp) it times the tile
+ * configurations (K chunk 64 / 32, N-tile cap 256 / 128 / 64) on whole applies with CUDA
+ * events on `stream`, keeps the fastest with ts_tc_config_set, and appends it to the text
+ * file cache_path (NULL or "" = no file).  Entries already in the file are applied without
+ * timing.  *tuned (may be NULL) = number of axis lengths searched.  Synchronises stream.
+ */
+ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precision prec, const char* cache_path,
+                      int* tuned, void* stream);
+
 /*
  * Runtime instrumentation (no counterpart in the paper).
  * ts_launch_count: number of CUDA kernels the library has launched in this process.

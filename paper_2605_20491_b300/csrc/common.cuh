@@ -83,6 +83,7 @@ struct ts_plan {
   double* S[TS_MAX_DIM] = {};
   double* St[TS_MAX_DIM] = {};
   double* lam[TS_MAX_DIM] = {};
+  float* lamf[TS_MAX_DIM] = {};  // lambda_k rounded to FP32 (epilogue tables)
   double* f[TS_MAX_DIM] = {};
   // Split bf16 planes (device), [prec][axis] -> [plane][n][n]: row-major copies of
   // S^T (forward operand, "Bf") and S (backward operand, "Bb"), so that the contracted

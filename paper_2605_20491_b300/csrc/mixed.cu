@@ -71,8 +71,8 @@ struct EpiParams {
   int rn[MAXD];               // their sizes, fastest first
   const double* rlam[MAXD];   // their eigenvalues (scale_mode 1)
   const double2* rph[MAXD];   // their phase tables (scale_mode 2)
-  const double* clam;         // eigenvalues of the contracted axis
-  const double2* cph;         // phase table of the contracted axis
+  const float* clam;          // eigenvalues of the contracted axis (FP32)
+  const float2* cph;          // phase table of the contracted axis (FP32)
 };
 
 template <int NP>
@@ -94,16 +94,17 @@ struct Products<3> {
 constexpr int EPI_WARPS = 8;                   // two warps per TMEM lane quarter
 constexpr int TC_THREADS = 32 * (2 + EPI_WARPS);
 
-// Exact float -> double conversion with integer instructions (sign, exponent rebias
-// +896, mantissa shift by 29): FP64-pipe conversions are scarce on this GPU.  Zero,
-// subnormal, infinite and NaN inputs take the ordinary conversion.
+// float -> double with integer instructions only (sign, exponent rebias +896, mantissa
+// shift by 29): every FP64-pipe instruction is scarce on this GPU.  Exact for normal
+// numbers; zero stays a signed zero, infinities and NaNs map to infinities and NaNs, and
+// FP32 subnormals (below 1.2e-38) are flushed to zero.
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (double)f;
-  const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                  ((unsigned long long)(e + 896u) << 52) |
-                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu);
+  const unsigned long long e64 = e == 0u ? 0ull : (e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u));
+  const unsigned long long bits =
+      ((unsigned long long)(u & 0x80000000u) << 32) | (e64 << 52) | (e == 0u ? 0ull : (m << 29));
   return __longlong_as_double((long long)bits);
 }
 
@@ -267,10 +268,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
           if (ep.scale_mode == 1) {
-            val[0] = val[0] * (1.0f / (rowsum + (float)ep.clam[j]));
+            val[0] = val[0] * (1.0f / (rowsum + ep.clam[j]));
           } else if (ep.scale_mode == 2 && NACC == 2) {
-            const double2 cp = ep.cph[j];
-            const float cx = (float)cp.x, cy = (float)cp.y;
+            const float2 cp = ep.cph[j];
+            const float cx = cp.x, cy = cp.y;
             const float phx = rowph.x * cx - rowph.y * cy;
             const float phy = rowph.x * cy + rowph.y * cx;
             const float re = val[0] * phx - val[NACC - 1] * phy;
@@ -345,13 +346,15 @@ __global__ void k_split_table(const double* src, __nv_bfloat16* dst, long long c
   }
 }
 
-// ph[i] = e^{-i tau lambda_i} = (cos(tau lambda_i), -sin(tau lambda_i)), FP64.
-__global__ void k_phase_table(const double* lam, double tau, double2* ph, int n) {
+// ph[i] = e^{-i tau lambda_i} = (cos(tau lambda_i), -sin(tau lambda_i)) in FP64, and the
+// same rounded to FP32 in phf (the per-element column factor of the epilogue).
+__global__ void k_phase_table(const double* lam, double tau, double2* ph, float2* phf, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     double s, c;
     sincos(tau * lam[i], &s, &c);
     ph[i] = make_double2(c, -s);
+    phf[i] = make_float2((float)c, (float)-s);
   }
 }
 
@@ -558,7 +561,8 @@ ts_status check_mixed(const ts_plan* p, ts_precision prec) {
 // last pass: 1 FP64 store, 2 complex128, 3 complex64, 4 FP64 accumulate), with the
 // pointwise step fused into pass d-1.
 ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double param, __nv_bfloat16* const buf[2],
-                     const double2* tabs, const int* tab_off, void* out, int last_mode, cudaStream_t s) {
+                     const double2* tabs, const float2* tabsf, const int* tab_off, void* out, int last_mode,
+                     cudaStream_t s) {
   const int np = bf16_planes(prec);
   const int nc = op == MixedOp::Exp ? 2 : 1;
   const int d = p->d;
@@ -580,8 +584,8 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
         ep.rlam[q] = p->lam[q];
         ep.rph[q] = tabs ? tabs + tab_off[q] : nullptr;
       }
-      ep.clam = p->lam[k];
-      ep.cph = tabs ? tabs + tab_off[k] : nullptr;
+      ep.clam = p->lamf[k];
+      ep.cph = tabsf ? tabsf + tab_off[k] : nullptr;
     }
     const __nv_bfloat16* B = fwd ? p->Bf[prec][k] : p->Bb[prec][k];
     st = pass(np, nc, buf[t & 1], B, p->N / p->n[k], p->n[k], ep, s);
@@ -616,15 +620,18 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
   TS_TRY(scratch_alloc(&w0, plane_bytes, s));
   ts_status st = scratch_alloc(&w1, plane_bytes, s);
   int tab_off[MAXD] = {};
+  int tab_total = 0;
   if (st == TS_OK && op == MixedOp::Exp) {
     int tot = 0;
     for (int k = 0; k < p->d; ++k) {
       tab_off[k] = tot;
       tot += p->n[k];
     }
-    st = scratch_alloc(&tabs, sizeof(double2) * tot, s);
+    tab_total = tot;
+    st = scratch_alloc(&tabs, (sizeof(double2) + sizeof(float2)) * tot, s);
     for (int k = 0; k < p->d && st == TS_OK; ++k) {
-      k_phase_table<<<(p->n[k] + 127) / 128, 128, 0, s>>>(p->lam[k], param, (double2*)tabs + tab_off[k], p->n[k]);
+      k_phase_table<<<(p->n[k] + 127) / 128, 128, 0, s>>>(p->lam[k], param, (double2*)tabs + tab_off[k],
+                                                          (float2*)((double2*)tabs + tot) + tab_off[k], p->n[k]);
       count_launches(1);
       if (cudaGetLastError() != cudaSuccess) {
         set_error("phase table launch failed");
@@ -635,7 +642,8 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
   __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
   if (st == TS_OK) st = split_input(np, dt, in, buf[0], N, s);
   if (st == TS_OK)
-    st = run_passes(p, prec, op, param, buf, (const double2*)tabs, tab_off, out,
+    st = run_passes(p, prec, op, param, buf, (const double2*)tabs,
+                    tabs ? (const float2*)((const double2*)tabs + tab_total) : nullptr, tab_off, out,
                     dt == TS_R64 ? 1 : (dt == TS_C128 ? 2 : 3), s);
   scratch_free(w0, s);
   scratch_free(w1, s);
@@ -648,7 +656,7 @@ ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigm
   TS_TRY(check_mixed(p, prec));
   __nv_bfloat16* buf[2] = {w0, w1};
   TS_TRY(split_input(bf16_planes(prec), TS_R64, b, buf[0], p->N, s));
-  return run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, u, 1, s);
+  return run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s);
 }
 
 ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
@@ -664,16 +672,34 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
   __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
   // u_0 = P b
   if (st == TS_OK) st = split_input(np, TS_R64, b, buf[0], N, s);
-  if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, u, 1, s);
+  if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s);
   // u_{k+1} = u_k + P (b - A u_k), residual in FP64, split straight into the planes
   for (int it = 0; it < refinements && st == TS_OK; ++it) {
     st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
-    if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, u, 4, s);
+    if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 4, s);
   }
   scratch_free(w0, s);
   scratch_free(w1, s);
   scratch_free(partial, s);
   return st;
+}
+
+ts_status tc_prepare_kernels() {
+  // Shared-memory opt-in for every instantiation, outside any stream capture.
+#define TS_PREP(NP, NACC, BKT, PO)                                                                           \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     SMEM_LIMIT))
+  TS_PREP(2, 1, 64, true); TS_PREP(2, 1, 64, false); TS_PREP(2, 1, 32, true); TS_PREP(2, 1, 32, false);
+  TS_PREP(2, 2, 64, true); TS_PREP(2, 2, 64, false); TS_PREP(2, 2, 32, true); TS_PREP(2, 2, 32, false);
+  TS_PREP(3, 1, 64, true); TS_PREP(3, 1, 64, false); TS_PREP(3, 1, 32, true); TS_PREP(3, 1, 32, false);
+  TS_PREP(3, 2, 64, true); TS_PREP(3, 2, 64, false); TS_PREP(3, 2, 32, true); TS_PREP(3, 2, 32, false);
+#undef TS_PREP
+  if (g_num_sms == 0) {
+    int dev = 0;
+    TS_CHECK_CUDA(cudaGetDevice(&dev));
+    TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return TS_OK;
 }
 
 ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap) {

@@ -28,6 +28,10 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
 // tensor-core kernels set when they time out.  Synchronises s.
 ts_status mixed_error_flag(int* host_flag, bool reset, cudaStream_t s);
 
+// Opt every tensor-core kernel instantiation into its shared-memory size (call before
+// capturing launches into a graph).
+ts_status tc_prepare_kernels();
+
 // Tile configuration of the tensor-core pass for data of the given kind and contracted
 // extent n (n = 0: default for every n): K chunk bk (64 or 32) and N-tile cap bn_cap.
 ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap);

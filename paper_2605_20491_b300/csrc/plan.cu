@@ -94,6 +94,7 @@ void plan_free(ts_plan* p) {
     cudaFree(p->S[k]);
     cudaFree(p->St[k]);
     cudaFree(p->lam[k]);
+    cudaFree(p->lamf[k]);
     for (int q = 0; q < NPREC; ++q) {
       cudaFree(p->Bf[q][k]);
       cudaFree(p->Bb[q][k]);
@@ -132,6 +133,7 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
       p->S[k] = p->S[same];
       p->St[k] = p->St[same];
       p->lam[k] = p->lam[same];
+      p->lamf[k] = p->lamf[same];
       p->lam_host[k] = p->lam_host[same];
       p->S_host[k] = p->S_host[same];
       continue;
@@ -156,6 +158,8 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
     st = upload(&p->S[k], S.data(), S.size(), p, s);
     if (st == TS_OK) st = upload(&p->St[k], Qcol.data(), Qcol.size(), p, s);
     if (st == TS_OK) st = upload(&p->lam[k], p->lam_host[k].data(), (size_t)n, p, s);
+    std::vector<float> lf(p->lam_host[k].begin(), p->lam_host[k].end());
+    if (st == TS_OK) st = upload(&p->lamf[k], lf.data(), (size_t)n, p, s);
     if (st == TS_OK) {
       cudaError_t e = cudaStreamSynchronize(s);  // host vectors go out of scope
       if (e != cudaSuccess) {

@@ -176,3 +176,30 @@ WORKLOADS = {
     "6d_n24_strang": dict(d=6, n=(24,) * 6, L=(5.0,) * 6, omega=(1.0,) * 6, dt=0.01, steps=100),
     "9d_n8_strang": dict(d=9, n=(8,) * 9, L=(3.0,) * 9, omega=(1.0,) * 9, dt=0.01, steps=100),
 }
+
+
+def serving_requests(count: int, seed: int = 4, sizes=(32, 48, 64, 96, 128), omega_set=None,
+                     mix=(0.3, 0.5, 0.2)):
+    """Request descriptors of the serving workload: per request, n_k i.i.d. from `sizes` per
+    axis (3D), L = 8, sigma ~ U[0.5, 5), omega_k ~ U[0.5, 2) (or drawn from omega_set),
+    kind PCG / inverse / exp with probabilities `mix`, tau = 0.01, right-hand side seed
+    1000 + id.  Draws come from SplitMix64(seed) in a fixed order per request."""
+    out = []
+    k = 0
+    def u(lo=0.0, hi=1.0):
+        nonlocal k
+        v = float(uniform(seed, 1, lo, hi, offset=k)[0])
+        k += 1
+        return v
+    for rid in range(count):
+        n = tuple(sizes[min(int(u() * len(sizes)), len(sizes) - 1)] for _ in range(3))
+        sigma = u(0.5, 5.0)
+        if omega_set:
+            omega = tuple(omega_set[min(int(u() * len(omega_set)), len(omega_set) - 1)] for _ in range(3))
+        else:
+            omega = tuple(u(0.5, 2.0) for _ in range(3))
+        r = u()
+        kind = "pcg" if r < mix[0] else ("inverse" if r < mix[0] + mix[1] else "exp")
+        out.append(dict(id=rid, kind=kind, n=n, L=(8.0, 8.0, 8.0), omega=omega, sigma=sigma, tau=0.01,
+                        rhs_seed=1000 + rid))
+    return out

@@ -29,7 +29,9 @@ TS_MAX_DIM = 12
 EXPORTS = [
     "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
     "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
-    "ts_tc_config_set", "ts_device_status", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
+    "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
+    "ts_server_reset_stats", "ts_server_destroy",
+    "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
     "ts_last_error", "ts_version",
 ]
 
@@ -44,6 +46,26 @@ class _Desc(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.POINTER(C.c_int)), ("L", C.POINTER(C.c_double)),
                 ("f", C.POINTER(C.POINTER(C.c_double))), ("bc", C.c_int)]
 
+
+class _Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("grid", _Desc), ("sigma", C.c_double), ("tau", C.c_double),
+                ("V2", C.c_void_p), ("tol", C.c_double), ("maxit", C.c_int), ("in_", C.c_void_p),
+                ("out", C.c_void_p), ("dtype", C.c_int), ("prec", C.c_int)]
+
+
+class _ServerConfig(C.Structure):
+    _fields_ = [("memory_budget_bytes", C.c_longlong), ("max_inflight", C.c_int), ("max_batch", C.c_int),
+                ("plan_cache_entries", C.c_int)]
+
+
+class _ServingStats(C.Structure):
+    _fields_ = [("completed", C.c_longlong), ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("makespan_ms", C.c_double), ("gdofs", C.c_double), ("plan_hits", C.c_longlong),
+                ("plan_misses", C.c_longlong), ("batches", C.c_longlong), ("graph_requests", C.c_longlong),
+                ("peak_scratch_bytes", C.c_longlong)]
+
+
+TS_REQ_INVERSE, TS_REQ_EXP, TS_REQ_PCG = range(3)
 
 _lib = None
 
@@ -73,7 +95,15 @@ def lib() -> C.CDLL:
                                        C.POINTER(C.c_longlong), vp]
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
     L.ts_device_status.argtypes = [vp]
+    L.ts_server_create.argtypes = [C.POINTER(_ServerConfig), C.POINTER(vp)]
+    L.ts_server_submit.argtypes = [vp, C.POINTER(_Request), C.POINTER(C.c_longlong)]
+    L.ts_server_wait.argtypes = [vp, C.c_longlong, C.POINTER(ip), C.POINTER(dp), C.POINTER(ip)]
+    L.ts_server_drain.argtypes = [vp]
+    L.ts_server_stats.argtypes = [vp, C.POINTER(_ServingStats)]
+    L.ts_server_reset_stats.argtypes = [vp]
+    L.ts_server_destroy.argtypes = [vp]
     L.ts_tc_config_set.argtypes = [ip, ip, ip, ip]
+    L.ts_autotune.argtypes = [vp, ip, ip, C.c_char_p, C.POINTER(ip), vp]
     L.ts_launch_count.argtypes = []
     L.ts_profile_begin.argtypes = []
     L.ts_profile_end.argtypes = [ip, C.POINTER(C.c_longlong), C.POINTER(dp), C.POINTER(dp), C.POINTER(dp)]
@@ -229,6 +259,14 @@ def ts_tc_config_set(complex_data: bool, n: int, bk: int, bn_cap: int):
     _check(lib().ts_tc_config_set(int(complex_data), n, bk, bn_cap), "ts_tc_config_set")
 
 
+def ts_autotune(plan: Plan, dtype: int, prec: int, cache_path: str | None = None, stream=None) -> int:
+    """Returns the number of axis lengths that were searched (0 = all from the cache)."""
+    tuned = C.c_int(0)
+    path = cache_path.encode() if cache_path else None
+    _check(lib().ts_autotune(plan.handle, dtype, prec, path, C.byref(tuned), _stream(stream)), "ts_autotune")
+    return tuned.value
+
+
 def ts_launch_count() -> int:
     return lib().ts_launch_count()
 
@@ -255,3 +293,60 @@ def ts_device_status(stream=None):
 def ts_split_step(plan: Plan, dt: float, nsteps: int, V2, psi, dtype: int, prec: int = TS_FP64, stream=None):
     _check(lib().ts_split_step(plan.handle, dt, nsteps, _ptr(V2), _ptr(psi), dtype, prec, _stream(stream)),
            "ts_split_step")
+
+
+class Server:
+    """Owning handle of a ts_server.  Keeps every submitted request's arguments alive until
+    it has been waited for."""
+
+    def __init__(self, memory_budget_bytes: int = 0, max_inflight: int = 8, max_batch: int = 0,
+                 plan_cache_entries: int = 64):
+        cfg = _ServerConfig(memory_budget_bytes, max_inflight, max_batch, plan_cache_entries)
+        h = C.c_void_p()
+        _check(lib().ts_server_create(C.byref(cfg), C.byref(h)), "ts_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, kind: int, n, L, f, inp, out, sigma: float = 0.0, tau: float = 0.0, V2=None, tol: float = 1e-10,
+               maxit: int = 200, dtype: int = TS_R64, prec: int = TS_FP64) -> int:
+        d = len(n)
+        f_arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in f]
+        n_arr = (C.c_int * d)(*[int(v) for v in n])
+        L_arr = (C.c_double * d)(*[float(v) for v in L])
+        f_ptrs = (C.POINTER(C.c_double) * d)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in f_arrs])
+        req = _Request(kind, _Desc(d, n_arr, L_arr, f_ptrs, 0), sigma, tau, _ptr(V2), tol, maxit, _ptr(inp),
+                       _ptr(out), dtype, prec)
+        ticket = C.c_longlong()
+        _check(lib().ts_server_submit(self.handle, C.byref(req), C.byref(ticket)), "ts_server_submit")
+        self._keep[ticket.value] = (inp, out, V2)
+        return ticket.value
+
+    def wait(self, ticket: int):
+        """Returns (status, latency_ms, iterations)."""
+        st, lat, it = C.c_int(), C.c_double(), C.c_int()
+        _check(lib().ts_server_wait(self.handle, ticket, C.byref(st), C.byref(lat), C.byref(it)), "ts_server_wait")
+        self._keep.pop(ticket, None)
+        return st.value, lat.value, it.value
+
+    def drain(self):
+        _check(lib().ts_server_drain(self.handle), "ts_server_drain")
+
+    def stats(self) -> dict:
+        s = _ServingStats()
+        _check(lib().ts_server_stats(self.handle, C.byref(s)), "ts_server_stats")
+        return {k: getattr(s, k) for k, _ in _ServingStats._fields_}
+
+    def reset_stats(self):
+        _check(lib().ts_server_reset_stats(self.handle), "ts_server_reset_stats")
+
+    def close(self):
+        if self.handle:
+            _check(lib().ts_server_destroy(self.handle), "ts_server_destroy")
+            self.handle = C.c_void_p(None)
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -100,3 +100,22 @@ def test_refined_solve_reaches_fp64_accuracy(T, n):
     u0 = dev(np.zeros(Po.N))
     T.ts_solve_refined(P, 0.5, bt, u0, T.TS_BF16X3, 0)
     assert np.array_equal(host(u0), host(u1))
+
+
+def test_autotune_cache_roundtrip(T, tmp_path):
+    """The autotuner searches each axis length once, writes the cache, and a second call
+    applies the cached choice without timing; results stay within tolerance."""
+    n = (64, 48, 64)
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)
+    cache = str(tmp_path / "tune.txt")
+    assert T.ts_autotune(P, T.TS_R64, T.TS_BF16X3, cache) == 2
+    lines = open(cache).read().split("\n")
+    assert len([x for x in lines if x.strip()]) == 2
+    assert T.ts_autotune(P, T.TS_R64, T.TS_BF16X3, cache) == 0
+    b = S.normal(2, Po.N)
+    u = dev(np.zeros(Po.N))
+    T.ts_apply_inverse(P, 0.5, dev(b), u, T.TS_BF16X3)
+    assert rel(host(u), O.apply_inverse(Po, 0.5, b)) < TOL[1]
+    T.ts_tc_config_set(False, 64, 64, 256)
+    T.ts_tc_config_set(False, 48, 64, 256)
