@@ -338,9 +338,10 @@ def run_ours(args):
     return 0
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture
-# summarised in profiles/; None until a capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture in
+# profiles/k_rot_tc_bf16x3_n512.md: 1.030e9 for a bf16-plane pass and 1.558e9 for an
+# FP64-output pass, weighted 15 : 3 as they occur in one refined solve.
+TRAFFIC_PER_LAUNCH = (15 * 1.030e9 + 3 * 1.558e9) / 18
 
 
 def main():

@@ -58,7 +58,9 @@ typedef enum {
   TS_BF16X3 = 1, /* 2-term bf16 splits of data and S_k, 3 products, FP32 accumulate (tcgen05) */
   TS_BF16X6 = 2, /* 3-term bf16 splits, 6 products, FP32 accumulate (tcgen05)              */
   TS_TF32X3 = 3, /* 2-term tf32 splits, 3 products (reserved)                              */
-  TS_FP16X3 = 4  /* 2-term fp16 splits with scaling (reserved)                             */
+  TS_FP16X3 = 4, /* 2-term fp16 splits with scaling (reserved)                            */
+  TS_FP32 = 5    /* plain FP32 (FFMA) fused small-n kernels: complex64 propagation with
+                    every n_k in {8, 16, 24, 32} (the paper's FP32 variant)              */
 } ts_precision;
 
 typedef enum { TS_R64 = 0, TS_C128 = 1, TS_C64 = 2 } ts_dtype;

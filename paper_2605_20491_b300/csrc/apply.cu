@@ -4,6 +4,7 @@
 #include "common.cuh"
 #include "mixed.cuh"
 #include "pointwise.cuh"
+#include "small_n.cuh"
 
 namespace ts {
 
@@ -71,12 +72,23 @@ ts_status fp64_pipeline(const ts_plan* p, const double* in, double* out, int nco
 
 ts_status apply_inverse_impl(const ts_plan* p, double sigma, const double* b, double* u, ts_precision prec,
                              cudaStream_t s) {
+  if (prec == TS_FP32) {
+    set_error("TS_FP32 is available for complex64 propagation only");
+    return TS_ERR_UNSUPPORTED;
+  }
   if (prec == TS_FP64) return fp64_pipeline(p, b, u, 1, 0, sigma, s);
   return mixed_apply(p, prec, MixedOp::Inverse, sigma, b, u, TS_R64, s);
 }
 
 ts_status apply_exp_impl(const ts_plan* p, double tau, const void* in, void* out, ts_dtype dt, ts_precision prec,
                          cudaStream_t s) {
+  if (prec == TS_FP32) {
+    if (dt != TS_C64) {
+      set_error("TS_FP32 propagation works on complex64 data");
+      return TS_ERR_UNSUPPORTED;
+    }
+    return small_n_propagate(p, tau, (const float2*)in, (float2*)out, nullptr, tau, 1, s);
+  }
   if (prec != TS_FP64) return mixed_apply(p, prec, MixedOp::Exp, tau, in, out, dt, s);
   if (dt == TS_C128) return fp64_pipeline(p, (const double*)in, (double*)out, 2, 1, tau, s);
   // complex64 data, FP64 arithmetic: widen, apply, narrow.

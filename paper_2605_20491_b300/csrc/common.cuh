@@ -12,7 +12,7 @@
 namespace ts {
 
 constexpr int MAXD = TS_MAX_DIM;
-constexpr int NPREC = 5;
+constexpr int NPREC = 6;
 constexpr int MAX_PLANES = 3;
 
 // Thread-local error message of the last failing call.
@@ -84,6 +84,8 @@ struct ts_plan {
   double* St[TS_MAX_DIM] = {};
   double* lam[TS_MAX_DIM] = {};
   float* lamf[TS_MAX_DIM] = {};  // lambda_k rounded to FP32 (epilogue tables)
+  float* Sf32[TS_MAX_DIM] = {};   // S_k and S_k^T rounded to FP32 (TS_FP32 small-n path)
+  float* Stf32[TS_MAX_DIM] = {};
   double* f[TS_MAX_DIM] = {};
   // Split bf16 planes (device), [prec][axis] -> [plane][n][n]: row-major copies of
   // S^T (forward operand, "Bf") and S (backward operand, "Bb"), so that the contracted

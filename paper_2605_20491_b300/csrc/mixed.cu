@@ -260,6 +260,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int jbase = n0 + col0;
         const int jn = ep.n - jbase < 16 ? ep.n - jbase : 16;
         long long idx = r + ep.R * (long long)jbase;
+        double prev[16];
+        if (!PLANES_OUT && ep.out_mode == 4) {
+          // u += delta: issue all 16 loads of the chunk before any store, so they overlap
+          const double* uo = reinterpret_cast<const double*>(ep.out);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) prev[i] = i < jn ? uo[idx + ep.R * (long long)i] : 0.0;
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i, idx += ep.R) {
           if (i >= jn) break;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           } else if (ep.out_mode == 1) {
             reinterpret_cast<double*>(ep.out)[idx] = f2d(val[0]);
           } else if (ep.out_mode == 4) {
-            reinterpret_cast<double*>(ep.out)[idx] += f2d(val[0]);
+            reinterpret_cast<double*>(ep.out)[idx] = prev[i] + f2d(val[0]);
           } else if (ep.out_mode == 2) {
             reinterpret_cast<double2*>(ep.out)[idx] = make_double2(f2d(val[0]), f2d(val[NACC - 1]));
           } else {

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "mixed.cuh"
+#include "small_n.cuh"
 
 namespace ts {
 
@@ -95,6 +96,8 @@ void plan_free(ts_plan* p) {
     cudaFree(p->St[k]);
     cudaFree(p->lam[k]);
     cudaFree(p->lamf[k]);
+    cudaFree(p->Sf32[k]);
+    cudaFree(p->Stf32[k]);
     for (int q = 0; q < NPREC; ++q) {
       cudaFree(p->Bf[q][k]);
       cudaFree(p->Bb[q][k]);
@@ -168,8 +171,10 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
       }
     }
   }
-  for (int q = 1; q < NPREC && st == TS_OK; ++q)
-    if (p->precision_mask & (1u << q)) st = build_split_tables(p, (ts_precision)q, s);
+  for (int q = 1; q < NPREC && st == TS_OK; ++q) {
+    if (!(p->precision_mask & (1u << q))) continue;
+    st = q == TS_FP32 ? build_small_tables(p, s) : build_split_tables(p, (ts_precision)q, s);
+  }
   if (st == TS_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

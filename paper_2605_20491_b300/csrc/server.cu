@@ -139,6 +139,9 @@ ts_status get_plan(ts_server* sv, Job& j) {
   desc.L = j.key.L.data();
   ts_plan* p = nullptr;
   unsigned mask = (1u << TS_BF16X3) | (1u << TS_BF16X6);
+  bool small = true;
+  for (int k = 0; k < j.req.grid.d; ++k) small &= j.key.n[k] == 8 || j.key.n[k] == 16 || j.key.n[k] == 24 || j.key.n[k] == 32;
+  if (small) mask |= 1u << TS_FP32;
   TS_TRY(ts_plan_create(&desc, mask, sv->capture_stream, &p));
   // Evict the least recently created plans beyond the cache size (none is in use: the
   // scheduler only evicts when nothing is in flight).

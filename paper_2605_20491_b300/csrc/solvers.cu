@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "mixed.cuh"
 #include "pointwise.cuh"
+#include "small_n.cuh"
 #include "solvers.cuh"
 
 namespace ts {
@@ -160,6 +161,13 @@ ts_status split_step_impl(const ts_plan* p, double dt, int nsteps, const double*
                           ts_precision prec, cudaStream_t s) {
   if (nsteps <= 0) return TS_OK;
   const long long N = p->N;
+  if (prec == TS_FP32) {
+    if (dtype != TS_C64) {
+      set_error("TS_FP32 split steps work on complex64 data");
+      return TS_ERR_UNSUPPORTED;
+    }
+    return small_n_propagate(p, dt, (const float2*)psi, (float2*)psi, V2, dt, nsteps, s);
+  }
   if (prec == TS_FP64 && dtype == TS_C64) {
     // FP64 arithmetic on complex64 data: widen once, run in complex128, narrow once.
     Scratch sc_mem(s);
