@@ -168,9 +168,20 @@ def run_reference(args):
 
 def run_profile_case(args):
     """Small fixed case for profiler captures (a few GB on the device): the refined solve
-    of the n = 512 workload only, warmup + steps times, nothing else."""
+    of the n = 512 workload only (or, with --workload 6d_n24_strang / 9d_n8_strang, the
+    complex64 FP32 Strang steps only), warmup + steps times, nothing else."""
     import torch
     from paper_2605_20491_b300 import tschrod as T
+    if args.workload in ("6d_n24_strang", "9d_n8_strang"):
+        w = synth.WORKLOADS[args.workload]
+        n, L = w["n"], w["L"]
+        P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << T.TS_FP32)
+        V2 = torch.from_numpy(synth.v2_soft_coulomb(n, L)).cuda()
+        x = torch.from_numpy(synth.sine_state(n, L).astype(np.float32)).cuda()
+        T.ts_split_step(P, w["dt"], args.warmup + args.steps, V2, x, T.TS_C64, T.TS_FP32)
+        torch.cuda.synchronize()
+        print("profile case done", flush=True)
+        return 0
     w = synth.WORKLOADS[WORKLOAD]
     P = T.ts_plan_create(w["n"], w["L"], synth.harmonic(w["n"], w["L"], w["omega"]), (1 << T.TS_BF16X3))
     b = torch.from_numpy(synth.normal(w["seed"], P.N)).cuda()
@@ -180,6 +191,128 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     T.ts_device_status()
     print("profile case done", flush=True)
+    return 0
+
+
+def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None):
+    """The serving workload: `count` requests (3D grids with n_k from {32, 48, 64, 96, 128},
+    30% PCG / 50% inverse / 20% exp), first submitted all at once (saturated throughput),
+    then again with Poisson arrivals at rate_factor x that throughput; returns the stats."""
+    import torch
+    prec = T.TS_BF16X3 if prec is None else prec
+    specs = synth.serving_requests(count, seed=seed, omega_set=omega_set)
+    reqs = []
+    for sp in specs:
+        n, L = sp["n"], sp["L"]
+        N = int(np.prod(n))
+        f = synth.harmonic(n, L, sp["omega"])
+        kw = dict(n=n, L=L, f=f, sigma=sp["sigma"], tau=sp["tau"], prec=prec)
+        if sp["kind"] == "exp":
+            kw.update(kind=T.TS_REQ_EXP, inp=torch.from_numpy(synth.complex_normal(sp["rhs_seed"], N)).cuda(),
+                      out=torch.empty(2 * N, dtype=torch.float64, device="cuda"), dtype=T.TS_C128)
+        else:
+            kw.update(inp=torch.from_numpy(synth.normal(sp["rhs_seed"], N)).cuda(),
+                      out=torch.zeros(N, dtype=torch.float64, device="cuda"), dtype=T.TS_R64)
+            if sp["kind"] == "pcg":
+                kw.update(kind=T.TS_REQ_PCG, V2=torch.from_numpy(synth.v2_cos_bumps(n, L, seed=1)).cuda(),
+                          tol=1e-10, maxit=200)
+            else:
+                kw.update(kind=T.TS_REQ_INVERSE)
+        reqs.append(kw)
+    torch.cuda.synchronize()
+    server = T.Server(max_inflight=16)
+    out = {}
+    for phase in ("saturated", "poisson"):
+        for kw in reqs:
+            if kw["kind"] == T.TS_REQ_PCG:
+                kw["out"].zero_()
+        torch.cuda.synchronize()
+        server.reset_stats()
+        if phase == "saturated":
+            tickets = [server.submit(**kw) for kw in reqs]
+        else:
+            rate = rate_factor * out["saturated"]["completed"] / (out["saturated"]["makespan_ms"] * 1e-3)
+            u = synth.uniform(seed + 17, count, 1e-12, 1.0)
+            gaps = -np.log(u) / rate
+            tickets = []
+            t0 = time.perf_counter()
+            t_next = 0.0
+            for kw, gap in zip(reqs, gaps):
+                t_next += gap
+                while time.perf_counter() - t0 < t_next:
+                    time.sleep(min(1e-4, max(0.0, t_next - (time.perf_counter() - t0))))
+                tickets.append(server.submit(**kw))
+        fails = 0
+        for t in tickets:
+            st, _, _ = server.wait(t)
+            fails += st != T.TS_OK
+        stats = server.stats()
+        stats["failed"] = fails
+        if phase == "poisson":
+            stats["arrival_rate_per_s"] = rate
+        out[phase] = stats
+    server.close()
+    out["requests"] = count
+    out["mix"] = "30% PCG (V2 = 5 cos cos cos + 8 Gaussian bumps, tol 1e-10) / 50% inverse / 20% exp (tau 0.01)"
+    out["grids"] = "3D, n_k iid from {32, 48, 64, 96, 128}"
+    out["omega"] = "U[0.5, 2) per axis" if omega_set is None else f"from {list(omega_set)}"
+    out["precision"] = "BF16X3 (PCG: BF16X3 preconditioner, FP64 recurrence)"
+    return out
+
+
+def run_secondary(args):
+    """One JSON line for a workload other than the benchmark's: the 3D n = 256 PCG /
+    shifted inverse iteration, the 6D / 9D Strang runs, or the serving workload."""
+    import torch
+    from paper_2605_20491_b300 import tschrod as T
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    name = args.workload
+    line = {"workload": name, "data": "synthetic"}
+    if name in ("6d_n24_strang", "9d_n8_strang"):
+        w = synth.WORKLOADS[name]
+        n, L = w["n"], w["L"]
+        P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << T.TS_FP32)
+        V2 = torch.from_numpy(synth.v2_soft_coulomb(n, L)).cuda()
+        psi0 = synth.sine_state(n, L)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for label, dt_, prec, steps in (("c64_fp32_fused", T.TS_C64, T.TS_FP32, w["steps"]),
+                                        ("c128_fp64", T.TS_C128, T.TS_FP64, 5)):
+            x = torch.from_numpy(psi0.astype(np.float32) if dt_ == T.TS_C64 else psi0).cuda()
+            T.ts_split_step(P, w["dt"], 2, V2, x, dt_, prec)
+            torch.cuda.synchronize()
+            T.ts_profile_begin()
+            e0.record()
+            T.ts_split_step(P, w["dt"], steps, V2, x, dt_, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            kind = T.PROF_SMALL_PASS if prec == T.TS_FP32 else T.PROF_FP64_PASS
+            nl, kms, fl, by = T.ts_profile_end(kind)
+            ms = e0.elapsed_time(e1) / steps
+            line[label] = {"ms_per_step": ms, "steps": steps, "gdofs": P.N / (ms * 1e-3) / 1e9,
+                           "kernel_launches": nl, "kernel_ms_per_step": kms / steps,
+                           "kernel_gbs": by / (kms * 1e-3) / 1e9 if kms else None,
+                           "kernel_tflops": fl / (kms * 1e-3) / 1e12 if kms else None}
+    elif name == "3d_n256_pcg":
+        w = synth.WORKLOADS[name]
+        n, L = w["n"], w["L"]
+        P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << T.TS_BF16X3)
+        V2h = synth.v2_cos_bumps(n, L, seed=w["v2_seed"])
+        V2 = torch.from_numpy(V2h).cuda()
+        lam1 = sum(T.ts_plan_eigs(P, k)[0] for k in range(3))
+        shift = lam1 + V2h.min() - 1.0
+        for label, prec in (("precond_bf16x3", T.TS_BF16X3), ("precond_fp64", T.TS_FP64)):
+            u = torch.zeros(P.N, dtype=torch.float64, device="cuda")
+            t0 = time.perf_counter()
+            lam, outer, pcg = T.ts_inverse_iteration(P, shift, V2, u, True, w["lambda_tol"], 400, w["pcg_tol"], 500,
+                                                     prec)
+            el = time.perf_counter() - t0
+            line[label] = {"lambda": lam, "outer_iters": outer, "pcg_iters": pcg, "seconds": el,
+                           "gdofs_per_pcg_iter": P.N * pcg / el / 1e9}
+        line["shift"] = shift
+    elif name == "serving":
+        line["continuous_omega"] = serving_run(T, args.requests)
+        line["discrete_omega"] = serving_run(T, args.requests, omega_set=(0.5, 1.0, 1.5, 2.0))
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -328,6 +461,11 @@ def run_ours(args):
             "roofline": roofline, "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N, "err_vs_fp64": e2e_err}}
+    if rank == 0 and not args.no_serving:
+        sv = serving_run(T, args.requests)
+        line["serving"] = sv
+        line["p50_ms"] = sv["poisson"]["p50_ms"]
+        line["p99_ms"] = sv["poisson"]["p99_ms"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample()
     T.ts_device_status()
@@ -353,9 +491,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the refined solve (for ncu captures); prints no JSON line")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--requests", type=int, default=128, help="requests of the serving run")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "3d_n256_pcg", "6d_n24_strang", "9d_n8_strang", "serving"])
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
+    if args.workload != WORKLOAD:
+        return run_secondary(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -60,29 +60,28 @@ __device__ __forceinline__ float2 vphase(float2 v, float theta, float V) {
 
 // Contract mode m of the tile in place along every fiber of that mode:
 // y_j = sum_i M[i][j] x_i with M row-major (M = S_k: forward, M = S_k^T: backward).
+// Tile-local indices are 32-bit; Tlo is a power of two (shift / mask) and N a constant.
 template <int N>
-__device__ void contract_mode(float2* tile, const float* M, int m, const GroupParams& p, int Tlo, int Thi) {
-  // tile axes (fastest first): t (Tlo), g_0 .. g_{nm-1} (padded), th (Thi)
-  long long st_m = Tlo;
+__device__ void contract_mode(float2* tile, const float* M, int m, const GroupParams& p, int lgTlo, int Thi) {
+  const int Tlo = 1 << lgTlo;
+  int st_m = Tlo;
   for (int j = 0; j < m; ++j) st_m *= p.npad[j];
-  long long inner_cnt = Tlo;
+  int inner_cnt = Tlo;
   for (int j = 0; j < m; ++j) inner_cnt *= N;
-  long long outer_cnt = Thi;
+  int outer_cnt = Thi;
   for (int j = m + 1; j < p.nm; ++j) outer_cnt *= N;
-  const long long fibers = inner_cnt * outer_cnt;
-  for (long long f = threadIdx.x; f < fibers; f += blockDim.x) {
-    long long in_i = f % inner_cnt, out_i = f / inner_cnt;
-    // inner address: t + Tlo * (g_0 + npad_0 * (g_1 + ...)) for axes below m
-    long long addr = in_i % Tlo;
-    long long rem = in_i / Tlo, mul = Tlo;
+  const int fibers = inner_cnt * outer_cnt;
+  for (int f = threadIdx.x; f < fibers; f += blockDim.x) {
+    const int in_i = f % inner_cnt, out_i = f / inner_cnt;
+    int addr = in_i & (Tlo - 1);
+    int rem = in_i >> lgTlo, mul = Tlo;
     for (int j = 0; j < m; ++j) {
       addr += (rem % N) * mul;
       rem /= N;
       mul *= p.npad[j];
     }
-    // outer address: above m, then th
-    long long mul2 = st_m * p.npad[m];
-    long long r2 = out_i;
+    int mul2 = st_m * p.npad[m];
+    int r2 = out_i;
     for (int j = m + 1; j < p.nm; ++j) {
       addr += (r2 % N) * mul2;
       r2 /= N;
@@ -92,28 +91,61 @@ __device__ void contract_mode(float2* tile, const float* M, int m, const GroupPa
     float2 x[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) x[i] = tile[addr + i * st_m];
+    // four outputs per 16-byte load of the matrix row: 8 FFMA per shared-memory load
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      float re = 0.f, im = 0.f;
+    for (int j = 0; j < N; j += 4) {
+      float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const float w = M[i * N + j];
-        re = fmaf(w, x[i].x, re);
-        im = fmaf(w, x[i].y, im);
+        const float4 w = *reinterpret_cast<const float4*>(M + i * N + j);
+        re[0] = fmaf(w.x, x[i].x, re[0]);
+        im[0] = fmaf(w.x, x[i].y, im[0]);
+        re[1] = fmaf(w.y, x[i].x, re[1]);
+        im[1] = fmaf(w.y, x[i].y, im[1]);
+        re[2] = fmaf(w.z, x[i].x, re[2]);
+        im[2] = fmaf(w.z, x[i].y, im[2]);
+        re[3] = fmaf(w.w, x[i].x, re[3]);
+        im[3] = fmaf(w.w, x[i].y, im[3]);
       }
-      tile[addr + j * st_m] = make_float2(re, im);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tile[addr + (j + q) * st_m] = make_float2(re[q], im[q]);
     }
   }
+}
+
+// Shared-memory index of tile element e (global order: t fastest, group indices, th) and
+// its group-flattened index g (unpadded).
+template <int N>
+__device__ __forceinline__ int tile_index(int e, int lgTlo, const GroupParams& p, int* g_out, int* th_out) {
+  const int Tlo = 1 << lgTlo;
+  const int t = e & (Tlo - 1);
+  int r = e >> lgTlo;
+  int sidx = t, mul = Tlo, g = 0, gm = 1;
+  for (int j = 0; j < p.nm; ++j) {
+    const int ij = r % N;
+    r /= N;
+    sidx += ij * mul;
+    mul *= p.npad[j];
+    g += ij * gm;
+    gm *= N;
+  }
+  *g_out = g;
+  *th_out = r;
+  return sidx + r * mul;
 }
 
 template <int N>
 __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, float2* Y, const GroupParams p) {
   extern __shared__ float2 smem[];
   float2* tile = smem;
-  const int Tlo = p.lo > 1 ? p.T : 1;
+  const int lgT = 31 - __clz(p.T);
+  const int lgTlo = p.lo > 1 ? lgT : 0;
+  const int Tlo = 1 << lgTlo;
   const int Thi = p.lo > 1 ? 1 : p.T;
-  const long long tile_pad = (long long)Tlo * p.Gpad * Thi;
-  float* mats = reinterpret_cast<float*>(tile + tile_pad);  // nm forward + nm backward matrices
+  const int tile_pad = Tlo * (int)p.Gpad * Thi;
+  float2* rowph = tile + tile_pad;                              // Tlo phase factors (middle pass)
+  // matrices start 16-byte aligned (tile_pad + Tlo rounded up to an even float2 count)
+  float* mats = reinterpret_cast<float*>(tile + ((tile_pad + Tlo + 1) & ~1));
   const int msz = N * N;
   for (int e = threadIdx.x; e < p.nm * msz; e += blockDim.x) {
     const int m = e / msz, q = e % msz;
@@ -122,30 +154,32 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
   }
   long long l0 = 0, h0 = 0;
   if (p.lo > 1) {
-    const long long lblocks = p.lo / Tlo;
-    l0 = (blockIdx.x % lblocks) * Tlo;
+    const long long lblocks = p.lo >> lgTlo;
+    l0 = (blockIdx.x % lblocks) << lgTlo;
     h0 = blockIdx.x / lblocks;
   } else {
     h0 = (long long)blockIdx.x * Thi;
   }
-  const long long cnt = (long long)Tlo * p.G * Thi;
-  // ---- load (global order: t fastest, then the group indices, then th)
-  for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const long long t = e % Tlo;
-    long long r = e / Tlo;
-    long long sidx = t, mul = Tlo;
-    long long g = 0, gm = 1;
-    for (int j = 0; j < p.nm; ++j) {
-      const long long ij = r % N;
-      r /= N;
-      sidx += ij * mul;
-      mul *= p.npad[j];
-      g += ij * gm;
-      gm *= N;
+  if (p.do_phase) {
+    // phase factor of the axes below the group, one per t (the last group has no axes above)
+    for (int t = threadIdx.x; t < Tlo; t += blockDim.x) {
+      long long q = l0 + t;
+      float2 ph = make_float2(1.f, 0.f);
+      for (int k = 0; k < p.k0; ++k) {
+        const int ik = (int)(q % p.n_all[k]);
+        q /= p.n_all[k];
+        ph = cmulf(ph, p.ph[k][ik]);
+      }
+      rowph[t] = ph;
     }
-    const long long th = r;
-    sidx += th * mul;
-    const long long gidx = (l0 + t) + p.lo * (g + p.G * (h0 + th));
+  }
+  const int cnt = Tlo * (int)p.G * Thi;
+  const long long gbase = l0 + p.lo * p.G * h0;
+  // ---- load (global order: t fastest, then the group indices, then th)
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    int g, th;
+    const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+    const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
     float2 v = X[gidx];
     if (p.V2 && p.theta_pre != 0.f) v = vphase(v, p.theta_pre, p.V2[gidx]);
     tile[sidx] = v;
@@ -153,65 +187,39 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
   __syncthreads();
   if (p.do_fwd) {
     for (int m = 0; m < p.nm; ++m) {
-      contract_mode<N>(tile, mats + m * msz, m, p, Tlo, Thi);
+      contract_mode<N>(tile, mats + m * msz, m, p, lgTlo, Thi);
       __syncthreads();
     }
   }
   if (p.do_phase) {
-    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const long long t = e % Tlo;
-      long long r = e / Tlo;
-      long long sidx = t, mul = Tlo;
-      float2 ph = make_float2(1.f, 0.f);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int t = e & (Tlo - 1);
+      int r = e >> lgTlo;
+      int sidx = t, mul = Tlo;
+      float2 ph = rowph[t];
       for (int j = 0; j < p.nm; ++j) {
-        const int ij = (int)(r % N);
+        const int ij = r % N;
         r /= N;
         sidx += ij * mul;
         mul *= p.npad[j];
         ph = cmulf(ph, p.ph[p.k0 + j][ij]);
       }
-      const long long th = r;
-      sidx += th * mul;
-      // axes below the group from l0 + t, above it from h0 + th
-      long long q = l0 + t;
-      for (int k = 0; k < p.k0; ++k) {
-        const int ik = (int)(q % p.n_all[k]);
-        q /= p.n_all[k];
-        ph = cmulf(ph, p.ph[k][ik]);
-      }
-      q = h0 + th;
-      for (int k = p.k0 + p.nm; k < p.d; ++k) {
-        const int ik = (int)(q % p.n_all[k]);
-        q /= p.n_all[k];
-        ph = cmulf(ph, p.ph[k][ik]);
-      }
+      sidx += r * mul;
       tile[sidx] = cmulf(tile[sidx], ph);
     }
     __syncthreads();
   }
   if (p.do_bwd) {
     for (int m = p.nm - 1; m >= 0; --m) {
-      contract_mode<N>(tile, mats + (p.nm + m) * msz, m, p, Tlo, Thi);
+      contract_mode<N>(tile, mats + (p.nm + m) * msz, m, p, lgTlo, Thi);
       __syncthreads();
     }
   }
   // ---- store
-  for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const long long t = e % Tlo;
-    long long r = e / Tlo;
-    long long sidx = t, mul = Tlo;
-    long long g = 0, gm = 1;
-    for (int j = 0; j < p.nm; ++j) {
-      const long long ij = r % N;
-      r /= N;
-      sidx += ij * mul;
-      mul *= p.npad[j];
-      g += ij * gm;
-      gm *= N;
-    }
-    const long long th = r;
-    sidx += th * mul;
-    const long long gidx = (l0 + t) + p.lo * (g + p.G * (h0 + th));
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    int g, th;
+    const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+    const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
     float2 v = tile[sidx];
     if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, p.V2[gidx]);
     Y[gidx] = v;
@@ -276,7 +284,8 @@ std::vector<Group> make_groups(const ts_plan* p) {
 template <int N>
 ts_status launch_group(const float2* X, float2* Y, const GroupParams& gp, cudaStream_t s) {
   const int Tlo = gp.lo > 1 ? gp.T : 1, Thi = gp.lo > 1 ? 1 : gp.T;
-  const size_t smem = sizeof(float2) * (size_t)Tlo * gp.Gpad * Thi + sizeof(float) * 2 * gp.nm * N * N;
+  const size_t smem = sizeof(float2) * (((size_t)Tlo * gp.Gpad * Thi + Tlo + 1) & ~size_t(1)) +
+                      sizeof(float) * 2 * gp.nm * N * N;
   static bool attr = false;
   if (!attr) {
     TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
