@@ -217,8 +217,10 @@ ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap);
  * Continuous-batching request server (no counterpart in the paper; it serves the paper's
  * three operations to many independent callers).  A scheduler thread admits queued
  * requests while fewer than max_inflight are on the GPU and their scratch fits
- * memory_budget_bytes, looks each grid's plan up in a cache keyed by (n_k, L_k, f_k)
- * (building it on a miss), captures every round of admitted inverse / exp requests into
+ * memory_budget_bytes.  Planner threads look each grid's plan up in a cache keyed by
+ * (n_k, L_k, f_k) ahead of admission (building it on a miss, on top of the process-wide
+ * per-axis eigendecomposition cache).  The scheduler captures every round of admitted
+ * inverse / exp requests into
  * one CUDA graph with one stream per request (their kernels overlap), and runs PCG
  * requests (which read one scalar back per iteration) on pooled host threads with their
  * own streams.  Results are bitwise the same alone and in a mix.  in / out / V2 are
@@ -244,7 +246,7 @@ typedef struct {
   long long memory_budget_bytes; /* scratch budget (<= 0: half the free device memory)   */
   int max_inflight;              /* requests on the GPU at once (<= 0: 8)                */
   int max_batch;                 /* requests per captured graph (<= 0: max_inflight)     */
-  int plan_cache_entries;        /* cached plans (<= 0: 64)                              */
+  int plan_cache_entries;        /* cached plans (<= 0: 1024)                            */
 } ts_server_config;
 
 typedef struct {

@@ -113,7 +113,7 @@ ts_status ts_plan_eigs(const ts_plan* plan, int axis, double* lambda_host) {
   clear_error();
   TS_REQUIRE(plan && lambda_host, "NULL argument");
   TS_REQUIRE(axis >= 0 && axis < plan->d, "axis %d out of range", axis);
-  std::memcpy(lambda_host, plan->lam_host[axis].data(), sizeof(double) * plan->n[axis]);
+  std::memcpy(lambda_host, plan->axis[axis]->lam_host.data(), sizeof(double) * plan->n[axis]);
   return TS_OK;
 }
 
@@ -121,7 +121,7 @@ ts_status ts_plan_eigvecs(const ts_plan* plan, int axis, double* S_host) {
   clear_error();
   TS_REQUIRE(plan && S_host, "NULL argument");
   TS_REQUIRE(axis >= 0 && axis < plan->d, "axis %d out of range", axis);
-  std::memcpy(S_host, plan->S_host[axis].data(), sizeof(double) * plan->n[axis] * plan->n[axis]);
+  std::memcpy(S_host, plan->axis[axis]->S_host.data(), sizeof(double) * plan->n[axis] * plan->n[axis]);
   return TS_OK;
 }
 

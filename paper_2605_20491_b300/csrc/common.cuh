@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -70,7 +72,37 @@ struct AxisParams {
 
 }  // namespace ts
 
-// The plan: per-axis device tables.  Axes with identical (n, L, f) share storage.
+namespace ts {
+
+// Device tables of one axis: the eigendecomposition of H_k = h^-2 tridiag(-1,2,-1) + diag f
+// and the copies derived from it.  Shared by every plan (and every request) whose axis has
+// the same (n, L, f) on the same device; freed when the last user lets go of it.
+struct AxisTables {
+  int device = 0;
+  int n = 0;
+  double L = 0.0;
+  std::vector<double> f;             // host copy of the samples (cache key)
+  void* block = nullptr;             // one allocation: S, St, lam, f, lamf
+  double* S = nullptr;               // row-major S[i][j], column j = eigenvector j
+  double* St = nullptr;              // S^T
+  double* lam = nullptr;             // eigenvalues, ascending
+  double* fdev = nullptr;            // potential samples
+  float* lamf = nullptr;             // eigenvalues rounded to FP32
+  // Split bf16 planes per precision, [plane][n][n]: S^T (forward operand, Bf) and S
+  // (backward operand, Bb), contracted index contiguous (K-major tensor-core operands).
+  __nv_bfloat16* Bf[NPREC] = {};
+  __nv_bfloat16* Bb[NPREC] = {};
+  float* Sf32 = nullptr;             // S and S^T rounded to FP32 (small-n path)
+  float* Stf32 = nullptr;
+  std::vector<double> lam_host, S_host;
+  long long bytes = 0;
+  std::mutex mu;                     // guards the lazily built precision copies
+  ~AxisTables();
+};
+
+}  // namespace ts
+
+// The plan: per-axis device tables (pointers into shared AxisTables).
 struct ts_plan {
   int device = 0;
   int d = 0;
@@ -79,24 +111,16 @@ struct ts_plan {
   long long N = 0;
   int nmax = 0;
   unsigned precision_mask = 1u;
-  // FP64 tables (device).  S: row-major S[i][j] (column j = eigenvector j); St = S^T.
+  std::shared_ptr<ts::AxisTables> axis[TS_MAX_DIM];
   double* S[TS_MAX_DIM] = {};
   double* St[TS_MAX_DIM] = {};
   double* lam[TS_MAX_DIM] = {};
-  float* lamf[TS_MAX_DIM] = {};  // lambda_k rounded to FP32 (epilogue tables)
-  float* Sf32[TS_MAX_DIM] = {};   // S_k and S_k^T rounded to FP32 (TS_FP32 small-n path)
+  float* lamf[TS_MAX_DIM] = {};
+  float* Sf32[TS_MAX_DIM] = {};
   float* Stf32[TS_MAX_DIM] = {};
   double* f[TS_MAX_DIM] = {};
-  // Split bf16 planes (device), [prec][axis] -> [plane][n][n]: row-major copies of
-  // S^T (forward operand, "Bf") and S (backward operand, "Bb"), so that the contracted
-  // index is contiguous in both (K-major tensor-core operands).
   __nv_bfloat16* Bf[ts::NPREC][TS_MAX_DIM] = {};
   __nv_bfloat16* Bb[ts::NPREC][TS_MAX_DIM] = {};
-  // Host copies.
-  std::vector<double> lam_host[TS_MAX_DIM];
-  std::vector<double> S_host[TS_MAX_DIM];
-  // Ownership: which axis owns each shared table (owner[k] == k owns it).
-  int owner[TS_MAX_DIM] = {};
   long long bytes = 0;
 };
 

@@ -526,23 +526,28 @@ unsigned grid_1d(long long N) {
 ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s) {
   const int np = bf16_planes(prec);
   if (np == 0) {
-    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X3, TS_BF16X6)", (int)prec);
+    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X3, TS_BF16X6, TS_FP32)", (int)prec);
     return TS_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < p->d; ++k) {
-    if (p->owner[k] != k) {
-      p->Bf[prec][k] = p->Bf[prec][p->owner[k]];
-      p->Bb[prec][k] = p->Bb[prec][p->owner[k]];
-      continue;
+    AxisTables* t = p->axis[k].get();
+    std::lock_guard<std::mutex> lk(t->mu);
+    if (!t->Bf[prec]) {
+      const long long cnt = (long long)t->n * t->n;
+      __nv_bfloat16 *bf = nullptr, *bb = nullptr;
+      TS_CHECK_CUDA(cudaMalloc(&bf, sizeof(__nv_bfloat16) * np * cnt));
+      TS_CHECK_CUDA(cudaMalloc(&bb, sizeof(__nv_bfloat16) * np * cnt));
+      // Forward operand B[j][i] = S[i][j] is the row-major S^T; backward B[i][j] = S[i][j].
+      k_split_table<<<grid_1d(cnt), 256, 0, s>>>(t->St, bf, cnt, np);
+      k_split_table<<<grid_1d(cnt), 256, 0, s>>>(t->S, bb, cnt, np);
+      TS_LAUNCHED(2);
+      TS_CHECK_CUDA(cudaStreamSynchronize(s));  // published to other plans only once complete
+      t->Bf[prec] = bf;
+      t->Bb[prec] = bb;
+      t->bytes += 2LL * np * cnt * (long long)sizeof(__nv_bfloat16);
     }
-    const long long cnt = (long long)p->n[k] * p->n[k];
-    TS_CHECK_CUDA(cudaMalloc(&p->Bf[prec][k], sizeof(__nv_bfloat16) * np * cnt));
-    TS_CHECK_CUDA(cudaMalloc(&p->Bb[prec][k], sizeof(__nv_bfloat16) * np * cnt));
-    p->bytes += 2LL * np * cnt * (long long)sizeof(__nv_bfloat16);
-    // Forward operand B[j][i] = S[i][j] is the row-major S^T; backward B[i][j] = S[i][j].
-    k_split_table<<<grid_1d(cnt), 256, 0, s>>>(p->St[k], p->Bf[prec][k], cnt, np);
-    k_split_table<<<grid_1d(cnt), 256, 0, s>>>(p->S[k], p->Bb[prec][k], cnt, np);
-    TS_LAUNCHED(2);
+    p->Bf[prec][k] = t->Bf[prec];
+    p->Bb[prec][k] = t->Bb[prec];
   }
   return TS_OK;
 }

@@ -5,10 +5,17 @@
 // is symmetric and T_k = S_k is orthogonal (T_k^{-1} = S_k^T).  Each H_k is
 // eigendecomposed in FP64 on the GPU (cuSOLVER syevd: eigenvalues ascending,
 // eigenvectors as columns); the tables stay resident on the device for every later apply.
+//
+// Axis tables are cached process-wide by (device, n, L, f): plans whose axes coincide
+// -- within one plan (isotropic grids) or across plans (a server's stream of requests on
+// a few distinct 1D operators) -- share one decomposition.  The cache keeps the most
+// recently built tables alive even when no plan holds them.
 #include <cusolverDn.h>
 
 #include <cmath>
 #include <cstring>
+#include <deque>
+#include <map>
 
 #include "common.cuh"
 #include "mixed.cuh"
@@ -16,100 +23,208 @@
 
 namespace ts {
 
+AxisTables::~AxisTables() {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+  cudaFree(block);
+  for (int q = 0; q < NPREC; ++q) {
+    cudaFree(Bf[q]);
+    cudaFree(Bb[q]);
+  }
+  cudaFree(Sf32);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+}
+
 namespace {
+
+// One cuSOLVER handle and workspace per host thread, grown on demand.
+struct Solver {
+  int device = -1;
+  cusolverDnHandle_t h = nullptr;
+  double *dA = nullptr, *dW = nullptr, *work = nullptr;
+  int* info = nullptr;
+  int cap_n = 0, cap_work = 0;
+  void release() {
+    if (h) cusolverDnDestroy(h);
+    cudaFree(dA);
+    cudaFree(dW);
+    cudaFree(work);
+    cudaFree(info);
+    *this = Solver();
+  }
+};
+thread_local Solver t_solver;
 
 ts_status eig_on_device(int n, const std::vector<double>& H, std::vector<double>& lam, std::vector<double>& Qcol,
                         cudaStream_t s) {
-  cusolverDnHandle_t h = nullptr;
-  if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) {
-    set_error("cusolverDnCreate failed");
+  Solver& sv = t_solver;
+  int dev = 0;
+  TS_CHECK_CUDA(cudaGetDevice(&dev));
+  if (sv.h && sv.device != dev) sv.release();
+  if (!sv.h) {
+    if (cusolverDnCreate(&sv.h) != CUSOLVER_STATUS_SUCCESS) {
+      set_error("cusolverDnCreate failed");
+      return TS_ERR_CUDA;
+    }
+    sv.device = dev;
+    TS_CHECK_CUDA(cudaMalloc(&sv.info, sizeof(int)));
+  }
+  cusolverDnSetStream(sv.h, s);
+  if (n > sv.cap_n) {
+    cudaFree(sv.dA);
+    cudaFree(sv.dW);
+    sv.dA = sv.dW = nullptr;
+    TS_CHECK_CUDA(cudaMalloc(&sv.dA, sizeof(double) * n * n));
+    TS_CHECK_CUDA(cudaMalloc(&sv.dW, sizeof(double) * n));
+    sv.cap_n = n;
+  }
+  int lwork = 0;
+  if (cusolverDnDsyevd_bufferSize(sv.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, sv.dA, n, sv.dW,
+                                  &lwork) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnDsyevd_bufferSize failed");
     return TS_ERR_CUDA;
   }
-  cusolverDnSetStream(h, s);
-  double *dA = nullptr, *dW = nullptr, *work = nullptr;
-  int* info = nullptr;
-  ts_status st = TS_OK;
-  int lwork = 0, hinfo = 0;
-  cudaError_t e = cudaMalloc(&dA, sizeof(double) * n * n);
-  if (e == cudaSuccess) e = cudaMalloc(&dW, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&info, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dA, H.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) {
-    set_error("plan: device allocation/copy failed: %s", cudaGetErrorString(e));
-    st = e == cudaErrorMemoryAllocation ? TS_ERR_NO_MEMORY : TS_ERR_CUDA;
+  if (lwork > sv.cap_work) {
+    cudaFree(sv.work);
+    sv.work = nullptr;
+    TS_CHECK_CUDA(cudaMalloc(&sv.work, sizeof(double) * (lwork > 0 ? lwork : 1)));
+    sv.cap_work = lwork;
   }
-  if (st == TS_OK &&
-      cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dW, &lwork) !=
-          CUSOLVER_STATUS_SUCCESS) {
-    set_error("cusolverDnDsyevd_bufferSize failed");
-    st = TS_ERR_CUDA;
-  }
-  if (st == TS_OK && cudaMalloc(&work, sizeof(double) * (lwork > 0 ? lwork : 1)) != cudaSuccess) {
-    set_error("plan: workspace allocation failed");
-    st = TS_ERR_NO_MEMORY;
-  }
-  if (st == TS_OK &&
-      cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dW, work, lwork, info) !=
-          CUSOLVER_STATUS_SUCCESS) {
+  TS_CHECK_CUDA(cudaMemcpyAsync(sv.dA, H.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, s));
+  if (cusolverDnDsyevd(sv.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, sv.dA, n, sv.dW, sv.work, lwork,
+                       sv.info) != CUSOLVER_STATUS_SUCCESS) {
     set_error("cusolverDnDsyevd failed");
-    st = TS_ERR_CUDA;
+    return TS_ERR_CUDA;
   }
-  if (st == TS_OK) {
-    lam.resize(n);
-    Qcol.resize((size_t)n * n);
-    e = cudaMemcpyAsync(lam.data(), dW, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Qcol.data(), dA, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_error("plan: eigendecomposition readback failed: %s", cudaGetErrorString(e));
-      st = TS_ERR_CUDA;
-    } else if (hinfo != 0) {
-      set_error("syevd returned info = %d", hinfo);
-      st = TS_ERR_CUDA;
-    }
+  lam.resize(n);
+  Qcol.resize((size_t)n * n);
+  int hinfo = 0;
+  TS_CHECK_CUDA(cudaMemcpyAsync(lam.data(), sv.dW, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(Qcol.data(), sv.dA, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(&hinfo, sv.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TS_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (hinfo != 0) {
+    set_error("syevd returned info = %d", hinfo);
+    return TS_ERR_CUDA;
   }
-  cudaFree(dA);
-  cudaFree(dW);
-  cudaFree(work);
-  cudaFree(info);
-  cusolverDnDestroy(h);
-  return st;
+  return TS_OK;
 }
 
-template <typename T>
-ts_status upload(T** dst, const T* src, size_t count, ts_plan* p, cudaStream_t s) {
-  TS_CHECK_CUDA(cudaMalloc((void**)dst, sizeof(T) * count));
-  p->bytes += (long long)(sizeof(T) * count);
-  TS_CHECK_CUDA(cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+struct AxisKey {
+  int device, n;
+  double L;
+  std::vector<double> f;
+  bool operator<(const AxisKey& o) const {
+    if (device != o.device) return device < o.device;
+    if (n != o.n) return n < o.n;
+    const int c = std::memcmp(&L, &o.L, sizeof(double));
+    if (c != 0) return c < 0;
+    return std::memcmp(f.data(), o.f.data(), sizeof(double) * f.size()) < 0;
+  }
+};
+
+std::mutex g_axis_mu;
+std::map<AxisKey, std::weak_ptr<AxisTables>> g_axis_map;
+std::deque<std::shared_ptr<AxisTables>> g_axis_keep;
+constexpr size_t AXIS_KEEP = 128;
+long long g_axis_hits = 0, g_axis_builds = 0;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+ts_status build_axis(const AxisKey& key, cudaStream_t s, std::shared_ptr<AxisTables>* out) {
+  auto t = std::make_shared<AxisTables>();
+  const int n = key.n;
+  t->device = key.device;
+  t->n = n;
+  t->L = key.L;
+  t->f = key.f;
+  const double h = 2.0 * key.L / (n + 1);
+  const double ih2 = 1.0 / (h * h);
+  std::vector<double> H((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    H[(size_t)i * n + i] = 2.0 * ih2 + key.f[i];
+    if (i > 0) H[(size_t)i * n + i - 1] = -ih2;
+    if (i + 1 < n) H[(size_t)i * n + i + 1] = -ih2;
+  }
+  std::vector<double> Qcol;
+  TS_TRY(eig_on_device(n, H, t->lam_host, Qcol, s));
+  // Qcol is column-major: Qcol[i + n j] = S[i][j], i.e. the row-major S^T.
+  t->S_host.resize((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) t->S_host[(size_t)i * n + j] = Qcol[(size_t)i + (size_t)n * j];
+  std::vector<float> lf(t->lam_host.begin(), t->lam_host.end());
+  const size_t oS = 0, oSt = align256(oS + 8ull * n * n), oLam = align256(oSt + 8ull * n * n),
+               oF = align256(oLam + 8ull * n), oLf = align256(oF + 8ull * n), total = align256(oLf + 4ull * n);
+  TS_CHECK_CUDA(cudaMalloc(&t->block, total));
+  t->bytes = (long long)total;
+  char* b = (char*)t->block;
+  t->S = (double*)(b + oS);
+  t->St = (double*)(b + oSt);
+  t->lam = (double*)(b + oLam);
+  t->fdev = (double*)(b + oF);
+  t->lamf = (float*)(b + oLf);
+  TS_CHECK_CUDA(cudaMemcpyAsync(t->S, t->S_host.data(), 8ull * n * n, cudaMemcpyHostToDevice, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(t->St, Qcol.data(), 8ull * n * n, cudaMemcpyHostToDevice, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(t->lam, t->lam_host.data(), 8ull * n, cudaMemcpyHostToDevice, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(t->fdev, key.f.data(), 8ull * n, cudaMemcpyHostToDevice, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(t->lamf, lf.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+  TS_CHECK_CUDA(cudaStreamSynchronize(s));  // host staging vectors go out of scope
+  *out = t;
+  return TS_OK;
+}
+
+ts_status get_axis(int device, int n, double L, const double* f, cudaStream_t s, std::shared_ptr<AxisTables>* out) {
+  AxisKey key{device, n, L, std::vector<double>(f, f + n)};
+  {
+    std::lock_guard<std::mutex> lk(g_axis_mu);
+    auto it = g_axis_map.find(key);
+    if (it != g_axis_map.end()) {
+      if (auto sp = it->second.lock()) {
+        ++g_axis_hits;
+        *out = sp;
+        return TS_OK;
+      }
+    }
+  }
+  std::shared_ptr<AxisTables> built;
+  TS_TRY(build_axis(key, s, &built));
+  std::lock_guard<std::mutex> lk(g_axis_mu);
+  auto it = g_axis_map.find(key);
+  if (it != g_axis_map.end()) {
+    if (auto sp = it->second.lock()) {  // another thread built it meanwhile: use that one
+      *out = sp;
+      return TS_OK;
+    }
+  }
+  ++g_axis_builds;
+  g_axis_map[key] = built;
+  g_axis_keep.push_back(built);
+  while (g_axis_keep.size() > AXIS_KEEP) g_axis_keep.pop_front();
+  for (auto m = g_axis_map.begin(); m != g_axis_map.end();)  // drop dead entries
+    m = m->second.expired() ? g_axis_map.erase(m) : std::next(m);
+  *out = built;
   return TS_OK;
 }
 
 }  // namespace
 
-void plan_free(ts_plan* p) {
-  if (!p) return;
-  for (int k = 0; k < p->d; ++k) {
-    if (p->owner[k] != k) continue;
-    cudaFree(p->S[k]);
-    cudaFree(p->St[k]);
-    cudaFree(p->lam[k]);
-    cudaFree(p->lamf[k]);
-    cudaFree(p->Sf32[k]);
-    cudaFree(p->Stf32[k]);
-    for (int q = 0; q < NPREC; ++q) {
-      cudaFree(p->Bf[q][k]);
-      cudaFree(p->Bb[q][k]);
-    }
-  }
-  for (int k = 0; k < p->d; ++k) cudaFree(p->f[k]);  // potential samples are per axis
-  delete p;
+void axis_cache_counters(long long* hits, long long* builds) {
+  std::lock_guard<std::mutex> lk(g_axis_mu);
+  if (hits) *hits = g_axis_hits;
+  if (builds) *builds = g_axis_builds;
 }
+
+void plan_free(ts_plan* p) { delete p; }
 
 ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, ts_plan** out) {
   ts_plan* p = new ts_plan();
-  TS_CHECK_CUDA(cudaGetDevice(&p->device));
+  ts_status st = TS_OK;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    set_error("cudaGetDevice failed: %s", cudaGetErrorString(e));
+    st = TS_ERR_CUDA;
+  }
   p->d = desc->d;
   p->N = 1;
   p->precision_mask = mask | 1u;
@@ -119,68 +234,24 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
     p->N *= desc->n[k];
     if (desc->n[k] > p->nmax) p->nmax = desc->n[k];
   }
-  ts_status st = TS_OK;
   for (int k = 0; k < p->d && st == TS_OK; ++k) {
-    const int n = p->n[k];
-    st = upload(&p->f[k], desc->f[k], (size_t)n, p, s);
+    st = get_axis(p->device, p->n[k], p->L[k], desc->f[k], s, &p->axis[k]);
     if (st != TS_OK) break;
-    // Share the decomposition with an earlier identical axis.
-    int same = -1;
-    for (int j = 0; j < k; ++j)
-      if (p->n[j] == n && p->L[j] == p->L[k] && std::memcmp(desc->f[j], desc->f[k], sizeof(double) * n) == 0) {
-        same = p->owner[j];
-        break;
-      }
-    if (same >= 0) {
-      p->owner[k] = same;
-      p->S[k] = p->S[same];
-      p->St[k] = p->St[same];
-      p->lam[k] = p->lam[same];
-      p->lamf[k] = p->lamf[same];
-      p->lam_host[k] = p->lam_host[same];
-      p->S_host[k] = p->S_host[same];
-      continue;
-    }
-    p->owner[k] = k;
-    const double h = 2.0 * p->L[k] / (n + 1);
-    const double ih2 = 1.0 / (h * h);
-    std::vector<double> H((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) {
-      H[(size_t)i * n + i] = 2.0 * ih2 + desc->f[k][i];
-      if (i > 0) H[(size_t)i * n + i - 1] = -ih2;
-      if (i + 1 < n) H[(size_t)i * n + i + 1] = -ih2;
-    }
-    std::vector<double> Qcol;
-    st = eig_on_device(n, H, p->lam_host[k], Qcol, s);
-    if (st != TS_OK) break;
-    // Qcol is column-major: Qcol[i + n j] = S[i][j], i.e. the row-major S^T.
-    std::vector<double> S((size_t)n * n);
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) S[(size_t)i * n + j] = Qcol[(size_t)i + (size_t)n * j];
-    p->S_host[k] = S;
-    st = upload(&p->S[k], S.data(), S.size(), p, s);
-    if (st == TS_OK) st = upload(&p->St[k], Qcol.data(), Qcol.size(), p, s);
-    if (st == TS_OK) st = upload(&p->lam[k], p->lam_host[k].data(), (size_t)n, p, s);
-    std::vector<float> lf(p->lam_host[k].begin(), p->lam_host[k].end());
-    if (st == TS_OK) st = upload(&p->lamf[k], lf.data(), (size_t)n, p, s);
-    if (st == TS_OK) {
-      cudaError_t e = cudaStreamSynchronize(s);  // host vectors go out of scope
-      if (e != cudaSuccess) {
-        set_error("plan upload failed: %s", cudaGetErrorString(e));
-        st = TS_ERR_CUDA;
-      }
-    }
+    AxisTables* t = p->axis[k].get();
+    p->S[k] = t->S;
+    p->St[k] = t->St;
+    p->lam[k] = t->lam;
+    p->lamf[k] = t->lamf;
+    p->f[k] = t->fdev;
   }
   for (int q = 1; q < NPREC && st == TS_OK; ++q) {
     if (!(p->precision_mask & (1u << q))) continue;
     st = q == TS_FP32 ? build_small_tables(p, s) : build_split_tables(p, (ts_precision)q, s);
   }
-  if (st == TS_OK) {
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_error("plan creation failed: %s", cudaGetErrorString(e));
-      st = TS_ERR_CUDA;
-    }
+  for (int k = 0; k < p->d && st == TS_OK; ++k) {
+    bool seen = false;
+    for (int j = 0; j < k; ++j) seen |= p->axis[j].get() == p->axis[k].get();
+    if (!seen) p->bytes += p->axis[k]->bytes;
   }
   if (st != TS_OK) {
     plan_free(p);

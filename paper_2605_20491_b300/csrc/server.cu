@@ -5,8 +5,10 @@
 //     and their scratch footprint fits the device-memory budget (requests that can never
 //     fit fail with TS_ERR_NO_MEMORY); requests that arrive while others run are admitted
 //     as slots and memory free up;
-//   * plans: each request's per-axis tables come from a plan cache keyed by the grid and
-//     the sampled V1 (n_k, L_k, f_k compared bit for bit); a miss builds the plan;
+//   * plans: planner threads build each request's plan ahead of admission (overlapping the
+//     GPU work of earlier requests), from a plan cache keyed by the grid and the sampled V1
+//     (n_k, L_k, f_k compared bit for bit); the per-axis eigendecompositions underneath
+//     are shared process-wide, so requests on a few distinct 1D operators rarely solve one;
 //   * batching: the inverse / exp requests admitted in one scheduling round are captured
 //     into ONE CUDA graph (the capture stream forks one stream per request, so their
 //     kernels overlap on the device) and launched; the graph's completion event completes
@@ -57,12 +59,17 @@ struct PlanKey {
   }
 };
 
+using PlanPtr = std::shared_ptr<ts_plan>;
+
 struct Job {
   long long ticket = 0;
   ts_request req{};
   PlanKey key;
   std::vector<std::vector<double>> f;  // copies of the V1 samples
+  PlanPtr plan_ref;                     // keeps the plan alive while the job runs
   ts_plan* plan = nullptr;
+  bool plan_ready = false;
+  ts_status plan_status = TS_OK;
   size_t footprint = 0;
   Clock::time_point t_submit, t_done;
   int stream_slot = -1;
@@ -104,8 +111,13 @@ struct ts_server {
   std::vector<cudaStream_t> streams;
   std::vector<bool> stream_busy;
   cudaStream_t capture_stream = nullptr;
-  std::map<ts::PlanKey, ts_plan*> plans;
+  std::map<ts::PlanKey, ts::PlanPtr> plans;
   std::deque<ts::PlanKey> plan_lru;
+  std::mutex plan_mu;
+  std::condition_variable cv_plan;
+  std::deque<std::shared_ptr<ts::Job>> to_plan;
+  std::vector<std::thread> planners;
+  std::vector<cudaStream_t> planner_streams;
   long long plan_hits = 0, plan_misses = 0, batches = 0, graph_requests = 0;
   std::vector<double> latencies_ms;
   double dof_done = 0.0;
@@ -123,42 +135,71 @@ struct ts_server {
 namespace ts {
 namespace {
 
-ts_status get_plan(ts_server* sv, Job& j) {
-  auto it = sv->plans.find(j.key);
-  if (it != sv->plans.end()) {
-    ++sv->plan_hits;
-    j.plan = it->second;
-    return TS_OK;
+// Plan of a job from the server's cache, built on a miss (called by planner threads).
+ts_status get_plan(ts_server* sv, Job& j, cudaStream_t s) {
+  {
+    std::lock_guard<std::mutex> lk(sv->plan_mu);
+    auto it = sv->plans.find(j.key);
+    if (it != sv->plans.end()) {
+      ++sv->plan_hits;
+      j.plan_ref = it->second;
+      j.plan = j.plan_ref.get();
+      return TS_OK;
+    }
   }
-  ++sv->plan_misses;
-  std::vector<const double*> fp(j.req.grid.d);
-  for (int k = 0; k < j.req.grid.d; ++k) fp[k] = j.f[k].data();
+  std::vector<const double*> fp(j.key.d);
+  for (int k = 0; k < j.key.d; ++k) fp[k] = j.f[k].data();
   ts_plan_desc desc = j.req.grid;
+  desc.d = j.key.d;
   desc.f = fp.data();
   desc.n = j.key.n.data();
   desc.L = j.key.L.data();
-  ts_plan* p = nullptr;
   unsigned mask = (1u << TS_BF16X3) | (1u << TS_BF16X6);
   bool small = true;
-  for (int k = 0; k < j.req.grid.d; ++k) small &= j.key.n[k] == 8 || j.key.n[k] == 16 || j.key.n[k] == 24 || j.key.n[k] == 32;
+  for (int k = 0; k < j.key.d; ++k) small &= j.key.n[k] == 8 || j.key.n[k] == 16 || j.key.n[k] == 24 || j.key.n[k] == 32;
   if (small) mask |= 1u << TS_FP32;
-  TS_TRY(ts_plan_create(&desc, mask, sv->capture_stream, &p));
-  // Evict the least recently created plans beyond the cache size (none is in use: the
-  // scheduler only evicts when nothing is in flight).
-  sv->plans[j.key] = p;
-  sv->plan_lru.push_back(j.key);
-  j.plan = p;
+  ts_plan* p = nullptr;
+  TS_TRY(ts_plan_create(&desc, mask, s, &p));
+  PlanPtr pp(p, [](ts_plan* q) { ts_plan_destroy(q); });
+  std::lock_guard<std::mutex> lk(sv->plan_mu);
+  auto it = sv->plans.find(j.key);
+  if (it != sv->plans.end()) {
+    pp = it->second;  // built concurrently by another planner
+  } else {
+    ++sv->plan_misses;
+    sv->plans[j.key] = pp;
+    sv->plan_lru.push_back(j.key);
+    while ((int)sv->plan_lru.size() > sv->cfg.plan_cache_entries) {  // running jobs keep their own reference
+      sv->plans.erase(sv->plan_lru.front());
+      sv->plan_lru.pop_front();
+    }
+  }
+  j.plan_ref = pp;
+  j.plan = pp.get();
   return TS_OK;
 }
 
-void evict_plans(ts_server* sv) {
-  while ((int)sv->plan_lru.size() > sv->cfg.plan_cache_entries && sv->inflight == 0) {
-    auto it = sv->plans.find(sv->plan_lru.front());
-    if (it != sv->plans.end()) {
-      ts_plan_destroy(it->second);
-      sv->plans.erase(it);
+void planner_loop(ts_server* sv, int idx) {
+  cudaSetDevice(sv->device);
+  while (true) {
+    std::shared_ptr<Job> jp;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv_plan.wait(lk, [&] { return sv->stop || !sv->to_plan.empty(); });
+      if (sv->to_plan.empty()) return;
+      jp = sv->to_plan.front();
+      sv->to_plan.pop_front();
     }
-    sv->plan_lru.pop_front();
+    ts_status st = get_plan(sv, *jp, sv->planner_streams[idx]);
+    char msg[256] = "";
+    if (st != TS_OK) snprintf(msg, sizeof(msg), "%s", ts_last_error());
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      jp->plan_status = st;
+      if (st != TS_OK) snprintf(jp->msg, sizeof(jp->msg), "%s", msg);
+      jp->plan_ready = true;
+    }
+    sv->cv_work.notify_all();
   }
 }
 
@@ -176,6 +217,7 @@ void finish(ts_server* sv, Job& j, ts_status st) {
   const double ms = std::chrono::duration<double, std::milli>(j.t_done - j.t_submit).count();
   sv->latencies_ms.push_back(ms);
   sv->dof_done += (double)(j.plan ? j.plan->N : 0);
+  j.plan_ref.reset();  // the cache may drop the plan now
   if (!sv->have_first || j.t_submit < sv->t_first) sv->t_first = j.t_submit;
   sv->have_first = true;
   if (j.t_done > sv->t_last) sv->t_last = j.t_done;
@@ -222,7 +264,7 @@ void worker_loop(ts_server* sv) {
     // 2. admission
     std::vector<std::shared_ptr<Job>> batch, pcg;
     while (!sv->pending.empty() && sv->inflight < sv->cfg.max_inflight &&
-           (int)batch.size() < sv->cfg.max_batch) {
+           (int)batch.size() < sv->cfg.max_batch && sv->pending.front()->plan_ready) {
       auto jp = sv->pending.front();
       if (jp->footprint > (size_t)sv->cfg.memory_budget_bytes) {
         sv->pending.pop_front();
@@ -243,9 +285,8 @@ void worker_loop(ts_server* sv) {
         }
       if (slot < 0) break;
       sv->pending.pop_front();
-      ts_status st = get_plan(sv, *jp);
+      ts_status st = jp->plan_status;
       if (st != TS_OK) {
-        snprintf(jp->msg, sizeof(jp->msg), "%s", ts_last_error());
         ++sv->inflight;
         sv->mem_used += jp->footprint;
         finish(sv, *jp, st);
@@ -305,7 +346,6 @@ void worker_loop(ts_server* sv) {
         sv->cv_done.notify_all();
       }
     }
-    evict_plans(sv);
     // 4. wait for new work or poll the GPU
     if (sv->batches_inflight.empty() && (sv->pending.empty() || sv->inflight >= sv->cfg.max_inflight))
       sv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
@@ -334,7 +374,7 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   if (cfg) sv->cfg = *cfg;
   if (sv->cfg.max_inflight <= 0) sv->cfg.max_inflight = 8;
   if (sv->cfg.max_batch <= 0) sv->cfg.max_batch = sv->cfg.max_inflight;
-  if (sv->cfg.plan_cache_entries <= 0) sv->cfg.plan_cache_entries = 64;
+  if (sv->cfg.plan_cache_entries <= 0) sv->cfg.plan_cache_entries = 1024;
   TS_CHECK_CUDA(cudaGetDevice(&sv->device));
   if (sv->cfg.memory_budget_bytes <= 0) {
     size_t fr = 0, tot = 0;
@@ -346,6 +386,10 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   for (auto& s : sv->streams) TS_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   TS_CHECK_CUDA(cudaStreamCreateWithFlags(&sv->capture_stream, cudaStreamNonBlocking));
   TS_TRY(tc_prepare_kernels());
+  const int nplanners = 2;
+  sv->planner_streams.resize(nplanners);
+  for (auto& s : sv->planner_streams) TS_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  for (int i = 0; i < nplanners; ++i) sv->planners.emplace_back(planner_loop, sv, i);
   sv->worker = std::thread(worker_loop, sv);
   *out = sv;
   return TS_OK;
@@ -386,8 +430,10 @@ ts_status ts_server_submit(ts_server* sv, const ts_request* r, long long* ticket
     jp->ticket = sv->next_ticket++;
     sv->jobs[jp->ticket] = jp;
     sv->pending.push_back(jp);
+    sv->to_plan.push_back(jp);
     *ticket = jp->ticket;
   }
+  sv->cv_plan.notify_one();
   sv->cv_work.notify_all();
   return TS_OK;
 }
@@ -459,9 +505,12 @@ ts_status ts_server_destroy(ts_server* sv) {
     sv->stop = true;
   }
   sv->cv_work.notify_all();
+  sv->cv_plan.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
-  for (auto& kv : sv->plans) ts_plan_destroy(kv.second);
+  for (auto& t : sv->planners) t.join();
+  sv->plans.clear();
   for (auto s : sv->streams) cudaStreamDestroy(s);
+  for (auto s : sv->planner_streams) cudaStreamDestroy(s);
   if (sv->capture_stream) cudaStreamDestroy(sv->capture_stream);
   delete sv;
   return TS_OK;

@@ -327,17 +327,21 @@ bool small_n_supported(const ts_plan* p) {
 
 ts_status build_small_tables(ts_plan* p, cudaStream_t s) {
   for (int k = 0; k < p->d; ++k) {
-    if (p->owner[k] != k) {
-      p->Sf32[k] = p->Sf32[p->owner[k]];
-      p->Stf32[k] = p->Stf32[p->owner[k]];
-      continue;
+    AxisTables* t = p->axis[k].get();
+    std::lock_guard<std::mutex> lk(t->mu);
+    if (!t->Sf32) {
+      const int cnt = t->n * t->n;
+      float* buf = nullptr;
+      TS_CHECK_CUDA(cudaMalloc(&buf, sizeof(float) * 2 * cnt));
+      k_to_f32_table<<<(cnt + 255) / 256, 256, 0, s>>>(t->S, t->St, buf, buf + cnt, cnt);
+      TS_LAUNCHED(1);
+      TS_CHECK_CUDA(cudaStreamSynchronize(s));
+      t->Stf32 = buf + cnt;
+      t->Sf32 = buf;
+      t->bytes += 8LL * cnt;
     }
-    const int cnt = p->n[k] * p->n[k];
-    TS_CHECK_CUDA(cudaMalloc(&p->Sf32[k], sizeof(float) * cnt));
-    TS_CHECK_CUDA(cudaMalloc(&p->Stf32[k], sizeof(float) * cnt));
-    p->bytes += 8LL * cnt;
-    k_to_f32_table<<<(cnt + 255) / 256, 256, 0, s>>>(p->S[k], p->St[k], p->Sf32[k], p->Stf32[k], cnt);
-    TS_LAUNCHED(1);
+    p->Sf32[k] = t->Sf32;
+    p->Stf32[k] = t->Stf32;
   }
   return TS_OK;
 }

@@ -300,7 +300,7 @@ class Server:
     it has been waited for."""
 
     def __init__(self, memory_budget_bytes: int = 0, max_inflight: int = 8, max_batch: int = 0,
-                 plan_cache_entries: int = 64):
+                 plan_cache_entries: int = 1024):
         cfg = _ServerConfig(memory_budget_bytes, max_inflight, max_batch, plan_cache_entries)
         h = C.c_void_p()
         _check(lib().ts_server_create(C.byref(cfg), C.byref(h)), "ts_server_create")
