@@ -207,10 +207,12 @@ ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double
  * Tile configuration of the split-precision tensor-core contraction (no counterpart in
  * the paper; set by the autotuner).  For real (complex_data = 0) or complex data and a
  * contracted axis of length n (n = 0: the default for all lengths): K chunk bk (64 =
- * 128-byte swizzled rows, 32 = 64-byte) and the cap bn_cap (multiple of 16, <= 256) on the
- * N tile.  Process-wide; takes effect for calls issued afterwards.
+ * 128-byte swizzled rows, 32 = 64-byte), the cap bn_cap (multiple of 16, <= 256) on the
+ * N tile, and `cluster` (1, 2 or 4): the number of CTAs of a thread-block cluster that
+ * share every S_k tile through TMA multicast, each loading 1/cluster of it.  Process-wide;
+ * takes effect for calls issued afterwards.
  */
-ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap);
+ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster);
 
 /* ------------------------------------------------------------------ serving ----- */
 /*
@@ -281,7 +283,7 @@ ts_status ts_server_destroy(ts_server* server);
  * Autotuner of the split-precision contraction (no counterpart in the paper).  For every
  * distinct axis length n of the plan and the data kind (dtype TS_R64: real data of
  * ts_apply_inverse; TS_C128: complex data of ts_apply_exp) it times the tile
- * configurations (K chunk 64 / 32, N-tile cap 256 / 128 / 64) on whole applies with CUDA
+ * configurations (K chunk 64 / 32, N-tile cap 256 / 128 / 64, cluster 1 / 2 / 4) on whole applies with CUDA
  * events on `stream`, keeps the fastest with ts_tc_config_set, and appends it to the text
  * file cache_path (NULL or "" = no file).  Entries already in the file are applied without
  * timing.  *tuned (may be NULL) = number of axis lengths searched.  Synchronises stream.

@@ -1,8 +1,9 @@
 // Autotuner of the split-precision tensor-core pass: for each distinct contracted extent
 // n of a plan and the data kind (real / complex), time the candidate tile configurations
-// (K chunk 64 or 32; N-tile cap 256, 128 or 64) on a whole apply with CUDA events, keep
-// the fastest through tc_config_set, and remember it in a plain-text cache file so later
-// processes skip the search.  Cache line: "<complex> <n> <prec> <bk> <bn_cap> <ms>".
+// (K chunk 64 or 32; N-tile cap 256, 128 or 64; 1, 2 or 4 CTAs per multicast cluster) on a
+// whole apply with CUDA events, keep the fastest through tc_config_set, and remember it in
+// a plain-text cache file so later processes skip the search.
+// Cache line: "<complex> <n> <prec> <bk> <bn_cap> <cluster> <ms>".
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -17,7 +18,7 @@ namespace ts {
 namespace {
 
 struct Entry {
-  int cplx, n, prec, bk, bn;
+  int cplx, n, prec, bk, bn, cm;
   double ms;
 };
 
@@ -29,7 +30,7 @@ std::vector<Entry> read_cache(const char* path) {
   while (std::getline(in, line)) {
     std::istringstream ss(line);
     Entry e{};
-    if (ss >> e.cplx >> e.n >> e.prec >> e.bk >> e.bn >> e.ms) out.push_back(e);
+    if (ss >> e.cplx >> e.n >> e.prec >> e.bk >> e.bn >> e.cm >> e.ms) out.push_back(e);
   }
   return out;
 }
@@ -37,7 +38,7 @@ std::vector<Entry> read_cache(const char* path) {
 void append_cache(const char* path, const Entry& e) {
   if (!path || !*path) return;
   std::ofstream out(path, std::ios::app);
-  out << e.cplx << " " << e.n << " " << e.prec << " " << e.bk << " " << e.bn << " " << e.ms << "\n";
+  out << e.cplx << " " << e.n << " " << e.prec << " " << e.bk << " " << e.bn << " " << e.cm << " " << e.ms << "\n";
 }
 
 ts_status time_apply(const ts_plan* p, ts_precision prec, bool cplx, void* in, void* out, cudaStream_t s,
@@ -102,7 +103,7 @@ extern "C" ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precisi
     for (const Entry& e : cache)
       if (e.cplx == cval && e.n == n && e.prec == (int)prec) hit = &e;
     if (hit) {
-      st = tc_config_set(cval, n, hit->bk, hit->bn);
+      st = tc_config_set(cval, n, hit->bk, hit->bn, hit->cm);
       continue;
     }
     if (!in) {
@@ -115,24 +116,27 @@ extern "C" ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precisi
       }
       if (st != TS_OK) break;
     }
-    Entry best{cval, n, (int)prec, 64, 256, 1e30};
+    Entry best{cval, n, (int)prec, 64, 256, 1, 1e30};
     const int bks[2] = {64, 32};
     const int bns[3] = {256, 128, 64};
+    const int cms[3] = {1, 2, 4};
     for (int bk : bks)
-      for (int bn : bns) {
-        if (st != TS_OK) break;
-        if (2 * (cplx ? 2 : 1) * bn > 512) continue;
-        st = tc_config_set(cval, n, bk, bn);
-        double ms = 0.0;
-        if (st == TS_OK) st = time_apply(plan, prec, cplx, in, out, s, 3, &ms);
-        if (st == TS_OK && ms < best.ms) {
-          best.bk = bk;
-          best.bn = bn;
-          best.ms = ms;
+      for (int bn : bns)
+        for (int cm : cms) {
+          if (st != TS_OK) break;
+          if (2 * (cplx ? 2 : 1) * bn > 512) continue;
+          st = tc_config_set(cval, n, bk, bn, cm);
+          double ms = 0.0;
+          if (st == TS_OK) st = time_apply(plan, prec, cplx, in, out, s, 3, &ms);
+          if (st == TS_OK && ms < best.ms) {
+            best.bk = bk;
+            best.bn = bn;
+            best.cm = cm;
+            best.ms = ms;
+          }
         }
-      }
     if (st == TS_OK) {
-      st = tc_config_set(cval, n, best.bk, best.bn);
+      st = tc_config_set(cval, n, best.bk, best.bn, best.cm);
       append_cache(cache_path, best);
       ++searched;
     }

@@ -201,9 +201,9 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
                                 lambda, outer_iters, pcg_iters, (cudaStream_t)stream);
 }
 
-ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap) {
+ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster) {
   clear_error();
-  return tc_config_set(complex_data, n, bk, bn_cap);
+  return tc_config_set(complex_data, n, bk, bn_cap, cluster);
 }
 
 ts_status ts_device_status(void* stream) {

@@ -108,7 +108,7 @@ __device__ __forceinline__ double f2d(float f) {
   return __longlong_as_double((long long)bits);
 }
 
-template <int NP, int NACC, int BKT, bool PLANES_OUT>
+template <int NP, int NACC, int BKT, bool PLANES_OUT, int CM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const EpiParams ep) {
   constexpr int SW = BKT * 2;  // bytes per smem row = swizzle width
@@ -133,7 +133,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int nk = (ep.n + BKT - 1) / BKT;
   const int mtiles = (int)((ep.R + BM - 1) / BM);
   const int ntiles = (ep.n + BN - 1) / BN;
-  const int total = mtiles * ntiles;
+  // Work units: with clusters of CM CTAs, unit t covers M tiles (t / ntiles) * CM + rank
+  // (one per CTA of the cluster) and N tile t % ntiles; the CTAs of a cluster share every
+  // B tile through TMA multicast, each loading BN / CM of its rows.
+  const int rank = CM > 1 ? (int)tc::cluster_ctarank() : 0;
+  const int unit0 = CM > 1 ? (int)tc::cluster_id_x() : (int)blockIdx.x;
+  const int unit_step = CM > 1 ? (int)tc::cluster_count_x() : (int)gridDim.x;
+  const int total = ((mtiles + CM - 1) / CM) * ntiles;
+  const uint16_t cta_mask = (uint16_t)((1u << CM) - 1u);
   const uint32_t acc_cols = NACC * BN;
   uint32_t ncols = 32;
   while (ncols < 2 * acc_cols) ncols <<= 1;
@@ -141,7 +148,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], CM);  // one arrival per CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&accf[b], 1);
@@ -158,6 +165,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
+  if (CM > 1) tc::cluster_sync();  // peers' barriers are initialised before any multicast
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -165,8 +173,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       // ---------------- TMA producer: a ring of NS stages that runs across tiles
       int it = 0;
-      for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int m0 = (t / ntiles) * BM, n0 = (t % ntiles) * BN;
+      const int bslice = BN / CM;
+      for (int t = unit0; t < total; t += unit_step) {
+        const int m0 = ((t / ntiles) * CM + rank) * BM, n0 = (t % ntiles) * BN;
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const int s = it % NS, round = it / NS;
           if (round > 0) tc::mbar_wait(&empty[s], (round - 1) & 1, &g_tc_error, 1);
@@ -175,8 +184,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int p = 0; p < NP; ++p)
               tc::tma_load_3d(sA + (size_t)s * A_STAGE + (c * NP + p) * A_TILE, &tmA, kc * BKT, m0, c * NP + p,
                               &full[s]);
-          for (int p = 0; p < NP; ++p)
-            tc::tma_load_3d(sB + (size_t)s * B_STAGE + p * B_TILE, &tmB, kc * BKT, n0, p, &full[s]);
+          for (int p = 0; p < NP; ++p) {
+            if (CM == 1)
+              tc::tma_load_3d(sB + (size_t)s * B_STAGE + p * B_TILE, &tmB, kc * BKT, n0, p, &full[s]);
+            else
+              tc::tma_load_3d_mc(sB + (size_t)s * B_STAGE + p * B_TILE + rank * bslice * SW, &tmB, kc * BKT,
+                                 n0 + rank * bslice, p, &full[s], cta_mask);
+          }
         }
       }
     }
@@ -185,7 +199,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // ---------------- MMA issuer
       const uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
       int it = 0, tl = 0;
-      for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+      for (int t = unit0; t < total; t += unit_step, ++tl) {
         const int ab = tl & 1, use = tl >> 1;
         if (use > 0) tc::mbar_wait(&acce[ab], (use - 1) & 1, &g_tc_error, 4);
         tc::tc_fence_after();
@@ -208,7 +222,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               }
             }
           }
-          tc::mma_commit(&empty[s]);
+          if (CM == 1)
+            tc::mma_commit(&empty[s]);
+          else
+            tc::mma_commit_mc(&empty[s], cta_mask);  // the stage is free once every CTA is done with it
         }
         tc::mma_commit(&accf[ab]);
       }
@@ -219,9 +236,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int g = warp & 3;
     const int half = (warp - 2) >> 2;
     int tl = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+    for (int t = unit0; t < total; t += unit_step, ++tl) {
       const int ab = tl & 1, use = tl >> 1;
-      const long long m0 = (long long)(t / ntiles) * BM;
+      const long long m0 = (long long)((t / ntiles) * CM + rank) * BM;
       const int n0 = (t % ntiles) * BN;
       tc::mbar_wait(&accf[ab], use & 1, &g_tc_error, 3);
       __syncwarp();
@@ -309,6 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncwarp();
   tc::tc_fence_before();
   __syncthreads();
+  if (CM > 1) tc::cluster_sync();  // no CTA leaves while a peer may still multicast into it
   if (warp == 0) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, ncols);
@@ -408,11 +426,15 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
 
 int g_num_sms = 0;
 
-template <int NP, int NACC, int BKT, bool PO>
+template <int NP, int NACC, int BKT, bool PO, int CM>
 ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
                         int bn_cap, cudaStream_t s) {
   int bn = ((n + 15) / 16) * 16;
   if (bn > bn_cap) bn = bn_cap;
+  if (CM > 1 && (bn % (8 * CM) != 0)) {
+    set_error("N tile %d cannot be split into %d multicast slices of whole 8-row atoms", bn, CM);
+    return TS_ERR_UNSUPPORTED;
+  }
   const int stage = NACC * NP * BM * BKT * 2 + NP * bn * BKT * 2;
   const int reserve = 1024 + 8 * (2 * MAX_STAGES + 6);
   int ns = (SMEM_LIMIT - reserve) / stage;
@@ -424,7 +446,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   const int smem = ns * stage + reserve;
   CUtensorMap ma, mb;
   TS_TRY(make_map(&ma, A, n, R, NACC * NP, BKT, BM));
-  TS_TRY(make_map(&mb, B, n, n, NP, BKT, bn));
+  TS_TRY(make_map(&mb, B, n, n, NP, BKT, bn / CM));
   ep.R = R;
   ep.n = n;
   ep.N = R * n;
@@ -433,7 +455,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     TS_CHECK_CUDA(
-        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
+        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
     attr_set = true;
   }
   if (g_num_sms == 0) {
@@ -441,12 +463,30 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
     TS_CHECK_CUDA(cudaGetDevice(&dev));
     TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  const long long tiles = ((R + BM - 1) / BM) * ((n + bn - 1) / bn);
-  TS_REQUIRE(tiles < (1LL << 31), "too many tiles");
-  const unsigned grid = (unsigned)(tiles < g_num_sms ? tiles : g_num_sms);
+  const long long mtiles = (R + BM - 1) / BM, ntiles = (n + bn - 1) / bn;
+  const long long units = ((mtiles + CM - 1) / CM) * ntiles;
+  TS_REQUIRE(units * CM < (1LL << 31), "too many tiles");
+  const long long max_clusters = g_num_sms / CM;
+  const unsigned grid = (unsigned)((units < max_clusters ? units : max_clusters) * CM);
   void* tok = nullptr;
   if (prof_enabled()) prof_begin_launch(s, &tok);
-  k_rot_tc<NP, NACC, BKT, PO><<<grid, TC_THREADS, smem, s>>>(ma, mb, ep);
+  if (CM == 1) {
+    k_rot_tc<NP, NACC, BKT, PO, 1><<<grid, TC_THREADS, smem, s>>>(ma, mb, ep);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CM;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_rot_tc<NP, NACC, BKT, PO, CM>, ma, mb, ep));
+  }
   TS_LAUNCHED(1);
   if (tok) {
     const double flops = 2.0 * Products<NP>::count * NACC * (double)R * n * n;
@@ -463,6 +503,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
 struct TcConfig {
   int bk = 64;
   int bn_cap = 256;
+  int cm = 1;  // CTAs per cluster sharing each B tile by multicast (1, 2 or 4)
 };
 
 std::mutex g_cfg_mu;
@@ -477,6 +518,7 @@ TcConfig lookup_config(int nacc, int n) {
   TcConfig c;
   c.bk = 64;
   c.bn_cap = nacc == 1 ? 256 : 128;
+  c.cm = 1;
   return c;
 }
 
@@ -485,6 +527,11 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
                       cudaStream_t s) {
   TcConfig c = lookup_config(NACC, n);
   if (2 * NACC * c.bn_cap > 512) c.bn_cap = 256 / NACC;  // two accumulator buffers must fit in TMEM
+  {
+    int bn = ((n + 15) / 16) * 16;
+    if (bn > c.bn_cap) bn = c.bn_cap;
+    while (c.cm > 1 && bn % (8 * c.cm) != 0) c.cm /= 2;  // multicast slices are whole 8-row atoms
+  }
   // Fall back to a narrower K chunk, then a narrower N tile, until two stages fit.
   const int reserve = 1024 + 8 * (2 * MAX_STAGES + 6);
   for (;;) {
@@ -500,11 +547,18 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
       break;
   }
   if (ep.out_mode == 0) {
-    if (c.bk == 32) return launch_pass_t<NP, NACC, 32, true>(A, B, R, n, ep, c.bn_cap, s);
-    return launch_pass_t<NP, NACC, 64, true>(A, B, R, n, ep, c.bn_cap, s);
+  #define TS_CM_DISPATCH(BKT, PO)                                                              \
+  switch (c.cm) {                                                                            \
+    case 2: return launch_pass_t<NP, NACC, BKT, PO, 2>(A, B, R, n, ep, c.bn_cap, s);         \
+    case 4: return launch_pass_t<NP, NACC, BKT, PO, 4>(A, B, R, n, ep, c.bn_cap, s);         \
+    default: return launch_pass_t<NP, NACC, BKT, PO, 1>(A, B, R, n, ep, c.bn_cap, s);        \
   }
-  if (c.bk == 32) return launch_pass_t<NP, NACC, 32, false>(A, B, R, n, ep, c.bn_cap, s);
-  return launch_pass_t<NP, NACC, 64, false>(A, B, R, n, ep, c.bn_cap, s);
+    if (c.bk == 32) TS_CM_DISPATCH(32, true);
+    TS_CM_DISPATCH(64, true);
+  }
+  if (c.bk == 32) TS_CM_DISPATCH(32, false);
+  TS_CM_DISPATCH(64, false);
+#undef TS_CM_DISPATCH
 }
 
 ts_status pass(int np, int nacc, const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n,
@@ -698,13 +752,15 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
 
 ts_status tc_prepare_kernels() {
   // Shared-memory opt-in for every instantiation, outside any stream capture.
-#define TS_PREP(NP, NACC, BKT, PO)                                                                           \
-  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+#define TS_PREP1(NP, NACC, BKT, PO, CM)                                                                          \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      SMEM_LIMIT))
+#define TS_PREP(NP, NACC, BKT, PO) TS_PREP1(NP, NACC, BKT, PO, 1); TS_PREP1(NP, NACC, BKT, PO, 2); TS_PREP1(NP, NACC, BKT, PO, 4)
   TS_PREP(2, 1, 64, true); TS_PREP(2, 1, 64, false); TS_PREP(2, 1, 32, true); TS_PREP(2, 1, 32, false);
   TS_PREP(2, 2, 64, true); TS_PREP(2, 2, 64, false); TS_PREP(2, 2, 32, true); TS_PREP(2, 2, 32, false);
   TS_PREP(3, 1, 64, true); TS_PREP(3, 1, 64, false); TS_PREP(3, 1, 32, true); TS_PREP(3, 1, 32, false);
   TS_PREP(3, 2, 64, true); TS_PREP(3, 2, 64, false); TS_PREP(3, 2, 32, true); TS_PREP(3, 2, 32, false);
+#undef TS_PREP1
 #undef TS_PREP
   if (g_num_sms == 0) {
     int dev = 0;
@@ -714,15 +770,17 @@ ts_status tc_prepare_kernels() {
   return TS_OK;
 }
 
-ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap) {
-  if ((bk != 32 && bk != 64) || bn_cap < 16 || bn_cap > 256 || bn_cap % 16 != 0 || n < 0) {
-    set_error("invalid tensor-core tile configuration (bk %d, bn_cap %d)", bk, bn_cap);
+ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster) {
+  if ((bk != 32 && bk != 64) || bn_cap < 16 || bn_cap > 256 || bn_cap % 16 != 0 || n < 0 ||
+      (cluster != 1 && cluster != 2 && cluster != 4)) {
+    set_error("invalid tensor-core tile configuration (bk %d, bn_cap %d, cluster %d)", bk, bn_cap, cluster);
     return TS_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lk(g_cfg_mu);
   TcConfig c;
   c.bk = bk;
   c.bn_cap = bn_cap;
+  c.cm = cluster;
   g_cfg[{complex_data ? 2 : 1, n}] = c;
   return TS_OK;
 }

@@ -33,8 +33,9 @@ ts_status mixed_error_flag(int* host_flag, bool reset, cudaStream_t s);
 ts_status tc_prepare_kernels();
 
 // Tile configuration of the tensor-core pass for data of the given kind and contracted
-// extent n (n = 0: default for every n): K chunk bk (64 or 32) and N-tile cap bn_cap.
-ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap);
+// extent n (n = 0: default for every n): K chunk bk (64 or 32), N-tile cap bn_cap and the
+// cluster size sharing each B tile by multicast (1, 2, 4).
+ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster);
 
 // Build the split planes of S_k^T and S_k for precision `prec` (plan creation).
 ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s);

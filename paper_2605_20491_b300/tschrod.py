@@ -102,7 +102,7 @@ def lib() -> C.CDLL:
     L.ts_server_stats.argtypes = [vp, C.POINTER(_ServingStats)]
     L.ts_server_reset_stats.argtypes = [vp]
     L.ts_server_destroy.argtypes = [vp]
-    L.ts_tc_config_set.argtypes = [ip, ip, ip, ip]
+    L.ts_tc_config_set.argtypes = [ip, ip, ip, ip, ip]
     L.ts_autotune.argtypes = [vp, ip, ip, C.c_char_p, C.POINTER(ip), vp]
     L.ts_launch_count.argtypes = []
     L.ts_profile_begin.argtypes = []
@@ -255,8 +255,8 @@ def ts_inverse_iteration(plan: Plan, shift: float, V2, u, init_from_plan: bool =
     return lam.value, outer.value, tot.value
 
 
-def ts_tc_config_set(complex_data: bool, n: int, bk: int, bn_cap: int):
-    _check(lib().ts_tc_config_set(int(complex_data), n, bk, bn_cap), "ts_tc_config_set")
+def ts_tc_config_set(complex_data: bool, n: int, bk: int, bn_cap: int, cluster: int = 1):
+    _check(lib().ts_tc_config_set(int(complex_data), n, bk, bn_cap, cluster), "ts_tc_config_set")
 
 
 def ts_autotune(plan: Plan, dtype: int, prec: int, cache_path: str | None = None, stream=None) -> int:
