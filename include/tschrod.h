@@ -313,6 +313,15 @@ ts_status ts_profile_end(int kind, long long* launches, double* total_ms, double
  */
 ts_status ts_device_status(void* stream);
 
+/*
+ * Self-test of the failure path above (no counterpart in the paper): launches one thread
+ * that waits, with the same bounded wait as the tensor-core kernels, on a barrier that
+ * nothing arrives on.  After `cycles` clock cycles (0 < cycles <= 4e9) the wait gives up,
+ * sets the device flag and the kernel returns; the next ts_device_status reports
+ * TS_ERR_TIMEOUT and the context stays usable.
+ */
+ts_status ts_selftest_wait_timeout(long long cycles, void* stream);
+
 /* Thread-local message of the calling thread's last failing call ("" if none). */
 const char* ts_last_error(void);
 

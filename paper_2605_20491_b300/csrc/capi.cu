@@ -206,6 +206,12 @@ ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap, int clus
   return tc_config_set(complex_data, n, bk, bn_cap, cluster);
 }
 
+ts_status ts_selftest_wait_timeout(long long cycles, void* stream) {
+  clear_error();
+  TS_REQUIRE(cycles > 0 && cycles <= 4000000000LL, "cycles must be in (0, 4e9]");
+  return wait_selftest(cycles, (cudaStream_t)stream);
+}
+
 ts_status ts_device_status(void* stream) {
   clear_error();
   int flag = 0;

@@ -785,6 +785,31 @@ ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster
   return TS_OK;
 }
 
+namespace {
+// One thread waits, with the kernels' bounded wait, on a barrier that nothing arrives on;
+// after `cycles` clocks the wait gives up, records code 9 and the kernel returns.
+__global__ void k_wait_selftest(long long cycles) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  tc::fence_barrier_init();
+  if (tc::mbar_try_wait(&bar, 0)) return;
+  const long long t0 = clock64();
+  while (!tc::mbar_try_wait(&bar, 0)) {
+    if (clock64() - t0 > cycles) {
+      atomicExch(&g_tc_error, 9);
+      return;
+    }
+  }
+}
+}  // namespace
+
+ts_status wait_selftest(long long cycles, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(cycles);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
 ts_status mixed_error_flag(int* host_flag, bool reset, cudaStream_t s) {
   TS_CHECK_CUDA(cudaMemcpyFromSymbolAsync(host_flag, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
   TS_CHECK_CUDA(cudaStreamSynchronize(s));

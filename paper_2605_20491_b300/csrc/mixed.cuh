@@ -37,6 +37,10 @@ ts_status tc_prepare_kernels();
 // cluster size sharing each B tile by multicast (1, 2, 4).
 ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster);
 
+// Self-test of the bounded device wait: a kernel waits `cycles` clocks on a barrier that
+// nothing arrives on, then records a timeout in the device flag and returns.
+ts_status wait_selftest(long long cycles, cudaStream_t s);
+
 // Build the split planes of S_k^T and S_k for precision `prec` (plan creation).
 ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s);
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
-    "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
+    "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_selftest_wait_timeout", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
     "ts_last_error", "ts_version",
 ]
 
@@ -95,6 +95,7 @@ def lib() -> C.CDLL:
                                        C.POINTER(C.c_longlong), vp]
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
     L.ts_device_status.argtypes = [vp]
+    L.ts_selftest_wait_timeout.argtypes = [C.c_longlong, vp]
     L.ts_server_create.argtypes = [C.POINTER(_ServerConfig), C.POINTER(vp)]
     L.ts_server_submit.argtypes = [vp, C.POINTER(_Request), C.POINTER(C.c_longlong)]
     L.ts_server_wait.argtypes = [vp, C.c_longlong, C.POINTER(ip), C.POINTER(dp), C.POINTER(ip)]
@@ -265,6 +266,10 @@ def ts_autotune(plan: Plan, dtype: int, prec: int, cache_path: str | None = None
     path = cache_path.encode() if cache_path else None
     _check(lib().ts_autotune(plan.handle, dtype, prec, path, C.byref(tuned), _stream(stream)), "ts_autotune")
     return tuned.value
+
+
+def ts_selftest_wait_timeout(cycles: int, stream=None):
+    _check(lib().ts_selftest_wait_timeout(cycles, _stream(stream)), "ts_selftest_wait_timeout")
 
 
 def ts_launch_count() -> int:
