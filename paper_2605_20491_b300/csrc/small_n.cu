@@ -8,7 +8,9 @@
 // tile of T consecutive lo-indices (or, for k0 = 0, T consecutive hi-indices) times all G
 // group indices: runs of >= 8 contiguous elements in HBM, so loads and stores coalesce.
 // Input and output may be the same array: a CTA reads its whole tile before writing it.
-// In shared memory the tile is stored with every group extent padded to an odd length,
+// CTAs are persistent over tiles and double-buffer them: while one tile is contracted the
+// next one arrives by cp.async.  In shared memory the tile is stored with every group
+// extent padded to an odd length,
 // so that the fibers of any mode start on distinct banks.  Each mode is contracted by
 // per-thread fibers held in registers (n complex values in, n out, 2 n^2 FFMA per fiber)
 // with the n x n matrix read from shared memory as broadcasts, in place.  The last group
@@ -134,95 +136,138 @@ __device__ __forceinline__ int tile_index(int e, int lgTlo, const GroupParams& p
   return sidx + r * mul;
 }
 
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
+
+// First element of tile b: (l0, h0) as in the tiling described at the top.
+__device__ __forceinline__ void tile_origin(long long b, int lgTlo, int Thi, const GroupParams& p, long long* l0,
+                                            long long* h0) {
+  if (p.lo > 1) {
+    const long long lblocks = p.lo >> lgTlo;
+    *l0 = (b % lblocks) << lgTlo;
+    *h0 = b / lblocks;
+  } else {
+    *l0 = 0;
+    *h0 = b * Thi;
+  }
+}
+
+// Persistent over tiles with two shared-memory tile buffers: the next tile's elements are
+// copied asynchronously (cp.async, one 8-byte copy per element into the padded layout)
+// while the current tile is contracted, so global-load latency overlaps arithmetic.
 template <int N>
-__global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, float2* Y, const GroupParams p) {
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, float2* Y, const GroupParams p,
+                                                               long long ntiles) {
   extern __shared__ float2 smem[];
-  float2* tile = smem;
   const int lgT = 31 - __clz(p.T);
   const int lgTlo = p.lo > 1 ? lgT : 0;
   const int Tlo = 1 << lgTlo;
   const int Thi = p.lo > 1 ? 1 : p.T;
   const int tile_pad = Tlo * (int)p.Gpad * Thi;
-  float2* rowph = tile + tile_pad;                              // Tlo phase factors (middle pass)
-  // matrices start 16-byte aligned (tile_pad + Tlo rounded up to an even float2 count)
-  float* mats = reinterpret_cast<float*>(tile + ((tile_pad + Tlo + 1) & ~1));
+  const int tile_stride = (tile_pad + 1) & ~1;  // keep every buffer 16-byte aligned
+  float2* buf[2] = {smem, smem + tile_stride};
+  float2* rowph = smem + 2 * tile_stride;                         // Tlo phase factors (middle pass)
+  float* mats = reinterpret_cast<float*>(smem + 2 * tile_stride + ((Tlo + 1) & ~1));
   const int msz = N * N;
   for (int e = threadIdx.x; e < p.nm * msz; e += blockDim.x) {
     const int m = e / msz, q = e % msz;
     if (p.do_fwd) mats[m * msz + q] = p.fwd[m][q];
     if (p.do_bwd) mats[(p.nm + m) * msz + q] = p.bwd[m][q];
   }
-  long long l0 = 0, h0 = 0;
-  if (p.lo > 1) {
-    const long long lblocks = p.lo >> lgTlo;
-    l0 = (blockIdx.x % lblocks) << lgTlo;
-    h0 = blockIdx.x / lblocks;
-  } else {
-    h0 = (long long)blockIdx.x * Thi;
-  }
-  if (p.do_phase) {
-    // phase factor of the axes below the group, one per t (the last group has no axes above)
-    for (int t = threadIdx.x; t < Tlo; t += blockDim.x) {
-      long long q = l0 + t;
-      float2 ph = make_float2(1.f, 0.f);
-      for (int k = 0; k < p.k0; ++k) {
-        const int ik = (int)(q % p.n_all[k]);
-        q /= p.n_all[k];
-        ph = cmulf(ph, p.ph[k][ik]);
-      }
-      rowph[t] = ph;
-    }
-  }
   const int cnt = Tlo * (int)p.G * Thi;
-  const long long gbase = l0 + p.lo * p.G * h0;
-  // ---- load (global order: t fastest, then the group indices, then th)
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    int g, th;
-    const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-    const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
-    float2 v = X[gidx];
-    if (p.V2 && p.theta_pre != 0.f) v = vphase(v, p.theta_pre, p.V2[gidx]);
-    tile[sidx] = v;
-  }
-  __syncthreads();
-  if (p.do_fwd) {
-    for (int m = 0; m < p.nm; ++m) {
-      contract_mode<N>(tile, mats + m * msz, m, p, lgTlo, Thi);
-      __syncthreads();
-    }
-  }
-  if (p.do_phase) {
+  auto issue_load = [&](long long b, float2* dst) {
+    long long l0, h0;
+    tile_origin(b, lgTlo, Thi, p, &l0, &h0);
+    const long long gbase = l0 + p.lo * p.G * h0;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int t = e & (Tlo - 1);
-      int r = e >> lgTlo;
-      int sidx = t, mul = Tlo;
-      float2 ph = rowph[t];
-      for (int j = 0; j < p.nm; ++j) {
-        const int ij = r % N;
-        r /= N;
-        sidx += ij * mul;
-        mul *= p.npad[j];
-        ph = cmulf(ph, p.ph[p.k0 + j][ij]);
-      }
-      sidx += r * mul;
-      tile[sidx] = cmulf(tile[sidx], ph);
+      int g, th;
+      const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+      cp_async8(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th));
+    }
+    cp_async_commit();
+  };
+  long long b = blockIdx.x;
+  if (b < ntiles) issue_load(b, buf[0]);
+  int cur = 0;
+  for (; b < ntiles; b += gridDim.x, cur ^= 1) {
+    const long long bn = b + gridDim.x;
+    if (bn < ntiles) {
+      issue_load(bn, buf[cur ^ 1]);
+      cp_async_wait<1>();  // the current tile's group has landed
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-  }
-  if (p.do_bwd) {
-    for (int m = p.nm - 1; m >= 0; --m) {
-      contract_mode<N>(tile, mats + (p.nm + m) * msz, m, p, lgTlo, Thi);
+    float2* tile = buf[cur];
+    long long l0, h0;
+    tile_origin(b, lgTlo, Thi, p, &l0, &h0);
+    const long long gbase = l0 + p.lo * p.G * h0;
+    if (p.V2 && p.theta_pre != 0.f) {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int g, th;
+        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
+        tile[sidx] = vphase(tile[sidx], p.theta_pre, p.V2[gidx]);
+      }
       __syncthreads();
     }
-  }
-  // ---- store
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    int g, th;
-    const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-    const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
-    float2 v = tile[sidx];
-    if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, p.V2[gidx]);
-    Y[gidx] = v;
+    if (p.do_fwd) {
+      for (int m = 0; m < p.nm; ++m) {
+        contract_mode<N>(tile, mats + m * msz, m, p, lgTlo, Thi);
+        __syncthreads();
+      }
+    }
+    if (p.do_phase) {
+      // phase factor of the axes below the group, one per t (the last group has no axes above)
+      for (int t = threadIdx.x; t < Tlo; t += blockDim.x) {
+        long long q = l0 + t;
+        float2 ph = make_float2(1.f, 0.f);
+        for (int k = 0; k < p.k0; ++k) {
+          const int ik = (int)(q % p.n_all[k]);
+          q /= p.n_all[k];
+          ph = cmulf(ph, p.ph[k][ik]);
+        }
+        rowph[t] = ph;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int t = e & (Tlo - 1);
+        int r = e >> lgTlo;
+        int sidx = t, mul = Tlo;
+        float2 ph = rowph[t];
+        for (int j = 0; j < p.nm; ++j) {
+          const int ij = r % N;
+          r /= N;
+          sidx += ij * mul;
+          mul *= p.npad[j];
+          ph = cmulf(ph, p.ph[p.k0 + j][ij]);
+        }
+        sidx += r * mul;
+        tile[sidx] = cmulf(tile[sidx], ph);
+      }
+      __syncthreads();
+    }
+    if (p.do_bwd) {
+      for (int m = p.nm - 1; m >= 0; --m) {
+        contract_mode<N>(tile, mats + (p.nm + m) * msz, m, p, lgTlo, Thi);
+        __syncthreads();
+      }
+    }
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      int g, th;
+      const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+      const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
+      float2 v = tile[sidx];
+      if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, p.V2[gidx]);
+      Y[gidx] = v;
+    }
+    __syncthreads();  // the buffer is refilled two iterations later
   }
 }
 
@@ -248,7 +293,7 @@ __global__ void k_to_f32_table(const double* S, const double* St, float* Sf, flo
   }
 }
 
-constexpr size_t TILE_BUDGET = 80 * 1024;  // bytes of complex64 tile per CTA
+constexpr size_t TILE_BUDGET = 48 * 1024;  // bytes of one complex64 tile buffer (two per CTA)
 
 int odd(int n) { return n | 1; }
 
@@ -281,21 +326,31 @@ std::vector<Group> make_groups(const ts_plan* p) {
   return gs;
 }
 
+int g_small_sms = 0;
+
 template <int N>
 ts_status launch_group(const float2* X, float2* Y, const GroupParams& gp, cudaStream_t s) {
   const int Tlo = gp.lo > 1 ? gp.T : 1, Thi = gp.lo > 1 ? 1 : gp.T;
-  const size_t smem = sizeof(float2) * (((size_t)Tlo * gp.Gpad * Thi + Tlo + 1) & ~size_t(1)) +
-                      sizeof(float) * 2 * gp.nm * N * N;
+  const size_t tile_stride = ((size_t)Tlo * gp.Gpad * Thi + 1) & ~size_t(1);
+  const size_t smem = sizeof(float2) * (2 * tile_stride + ((Tlo + 1) & ~1)) + sizeof(float) * 2 * gp.nm * N * N;
   static bool attr = false;
   if (!attr) {
     TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
-  const long long blocks = gp.lo > 1 ? (gp.lo / Tlo) * gp.hi : gp.hi / Thi;
-  TS_REQUIRE(blocks < (1LL << 31), "small-n grid too large");
+  if (g_small_sms == 0) {
+    int dev = 0;
+    TS_CHECK_CUDA(cudaGetDevice(&dev));
+    TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_small_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long long tiles = gp.lo > 1 ? (gp.lo / Tlo) * gp.hi : gp.hi / Thi;
+  int per_sm = 0;
+  TS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_group<N>, SMALL_THREADS, smem));
+  if (per_sm < 1) per_sm = 1;
+  const long long grid = tiles < (long long)g_small_sms * per_sm ? tiles : (long long)g_small_sms * per_sm;
   void* tok = nullptr;
   if (prof_enabled()) prof_begin_launch(s, &tok);
-  k_small_group<N><<<(unsigned)blocks, SMALL_THREADS, smem, s>>>(X, Y, gp);
+  k_small_group<N><<<(unsigned)grid, SMALL_THREADS, smem, s>>>(X, Y, gp, tiles);
   TS_LAUNCHED(1);
   if (tok) {
     const long long N_all = gp.lo * gp.G * gp.hi;
