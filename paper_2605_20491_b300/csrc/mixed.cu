@@ -739,9 +739,14 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
   // u_0 = P b
   if (st == TS_OK) st = split_input(np, TS_R64, b, buf[0], N, s);
   if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s);
-  // u_{k+1} = u_k + P (b - A u_k), residual in FP64, split straight into the planes
+  // u_{k+1} = u_k + P (b - A u_k), residual in FP64 (its Laplacian part in exact fixed
+  // point on isotropic grids), split straight into the planes
+  const bool fixed = isotropic_h(p);
   for (int it = 0; it < refinements && st == TS_OK; ++it) {
-    st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
+    if (fixed)
+      st = residual_split_fixed(p, sigma, u, b, buf[0], np, (int*)partial, s);
+    else
+      st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
     if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 4, s);
   }
   scratch_free(w0, s);

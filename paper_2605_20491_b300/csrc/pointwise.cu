@@ -189,6 +189,182 @@ __global__ void k_stencil(AxisParams a, const double* __restrict__ V2, double si
   }
 }
 
+// Largest biased exponent over x (integer max of the exponent bits; order-independent).
+__global__ void k_max_exponent(const double* __restrict__ x, long long N, int* out) {
+  int m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, (int)((__double_as_longlong(x[i]) >> 52) & 0x7FF));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// x as a fixed-point integer with the scale 2^(1022 + H - emax), H = 53 + P: the mantissa
+// with its implicit bit, pre-shifted left by P, then shifted right by t = emax - e; integer
+// instructions only.  Exact when t <= P; otherwise the magnitude is truncated toward zero
+// onto the fixed-point grid.  |result| < 2^H whenever e <= emax; zero and subnormals give 0.
+__device__ __forceinline__ long long to_fixed(double x, int emax, int P) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  const long long m = ((bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52)) << P;
+  int t = emax - e;
+  t = (e == 0 || t > 63) ? 63 : t;  // m < 2^63, so a shift by 63 gives 0
+  const long long sgn = bits >> 63;  // 0 or -1
+  return ((m >> t) ^ sgn) - sgn;
+}
+
+// Residual r = b - (-Delta_h + V1 + sigma) u split into bf16 planes, for grids with the
+// same h on every axis.  The Laplacian part sum_k (2u - u_{-e_k} - u_{+e_k}) -- where all the
+// cancellation happens -- is evaluated exactly in 64-bit fixed point (one global scale from
+// the largest exponent of u, headroom H bits so that 4d |U| < 2^63); the rest is FP64:
+//   r = (b - (sigma + V1) u) - h^-2 2^(emax - 1022 - H) * L_int.
+// About 5 FP64-pipe instructions per point instead of 9; the integer work runs on the
+// otherwise idle integer pipe.
+template <int NP>
+__global__ void k_residual_fixed(AxisParams a, double sigma, const double* __restrict__ x,
+                                 const double* __restrict__ b, __nv_bfloat16* __restrict__ planes, long long N,
+                                 const int* __restrict__ emax_ptr, int H) {
+  const int emax = *emax_ptr;
+  const double cs = ldexp(a.ih2[0], emax - 1022 - H);
+  const int P = H - 53;
+  const int n0 = a.n[0];
+  int G = 1;
+  while (G < n0 && G < 32) G <<= 1;
+  const int rows_per_warp = 32 / G;
+  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
+  const long long R = N / n0;
+  const long long warps_total = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long twod = 2LL * a.d;
+  for (long long rb = wid * rows_per_warp; rb < R; rb += warps_total * rows_per_warp) {
+    const long long row = rb + sub;
+    if (row >= R) continue;
+    long long q = row;
+    double drow = sigma;
+    unsigned lo_mask = 0, hi_mask = 0;
+    for (int k = 1; k < a.d; ++k) {
+      long long qq = q / a.n[k];
+      int i = (int)(q - qq * a.n[k]);
+      q = qq;
+      drow += a.tab[k][i];
+      if (i == 0) lo_mask |= 1u << k;
+      if (i == a.n[k] - 1) hi_mask |= 1u << k;
+    }
+    const long long base = row * n0;
+    for (int i0 = gl; i0 < n0; i0 += G) {
+      const long long idx = base + i0;
+      const double xc = x[idx];
+      long long L = twod * to_fixed(xc, emax, P);
+      if (i0 > 0) L -= to_fixed(x[idx - 1], emax, P);
+      if (i0 + 1 < n0) L -= to_fixed(x[idx + 1], emax, P);
+      for (int k = 1; k < a.d; ++k) {
+        if (!((lo_mask >> k) & 1u)) L -= to_fixed(x[idx - a.stride[k]], emax, P);
+        if (!((hi_mask >> k) & 1u)) L -= to_fixed(x[idx + a.stride[k]], emax, P);
+      }
+      const double diag = drow + a.tab[0][i0];
+      const double r = fma(-cs, __ll2double_rn(L), fma(-diag, xc, b[idx]));
+      split_store<NP>((float)r, planes, N, idx);
+    }
+  }
+}
+
+// The same residual for d = 3, converting every value to fixed point once: a block owns a
+// 32 x 16 tile of axes (0, 1) and marches along axis 2 over MZ planes.  The axis-2 neighbours
+// come from a three-plane register queue; the axis-0/1 neighbours from a shared-memory copy
+// of the current plane with a one-cell halo (converted by warps 0-2: top row, bottom row,
+// left and right columns).  The next plane's x and the current plane's b are loaded one
+// step ahead.  H = 58 (4d |U| < 2^62), so P = 5.
+constexpr int MX = 32, MY = 16, MZ = 32;
+template <int NP>
+__global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double sigma, const double* __restrict__ x,
+                                                         const double* __restrict__ b,
+                                                         __nv_bfloat16* __restrict__ planes, long long N,
+                                                         const int* __restrict__ emax_ptr) {
+  constexpr int H = 58, P = H - 53;
+  __shared__ long long sU[2][MY + 2][MX + 2];
+  const int emax = *emax_ptr;
+  const double cs = ldexp(a.ih2[0], emax - 1022 - H);
+  const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
+  const long long s2 = (long long)n0 * n1;
+  const int tiles0 = (n0 + MX - 1) / MX, tiles1 = (n1 + MY - 1) / MY;
+  int bid = blockIdx.x;
+  const int t0 = bid % tiles0;
+  bid /= tiles0;
+  const int t1 = bid % tiles1;
+  const int z0 = (bid / tiles1) * MZ, z1 = min(z0 + MZ, n2);
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  const int i0 = t0 * MX + lx;
+  const int ia = t1 * MY + ly, ib = ia + 8;
+  const bool va = i0 < n0 && ia < n1, vb = i0 < n0 && ib < n1;
+  const long long oa = (long long)ia * n0 + i0, ob = (long long)ib * n0 + i0;
+  // halo cell of this thread (warps 0-2): smem (hy, hx), grid (hi0, hi1)
+  int hy = 0, hx = 0, hi0 = -1, hi1 = -1;
+  if (ly == 0) { hy = 0; hx = lx + 1; hi0 = i0; hi1 = t1 * MY - 1; }
+  else if (ly == 1) { hy = MY + 1; hx = lx + 1; hi0 = i0; hi1 = t1 * MY + MY; }
+  else if (ly == 2) {
+    hy = (lx & 15) + 1;
+    hx = lx < 16 ? 0 : MX + 1;
+    hi0 = lx < 16 ? t0 * MX - 1 : t0 * MX + MX;
+    hi1 = t1 * MY + (lx & 15);
+  }
+  const bool hv = ly < 3 && hi0 >= 0 && hi0 < n0 && hi1 >= 0 && hi1 < n1;
+  const long long oh = hv ? (long long)hi1 * n0 + hi0 : 0;
+  const double ca = va ? sigma + a.tab[0][i0] + a.tab[1][ia] : 0.0;
+  const double cb = vb ? sigma + a.tab[0][i0] + a.tab[1][ib] : 0.0;
+  const double* f2 = a.tab[2];
+
+  auto ld = [&](bool v, const double* base, long long off, int z) -> double {
+    return v ? base[off + z * s2] : 0.0;
+  };
+  long long Upa = to_fixed(ld(va && z0 > 0, x, oa, z0 - 1), emax, P);
+  long long Upb = to_fixed(ld(vb && z0 > 0, x, ob, z0 - 1), emax, P);
+  double xca = ld(va, x, oa, z0), xcb = ld(vb, x, ob, z0);
+  long long Uca = to_fixed(xca, emax, P), Ucb = to_fixed(xcb, emax, P);
+  sU[0][ly + 1][lx + 1] = Uca;
+  sU[0][ly + 9][lx + 1] = Ucb;
+  if (ly < 3) sU[0][hy][hx] = to_fixed(ld(hv, x, oh, z0), emax, P);
+  // one step ahead: x of plane z0 + 1 (own cells and halo), b of plane z0
+  double xna = ld(va && z0 + 1 < n2, x, oa, z0 + 1), xnb = ld(vb && z0 + 1 < n2, x, ob, z0 + 1);
+  double xnh = ld(hv && z0 + 1 < z1, x, oh, z0 + 1);
+  double ba = ld(va, b, oa, z0), bb = ld(vb, b, ob, z0);
+  int buf = 0;
+  for (int z = z0; z < z1; ++z) {
+    const long long Una = to_fixed(xna, emax, P), Unb = to_fixed(xnb, emax, P);
+    const long long Unh = to_fixed(xnh, emax, P);
+    const double xa = xca, xb = xcb, b_a = ba, b_b = bb;
+    xca = xna;
+    xcb = xnb;
+    // issue the loads of the next step
+    xna = ld(va && z + 2 < n2, x, oa, z + 2);
+    xnb = ld(vb && z + 2 < n2, x, ob, z + 2);
+    xnh = ld(hv && z + 2 < z1, x, oh, z + 2);
+    ba = ld(va && z + 1 < z1, b, oa, z + 1);
+    bb = ld(vb && z + 1 < z1, b, ob, z + 1);
+    __syncthreads();
+    const long long(*T)[MX + 2] = sU[buf];
+    const long long La = 6 * Uca - Upa - Una - T[ly + 1][lx] - T[ly + 1][lx + 2] - T[ly][lx + 1] - T[ly + 2][lx + 1];
+    const long long Lb = 6 * Ucb - Upb - Unb - T[ly + 9][lx] - T[ly + 9][lx + 2] - T[ly + 8][lx + 1] -
+                         T[ly + 10][lx + 1];
+    const double fz = f2[z];
+    const long long zoff = z * s2;
+    if (va) {
+      const double r = fma(-cs, __ll2double_rn(La), fma(-(ca + fz), xa, b_a));
+      split_store<NP>((float)r, planes, N, oa + zoff);
+    }
+    if (vb) {
+      const double r = fma(-cs, __ll2double_rn(Lb), fma(-(cb + fz), xb, b_b));
+      split_store<NP>((float)r, planes, N, ob + zoff);
+    }
+    sU[buf ^ 1][ly + 1][lx + 1] = Una;
+    sU[buf ^ 1][ly + 9][lx + 1] = Unb;
+    if (ly < 3) sU[buf ^ 1][hy][hx] = Unh;
+    Upa = Uca;
+    Upb = Ucb;
+    Uca = Una;
+    Ucb = Unb;
+    buf ^= 1;
+  }
+}
+
 // partial sums of (a.b) and (c.d) (c, d may be NULL).
 __global__ void k_dot2(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
                        const double* __restrict__ d, long long N, double* partial) {
@@ -357,6 +533,38 @@ ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigm
     k_stencil<2, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
   else
     k_stencil<2, 3><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
+bool isotropic_h(const ts_plan* p) {
+  for (int k = 1; k < p->d; ++k)
+    if (2.0 * p->L[k] / (p->n[k] + 1) != 2.0 * p->L[0] / (p->n[0] + 1)) return false;
+  return true;
+}
+
+ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, const double* b,
+                               __nv_bfloat16* planes, int np, int* emax_dev, cudaStream_t s) {
+  TS_CHECK_CUDA(cudaMemsetAsync(emax_dev, 0, sizeof(int), s));
+  k_max_exponent<<<grid_for(p->N), 256, 0, s>>>(x, p->N, emax_dev);
+  TS_LAUNCHED(1);
+  int H = 62;  // headroom: 2d |U| + 2d |U| < 2^63
+  for (long long t = 4LL * p->d; t > 1; t = (t + 1) / 2) --H;
+  const AxisParams a = axis_params(p, false);
+  if (p->d == 3) {
+    const long long blocks = (long long)((p->n[0] + MX - 1) / MX) * ((p->n[1] + MY - 1) / MY) *
+                             ((p->n[2] + MZ - 1) / MZ);
+    if (np == 2)
+      k_residual_march3<2><<<(unsigned)blocks, 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev);
+    else
+      k_residual_march3<3><<<(unsigned)blocks, 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev);
+    TS_LAUNCHED(1);
+    return TS_OK;
+  }
+  if (np == 2)
+    k_residual_fixed<2><<<grid_for(p->N), 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev, H);
+  else
+    k_residual_fixed<3><<<grid_for(p->N), 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev, H);
   TS_LAUNCHED(1);
   return TS_OK;
 }

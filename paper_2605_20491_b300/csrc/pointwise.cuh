@@ -18,6 +18,12 @@ ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, con
 // planes (np bf16 planes of N values) = split(b - (A + V2 + sigma) x); partial sums only.
 ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigma, const double* x,
                                  const double* b, __nv_bfloat16* planes, int np, double* partial, cudaStream_t s);
+// True when every axis has the same grid spacing h.
+bool isotropic_h(const ts_plan* p);
+// As stencil_residual_split without V2, for isotropic grids: the Laplacian part in exact
+// 64-bit fixed point (scale from the largest exponent of x, found into emax_dev).
+ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, const double* b,
+                               __nv_bfloat16* planes, int np, int* emax_dev, cudaStream_t s);
 // out2[0] = a.b (b == NULL: sum of a), out2[1] = c.d (c, d may be NULL).
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s);

@@ -102,6 +102,40 @@ def test_refined_solve_reaches_fp64_accuracy(T, n):
     assert np.array_equal(host(u0), host(u1))
 
 
+@pytest.mark.parametrize("n", [(40, 24, 56), (72, 40, 40), (24, 40), (16, 8, 24, 32)])
+def test_refined_solve_isotropic_ragged(T, n):
+    """Equal spacing h = 1/2 on axes of unequal, ragged lengths (the residual's fixed-point
+    Laplacian: tile edges along every axis, d = 2, 3, 4) reaches FP64 accuracy."""
+    L = tuple((k + 1) / 4.0 for k in n)
+    f = S.harmonic(n, L, tuple(1.0 + 0.2 * k for k in range(len(n))))
+    P, Po = plans(n, L, f, MASK)
+    b = S.normal(6, Po.N)
+    u = dev(np.zeros(Po.N))
+    T.ts_solve_refined(P, 0.25, dev(b), u, T.TS_BF16X3, 2)
+    assert rel(host(u), O.apply_inverse(Po, 0.25, b)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [(64, 64, 64), (48, 40, 32)])
+def test_refined_solve_zero_rhs_and_power_of_two_scaling(T, n):
+    """b = 0 gives u = 0 exactly.  Every step of the refined solve commutes with scaling by a
+    power of two (bf16 splits, FP32 products and tables, the residual's global fixed-point
+    exponent), so u(2^k b) equals 2^k u(b) bit for bit on isotropic and anisotropic grids."""
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)
+    u = dev(np.full(Po.N, 3.0))
+    T.ts_solve_refined(P, 0.5, dev(np.zeros(Po.N)), u, T.TS_BF16X3, 2)
+    assert not host(u).any()
+    b = S.normal(5, Po.N) * (1.0 + 1e3 * (np.arange(Po.N) % 7 == 0))
+    ref = dev(np.zeros(Po.N))
+    T.ts_solve_refined(P, 0.5, dev(b), ref, T.TS_BF16X3, 2)
+    ref = host(ref)
+    assert rel(ref, O.apply_inverse(Po, 0.5, b)) < 1e-12
+    for k in (-20, 37):
+        uk = dev(np.zeros(Po.N))
+        T.ts_solve_refined(P, 0.5, dev(np.ldexp(b, k)), uk, T.TS_BF16X3, 2)
+        assert np.array_equal(host(uk), np.ldexp(ref, k))
+
+
 def test_autotune_cache_roundtrip(T, tmp_path):
     """The autotuner searches each axis length once, writes the cache, and a second call
     applies the cached choice without timing; results stay within tolerance."""
