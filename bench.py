@@ -168,8 +168,9 @@ def run_reference(args):
 
 def run_profile_case(args):
     """Small fixed case for profiler captures (a few GB on the device): the refined solve
-    of the n = 512 workload only (or, with --workload 6d_n24_strang / 9d_n8_strang, the
-    complex64 FP32 Strang steps only), warmup + steps times, nothing else."""
+    of the n = 512 workload only (with --profile-n m: on an m^3 grid of the same box and
+    potential), or, with --workload 6d_n24_strang / 9d_n8_strang, the complex64 FP32 Strang
+    steps only; warmup + steps times, nothing else."""
     import torch
     from paper_2605_20491_b300 import tschrod as T
     if args.workload in ("6d_n24_strang", "9d_n8_strang"):
@@ -183,7 +184,8 @@ def run_profile_case(args):
         print("profile case done", flush=True)
         return 0
     w = synth.WORKLOADS[WORKLOAD]
-    P = T.ts_plan_create(w["n"], w["L"], synth.harmonic(w["n"], w["L"], w["omega"]), (1 << T.TS_BF16X3))
+    n = (args.profile_n,) * 3 if args.profile_n else w["n"]
+    P = T.ts_plan_create(n, w["L"], synth.harmonic(n, w["L"], w["omega"]), (1 << T.TS_BF16X3))
     b = torch.from_numpy(synth.normal(w["seed"], P.N)).cuda()
     x = torch.empty_like(b)
     for _ in range(args.warmup + args.steps):
@@ -491,6 +493,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the refined solve (for ncu captures); prints no JSON line")
+    ap.add_argument("--profile-n", type=int, default=0,
+                    help="grid points per axis of the --profile-case refined solve (default: the workload's)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving run")
     ap.add_argument("--workload", default=WORKLOAD,

@@ -212,6 +212,40 @@ __device__ __forceinline__ long long to_fixed(double x, int emax, int P) {
   return ((m >> t) ^ sgn) - sgn;
 }
 
+// v -> double, rounded to nearest even, with integer instructions only (|v| < 2^63): the
+// magnitude is normalised with a count of leading zeros, its top 53 bits kept and rounded on
+// the 11 bits below them; a carry out of the mantissa bumps the exponent through the add.
+__device__ __forceinline__ double i64_to_f64(long long v) {
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ULL;
+  unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll(a);
+  a <<= (lz & 63);
+  unsigned long long m = a >> 11;
+  const unsigned rem = (unsigned)a & 0x7FFu;
+  m += (rem > 0x400u || (rem == 0x400u && (m & 1ULL))) ? 1ULL : 0ULL;
+  const unsigned long long mag = ((unsigned long long)(1023 + 63 - 1 - lz) << 52) + m;
+  return __longlong_as_double((long long)(a == 0 ? 0ULL : (sgn | mag)));
+}
+
+// v -> float, rounded to nearest even, with 32-bit integer instructions only: the top 23
+// fraction bits rounded on the 29 below them, exponent rebased from 1023 to 127.  Results
+// below the normal float range are flushed to zero (signed), above it give infinity; NaN
+// stays NaN.
+__device__ __forceinline__ float f64_to_f32(double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned lo = (unsigned)bits, hi = (unsigned)(bits >> 32);
+  const unsigned sgn = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1FFFFFFFu;
+  m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  unsigned f = ((unsigned)(e - 896) << 23) + m;
+  f = e <= 896 ? 0u : f;
+  f = e >= 1151 ? 0x7F800000u : f;
+  f = (e == 2047 && ((hi & 0xFFFFFu) | lo)) ? 0x7FC00000u : f;
+  return __uint_as_float(sgn | f);
+}
+
 // Residual r = b - (-Delta_h + V1 + sigma) u split into bf16 planes, for grids with the
 // same h on every axis.  The Laplacian part sum_k (2u - u_{-e_k} - u_{+e_k}) -- where all the
 // cancellation happens -- is evaluated exactly in 64-bit fixed point (one global scale from
@@ -272,7 +306,9 @@ __global__ void k_residual_fixed(AxisParams a, double sigma, const double* __res
 // come from a three-plane register queue; the axis-0/1 neighbours from a shared-memory copy
 // of the current plane with a one-cell halo (converted by warps 0-2: top row, bottom row,
 // left and right columns).  The next plane's x and the current plane's b are loaded one
-// step ahead.  H = 58 (4d |U| < 2^62), so P = 5.
+// step ahead.  H = 58 (4d |U| < 2^62), so P = 5.  The conversions of the Laplacian to
+// double and of the residual to float run on the integer pipe: three FP64 instructions per
+// point remain (diagonal sum, two FMAs).
 constexpr int MX = 32, MY = 16, MZ = 32;
 template <int NP>
 __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double sigma, const double* __restrict__ x,
@@ -347,12 +383,12 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
     const double fz = f2[z];
     const long long zoff = z * s2;
     if (va) {
-      const double r = fma(-cs, __ll2double_rn(La), fma(-(ca + fz), xa, b_a));
-      split_store<NP>((float)r, planes, N, oa + zoff);
+      const double r = fma(-cs, i64_to_f64(La), fma(-(ca + fz), xa, b_a));
+      split_store<NP>(f64_to_f32(r), planes, N, oa + zoff);
     }
     if (vb) {
-      const double r = fma(-cs, __ll2double_rn(Lb), fma(-(cb + fz), xb, b_b));
-      split_store<NP>((float)r, planes, N, ob + zoff);
+      const double r = fma(-cs, i64_to_f64(Lb), fma(-(cb + fz), xb, b_b));
+      split_store<NP>(f64_to_f32(r), planes, N, ob + zoff);
     }
     sU[buf ^ 1][ly + 1][lx + 1] = Una;
     sU[buf ^ 1][ly + 9][lx + 1] = Unb;
