@@ -59,6 +59,7 @@ constexpr int SMEM_LIMIT = 232448;  // 227 KB opt-in shared memory per CTA
 
 struct EpiParams {
   int out_mode;    // 0: bf16 planes, 1: FP64 real, 2: complex128, 3: complex64, 4: FP64 real +=
+  int* emax_out;   // out_mode 1 / 4: atomic max of the stored values' biased exponents (NULL: none)
   int scale_mode;  // 0: none, 1: inverse 1/(Lambda + sigma), 2: phase e^{-i tau Lambda}
   long long R;     // rows of the pass
   int n;           // contracted (= output column) extent
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // (tile rows) and every other 16-column chunk (half (w - 2) / 4).
     const int g = warp & 3;
     const int half = (warp - 2) >> 2;
+    int emx = 0;  // largest biased exponent stored by this thread (out_mode 1 / 4)
     int tl = 0;
     for (int t = unit0; t < total; t += unit_step, ++tl) {
       const int ab = tl & 1, use = tl >> 1;
@@ -308,9 +310,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
           } else if (ep.out_mode == 1) {
-            reinterpret_cast<double*>(ep.out)[idx] = f2d(val[0]);
+            const double o = f2d(val[0]);
+            reinterpret_cast<double*>(ep.out)[idx] = o;
+            emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
           } else if (ep.out_mode == 4) {
-            reinterpret_cast<double*>(ep.out)[idx] = prev[i] + f2d(val[0]);
+            const double o = prev[i] + f2d(val[0]);
+            reinterpret_cast<double*>(ep.out)[idx] = o;
+            emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
           } else if (ep.out_mode == 2) {
             reinterpret_cast<double2*>(ep.out)[idx] = make_double2(f2d(val[0]), f2d(val[NACC - 1]));
           } else {
@@ -321,6 +327,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acce[ab]);
+    }
+    if (!PLANES_OUT && ep.emax_out) {
+      for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
+      if (lane == 0) atomicMax(ep.emax_out, emx);
     }
   }
   __syncwarp();
@@ -625,10 +635,11 @@ ts_status check_mixed(const ts_plan* p, ts_precision prec) {
 
 // The 2d contraction passes of one apply: planes in buf[0] -> ... -> `out` (out_mode of the
 // last pass: 1 FP64 store, 2 complex128, 3 complex64, 4 FP64 accumulate), with the
-// pointwise step fused into pass d-1.
+// pointwise step fused into pass d-1.  emax_out (modes 1 / 4, may be NULL): raised to the
+// largest biased exponent of the stored values (the caller zeroes it first).
 ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double param, __nv_bfloat16* const buf[2],
                      const double2* tabs, const float2* tabsf, const int* tab_off, void* out, int last_mode,
-                     cudaStream_t s) {
+                     cudaStream_t s, int* emax_out = nullptr) {
   const int np = bf16_planes(prec);
   const int nc = op == MixedOp::Exp ? 2 : 1;
   const int d = p->d;
@@ -640,6 +651,7 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
     EpiParams ep{};
     ep.out_mode = last ? last_mode : 0;
     ep.out = last ? out : (void*)buf[(t + 1) & 1];
+    ep.emax_out = last ? emax_out : nullptr;
     ep.scale_mode = 0;
     if (t == d - 1) {
       ep.scale_mode = op == MixedOp::Inverse ? 1 : 2;
@@ -736,18 +748,34 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
   ts_status st = scratch_alloc(&w1, plane_bytes, s);
   if (st == TS_OK) st = scratch_alloc(&partial, sizeof(double) * 2 * RED_BLOCKS, s);
   __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
+  // On isotropic grids the residual's Laplacian is summed in exact fixed point, scaled by
+  // the largest exponent of u; the pass that writes u finds it on the way out.
+  const bool fixed = isotropic_h(p);
+  int* emax = (int*)partial;
+  auto zero_emax = [&]() -> ts_status {
+    if (fixed && cudaMemsetAsync(emax, 0, sizeof(int), s) != cudaSuccess) {
+      set_error("memset failed");
+      return TS_ERR_CUDA;
+    }
+    return TS_OK;
+  };
   // u_0 = P b
   if (st == TS_OK) st = split_input(np, TS_R64, b, buf[0], N, s);
-  if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s);
-  // u_{k+1} = u_k + P (b - A u_k), residual in FP64 (its Laplacian part in exact fixed
-  // point on isotropic grids), split straight into the planes
-  const bool fixed = isotropic_h(p);
+  if (st == TS_OK && refinements > 0) st = zero_emax();
+  if (st == TS_OK)
+    st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s,
+                    fixed && refinements > 0 ? emax : nullptr);
+  // u_{k+1} = u_k + P (b - A u_k), residual in FP64, split straight into the planes
   for (int it = 0; it < refinements && st == TS_OK; ++it) {
+    const bool more = it + 1 < refinements;
     if (fixed)
-      st = residual_split_fixed(p, sigma, u, b, buf[0], np, (int*)partial, s);
+      st = residual_split_fixed(p, sigma, u, b, buf[0], np, emax, s);
     else
       st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
-    if (st == TS_OK) st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 4, s);
+    if (st == TS_OK && more) st = zero_emax();
+    if (st == TS_OK)
+      st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 4, s,
+                      fixed && more ? emax : nullptr);
   }
   scratch_free(w0, s);
   scratch_free(w1, s);

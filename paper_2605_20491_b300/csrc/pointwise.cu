@@ -189,15 +189,6 @@ __global__ void k_stencil(AxisParams a, const double* __restrict__ V2, double si
   }
 }
 
-// Largest biased exponent over x (integer max of the exponent bits; order-independent).
-__global__ void k_max_exponent(const double* __restrict__ x, long long N, int* out) {
-  int m = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    m = max(m, (int)((__double_as_longlong(x[i]) >> 52) & 0x7FF));
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
-}
-
 // x as a fixed-point integer with the scale 2^(1022 + H - emax), H = 53 + P: the mantissa
 // with its implicit bit, pre-shifted left by P, then shifted right by t = emax - e; integer
 // instructions only.  Exact when t <= P; otherwise the magnitude is truncated toward zero
@@ -580,10 +571,7 @@ bool isotropic_h(const ts_plan* p) {
 }
 
 ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, const double* b,
-                               __nv_bfloat16* planes, int np, int* emax_dev, cudaStream_t s) {
-  TS_CHECK_CUDA(cudaMemsetAsync(emax_dev, 0, sizeof(int), s));
-  k_max_exponent<<<grid_for(p->N), 256, 0, s>>>(x, p->N, emax_dev);
-  TS_LAUNCHED(1);
+                               __nv_bfloat16* planes, int np, const int* emax_dev, cudaStream_t s) {
   int H = 62;  // headroom: 2d |U| + 2d |U| < 2^63
   for (long long t = 4LL * p->d; t > 1; t = (t + 1) / 2) --H;
   const AxisParams a = axis_params(p, false);

@@ -21,9 +21,10 @@ ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigm
 // True when every axis has the same grid spacing h.
 bool isotropic_h(const ts_plan* p);
 // As stencil_residual_split without V2, for isotropic grids: the Laplacian part in exact
-// 64-bit fixed point (scale from the largest exponent of x, found into emax_dev).
+// 64-bit fixed point, scaled by *emax_dev, which must hold the largest biased exponent of
+// the values of x (a larger value is safe and costs precision; a smaller one overflows).
 ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, const double* b,
-                               __nv_bfloat16* planes, int np, int* emax_dev, cudaStream_t s);
+                               __nv_bfloat16* planes, int np, const int* emax_dev, cudaStream_t s);
 // out2[0] = a.b (b == NULL: sum of a), out2[1] = c.d (c, d may be NULL).
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s);
