@@ -65,6 +65,8 @@ class _ServingStats(C.Structure):
                 ("peak_scratch_bytes", C.c_longlong)]
 
 
+TS_TC_PAIR = -2  # ts_tc_config_set cluster value: CTA pairs sharing each MMA
+TS_TC_SWAPPED = -3  # ts_tc_config_set cluster value: S_k as the 128-row MMA operand
 TS_REQ_INVERSE, TS_REQ_EXP, TS_REQ_PCG = range(3)
 
 _lib = None
@@ -258,6 +260,11 @@ def ts_inverse_iteration(plan: Plan, shift: float, V2, u, init_from_plan: bool =
 
 def ts_tc_config_set(complex_data: bool, n: int, bk: int, bn_cap: int, cluster: int = 1):
     _check(lib().ts_tc_config_set(int(complex_data), n, bk, bn_cap, cluster), "ts_tc_config_set")
+
+
+def ts_tc_config_reset(complex_data: bool, n: int = 0):
+    """Forget the tile configuration for (complex_data, n): the built-in choice applies again."""
+    _check(lib().ts_tc_config_set(int(complex_data), n, 0, 0, 0), "ts_tc_config_set")
 
 
 def ts_autotune(plan: Plan, dtype: int, prec: int, cache_path: str | None = None, stream=None) -> int:
