@@ -211,14 +211,12 @@ ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double
  * N tile, and `cluster`: 1, 2 or 4 = the number of CTAs of a thread-block cluster that
  * share every S_k tile through TMA multicast, each loading 1/cluster of it; TS_TC_PAIR =
  * CTA pairs that share each tensor-core instruction (tcgen05 cta_group::2: 256-row units,
- * each CTA staging its own 128 rows and half of the S_k tile); TS_TC_SWAPPED = S_k as the
- * 128-row operand and the data rows as the N tile (bn_cap caps the data rows per tile), so
- * that the epilogue writes 16-byte vectors; the default for n a multiple of 128.
- * bk = bn_cap = cluster = 0 forgets the entry for (complex_data, n), restoring the
- * built-in choice.  Process-wide; takes effect for calls issued afterwards.
+ * each CTA staging its own 128 rows and half of the S_k tile; the built-in choice for real
+ * data on axes of 256 points or more).  bk = bn_cap = cluster = 0 forgets the entry for
+ * (complex_data, n), restoring the built-in choice.  Process-wide; takes effect for calls
+ * issued afterwards.
  */
 #define TS_TC_PAIR (-2)
-#define TS_TC_SWAPPED (-3)
 ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster);
 
 /* ------------------------------------------------------------------ serving ----- */
@@ -290,8 +288,7 @@ ts_status ts_server_destroy(ts_server* server);
  * Autotuner of the split-precision contraction (no counterpart in the paper).  For every
  * distinct axis length n of the plan and the data kind (dtype TS_R64: real data of
  * ts_apply_inverse; TS_C128: complex data of ts_apply_exp) it times the tile
- * configurations (K chunk 64 / 32, N-tile cap 256 / 128 / 64, cluster 1 / 2 / 4 / TS_TC_PAIR /
- * TS_TC_SWAPPED) on whole
+ * configurations (K chunk 64 / 32, N-tile cap 256 / 128 / 64, cluster 1 / 2 / 4 / TS_TC_PAIR) on whole
  * applies with CUDA
  * events on `stream`, keeps the fastest with ts_tc_config_set, and appends it to the text
  * file cache_path (NULL or "" = no file).  Entries already in the file are applied without

@@ -1,7 +1,7 @@
 // Autotuner of the split-precision tensor-core pass: for each distinct contracted extent
 // n of a plan and the data kind (real / complex), time the candidate tile configurations
-// (K chunk 64 or 32; N-tile cap 256, 128 or 64; 1, 2 or 4 CTAs per multicast cluster, CTA
-// pairs sharing each MMA, or swapped operands) on a
+// (K chunk 64 or 32; N-tile cap 256, 128 or 64; 1, 2 or 4 CTAs per multicast cluster, or CTA
+// pairs sharing each MMA) on a
 // whole apply with CUDA events, keep the fastest through tc_config_set, and remember it in
 // a plain-text cache file so later processes skip the search.
 // Cache line: "<complex> <n> <prec> <bk> <bn_cap> <cluster> <ms>".
@@ -120,7 +120,7 @@ extern "C" ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precisi
     Entry best{cval, n, (int)prec, 64, 256, 1, 1e30};
     const int bks[2] = {64, 32};
     const int bns[3] = {256, 128, 64};
-    const int cms[5] = {1, 2, 4, TS_TC_PAIR, TS_TC_SWAPPED};
+    const int cms[4] = {1, 2, 4, TS_TC_PAIR};
     for (int bk : bks)
       for (int bn : bns)
         for (int cm : cms) {

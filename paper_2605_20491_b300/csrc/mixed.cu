@@ -74,34 +74,7 @@ struct EpiParams {
   const double2* rph[MAXD];   // their phase tables (scale_mode 2)
   const float* clam;          // eigenvalues of the contracted axis (FP32)
   const float2* cph;          // phase table of the contracted axis (FP32)
-  const float* rlamf0;        // FP32 eigenvalues of the first row axis (swapped passes, scale 1)
-  const float2* rph0f;        // FP32 phase table of the first row axis (swapped passes, scale 2)
-  int vec_ok;                 // swapped passes: 16-byte vector stores allowed (R % 8 == 0, aligned out)
 };
-
-// sigma + the row axes' eigenvalues (scale 1) or the product of their phases (scale 2) for
-// data row r, in FP64 from the per-axis tables (the first row axis varies fastest).
-__device__ __forceinline__ float row_sum_full(const EpiParams& ep, long long r) {
-  double s = ep.sigma;
-  for (int k = 0; k < ep.rd; ++k) {
-    const long long q = r / ep.rn[k];
-    s += ep.rlam[k][(int)(r - q * ep.rn[k])];
-    r = q;
-  }
-  return (float)s;
-}
-__device__ __forceinline__ float2 row_phase_full(const EpiParams& ep, long long r) {
-  double pr = 1.0, pi = 0.0;
-  for (int k = 0; k < ep.rd; ++k) {
-    const long long q = r / ep.rn[k];
-    const double2 ph = ep.rph[k][(int)(r - q * ep.rn[k])];
-    r = q;
-    const double tr = pr * ph.x - pi * ph.y;
-    pi = pr * ph.y + pi * ph.x;
-    pr = tr;
-  }
-  return make_float2((float)pr, (float)pi);
-}
 
 template <int NP>
 struct Products;
@@ -148,18 +121,10 @@ __device__ __forceinline__ double f2d(float f) {
 // Both CTAs' TMA loads complete on the leader's stage barrier (the leader alone expects
 // their bytes); commits are multicast to both CTAs; both epilogues arrive on the leader's
 // accumulator-drained barrier.
-//
-// TR (swapped operands): the S_k tile is the 128-row M operand (output columns j) and the
-// data rows are the N operand, so D^T lands in TMEM: each TMEM lane is one output column
-// and each thread of the epilogue holds 16 consecutive data rows r of it, which are
-// contiguous in the rotating-form output Y[r + R j].  The epilogue then writes 16-byte
-// vectors (8 bf16 of one plane, 2 doubles) instead of one 2-byte element per thread and
-// instruction, and u += delta reads 16-byte vectors.  For n a multiple of 128.
-template <int NP, int NACC, int BKT, bool PLANES_OUT, int CM, bool PAIR, bool TR>
+template <int NP, int NACC, int BKT, bool PLANES_OUT, int CM, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const EpiParams ep) {
   static_assert(!PAIR || CM == 1, "CTA pairs do not combine with B multicast");
-  static_assert(!TR || (CM == 1 && !PAIR), "swapped operands run without clusters");
   constexpr int SW = BKT * 2;  // bytes per smem row = swizzle width
   constexpr int CL = PAIR ? 2 : CM;  // CTAs per cluster
   constexpr int CG = PAIR ? 2 : 1;   // tcgen05 CTA group
@@ -167,12 +132,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int BN = ep.bn;
   const int NS = ep.nstages;
-  // A tiles: 128 rows (data rows, or S_k rows when TR); B tiles: BN rows (S_k rows, or
-  // data rows when TR); the data operand carries NACC components.
   const uint32_t A_TILE = BM * BKT * 2;
   const uint32_t B_TILE = (uint32_t)(PAIR ? BN / 2 : BN) * BKT * 2;
-  const uint32_t A_STAGE = (TR ? 1 : NACC) * NP * A_TILE;
-  const uint32_t B_STAGE = (TR ? NACC : 1) * NP * B_TILE;
+  const uint32_t A_STAGE = NACC * NP * A_TILE;
+  const uint32_t B_STAGE = NP * B_TILE;
   uint8_t* sA = smem;
   uint8_t* sB = smem + (size_t)NS * A_STAGE;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NS * (A_STAGE + B_STAGE));
@@ -184,11 +147,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (ep.n + BKT - 1) / BKT;
-  // M tiles over the data rows and N tiles over the output columns (TR: the other way
-  // round, with unit t covering N tile t / mtiles and M tile t % mtiles, so that CTAs busy
-  // at the same time share the data tile through L2).
-  const int mtiles = TR ? (ep.n + BM - 1) / BM : (int)((ep.R + BM - 1) / BM);
-  const int ntiles = TR ? (int)((ep.R + BN - 1) / BN) : (ep.n + BN - 1) / BN;
+  const int mtiles = (int)((ep.R + BM - 1) / BM);
+  const int ntiles = (ep.n + BN - 1) / BN;
   // Work units: with clusters of CL CTAs, unit t covers M tiles (t / ntiles) * CL + rank
   // (one per CTA of the cluster) and N tile t % ntiles.  Multicast clusters (CM > 1) share
   // every B tile through TMA multicast, each CTA loading BN / CM of its rows; pairs split the
@@ -232,22 +192,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int it = 0;
       const int bslice = BN / CM;
       for (int t = unit0; t < total; t += unit_step) {
-        const int m0 = TR ? (t % mtiles) * BM : ((t / ntiles) * CL + rank) * BM;
-        const int n0 = TR ? (t / mtiles) * BN : (t % ntiles) * BN;
+        const int m0 = ((t / ntiles) * CL + rank) * BM, n0 = (t % ntiles) * BN;
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const int s = it % NS, round = it / NS;
           if (round > 0) tc::mbar_wait(&empty[s], (round - 1) & 1, &g_tc_error, 1);
-          if (TR) {
-            // A = S_k rows m0.., B = data rows n0.. (NACC components)
-            tc::mbar_arrive_expect_tx(&full[s], A_STAGE + B_STAGE);
-            for (int p = 0; p < NP; ++p)
-              tc::tma_load_3d(sA + (size_t)s * A_STAGE + p * A_TILE, &tmA, kc * BKT, m0, p, &full[s]);
-            for (int c = 0; c < NACC; ++c)
-              for (int p = 0; p < NP; ++p)
-                tc::tma_load_3d(sB + (size_t)s * B_STAGE + (c * NP + p) * B_TILE, &tmB, kc * BKT, n0, c * NP + p,
-                                &full[s]);
-            continue;
-          }
           if (PAIR) {
             // both CTAs' boxes complete on the leader's barrier; the leader expects all of them
             const uint32_t lead_full = tc::mapa_shared(&full[s], 0);
@@ -296,17 +244,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int ks = 0; ks < BKT / UMMA_K; ++ks) {
 #pragma unroll
             for (int q = 0; q < Products<NP>::count; ++q) {
-              if (TR) {
-                // product q: data plane a(q) times S_k plane b(q), as D^T = S_k X^T
-                const uint64_t adesc = tc::desc_sw<SW>(a0 + Products<NP>::b(q) * A_TILE + ks * 32);
-#pragma unroll
-                for (int c = 0; c < NACC; ++c) {
-                  const uint64_t bdesc =
-                      tc::desc_sw<SW>(b0 + (c * NP + Products<NP>::a(q)) * B_TILE + ks * 32);
-                  tc::mma_bf16(dbase + (uint32_t)(c * BN), adesc, bdesc, idesc, (kc | ks | q) != 0);
-                }
-                continue;
-              }
               const uint64_t bdesc = tc::desc_sw<SW>(b0 + Products<NP>::b(q) * B_TILE + ks * 32);
 #pragma unroll
               for (int c = 0; c < NACC; ++c) {
@@ -330,166 +267,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         else
           tc::mma_commit(&accf[ab]);
       }
-    }
-  } else if (TR) {
-    // ---------------- epilogue, swapped operands: warp w reads TMEM lanes 32 (w % 4) + 0..31
-    // (output columns j) and the 16-column chunks (w - 2) / 4 + k EPI_WARPS / 4 (data rows).
-    const int g = warp & 3;
-    const int part = (warp - 2) >> 2;
-    const int rn0 = ep.rd > 0 ? ep.rn[0] : 1;
-    int emx = 0;
-    int tl = 0;
-    for (int t = unit0; t < total; t += unit_step, ++tl) {
-      const int ab = tl & 1, use = tl >> 1;
-      const int jt = t % mtiles, rt = t / mtiles;
-      tc::mbar_wait(&accf[ab], use & 1, &g_tc_error, 3);
-      __syncwarp();
-      tc::tc_fence_after();
-      const int j = jt * BM + g * 32 + lane;
-      const bool j_ok = j < ep.n;
-      float cl = 0.f;
-      float2 cp = make_float2(1.f, 0.f);
-      if (j_ok && ep.scale_mode == 1) cl = ep.clam[j];
-      if (j_ok && ep.scale_mode == 2) cp = ep.cph[j];
-      const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
-      for (int col0 = part * 16; col0 < BN; col0 += 16 * (EPI_WARPS / 4)) {
-        uint32_t v[NACC][16];
-#pragma unroll
-        for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
-        tc::tmem_ld_wait();
-        const long long r0 = (long long)rt * BN + col0;  // first data row of the chunk
-        if (!j_ok || r0 >= ep.R) continue;
-        const int rcount = ep.R - r0 < 16 ? (int)(ep.R - r0) : 16;
-        float val[NACC][16];
-#pragma unroll
-        for (int c = 0; c < NACC; ++c)
-#pragma unroll
-          for (int i = 0; i < 16; ++i) val[c][i] = __uint_as_float(v[c][i]);
-        if (ep.scale_mode != 0) {
-          // row factors: the axes after the first once per chunk (FP64), the first per row
-          // (FP32 table) while the chunk stays inside one run of it, else row by row
-          const unsigned q0 = (unsigned)r0 / (unsigned)rn0;  // r0 < R < 2^31
-          const int i0 = (int)((unsigned)r0 - q0 * (unsigned)rn0);
-          const bool fast = i0 + 16 <= rn0;
-          double sacc = ep.sigma, pr = 1.0, pi = 0.0;
-          unsigned q = q0;
-          for (int k = 1; k < ep.rd; ++k) {
-            const unsigned qq = q / (unsigned)ep.rn[k];
-            const int ik = (int)(q - qq * (unsigned)ep.rn[k]);
-            q = qq;
-            if (ep.scale_mode == 1) {
-              sacc += ep.rlam[k][ik];
-            } else {
-              const double2 ph = ep.rph[k][ik];
-              const double tr = pr * ph.x - pi * ph.y;
-              pi = pr * ph.y + pi * ph.x;
-              pr = tr;
-            }
-          }
-          const float sb = (float)sacc;
-          const float2 pb = make_float2((float)pr, (float)pi);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            if (ep.scale_mode == 1) {
-              float rs = sb;
-              if (ep.rd > 0) rs = fast ? sb + ep.rlamf0[i0 + i] : (i < rcount ? row_sum_full(ep, r0 + i) : 0.f);
-              val[0][i] = val[0][i] * (1.0f / (rs + cl));
-            } else if (NACC == 2) {
-              float2 rp = pb;
-              if (ep.rd > 0) {
-                if (fast) {
-                  const float2 f = ep.rph0f[i0 + i];
-                  rp = make_float2(pb.x * f.x - pb.y * f.y, pb.x * f.y + pb.y * f.x);
-                } else {
-                  rp = i < rcount ? row_phase_full(ep, r0 + i) : make_float2(0.f, 0.f);
-                }
-              }
-              const float phx = rp.x * cp.x - rp.y * cp.y;
-              const float phy = rp.x * cp.y + rp.y * cp.x;
-              const float re = val[0][i] * phx - val[NACC - 1][i] * phy;
-              const float im = val[0][i] * phy + val[NACC - 1][i] * phx;
-              val[0][i] = re;
-              val[NACC - 1][i] = im;
-            }
-          }
-        }
-        const long long idx0 = r0 + ep.R * (long long)j;
-        const bool vec = rcount == 16 && ep.vec_ok;
-        if (PLANES_OUT) {
-          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
-#pragma unroll
-          for (int c = 0; c < NACC; ++c) {
-            __nv_bfloat16* oc = o + (long long)c * NP * ep.N;
-            if (vec) {
-              // the split of split_store, two rows at a time with packed conversions
-              uint32_t w[NP][8];
-#pragma unroll
-              for (int i2 = 0; i2 < 8; ++i2) {
-                const float a = val[c][2 * i2], b = val[c][2 * i2 + 1];
-                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-                const float ra = a - __low2float(h), rb = b - __high2float(h);
-                const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
-                w[0][i2] = *reinterpret_cast<const uint32_t*>(&h);
-                w[1][i2] = *reinterpret_cast<const uint32_t*>(&m);
-                if (NP == 3) {
-                  const __nv_bfloat162 l = __floats2bfloat162_rn(ra - __low2float(m), rb - __high2float(m));
-                  w[NP - 1][i2] = *reinterpret_cast<const uint32_t*>(&l);
-                }
-              }
-#pragma unroll
-              for (int p = 0; p < NP; ++p) {
-                uint4* dst = reinterpret_cast<uint4*>(oc + (long long)p * ep.N + idx0);
-                dst[0] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-                dst[1] = make_uint4(w[p][4], w[p][5], w[p][6], w[p][7]);
-              }
-            } else {
-              for (int i = 0; i < rcount; ++i) split_store<NP>(val[c][i], oc, ep.N, idx0 + i);
-            }
-          }
-        } else if (ep.out_mode == 1 || ep.out_mode == 4) {
-          double* o = reinterpret_cast<double*>(ep.out) + idx0;
-          if (vec) {
-            double2 prev[8];
-#pragma unroll
-            for (int i2 = 0; i2 < 8; ++i2)
-              prev[i2] = ep.out_mode == 4 ? reinterpret_cast<const double2*>(o)[i2] : make_double2(0.0, 0.0);
-#pragma unroll
-            for (int i2 = 0; i2 < 8; ++i2) {
-              const double2 r2 = make_double2(prev[i2].x + f2d(val[0][2 * i2]), prev[i2].y + f2d(val[0][2 * i2 + 1]));
-              reinterpret_cast<double2*>(o)[i2] = r2;
-              emx = max(emx, max((__double2hiint(r2.x) >> 20) & 0x7FF, (__double2hiint(r2.y) >> 20) & 0x7FF));
-            }
-          } else {
-            for (int i = 0; i < rcount; ++i) {
-              const double r1 = (ep.out_mode == 4 ? o[i] : 0.0) + f2d(val[0][i]);
-              o[i] = r1;
-              emx = max(emx, (__double2hiint(r1) >> 20) & 0x7FF);
-            }
-          }
-        } else if (ep.out_mode == 2) {
-          double2* o = reinterpret_cast<double2*>(ep.out) + idx0;
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (i < rcount) o[i] = make_double2(f2d(val[0][i]), f2d(val[NACC - 1][i]));
-        } else {
-          float2* o = reinterpret_cast<float2*>(ep.out) + idx0;
-          if (vec) {
-#pragma unroll
-            for (int i2 = 0; i2 < 8; ++i2)
-              reinterpret_cast<float4*>(o)[i2] = make_float4(val[0][2 * i2], val[NACC - 1][2 * i2],
-                                                             val[0][2 * i2 + 1], val[NACC - 1][2 * i2 + 1]);
-          } else {
-            for (int i = 0; i < rcount; ++i) o[i] = make_float2(val[0][i], val[NACC - 1][i]);
-          }
-        }
-      }
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&acce[ab]);
-    }
-    if (!PLANES_OUT && ep.emax_out) {
-      for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
-      if (lane == 0) atomicMax(ep.emax_out, emx);
     }
   } else {
     // ---------------- epilogue: warps 2..EPI_WARPS+1.  Warp w reads TMEM lanes
@@ -701,15 +478,13 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
 
 int g_num_sms = 0;
 
-template <int NP, int NACC, int BKT, bool PO, int CM, bool PAIR, bool TR>
+template <int NP, int NACC, int BKT, bool PO, int CM, bool PAIR>
 ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
                         int bn_cap, cudaStream_t s) {
   constexpr int CL = PAIR ? 2 : CM;
-  // pairs: N tiles in multiples of 32 (every such N is a valid M = 256 shape); swapped
-  // operands: the N tile runs over the R data rows
+  // pairs: N tiles in multiples of 32 (every such N is a valid M = 256 shape)
   const int bq = PAIR ? 32 : 16;
-  const long long next = TR ? R : n;
-  int bn = (int)(((next < 256 ? next : 256) + bq - 1) / bq) * bq;
+  int bn = ((n + bq - 1) / bq) * bq;
   if (bn > bn_cap) bn = bn_cap;
   if (PAIR && bn % 32 != 0) {
     set_error("CTA pairs need an N-tile cap that is a multiple of 32 (got %d)", bn_cap);
@@ -719,8 +494,8 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
     set_error("N tile %d cannot be split into %d multicast slices of whole 8-row atoms", bn, CM);
     return TS_ERR_UNSUPPORTED;
   }
-  const int b_rows = PAIR ? bn / 2 : bn;  // rows of the B tile staged per CTA (bn % 16 == 0)
-  const int stage = TR ? NP * BM * BKT * 2 + NACC * NP * bn * BKT * 2 : NACC * NP * BM * BKT * 2 + NP * b_rows * BKT * 2;
+  const int b_rows = PAIR ? bn / 2 : bn;  // rows of the S_k tile staged per CTA (bn % 16 == 0)
+  const int stage = NACC * NP * BM * BKT * 2 + NP * b_rows * BKT * 2;
   const int reserve = 1024 + 8 * (2 * MAX_STAGES + 6);
   int ns = (SMEM_LIMIT - reserve) / stage;
   if (ns > MAX_STAGES) ns = MAX_STAGES;
@@ -730,14 +505,8 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   }
   const int smem = ns * stage + reserve;
   CUtensorMap ma, mb;
-  if (TR) {
-    TS_TRY(make_map(&ma, B, n, n, NP, BKT, BM));          // S_k planes, 128-row boxes
-    TS_TRY(make_map(&mb, A, n, R, NACC * NP, BKT, bn));   // data planes, bn-row boxes
-  } else {
-    TS_TRY(make_map(&ma, A, n, R, NACC * NP, BKT, BM));
-    TS_TRY(make_map(&mb, B, n, n, NP, BKT, PAIR ? bn / 2 : bn / CM));
-  }
-  ep.vec_ok = TR && R % 8 == 0 && (reinterpret_cast<uintptr_t>(ep.out) & 15) == 0;
+  TS_TRY(make_map(&ma, A, n, R, NACC * NP, BKT, BM));
+  TS_TRY(make_map(&mb, B, n, n, NP, BKT, PAIR ? bn / 2 : bn / CM));
   ep.R = R;
   ep.n = n;
   ep.N = R * n;
@@ -746,7 +515,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     TS_CHECK_CUDA(
-        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM, PAIR, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              SMEM_LIMIT));
     attr_set = true;
   }
@@ -755,8 +524,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
     TS_CHECK_CUDA(cudaGetDevice(&dev));
     TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  const long long mtiles = TR ? (n + BM - 1) / BM : (R + BM - 1) / BM;
-  const long long ntiles = TR ? (R + bn - 1) / bn : (n + bn - 1) / bn;
+  const long long mtiles = (R + BM - 1) / BM, ntiles = (n + bn - 1) / bn;
   const long long units = ((mtiles + CL - 1) / CL) * ntiles;
   TS_REQUIRE(units * CL < (1LL << 31), "too many tiles");
   const long long max_clusters = g_num_sms / CL;
@@ -764,7 +532,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   void* tok = nullptr;
   if (prof_enabled()) prof_begin_launch(s, &tok);
   if (CL == 1) {
-    k_rot_tc<NP, NACC, BKT, PO, 1, false, TR><<<grid, TC_THREADS, smem, s>>>(ma, mb, ep);
+    k_rot_tc<NP, NACC, BKT, PO, 1, false><<<grid, TC_THREADS, smem, s>>>(ma, mb, ep);
   } else {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -778,7 +546,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    TS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_rot_tc<NP, NACC, BKT, PO, CM, PAIR, false>, ma, mb, ep));
+    TS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_rot_tc<NP, NACC, BKT, PO, CM, PAIR>, ma, mb, ep));
   }
   TS_LAUNCHED(1);
   if (tok) {
@@ -798,7 +566,6 @@ struct TcConfig {
   int bn_cap = 256;
   int cm = 1;         // CTAs per cluster sharing each B tile by multicast (1, 2 or 4)
   bool pair = false;  // CTA pairs sharing each MMA (cta_group::2, 256-row units); cm is then 1
-  bool tr = false;    // swapped operands (S_k as the 128-row M operand); no clusters
 };
 
 std::mutex g_cfg_mu;
@@ -814,8 +581,9 @@ TcConfig lookup_config(int nacc, int n) {
   c.bk = 64;
   c.bn_cap = nacc == 1 ? 256 : 128;
   c.cm = 1;
-  c.pair = false;
-  c.tr = n > 0 && n % BM == 0;  // whole 128-column tiles: the swapped epilogue writes vectors
+  // real data on long axes: CTA pairs (each SM stages half of the S_k tile); measured on the
+  // BF16X3 plane passes at n = 512: 0.299 ms against 0.321 ms for single CTAs
+  c.pair = nacc == 1 && n >= 256;
   return c;
 }
 
@@ -829,10 +597,6 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
     if (bn > c.bn_cap) bn = c.bn_cap;
     while (c.cm > 1 && bn % (8 * c.cm) != 0) c.cm /= 2;  // multicast slices are whole 8-row atoms
   }
-  if (c.tr) {
-    c.cm = 1;
-    c.pair = false;
-  }
   if (c.pair) c.cm = 1;
   if (c.bn_cap % 32 != 0) c.pair = false;
   // Fall back to a narrower K chunk, then a narrower N tile, until two stages fit.
@@ -841,9 +605,7 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
     const int bq = c.pair ? 32 : 16;
     int bn = ((n + bq - 1) / bq) * bq;
     if (bn > c.bn_cap) bn = c.bn_cap;
-    if (c.tr) bn = c.bn_cap;  // the N tile runs over the data rows
-    const int stage = c.tr ? NP * BM * c.bk * 2 + NACC * NP * bn * c.bk * 2
-                           : NACC * NP * BM * c.bk * 2 + NP * (c.pair ? bn / 2 : bn) * c.bk * 2;
+    const int stage = NACC * NP * BM * c.bk * 2 + NP * (c.pair ? bn / 2 : bn) * c.bk * 2;
     if ((SMEM_LIMIT - reserve) / stage >= 2) break;
     if (c.bk == 64)
       c.bk = 32;
@@ -854,13 +616,15 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
     if (c.bn_cap % 32 != 0) c.pair = false;
   }
   if (ep.out_mode == 0) {
-  #define TS_CM_DISPATCH(BKT, PO)                                                              \
-  if (c.tr) return launch_pass_t<NP, NACC, BKT, PO, 1, false, true>(A, B, R, n, ep, c.bn_cap, s); \
-  if (c.pair) return launch_pass_t<NP, NACC, BKT, PO, 1, true, false>(A, B, R, n, ep, c.bn_cap, s); \
-  switch (c.cm) {                                                                                 \
-    case 2: return launch_pass_t<NP, NACC, BKT, PO, 2, false, false>(A, B, R, n, ep, c.bn_cap, s); \
-    case 4: return launch_pass_t<NP, NACC, BKT, PO, 4, false, false>(A, B, R, n, ep, c.bn_cap, s); \
-    default: return launch_pass_t<NP, NACC, BKT, PO, 1, false, false>(A, B, R, n, ep, c.bn_cap, s); \
+  // one statement (a braced block), so that `if (c.bk == 32) TS_CM_DISPATCH(32, ..)` guards all of it
+  #define TS_CM_DISPATCH(BKT, PO)                                                                   \
+  {                                                                                                \
+    if (c.pair) return launch_pass_t<NP, NACC, BKT, PO, 1, true>(A, B, R, n, ep, c.bn_cap, s);    \
+    switch (c.cm) {                                                                                \
+      case 2: return launch_pass_t<NP, NACC, BKT, PO, 2, false>(A, B, R, n, ep, c.bn_cap, s);      \
+      case 4: return launch_pass_t<NP, NACC, BKT, PO, 4, false>(A, B, R, n, ep, c.bn_cap, s);      \
+      default: return launch_pass_t<NP, NACC, BKT, PO, 1, false>(A, B, R, n, ep, c.bn_cap, s);     \
+    }                                                                                              \
   }
     if (c.bk == 32) TS_CM_DISPATCH(32, true);
     TS_CM_DISPATCH(64, true);
@@ -963,8 +727,6 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
       }
       ep.clam = p->lamf[k];
       ep.cph = tabsf ? tabsf + tab_off[k] : nullptr;
-      ep.rlamf0 = d > 1 ? p->lamf[0] : nullptr;
-      ep.rph0f = d > 1 && tabsf ? tabsf + tab_off[0] : nullptr;
     }
     const __nv_bfloat16* B = fwd ? p->Bf[prec][k] : p->Bb[prec][k];
     st = pass(np, nc, buf[t & 1], B, p->N / p->n[k], p->n[k], ep, s);
@@ -1086,13 +848,12 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
 
 ts_status tc_prepare_kernels() {
   // Shared-memory opt-in for every instantiation, outside any stream capture.
-#define TS_PREP1(NP, NACC, BKT, PO, CM, PAIR, TR)                                                      \
-  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM, PAIR, TR>,                        \
+#define TS_PREP1(NP, NACC, BKT, PO, CM, PAIR)                                                          \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM, PAIR>,                            \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT))
 #define TS_PREP(NP, NACC, BKT, PO)                                                                     \
-  TS_PREP1(NP, NACC, BKT, PO, 1, false, false); TS_PREP1(NP, NACC, BKT, PO, 2, false, false);           \
-  TS_PREP1(NP, NACC, BKT, PO, 4, false, false); TS_PREP1(NP, NACC, BKT, PO, 1, true, false);            \
-  TS_PREP1(NP, NACC, BKT, PO, 1, false, true)
+  TS_PREP1(NP, NACC, BKT, PO, 1, false); TS_PREP1(NP, NACC, BKT, PO, 2, false);                         \
+  TS_PREP1(NP, NACC, BKT, PO, 4, false); TS_PREP1(NP, NACC, BKT, PO, 1, true)
   TS_PREP(2, 1, 64, true); TS_PREP(2, 1, 64, false); TS_PREP(2, 1, 32, true); TS_PREP(2, 1, 32, false);
   TS_PREP(2, 2, 64, true); TS_PREP(2, 2, 64, false); TS_PREP(2, 2, 32, true); TS_PREP(2, 2, 32, false);
   TS_PREP(3, 1, 64, true); TS_PREP(3, 1, 64, false); TS_PREP(3, 1, 32, true); TS_PREP(3, 1, 32, false);
@@ -1114,7 +875,7 @@ ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster
     return TS_OK;
   }
   if ((bk != 32 && bk != 64) || bn_cap < 16 || bn_cap > 256 || bn_cap % 16 != 0 || n < 0 ||
-      (cluster != 1 && cluster != 2 && cluster != 4 && cluster != TS_TC_PAIR && cluster != TS_TC_SWAPPED)) {
+      (cluster != 1 && cluster != 2 && cluster != 4 && cluster != TS_TC_PAIR)) {
     set_error("invalid tensor-core tile configuration (bk %d, bn_cap %d, cluster %d)", bk, bn_cap, cluster);
     return TS_ERR_INVALID_ARG;
   }
@@ -1123,8 +884,7 @@ ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster
   c.bk = bk;
   c.bn_cap = bn_cap;
   c.pair = cluster == TS_TC_PAIR;
-  c.tr = cluster == TS_TC_SWAPPED;
-  c.cm = c.pair || c.tr ? 1 : cluster;
+  c.cm = c.pair ? 1 : cluster;
   g_cfg[{complex_data ? 2 : 1, n}] = c;
   return TS_OK;
 }

@@ -66,7 +66,6 @@ class _ServingStats(C.Structure):
 
 
 TS_TC_PAIR = -2  # ts_tc_config_set cluster value: CTA pairs sharing each MMA
-TS_TC_SWAPPED = -3  # ts_tc_config_set cluster value: S_k as the 128-row MMA operand
 TS_REQ_INVERSE, TS_REQ_EXP, TS_REQ_PCG = range(3)
 
 _lib = None

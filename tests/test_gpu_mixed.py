@@ -193,65 +193,6 @@ def test_cta_pairs_match_single_cta(T, n, caps):
     assert np.array_equal(out_pair, out_one)
 
 
-SWAP_SHAPES = [(128, 128, 128), (256, 40, 8), (40, 24, 8), (264, 16), (16, 24), (136, 24, 40), (256,), (384, 24)]
-
-
-@pytest.mark.parametrize("n", SWAP_SHAPES)
-def test_swapped_operands_match_oracle(T, n):
-    """S_k as the 128-row MMA operand, each epilogue thread writing 16 consecutive data rows
-    as 16-byte vectors: BF16X3 inverse (its scale pass with the first row axis in whole runs
-    of 16 rows or not), BF16X6 complex exponential, the refined solve (u += delta), ragged
-    data-row tails (scalar stores) and 1-D grids stay within the split tolerances of the
-    oracle and agree with the unswapped passes to accumulation-order rounding."""
-    L, f = harmonic_case(n)
-    P, Po = plans(n, L, f, MASK)
-    b = S.normal(2, Po.N)
-    psi = S.complex_normal(3, Po.N)
-
-    def run(cluster):
-        try:
-            T.ts_tc_config_set(False, 0, 64, 256, cluster)
-            T.ts_tc_config_set(True, 0, 64, 128, cluster)
-            u = dev(np.zeros(Po.N))
-            T.ts_apply_inverse(P, 0.5, dev(b), u, T.TS_BF16X3)
-            out = dev(np.zeros(2 * Po.N))
-            T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C128, T.TS_BF16X6)
-            ur = dev(np.zeros(Po.N))
-            T.ts_solve_refined(P, 0.5, dev(b), ur, T.TS_BF16X3, 2)
-            T.ts_device_status()
-        finally:
-            T.ts_tc_config_reset(False)
-            T.ts_tc_config_reset(True)
-        return host(u), host(out), host(ur)
-
-    us, outs, urs = run(T.TS_TC_SWAPPED)
-    u1, out1, _ = run(1)
-    want = O.apply_inverse(Po, 0.5, b)
-    assert rel(us, want) < TOL[1]
-    assert rel(outs, O.apply_exp(Po, 0.01, psi)) < TOL[2]
-    assert rel(urs, want) < 1e-12
-    assert rel(us, u1) < 1e-6
-    assert rel(outs, out1) < 1e-6
-
-
-def test_swapped_operands_unaligned_output(T):
-    """An output pointer that is not 16-byte aligned turns the swapped epilogue's vector
-    stores (and the u += delta vector loads) into element stores; results are unchanged."""
-    n = (128, 16, 24)
-    L, f = harmonic_case(n)
-    P, Po = plans(n, L, f, MASK)
-    b = S.normal(2, Po.N)
-    want = O.apply_inverse(Po, 0.5, b)
-    buf = dev(np.zeros(Po.N + 1))
-    u = buf[1:]
-    T.ts_apply_inverse(P, 0.5, dev(b), u, T.TS_BF16X3)
-    assert rel(host(u), want) < TOL[1]
-    buf2 = dev(np.zeros(Po.N + 1))
-    ur = buf2[1:]
-    T.ts_solve_refined(P, 0.5, dev(b), ur, T.TS_BF16X3, 2)
-    assert rel(host(ur), want) < 1e-12
-
-
 @pytest.mark.parametrize("cluster", [2, 4])
 @pytest.mark.parametrize("n", [(64, 64, 64), (40, 24, 8), (264, 16), (128, 96, 48)])
 def test_multicast_clusters_match_oracle(T, n, cluster):
