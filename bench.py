@@ -478,10 +478,11 @@ def run_ours(args):
     return 0
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture in
-# profiles/k_rot_tc_bf16x3_n512.md: 1.030e9 for a bf16-plane pass and 1.558e9 for an
-# FP64-output pass, weighted 15 : 3 as they occur in one refined solve.
-TRAFFIC_PER_LAUNCH = (15 * 1.030e9 + 3 * 1.558e9) / 18
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu captures in
+# profiles/k_rot_tc_bf16x3_n512.md (CTA-pair kernel): 1.0313e9 for a bf16-plane pass,
+# 1.5573e9 for the FP64-store pass of u_0 and 2.6363e9 for a u += delta pass, weighted
+# 15 : 1 : 2 as they occur in one refined solve.
+TRAFFIC_PER_LAUNCH = (15 * 1.0313e9 + 1 * 1.5573e9 + 2 * 2.6363e9) / 18
 
 
 def main():
