@@ -303,7 +303,8 @@ ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precision prec, co
  * ts_profile_begin: start recording a CUDA event pair around every launch of the
  *   contraction kernels (on the launching stream); clears earlier records.
  * ts_profile_end: stop recording and sum the records of one kernel kind
- *   (0 = split-precision tensor-core pass, 1 = FP64 pass, 2 = small-n fused pass):
+ *   (0 = split-precision tensor-core pass, 1 = FP64 pass, 2 = small-n fused pass,
+ *   3 = refinement residual with the exact fixed-point Laplacian):
  *   launches, total device time in ms, algorithmic FLOPs and algorithmic HBM bytes.
  *   Synchronises on the recorded events.  Any pointer may be NULL.
  */

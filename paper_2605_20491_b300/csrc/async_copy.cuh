@@ -1,0 +1,30 @@
+// cp.async (global -> shared, Ampere-style asynchronous copies) wrappers shared by the
+// small-n contraction and the refinement residual: 8-byte copies, optionally zero-filled,
+// grouped with commit_group / wait_group.
+#pragma once
+#include <cstdint>
+
+namespace ts {
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gmem_src)
+               : "memory");
+}
+
+// As cp_async8, but when `valid` is false nothing is read and the 8 bytes are zeroed
+// (gmem_src must still be a valid address).
+__device__ __forceinline__ void cp_async8_zfill(void* smem_dst, const void* gmem_src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gmem_src), "r"(valid ? 8 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most NPEND of this thread's most recent groups are still in flight.
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
+
+}  // namespace ts

@@ -42,7 +42,7 @@ void count_launches(int k);
 
 // Live per-kernel timing (ts_profile_begin / ts_profile_end): when enabled, the launch
 // sites of the contraction kernels bracket each launch with CUDA events on its stream.
-enum ProfKind { PROF_TC_PASS = 0, PROF_FP64_PASS = 1, PROF_SMALL_PASS = 2, PROF_NKINDS = 3 };
+enum ProfKind { PROF_TC_PASS = 0, PROF_FP64_PASS = 1, PROF_SMALL_PASS = 2, PROF_RESIDUAL = 3, PROF_NKINDS = 4 };
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, void** token);
 void prof_end_launch(cudaStream_t s, void* token, int kind, double flops, double bytes);

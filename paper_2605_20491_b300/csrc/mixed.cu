@@ -806,10 +806,12 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
   const int np = bf16_planes(prec);
   const long long N = p->N;
   const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)np * N;
-  void *w0 = nullptr, *w1 = nullptr, *partial = nullptr;
+  void *w0 = nullptr, *w1 = nullptr, *partial = nullptr, *qtab = nullptr;
   TS_TRY(scratch_alloc(&w0, plane_bytes, s));
   ts_status st = scratch_alloc(&w1, plane_bytes, s);
   if (st == TS_OK) st = scratch_alloc(&partial, sizeof(double) * 2 * RED_BLOCKS, s);
+  if (st == TS_OK && qtable_count(p) > 0 && refinements > 0)
+    st = scratch_alloc(&qtab, sizeof(long long) * qtable_count(p), s);
   __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
   // On isotropic grids the residual's Laplacian is summed in exact fixed point, scaled by
   // the largest exponent of u; the pass that writes u finds it on the way out.
@@ -832,7 +834,7 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
   for (int it = 0; it < refinements && st == TS_OK; ++it) {
     const bool more = it + 1 < refinements;
     if (fixed)
-      st = residual_split_fixed(p, sigma, u, b, buf[0], np, emax, s);
+      st = residual_split_fixed(p, sigma, u, b, buf[0], np, emax, (long long*)qtab, s);
     else
       st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
     if (st == TS_OK && more) st = zero_emax();
@@ -843,6 +845,7 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
   scratch_free(w0, s);
   scratch_free(w1, s);
   scratch_free(partial, s);
+  scratch_free(qtab, s);
   return st;
 }
 

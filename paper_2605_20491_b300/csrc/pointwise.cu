@@ -7,6 +7,7 @@
 // (148 SMs x 4) CTAs so that reductions see a fixed partition of the index space and
 // return bit-identical sums on every call (two-level reduction: per-CTA partials in a
 // fixed order, then one CTA sums the partials in a fixed order).
+#include "async_copy.cuh"
 #include "common.cuh"
 #include "pointwise.cuh"
 #include "split.cuh"
@@ -292,21 +293,55 @@ __global__ void k_residual_fixed(AxisParams a, double sigma, const double* __res
   }
 }
 
+// (Q * U) >> F for 64-bit Q and U with the 128-bit product (floor), 0 < F < 64, for
+// results that fit in 64 bits.
+__device__ __forceinline__ long long mul_shift(long long q, long long u, int F) {
+  const unsigned long long lo = (unsigned long long)q * (unsigned long long)u;
+  const long long hi = __mul64hi(q, u);
+  return (long long)((unsigned long long)hi << (64 - F)) | (long long)(lo >> F);
+}
+
+// Q tables of the folded diagonal: Q[0] = sigma / h^-2, then f_0 / h^-2, f_1 / h^-2,
+// f_2 / h^-2, each as a fixed-point integer with F fractional bits (rounded to nearest).
+__global__ void k_qtables(const double* f0, int n0, const double* f1, int n1, const double* f2, int n2, double sigma,
+                          double ih2, int F, long long* Q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = 1 + n0 + n1 + n2;
+  if (i >= total) return;
+  double v;
+  if (i == 0) v = sigma;
+  else if (i <= n0) v = f0[i - 1];
+  else if (i <= n0 + n1) v = f1[i - 1 - n0];
+  else v = f2[i - 1 - n0 - n1];
+  Q[i] = llrint(ldexp(v / ih2, F));
+}
+
 // The same residual for d = 3, converting every value to fixed point once: a block owns a
 // 32 x 16 tile of axes (0, 1) and marches along axis 2 over MZ planes.  The axis-2 neighbours
 // come from a three-plane register queue; the axis-0/1 neighbours from a shared-memory copy
 // of the current plane with a one-cell halo (converted by warps 0-2: top row, bottom row,
-// left and right columns).  The next plane's x and the current plane's b are loaded one
-// step ahead.  H = 58 (4d |U| < 2^62), so P = 5.  The conversions of the Laplacian to
-// double and of the residual to float run on the integer pipe: three FP64 instructions per
-// point remain (diagonal sum, two FMAs).
+// left and right columns).  Loads run RD - 1 steps ahead through a per-thread ring in
+// shared memory filled by cp.async (each thread lands exactly the values it reads later:
+// its two cells of x and b and its halo cell), so that enough bytes are in flight to cover
+// HBM latency without holding them in registers.  The conversion of the residual to float
+// runs on the integer pipe.
+// QF = false: H = 58 (4d |U| < 2^62); three FP64 instructions per point remain (diagonal
+//   sum, two FMAs).
+// QF = true: the diagonal (sigma + V1) u joins the fixed-point sum as (Q_a + Q_z) U >> F,
+//   with Q = (sigma + f_0 + f_1) / h^-2 per thread and f_2 / h^-2 per plane from the Q
+//   tables (F fractional bits) and a 128-bit integer product; H = 53 + P leaves room for
+//   4d |U| + |Q U| / 2^F.  One FP64 instruction per point remains: r = b - c_s L.
 constexpr int MX = 32, MY = 16, MZ = 32;
-template <int NP>
-__global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double sigma, const double* __restrict__ x,
+constexpr int RD = 4;           // ring depth (groups in flight: RD - 1)
+constexpr int RING_VALUES = 5;  // per thread and group: x(z+1) of both cells, halo x(z+1), b(z) of both cells
+constexpr int RING_BYTES = RD * RING_VALUES * 256 * 8;
+template <int NP, int P, bool QF>
+__global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double sigma, const long long* __restrict__ Q,
+                                                         int F, const double* __restrict__ x,
                                                          const double* __restrict__ b,
                                                          __nv_bfloat16* __restrict__ planes, long long N,
                                                          const int* __restrict__ emax_ptr) {
-  constexpr int H = 58, P = H - 53;
+  constexpr int H = 53 + P;
   __shared__ long long sU[2][MY + 2][MX + 2];
   const int emax = *emax_ptr;
   const double cs = ldexp(a.ih2[0], emax - 1022 - H);
@@ -335,10 +370,48 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
   }
   const bool hv = ly < 3 && hi0 >= 0 && hi0 < n0 && hi1 >= 0 && hi1 < n1;
   const long long oh = hv ? (long long)hi1 * n0 + hi0 : 0;
-  const double ca = va ? sigma + a.tab[0][i0] + a.tab[1][ia] : 0.0;
-  const double cb = vb ? sigma + a.tab[0][i0] + a.tab[1][ib] : 0.0;
+  const double ca = !QF && va ? sigma + a.tab[0][i0] + a.tab[1][ia] : 0.0;
+  const double cb = !QF && vb ? sigma + a.tab[0][i0] + a.tab[1][ib] : 0.0;
+  const long long qa = QF && va ? Q[0] + Q[1 + i0] + Q[1 + n0 + ia] : 0;
+  const long long qb = QF && vb ? Q[0] + Q[1 + i0] + Q[1 + n0 + ib] : 0;
   const double* f2 = a.tab[2];
+  const long long* q2 = QF ? Q + 1 + n0 + n1 : nullptr;
 
+  // ring[g][v][thread]: group g % RD, value v (0, 1: x of cells a, b at z + 1; 2: halo x at
+  // z + 1; 3, 4: b of cells a, b at z), consecutive threads in consecutive words
+  static_assert((RD & (RD - 1)) == 0, "ring depth is a power of two");
+  extern __shared__ double ring[];
+  double* const my_ring = ring + threadIdx.x;
+  // group of step z: x(z + 1) of both cells and of the halo cell, b(z) of both cells;
+  // out-of-range values are zero-filled (Dirichlet zeros outside the grid).  Source
+  // pointers advance by one plane per issued group; invalid cells read nothing.
+  const double* sxa = x + (va ? oa + (long long)(z0 + 1) * s2 : 0);
+  const double* sxb = x + (vb ? ob + (long long)(z0 + 1) * s2 : 0);
+  const double* sxh = x + (hv ? oh + (long long)(z0 + 1) * s2 : 0);
+  const double* sba = b + (va ? oa + (long long)z0 * s2 : 0);
+  const double* sbb = b + (vb ? ob + (long long)z0 * s2 : 0);
+  const long long sa_step = va ? s2 : 0, sb_step = vb ? s2 : 0, sh_step = hv ? s2 : 0;
+  auto issue = [&](int z) {
+    if (z < z1) {
+      double* dst = my_ring + ((z - z0) & (RD - 1)) * (RING_VALUES * 256);
+      const bool xn = z + 1 < n2, hn = hv && z + 1 < z1;
+      cp_async8_zfill(dst, va && xn ? sxa : x, va && xn);  // past the last plane: no address
+      cp_async8_zfill(dst + 256, vb && xn ? sxb : x, vb && xn);
+      if (ly < 3) cp_async8_zfill(dst + 512, hn ? sxh : x, hn);
+      cp_async8_zfill(dst + 768, sba, va);
+      cp_async8_zfill(dst + 1024, sbb, vb);
+      sxa += sa_step;
+      sxb += sb_step;
+      sxh += sh_step;
+      sba += sa_step;
+      sbb += sb_step;
+    }
+    cp_async_commit();  // an empty group past the end keeps the group count uniform
+  };
+  for (int k = 0; k < RD - 1; ++k) issue(z0 + k);
+  // output pointers of the two cells' plane-0 elements, advanced one plane per step
+  __nv_bfloat16* pa = planes + (va ? oa + (long long)z0 * s2 : 0);
+  __nv_bfloat16* pb = planes + (vb ? ob + (long long)z0 * s2 : 0);
   auto ld = [&](bool v, const double* base, long long off, int z) -> double {
     return v ? base[off + z * s2] : 0.0;
   };
@@ -349,38 +422,47 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
   sU[0][ly + 1][lx + 1] = Uca;
   sU[0][ly + 9][lx + 1] = Ucb;
   if (ly < 3) sU[0][hy][hx] = to_fixed(ld(hv, x, oh, z0), emax, P);
-  // one step ahead: x of plane z0 + 1 (own cells and halo), b of plane z0
-  double xna = ld(va && z0 + 1 < n2, x, oa, z0 + 1), xnb = ld(vb && z0 + 1 < n2, x, ob, z0 + 1);
-  double xnh = ld(hv && z0 + 1 < z1, x, oh, z0 + 1);
-  double ba = ld(va, b, oa, z0), bb = ld(vb, b, ob, z0);
   int buf = 0;
   for (int z = z0; z < z1; ++z) {
+    cp_async_wait<RD - 2>();  // this step's group has landed (this thread's own copies)
+    const double* src = my_ring + ((z - z0) & (RD - 1)) * (RING_VALUES * 256);
+    const double xna = src[0], xnb = src[256];
+    const double xnh = ly < 3 ? src[512] : 0.0;
+    const double b_a = src[768], b_b = src[1024];
+    issue(z + RD - 1);  // refills the slot read in the previous step (by this same thread)
     const long long Una = to_fixed(xna, emax, P), Unb = to_fixed(xnb, emax, P);
     const long long Unh = to_fixed(xnh, emax, P);
-    const double xa = xca, xb = xcb, b_a = ba, b_b = bb;
+    const double xa = xca, xb = xcb;
     xca = xna;
     xcb = xnb;
-    // issue the loads of the next step
-    xna = ld(va && z + 2 < n2, x, oa, z + 2);
-    xnb = ld(vb && z + 2 < n2, x, ob, z + 2);
-    xnh = ld(hv && z + 2 < z1, x, oh, z + 2);
-    ba = ld(va && z + 1 < z1, b, oa, z + 1);
-    bb = ld(vb && z + 1 < z1, b, ob, z + 1);
     __syncthreads();
     const long long(*T)[MX + 2] = sU[buf];
     const long long La = 6 * Uca - Upa - Una - T[ly + 1][lx] - T[ly + 1][lx + 2] - T[ly][lx + 1] - T[ly + 2][lx + 1];
     const long long Lb = 6 * Ucb - Upb - Unb - T[ly + 9][lx] - T[ly + 9][lx + 2] - T[ly + 8][lx + 1] -
                          T[ly + 10][lx + 1];
-    const double fz = f2[z];
-    const long long zoff = z * s2;
-    if (va) {
-      const double r = fma(-cs, i64_to_f64(La), fma(-(ca + fz), xa, b_a));
-      split_store<NP>(f64_to_f32(r), planes, N, oa + zoff);
+    if (QF) {
+      const long long qz = q2[z];
+      if (va) {
+        const double r = fma(-cs, __ll2double_rn(La + mul_shift(qa + qz, Uca, F)), b_a);
+        split_store<NP>(f64_to_f32(r), pa, N, 0);
+      }
+      if (vb) {
+        const double r = fma(-cs, __ll2double_rn(Lb + mul_shift(qb + qz, Ucb, F)), b_b);
+        split_store<NP>(f64_to_f32(r), pb, N, 0);
+      }
+    } else {
+      const double fz = f2[z];
+      if (va) {
+        const double r = fma(-cs, i64_to_f64(La), fma(-(ca + fz), xa, b_a));
+        split_store<NP>(f64_to_f32(r), pa, N, 0);
+      }
+      if (vb) {
+        const double r = fma(-cs, i64_to_f64(Lb), fma(-(cb + fz), xb, b_b));
+        split_store<NP>(f64_to_f32(r), pb, N, 0);
+      }
     }
-    if (vb) {
-      const double r = fma(-cs, i64_to_f64(Lb), fma(-(cb + fz), xb, b_b));
-      split_store<NP>(f64_to_f32(r), planes, N, ob + zoff);
-    }
+    pa += sa_step;
+    pb += sb_step;
     sU[buf ^ 1][ly + 1][lx + 1] = Una;
     sU[buf ^ 1][ly + 9][lx + 1] = Unb;
     if (ly < 3) sU[buf ^ 1][hy][hx] = Unh;
@@ -570,18 +652,85 @@ bool isotropic_h(const ts_plan* p) {
   return true;
 }
 
+int qtable_count(const ts_plan* p) { return p->d == 3 ? 1 + p->n[0] + p->n[1] + p->n[2] : 0; }
+
+namespace {
+ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const double* x, const double* b,
+                                      __nv_bfloat16* planes, int np, const int* emax_dev, long long* qtab,
+                                      cudaStream_t s);
+}  // namespace
+
+// Times the kernel (profiling kind PROF_RESIDUAL: x, b in, NP bf16 planes out).
 ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, const double* b,
-                               __nv_bfloat16* planes, int np, const int* emax_dev, cudaStream_t s) {
+                               __nv_bfloat16* planes, int np, const int* emax_dev, long long* qtab, cudaStream_t s) {
+  void* tok = nullptr;
+  if (prof_enabled()) prof_begin_launch(s, &tok);
+  const ts_status st = residual_split_fixed_launch(p, sigma, x, b, planes, np, emax_dev, qtab, s);
+  if (tok) prof_end_launch(s, tok, PROF_RESIDUAL, 0.0, (16.0 + 2.0 * np) * (double)p->N);
+  return st;
+}
+
+namespace {
+template <int NP, int P, bool QF>
+ts_status launch_march3(long long blocks, const AxisParams& a, double sigma, const long long* Q, int F,
+                        const double* x, const double* b, __nv_bfloat16* planes, long long N, const int* emax_dev,
+                        cudaStream_t s) {
+  static bool attr_set = false;  // per instantiation: the ring is dynamic shared memory
+  if (!attr_set) {
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_residual_march3<NP, P, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       RING_BYTES));
+    attr_set = true;
+  }
+  k_residual_march3<NP, P, QF><<<(unsigned)blocks, 256, RING_BYTES, s>>>(a, sigma, Q, F, x, b, planes, N, emax_dev);
+  return TS_OK;
+}
+
+ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const double* x, const double* b,
+                                      __nv_bfloat16* planes, int np, const int* emax_dev, long long* qtab,
+                                      cudaStream_t s) {
   int H = 62;  // headroom: 2d |U| + 2d |U| < 2^63
   for (long long t = 4LL * p->d; t > 1; t = (t + 1) / 2) --H;
   const AxisParams a = axis_params(p, false);
   if (p->d == 3) {
     const long long blocks = (long long)((p->n[0] + MX - 1) / MX) * ((p->n[1] + MY - 1) / MY) *
                              ((p->n[2] + MZ - 1) / MZ);
+    // Folded diagonal: q_max bounds |sigma + V1| / h^-2; H leaves room for
+    // (4d + q_max + 1) 2^H <= 2^62, F for q_max 2^F < 2^62; needs H >= 53.
+    double fmax = std::fabs(sigma);
+    for (int k = 0; k < 3; ++k) {
+      double m = 0.0;
+      for (double v : p->axis[k]->f) m = std::fmax(m, std::fabs(v));
+      fmax += m;
+    }
+    const double qmax = fmax / a.ih2[0];
+    int Hq = 58;
+    while (Hq >= 53 && std::ldexp(4.0 * p->d + qmax + 1.0, Hq) > std::ldexp(1.0, 62)) --Hq;
+    int F = 62;
+    while (F > Hq && std::ldexp(qmax + 1.0, F) >= std::ldexp(1.0, 62)) --F;
+    if (qtab && Hq >= 53 && F >= Hq && std::isfinite(qmax)) {
+      const int total = qtable_count(p);
+      k_qtables<<<(total + 127) / 128, 128, 0, s>>>(p->f[0], p->n[0], p->f[1], p->n[1], p->f[2], p->n[2], sigma,
+                                                    a.ih2[0], F, qtab);
+      TS_LAUNCHED(1);
+#define TS_QF_CASE(PP)                                                                                  \
+  case PP:                                                                                              \
+    if (np == 2)                                                                                        \
+      TS_TRY((launch_march3<2, PP, true>(blocks, a, sigma, qtab, F, x, b, planes, p->N, emax_dev, s)));  \
+    else                                                                                                \
+      TS_TRY((launch_march3<3, PP, true>(blocks, a, sigma, qtab, F, x, b, planes, p->N, emax_dev, s)));  \
+    break;
+      switch (Hq - 53) {
+        TS_QF_CASE(0) TS_QF_CASE(1) TS_QF_CASE(2) TS_QF_CASE(3) TS_QF_CASE(4)
+        default: TS_QF_CASE(5)
+      }
+#undef TS_QF_CASE
+      TS_LAUNCHED(1);
+      return TS_OK;
+    }
     if (np == 2)
-      k_residual_march3<2><<<(unsigned)blocks, 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev);
+      TS_TRY((launch_march3<2, 5, false>(blocks, a, sigma, nullptr, 0, x, b, planes, p->N, emax_dev, s)));
     else
-      k_residual_march3<3><<<(unsigned)blocks, 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev);
+      TS_TRY((launch_march3<3, 5, false>(blocks, a, sigma, nullptr, 0, x, b, planes, p->N, emax_dev, s)));
     TS_LAUNCHED(1);
     return TS_OK;
   }
@@ -592,6 +741,7 @@ ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, 
   TS_LAUNCHED(1);
   return TS_OK;
 }
+}  // namespace
 
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s) {

@@ -23,8 +23,12 @@ bool isotropic_h(const ts_plan* p);
 // As stencil_residual_split without V2, for isotropic grids: the Laplacian part in exact
 // 64-bit fixed point, scaled by *emax_dev, which must hold the largest biased exponent of
 // the values of x (a larger value is safe and costs precision; a smaller one overflows).
+// qtab (may be NULL): qtable_count(p) int64 of device scratch; when given (d = 3), the
+// diagonal (sigma + V1) x is folded into the exact fixed-point sum too, leaving one FP64
+// instruction per point, unless sigma + V1 is too large against h^-2 for 53 bits of headroom.
 ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, const double* b,
-                               __nv_bfloat16* planes, int np, const int* emax_dev, cudaStream_t s);
+                               __nv_bfloat16* planes, int np, const int* emax_dev, long long* qtab, cudaStream_t s);
+int qtable_count(const ts_plan* p);
 // out2[0] = a.b (b == NULL: sum of a), out2[1] = c.d (c, d may be NULL).
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "async_copy.cuh"
 #include "small_n.cuh"
 
 namespace ts {
@@ -135,15 +136,6 @@ __device__ __forceinline__ int tile_index(int e, int lgTlo, const GroupParams& p
   *th_out = r;
   return sidx + r * mul;
 }
-
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
-               "l"(gmem_src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
 
 // First element of tile b: (l0, h0) as in the tiling described at the top.
 __device__ __forceinline__ void tile_origin(long long b, int lgTlo, int Thi, const GroupParams& p, long long* l0,

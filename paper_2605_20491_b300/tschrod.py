@@ -286,7 +286,7 @@ def ts_profile_begin():
     _check(lib().ts_profile_begin(), "ts_profile_begin")
 
 
-PROF_TC_PASS, PROF_FP64_PASS, PROF_SMALL_PASS = range(3)
+PROF_TC_PASS, PROF_FP64_PASS, PROF_SMALL_PASS, PROF_RESIDUAL = range(4)
 
 
 def ts_profile_end(kind: int):
