@@ -21,6 +21,7 @@ of the same workload; multi-GPU launches run one independent replica per rank.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -58,18 +59,22 @@ def load_peaks():
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.window = None  # (t0, t1) host wall-clock seconds of the timed region
+
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -83,22 +88,24 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), [nm for nm, v in zip(names, f[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+        inside = [r for r in rows if self.window and self.window[0] <= r[0] <= self.window[1]]
+        use = inside or rows  # a region shorter than the sampling period keeps the nearby samples
+        sm = [r[1] for r in use]
+        mx = [r[2] for r in use]
+        reasons = sorted({nm for r in use for nm in r[3]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
 
 
 def dist_env():
@@ -388,15 +395,16 @@ def run_ours(args):
     def step():
         T.ts_solve_refined(P, sigma, b, x, T.TS_BF16X3, REFINEMENTS)
 
+    clocks = ClockSampler(local)
+    clocks.start()  # started before the warm-up so that it samples from the first timed step
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     err = ((x - u64).norm() / nrm).item()
 
-    clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_wall0 = time.time()
     launches0 = T.ts_launch_count()
     T.ts_profile_begin()
     e0.record()
@@ -404,8 +412,10 @@ def run_ours(args):
         step()
     e1.record()
     torch.cuda.synchronize()
+    clocks.mark(t_wall0, time.time())
     barrier()
     tc_launches, tc_ms, tc_flops, tc_bytes = T.ts_profile_end(T.PROF_TC_PASS)
+    res_launches, res_ms, _, res_bytes = T.ts_profile_end(T.PROF_RESIDUAL)
     launches = T.ts_launch_count() - launches0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -415,24 +425,44 @@ def run_ours(args):
         ms = t.item()
     value = world * N / (ms * 1e-3) / 1e9
 
-    # End to end through the public API with host buffers: H2D of b, solve, D2H of u.
-    u_host = torch.empty_like(b_host).pin_memory()
-    bd = torch.empty_like(b)
+    # End to end through the public API with host buffers: every step copies its right-hand
+    # side from pinned host memory, solves, and copies its solution back.  Steps are
+    # pipelined over two buffer sets and three streams, as a serving loop would run them:
+    # the upload of step k+1 and the download of step k-1 overlap the solve of step k.
+    s_h2d, s_cmp, s_d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    bd = [torch.empty_like(b) for _ in range(2)]
+    xd = [torch.empty_like(b) for _ in range(2)]
+    u_host = [torch.empty_like(b_host).pin_memory() for _ in range(2)]
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("h2d", "cmp", "d2h")}
+    for j in range(2):
+        for k in ev:
+            ev[k][j].record(torch.cuda.current_stream())
 
-    def e2e_step():
-        bd.copy_(b_host, non_blocking=True)
-        T.ts_solve_refined(P, sigma, bd, x, T.TS_BF16X3, REFINEMENTS)
-        u_host.copy_(x, non_blocking=True)
+    def e2e_run(n_steps):
+        for k in range(n_steps):
+            j = k % 2
+            with torch.cuda.stream(s_h2d):
+                s_h2d.wait_event(ev["cmp"][j])  # bd[j] is free once step k-2 has been solved
+                bd[j].copy_(b_host, non_blocking=True)
+                ev["h2d"][j].record(s_h2d)
+            s_cmp.wait_event(ev["h2d"][j])
+            s_cmp.wait_event(ev["d2h"][j])  # xd[j] is free once step k-2 has been downloaded
+            T.ts_solve_refined(P, sigma, bd[j], xd[j], T.TS_BF16X3, REFINEMENTS, stream=s_cmp)
+            ev["cmp"][j].record(s_cmp)
+            with torch.cuda.stream(s_d2h):
+                s_d2h.wait_event(ev["cmp"][j])
+                u_host[j].copy_(xd[j], non_blocking=True)
+                ev["d2h"][j].record(s_d2h)
         torch.cuda.synchronize()
+        return (n_steps - 1) % 2
 
-    e2e_step()
-    n_e2e = max(3, args.steps // 2)
+    e2e_run(2)
+    n_e2e = max(4, args.steps // 2)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        e2e_step()
+    last = e2e_run(n_e2e)
     e2e_ms = (time.perf_counter() - t0) / n_e2e * 1e3
-    e2e_err = float(np.linalg.norm(u_host.numpy() - u64.cpu().numpy()) / nrm)
+    e2e_err = float(np.linalg.norm(u_host[last].numpy() - u64.cpu().numpy()) / nrm)
 
     peaks, peaks_src = load_peaks()
     avg_launch_ms = tc_ms / max(1, tc_launches)
@@ -460,9 +490,18 @@ def run_ours(args):
             "mixed_single_apply": {"prec": "BF16X3", "ms": mixed1_ms, "gdofs": N / (mixed1_ms * 1e-3) / 1e9,
                                    "err_vs_fp64": mixed1_err},
             "speedup_vs_fp64": fp64_ms / ms,
-            "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+            "roofline": roofline,
+            # second kernel of the step: the refinement residual (HBM-streaming; x, b in, planes out)
+            "residual_kernel": {"kernel": "k_residual_march3", "launches": res_launches,
+                                "avg_launch_ms": res_ms / max(1, res_launches),
+                                "achieved_gbs": res_bytes / max(1e-9, res_ms * 1e-3) / 1e9,
+                                "peak_gbs": peaks["hbm_gbs"],
+                                "frac": res_bytes / max(1e-9, res_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                "share_of_step": res_ms / max(1e-9, ms * args.steps)},
+            "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N, "err_vs_fp64": e2e_err}}
+                    "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N, "err_vs_fp64": e2e_err,
+                    "pipelining": "2 buffer sets, 3 streams: upload k+1 and download k-1 overlap solve k"}}
     if rank == 0 and not args.no_serving:
         sv = serving_run(T, args.requests)
         line["serving"] = sv
@@ -488,7 +527,7 @@ TRAFFIC_PER_LAUNCH = (15 * 1.0313e9 + 1 * 1.5573e9 + 2 * 2.6363e9) / 18
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
