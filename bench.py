@@ -40,9 +40,12 @@ from paper_2605_20491_b300 import synth  # noqa: E402
 WORKLOAD = "3d_n512_apply"
 METRIC = "GDoF/s of (-Delta+V1)^-1 apply, FP64 vs mixed at stated err; p50/p99 latency"
 UNIT = "GDoF/s"
-# Refinements after the first split-precision apply: each multiplies the error by about
-# the single-apply error (1.6e-5 measured at n = 512), so two give ~1e-14 < 1e-10.
-REFINEMENTS = 2
+# Precision of each apply of the refined solve (u_0 = P_0 b, then one refinement per further
+# entry).  The error contracts by each apply's relative error; measured at n = 512:
+# BF16X3 1.6e-5 per apply, BF16X1 5.6e-3; {3, 3} ends at 7.8e-10 (above the target),
+# {3, 3, 3} at 2.2e-14 in 8.79 ms, {3, 3, 1} at 5.2e-12 in 7.91 ms: the last refinement only
+# needs a coarse inverse.
+SCHEDULE = ("TS_BF16X3", "TS_BF16X3", "TS_BF16X1")
 # PCG (V2 = 0) tolerance for the alternative CG-accelerated solve reported beside it.
 PCG_TOL = 1e-12
 ERR_TARGET = 1e-10
@@ -192,11 +195,11 @@ def run_profile_case(args):
         return 0
     w = synth.WORKLOADS[WORKLOAD]
     n = (args.profile_n,) * 3 if args.profile_n else w["n"]
-    P = T.ts_plan_create(n, w["L"], synth.harmonic(n, w["L"], w["omega"]), (1 << T.TS_BF16X3))
+    P = T.ts_plan_create(n, w["L"], synth.harmonic(n, w["L"], w["omega"]), (1 << T.TS_BF16X3) | (1 << T.TS_BF16X1))
     b = torch.from_numpy(synth.normal(w["seed"], P.N)).cuda()
     x = torch.empty_like(b)
     for _ in range(args.warmup + args.steps):
-        T.ts_solve_refined(P, w["sigma"], b, x, T.TS_BF16X3, REFINEMENTS)
+        T.ts_solve_schedule(P, w["sigma"], b, x, [getattr(T, q) for q in SCHEDULE])
     torch.cuda.synchronize()
     T.ts_device_status()
     print("profile case done", flush=True)
@@ -345,8 +348,9 @@ def run_ours(args):
     w = synth.WORKLOADS[WORKLOAD]
     n, L = w["n"], w["L"]
     f = synth.harmonic(n, L, w["omega"])
-    mask = (1 << T.TS_BF16X3)
+    mask = (1 << T.TS_BF16X3) | (1 << T.TS_BF16X1)
     P = T.ts_plan_create(n, L, f, mask)
+    sched = [getattr(T, q) for q in SCHEDULE]
     N = P.N
     sigma = w["sigma"]
     b_host = torch.from_numpy(synth.normal(w["seed"], N)).pin_memory()
@@ -393,7 +397,7 @@ def run_ours(args):
     pcg_err = ((x - u64).norm() / nrm).item()
 
     def step():
-        T.ts_solve_refined(P, sigma, b, x, T.TS_BF16X3, REFINEMENTS)
+        T.ts_solve_schedule(P, sigma, b, x, sched)
 
     clocks = ClockSampler(local)
     clocks.start()  # started before the warm-up so that it samples from the first timed step
@@ -416,6 +420,7 @@ def run_ours(args):
     barrier()
     tc_launches, tc_ms, tc_flops, tc_bytes = T.ts_profile_end(T.PROF_TC_PASS)
     res_launches, res_ms, _, res_bytes = T.ts_profile_end(T.PROF_RESIDUAL)
+    x1_launches, x1_ms, x1_flops, x1_bytes = T.ts_profile_end(T.PROF_TC_PASS_X1)
     launches = T.ts_launch_count() - launches0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -447,7 +452,7 @@ def run_ours(args):
                 ev["h2d"][j].record(s_h2d)
             s_cmp.wait_event(ev["h2d"][j])
             s_cmp.wait_event(ev["d2h"][j])  # xd[j] is free once step k-2 has been downloaded
-            T.ts_solve_refined(P, sigma, bd[j], xd[j], T.TS_BF16X3, REFINEMENTS, stream=s_cmp)
+            T.ts_solve_schedule(P, sigma, bd[j], xd[j], sched, stream=s_cmp)
             ev["cmp"][j].record(s_cmp)
             with torch.cuda.stream(s_d2h):
                 s_d2h.wait_event(ev["cmp"][j])
@@ -468,7 +473,7 @@ def run_ours(args):
     avg_launch_ms = tc_ms / max(1, tc_launches)
     achieved = (tc_flops / max(1, tc_launches)) / (avg_launch_ms * 1e-3) / 1e12 if tc_launches else None
     peak = peaks["bf16_tflops_sustained"]
-    roofline = {"bound": "tensor", "kernel": "k_rot_tc (BF16X3 split pass)", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "tensor", "kernel": "k_rot_tc (BF16X3 split passes)", "achieved": achieved, "peak": peak,
                 "peak_kind": f"bf16 dense sustained ({peaks_src})", "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": TRAFFIC_PER_LAUNCH,
@@ -478,10 +483,12 @@ def run_ours(args):
                 "share_of_step": tc_ms / (ms * args.steps)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16 splits (x3, x1) + f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": list(n), "L": list(L), "omega": list(w["omega"]), "sigma": sigma,
-                       "rhs": "iid N(0,1), SplitMix64 seed 2", "solve": "BF16X3 split tcgen05 inverse + "
-                       f"{REFINEMENTS} FP64-residual refinements", "l2": "inputs larger than L2 (1.07 GB per vector)",
+                       "rhs": "iid N(0,1), SplitMix64 seed 2",
+                       "solve": "split tcgen05 inverses " + " -> ".join(q[3:] for q in SCHEDULE)
+                       + " (u_0, then refinements with FP64 residuals)",
+                       "l2": "inputs larger than L2 (1.07 GB per vector)",
                        "parallelism": f"replicas x{world}"},
             "err_vs_fp64": err, "err_target": ERR_TARGET,
             "pcg": {"ms": pcg_ms, "iters": pcg_it, "tol": PCG_TOL, "err_vs_fp64": pcg_err,
@@ -491,6 +498,14 @@ def run_ours(args):
                                    "err_vs_fp64": mixed1_err},
             "speedup_vs_fp64": fp64_ms / ms,
             "roofline": roofline,
+            # the one-plane passes of the last refinement (same kernel, HBM-bound)
+            "x1_passes": {"kernel": "k_rot_tc (BF16X1, one bf16 plane)", "launches": x1_launches,
+                          "avg_launch_ms": x1_ms / max(1, x1_launches),
+                          "achieved_gbs": x1_bytes / max(1e-9, x1_ms * 1e-3) / 1e9,
+                          "achieved_tflops": x1_flops / max(1e-9, x1_ms * 1e-3) / 1e12,
+                          "peak_gbs": peaks["hbm_gbs"],
+                          "frac": x1_bytes / max(1e-9, x1_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                          "share_of_step": x1_ms / max(1e-9, ms * args.steps)},
             # second kernel of the step: the refinement residual (HBM-streaming; x, b in, planes out)
             "residual_kernel": {"kernel": "k_residual_march3", "launches": res_launches,
                                 "avg_launch_ms": res_ms / max(1, res_launches),
@@ -520,8 +535,9 @@ def run_ours(args):
 # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu captures in
 # profiles/k_rot_tc_bf16x3_n512.md (CTA-pair kernel): 1.0313e9 for a bf16-plane pass,
 # 1.5573e9 for the FP64-store pass of u_0 and 2.6363e9 for a u += delta pass, weighted
-# 15 : 1 : 2 as they occur in one refined solve.
-TRAFFIC_PER_LAUNCH = (15 * 1.0313e9 + 1 * 1.5573e9 + 2 * 2.6363e9) / 18
+# 10 : 1 : 1 as the BF16X3 passes occur in one solve of the schedule (the BF16X1 passes
+# of the last refinement are reported separately).
+TRAFFIC_PER_LAUNCH = (10 * 1.0313e9 + 1 * 1.5573e9 + 1 * 2.6363e9) / 12
 
 
 def main():

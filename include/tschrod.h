@@ -59,8 +59,10 @@ typedef enum {
   TS_BF16X6 = 2, /* 3-term bf16 splits, 6 products, FP32 accumulate (tcgen05)              */
   TS_TF32X3 = 3, /* 2-term tf32 splits, 3 products (reserved)                              */
   TS_FP16X3 = 4, /* 2-term fp16 splits with scaling (reserved)                            */
-  TS_FP32 = 5    /* plain FP32 (FFMA) fused small-n kernels: complex64 propagation with
+  TS_FP32 = 5,   /* plain FP32 (FFMA) fused small-n kernels: complex64 propagation with
                     every n_k in {8, 16, 24, 32} (the paper's FP32 variant)              */
+  TS_BF16X1 = 6  /* one bf16 plane, one product, FP32 accumulate (tcgen05): a cheap,
+                    coarse inverse (relative error ~1e-2) for the late refinements      */
 } ts_precision;
 
 typedef enum { TS_R64 = 0, TS_C128 = 1, TS_C64 = 2 } ts_dtype;
@@ -142,6 +144,17 @@ ts_status ts_apply_inverse_noalloc(const ts_plan* plan, double sigma, const doub
  * reach FP64 rounding.  No host synchronisation.  b, u: N doubles, must not alias.
  * prec = TS_FP64 performs the plain FP64 apply (refinements ignored).
  */
+/*
+ * The same refinement with a precision per apply (no counterpart in the paper): schedule[0]
+ * is the precision of u_0 = P b, schedule[k] that of refinement k (count = 1 + the number of
+ * refinements, 1..17; split precisions only, each in the plan's mask).  The error after
+ * the schedule is about the product of the applies' relative errors, so the late
+ * refinements can use a coarser, cheaper inverse: {TS_BF16X3, TS_BF16X3, TS_BF16X1} takes
+ * ~1.6e-5 -> ~2.5e-10 -> ~1e-12 at a third of the tensor work for the last apply.
+ */
+ts_status ts_solve_schedule(const ts_plan* plan, double sigma, const double* b, double* u,
+                            const ts_precision* schedule, int count, void* stream);
+
 ts_status ts_solve_refined(const ts_plan* plan, double sigma, const double* b, double* u,
                            ts_precision prec, int refinements, void* stream);
 
@@ -303,8 +316,9 @@ ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precision prec, co
  * ts_profile_begin: start recording a CUDA event pair around every launch of the
  *   contraction kernels (on the launching stream); clears earlier records.
  * ts_profile_end: stop recording and sum the records of one kernel kind
- *   (0 = split-precision tensor-core pass, 1 = FP64 pass, 2 = small-n fused pass,
- *   3 = refinement residual with the exact fixed-point Laplacian):
+ *   (0 = split-precision tensor-core pass with 2 or 3 bf16 planes, 1 = FP64 pass, 2 = small-n
+ *   fused pass, 3 = refinement residual with the exact fixed-point Laplacian, 4 = tensor-core
+ *   pass with one bf16 plane):
  *   launches, total device time in ms, algorithmic FLOPs and algorithmic HBM bytes.
  *   Synchronises on the recorded events.  Any pointer may be NULL.
  */

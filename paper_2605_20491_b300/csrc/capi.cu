@@ -160,6 +160,19 @@ ts_status ts_solve_refined(const ts_plan* plan, double sigma, const double* b, d
   return mixed_refine(plan, prec, sigma, b, u, refinements, (cudaStream_t)stream);
 }
 
+ts_status ts_solve_schedule(const ts_plan* plan, double sigma, const double* b, double* u,
+                            const ts_precision* schedule, int count, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(b && u && b != u, "b and u must be non-NULL and distinct");
+  TS_REQUIRE(schedule, "schedule is NULL");
+  TS_REQUIRE(count >= 1 && count <= 17, "count must be in [1, 17]");
+  for (int k = 0; k < count; ++k) {
+    TS_TRY(check_prec(plan, schedule[k]));
+    TS_REQUIRE(schedule[k] != TS_FP64 && schedule[k] != TS_FP32, "schedule[%d]: split precisions only", k);
+  }
+  return mixed_solve_schedule(plan, schedule, count, sigma, b, u, (cudaStream_t)stream);
+}
+
 ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void* psi_out, ts_dtype dtype,
                        ts_precision prec, void* stream) {
   TS_API_BEGIN(plan);

@@ -14,7 +14,7 @@
 namespace ts {
 
 constexpr int MAXD = TS_MAX_DIM;
-constexpr int NPREC = 6;
+constexpr int NPREC = 7;
 constexpr int MAX_PLANES = 3;
 
 // Thread-local error message of the last failing call.
@@ -42,7 +42,14 @@ void count_launches(int k);
 
 // Live per-kernel timing (ts_profile_begin / ts_profile_end): when enabled, the launch
 // sites of the contraction kernels bracket each launch with CUDA events on its stream.
-enum ProfKind { PROF_TC_PASS = 0, PROF_FP64_PASS = 1, PROF_SMALL_PASS = 2, PROF_RESIDUAL = 3, PROF_NKINDS = 4 };
+enum ProfKind {
+  PROF_TC_PASS = 0,     // split-precision tensor-core pass, 2 or 3 bf16 planes
+  PROF_FP64_PASS = 1,
+  PROF_SMALL_PASS = 2,
+  PROF_RESIDUAL = 3,
+  PROF_TC_PASS_X1 = 4,  // the same kernel with one bf16 plane (BF16X1)
+  PROF_NKINDS = 5
+};
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, void** token);
 void prof_end_launch(cudaStream_t s, void* token, int kind, double flops, double bytes);

@@ -6,11 +6,12 @@
 // carried as NP bf16 "planes" whose sum reproduces the value (x = x_0 + x_1 (+ x_2), each
 // plane the bf16 rounding of what the previous planes leave), following the multi-term
 // bf16 products of Henry, Tang & Heinecke (2019):
+//     NP = 1 (TS_BF16X1): x0 b0                                          (~8 bits)
 //     NP = 2 (TS_BF16X3): x0 b0 + x0 b1 + x1 b0                          (~16 bits)
 //     NP = 3 (TS_BF16X6): x0 b0 + x0 b1 + x1 b0 + x1 b1 + x0 b2 + x2 b0  (~24 bits)
 // All products of one output tile accumulate in one FP32 accumulator in tensor memory.
 //
-// Kernel structure: persistent (one CTA per SM, 320 threads), 128 x BN output tiles
+// Kernel structure: persistent (one CTA per SM, 576 threads), 128 x BN output tiles
 // handed out round-robin with the N tile fastest, so that the CTAs working on the same
 // 128 rows run together and share the X tile through L2:
 //   warp 0 lane 0  -- TMA producer: for each K chunk (BK = 64 with the 128-byte swizzle
@@ -20,13 +21,15 @@
 //   warp 1 lane 0  -- MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16) for
 //                     every (plane pair, K step) into one of two TMEM accumulator buffers;
 //                     commits free the ring slots and hand the buffer to the epilogue;
-//   warps 2..9     -- epilogue, overlapped with the next tile's MMAs: tcgen05.ld of the
+//   warps 2..17    -- epilogue, overlapped with the next tile's MMAs: tcgen05.ld of the
 //                     accumulator rows (warp w owns TMEM lanes 32 (w % 4) + 0..31 and
-//                     every other 16-column chunk),
+//                     every fourth 16-column chunk),
 //                     optional fused pointwise step 3 (1/(Lambda + sigma) or
 //                     e^{-i tau Lambda}, Lambda from per-axis tables), then either the NP
 //                     bf16 planes of the next pass or the final FP64 / complex128 /
 //                     complex64 result, stored transposed.
+// On long real axes CTA pairs (clusters of two) share every MMA instead (cta_group::2,
+// 256-row units, each CTA staging half of the B tile); see k_rot_tc.
 // Complex data is planar inside the pipeline (re and im planes); a complex tile keeps
 // two accumulators (re, im) that share every B tile, so the phase multiply can mix them.
 #include <cudaTypedefs.h>
@@ -43,6 +46,7 @@
 namespace ts {
 
 int bf16_planes(ts_precision prec) {
+  if (prec == TS_BF16X1) return 1;
   if (prec == TS_BF16X3) return 2;
   if (prec == TS_BF16X6) return 3;
   return 0;
@@ -78,6 +82,12 @@ struct EpiParams {
 
 template <int NP>
 struct Products;
+template <>
+struct Products<1> {
+  static constexpr int count = 1;
+  __device__ static int a(int) { return 0; }
+  __device__ static int b(int) { return 0; }
+};
 template <>
 struct Products<2> {
   static constexpr int count = 3;
@@ -554,7 +564,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
     const double bytes = (double)NACC * R * n * 2.0 * NP * (ep.out_mode == 0 ? 2.0 : 1.0) +
                          (ep.out_mode == 1 ? 8.0 : ep.out_mode == 2 ? 16.0 : ep.out_mode == 3 ? 8.0
                                                  : ep.out_mode == 4 ? 16.0 : 0.0) * R * n;
-    prof_end_launch(s, tok, PROF_TC_PASS, flops, bytes);
+    prof_end_launch(s, tok, NP == 1 ? PROF_TC_PASS_X1 : PROF_TC_PASS, flops, bytes);
   }
   return TS_OK;
 }
@@ -636,6 +646,8 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
 
 ts_status pass(int np, int nacc, const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n,
                const EpiParams& ep, cudaStream_t s) {
+  if (np == 1 && nacc == 1) return launch_pass<1, 1>(A, B, R, n, ep, s);
+  if (np == 1 && nacc == 2) return launch_pass<1, 2>(A, B, R, n, ep, s);
   if (np == 2 && nacc == 1) return launch_pass<2, 1>(A, B, R, n, ep, s);
   if (np == 2 && nacc == 2) return launch_pass<2, 2>(A, B, R, n, ep, s);
   if (np == 3 && nacc == 1) return launch_pass<3, 1>(A, B, R, n, ep, s);
@@ -653,7 +665,7 @@ unsigned grid_1d(long long N) {
 ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s) {
   const int np = bf16_planes(prec);
   if (np == 0) {
-    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X3, TS_BF16X6, TS_FP32)", (int)prec);
+    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X1, TS_BF16X3, TS_BF16X6, TS_FP32)", (int)prec);
     return TS_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < p->d; ++k) {
@@ -683,7 +695,7 @@ namespace {
 
 ts_status check_mixed(const ts_plan* p, ts_precision prec) {
   if (bf16_planes(prec) == 0) {
-    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X3, TS_BF16X6)", (int)prec);
+    set_error("precision %d is not implemented (available: TS_FP64, TS_BF16X1, TS_BF16X3, TS_BF16X6)", (int)prec);
     return TS_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < p->d; ++k) {
@@ -735,15 +747,17 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
 }
 
 ts_status split_input(int np, ts_dtype dt, const void* in, __nv_bfloat16* planes, long long N, cudaStream_t s) {
+#define TS_SPLIT(MODE)                                                   \
+  (np == 1   ? k_split_input<1, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N) \
+   : np == 2 ? k_split_input<2, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N) \
+             : k_split_input<3, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N))
   if (dt == TS_R64)
-    np == 2 ? k_split_input<2, 0><<<grid_1d(N), 256, 0, s>>>(in, planes, N)
-            : k_split_input<3, 0><<<grid_1d(N), 256, 0, s>>>(in, planes, N);
+    TS_SPLIT(0);
   else if (dt == TS_C128)
-    np == 2 ? k_split_input<2, 1><<<grid_1d(N), 256, 0, s>>>(in, planes, N)
-            : k_split_input<3, 1><<<grid_1d(N), 256, 0, s>>>(in, planes, N);
+    TS_SPLIT(1);
   else
-    np == 2 ? k_split_input<2, 2><<<grid_1d(N), 256, 0, s>>>(in, planes, N)
-            : k_split_input<3, 2><<<grid_1d(N), 256, 0, s>>>(in, planes, N);
+    TS_SPLIT(2);
+#undef TS_SPLIT
   TS_LAUNCHED(1);
   return TS_OK;
 }
@@ -802,10 +816,21 @@ ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigm
 
 ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
                        int refinements, cudaStream_t s) {
-  TS_TRY(check_mixed(p, prec));
-  const int np = bf16_planes(prec);
+  ts_precision sched[17];
+  for (int k = 0; k <= refinements && k < 17; ++k) sched[k] = prec;
+  return mixed_solve_schedule(p, sched, refinements + 1, sigma, b, u, s);
+}
+
+ts_status mixed_solve_schedule(const ts_plan* p, const ts_precision* sched, int count, double sigma,
+                               const double* b, double* u, cudaStream_t s) {
+  int npmax = 0;
+  for (int k = 0; k < count; ++k) {
+    TS_TRY(check_mixed(p, sched[k]));
+    npmax = bf16_planes(sched[k]) > npmax ? bf16_planes(sched[k]) : npmax;
+  }
+  const int refinements = count - 1;
   const long long N = p->N;
-  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)np * N;
+  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)npmax * N;
   void *w0 = nullptr, *w1 = nullptr, *partial = nullptr, *qtab = nullptr;
   TS_TRY(scratch_alloc(&w0, plane_bytes, s));
   ts_status st = scratch_alloc(&w1, plane_bytes, s);
@@ -824,15 +849,17 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
     }
     return TS_OK;
   };
-  // u_0 = P b
-  if (st == TS_OK) st = split_input(np, TS_R64, b, buf[0], N, s);
+  // u_0 = P_0 b
+  if (st == TS_OK) st = split_input(bf16_planes(sched[0]), TS_R64, b, buf[0], N, s);
   if (st == TS_OK && refinements > 0) st = zero_emax();
   if (st == TS_OK)
-    st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s,
+    st = run_passes(p, sched[0], MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s,
                     fixed && refinements > 0 ? emax : nullptr);
-  // u_{k+1} = u_k + P (b - A u_k), residual in FP64, split straight into the planes
+  // u_{k+1} = u_k + P_{k+1} (b - A u_k), residual in FP64, split straight into the planes
   for (int it = 0; it < refinements && st == TS_OK; ++it) {
     const bool more = it + 1 < refinements;
+    const ts_precision prec = sched[it + 1];
+    const int np = bf16_planes(prec);
     if (fixed)
       st = residual_split_fixed(p, sigma, u, b, buf[0], np, emax, (long long*)qtab, s);
     else
@@ -857,6 +884,8 @@ ts_status tc_prepare_kernels() {
 #define TS_PREP(NP, NACC, BKT, PO)                                                                     \
   TS_PREP1(NP, NACC, BKT, PO, 1, false); TS_PREP1(NP, NACC, BKT, PO, 2, false);                         \
   TS_PREP1(NP, NACC, BKT, PO, 4, false); TS_PREP1(NP, NACC, BKT, PO, 1, true)
+  TS_PREP(1, 1, 64, true); TS_PREP(1, 1, 64, false); TS_PREP(1, 1, 32, true); TS_PREP(1, 1, 32, false);
+  TS_PREP(1, 2, 64, true); TS_PREP(1, 2, 64, false); TS_PREP(1, 2, 32, true); TS_PREP(1, 2, 32, false);
   TS_PREP(2, 1, 64, true); TS_PREP(2, 1, 64, false); TS_PREP(2, 1, 32, true); TS_PREP(2, 1, 32, false);
   TS_PREP(2, 2, 64, true); TS_PREP(2, 2, 64, false); TS_PREP(2, 2, 32, true); TS_PREP(2, 2, 32, false);
   TS_PREP(3, 1, 64, true); TS_PREP(3, 1, 64, false); TS_PREP(3, 1, 32, true); TS_PREP(3, 1, 32, false);

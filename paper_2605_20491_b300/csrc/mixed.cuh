@@ -23,6 +23,9 @@ ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigm
 // u_{k+1} = u_k + P (b - A u_k), P the split-precision inverse, residuals in FP64.
 ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
                        int refinements, cudaStream_t s);
+// The same with a precision per apply: sched[0] for u_0, sched[k] for refinement k.
+ts_status mixed_solve_schedule(const ts_plan* p, const ts_precision* sched, int count, double sigma,
+                               const double* b, double* u, cudaStream_t s);
 
 // Reads (and optionally clears) the flag that bounded device-side waits of the
 // tensor-core kernels set when they time out.  Synchronises s.

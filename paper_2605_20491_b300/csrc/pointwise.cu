@@ -638,7 +638,9 @@ ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, con
 ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigma, const double* x,
                                  const double* b, __nv_bfloat16* planes, int np, double* partial, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  if (np == 2)
+  if (np == 1)
+    k_stencil<2, 1><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
+  else if (np == 2)
     k_stencil<2, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
   else
     k_stencil<2, 3><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
@@ -714,7 +716,9 @@ ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const doub
       TS_LAUNCHED(1);
 #define TS_QF_CASE(PP)                                                                                  \
   case PP:                                                                                              \
-    if (np == 2)                                                                                        \
+    if (np == 1)                                                                                        \
+      TS_TRY((launch_march3<1, PP, true>(blocks, a, sigma, qtab, F, x, b, planes, p->N, emax_dev, s)));  \
+    else if (np == 2)                                                                                   \
       TS_TRY((launch_march3<2, PP, true>(blocks, a, sigma, qtab, F, x, b, planes, p->N, emax_dev, s)));  \
     else                                                                                                \
       TS_TRY((launch_march3<3, PP, true>(blocks, a, sigma, qtab, F, x, b, planes, p->N, emax_dev, s)));  \
@@ -727,14 +731,18 @@ ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const doub
       TS_LAUNCHED(1);
       return TS_OK;
     }
-    if (np == 2)
+    if (np == 1)
+      TS_TRY((launch_march3<1, 5, false>(blocks, a, sigma, nullptr, 0, x, b, planes, p->N, emax_dev, s)));
+    else if (np == 2)
       TS_TRY((launch_march3<2, 5, false>(blocks, a, sigma, nullptr, 0, x, b, planes, p->N, emax_dev, s)));
     else
       TS_TRY((launch_march3<3, 5, false>(blocks, a, sigma, nullptr, 0, x, b, planes, p->N, emax_dev, s)));
     TS_LAUNCHED(1);
     return TS_OK;
   }
-  if (np == 2)
+  if (np == 1)
+    k_residual_fixed<1><<<grid_for(p->N), 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev, H);
+  else if (np == 2)
     k_residual_fixed<2><<<grid_for(p->N), 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev, H);
   else
     k_residual_fixed<3><<<grid_for(p->N), 256, 0, s>>>(a, sigma, x, b, planes, p->N, emax_dev, H);

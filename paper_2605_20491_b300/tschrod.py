@@ -21,14 +21,14 @@ TS_OK, TS_ERR_INVALID_ARG, TS_ERR_NO_MEMORY, TS_ERR_CUDA, TS_ERR_NOT_CONVERGED, 
     TS_ERR_TIMEOUT = range(7)
 STATUS_NAMES = ["TS_OK", "TS_ERR_INVALID_ARG", "TS_ERR_NO_MEMORY", "TS_ERR_CUDA", "TS_ERR_NOT_CONVERGED",
                 "TS_ERR_UNSUPPORTED", "TS_ERR_TIMEOUT"]
-TS_FP64, TS_BF16X3, TS_BF16X6, TS_TF32X3, TS_FP16X3, TS_FP32 = range(6)
+TS_FP64, TS_BF16X3, TS_BF16X6, TS_TF32X3, TS_FP16X3, TS_FP32, TS_BF16X1 = range(7)
 TS_R64, TS_C128, TS_C64 = range(3)
 TS_MAX_DIM = 12
 
 #: Every extern "C" symbol that include/tschrod.h declares.
 EXPORTS = [
     "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
-    "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
+    "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_solve_schedule", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
     "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_selftest_wait_timeout", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
@@ -89,6 +89,7 @@ def lib() -> C.CDLL:
     L.ts_apply_inverse.argtypes = [vp, dp, vp, vp, ip, vp]
     L.ts_apply_exp.argtypes = [vp, dp, vp, vp, ip, ip, vp]
     L.ts_solve_refined.argtypes = [vp, dp, vp, vp, ip, ip, vp]
+    L.ts_solve_schedule.argtypes = [vp, dp, vp, vp, C.POINTER(ip), ip, vp]
     L.ts_apply_inverse_noalloc.argtypes = [vp, dp, vp, vp, ip, vp]
     L.ts_apply_operator.argtypes = [vp, dp, vp, vp, vp, vp]
     L.ts_pcg.argtypes = [vp, dp, dp, vp, vp, vp, dp, ip, ip, C.POINTER(ip), C.POINTER(dp), vp]
@@ -223,6 +224,13 @@ def ts_solve_refined(plan: Plan, sigma: float, b, u, prec: int = TS_BF16X3, refi
            "ts_solve_refined")
 
 
+def ts_solve_schedule(plan: Plan, sigma: float, b, u, schedule, stream=None):
+    """u_0 = P_0 b, then one refinement per further entry of `schedule` (precisions)."""
+    arr = (C.c_int * len(schedule))(*schedule)
+    _check(lib().ts_solve_schedule(plan.handle, sigma, _ptr(b), _ptr(u), arr, len(schedule), _stream(stream)),
+           "ts_solve_schedule")
+
+
 def ts_apply_exp(plan: Plan, tau: float, psi_in, psi_out, dtype: int, prec: int = TS_FP64, stream=None):
     _check(lib().ts_apply_exp(plan.handle, tau, _ptr(psi_in), _ptr(psi_out), dtype, prec, _stream(stream)),
            "ts_apply_exp")
@@ -286,7 +294,7 @@ def ts_profile_begin():
     _check(lib().ts_profile_begin(), "ts_profile_begin")
 
 
-PROF_TC_PASS, PROF_FP64_PASS, PROF_SMALL_PASS, PROF_RESIDUAL = range(4)
+PROF_TC_PASS, PROF_FP64_PASS, PROF_SMALL_PASS, PROF_RESIDUAL, PROF_TC_PASS_X1 = range(5)
 
 
 def ts_profile_end(kind: int):

@@ -216,3 +216,64 @@ def test_multicast_clusters_match_oracle(T, n, cluster):
         T.ts_tc_config_reset(True)
     assert rel(host(u), O.apply_inverse(Po, 0.5, b)) < TOL[1]
     assert rel(host(out), O.apply_exp(Po, 0.01, psi)) < TOL[2]
+
+
+MASK1 = MASK | (1 << 6)  # TS_BF16X1
+
+
+@pytest.mark.parametrize("n", [(64, 64, 64), (40, 24, 8), (128, 96, 48)])
+def test_bf16x1_apply_is_coarse_inverse(T, n):
+    """One bf16 plane and one product per contraction: the inverse and the complex
+    exponential agree with the oracle to the bf16 rounding of the data and of S_k
+    accumulated over 2d passes (a few 1e-3 relative)."""
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK1)
+    b = S.normal(2, Po.N)
+    u = dev(np.zeros(Po.N))
+    T.ts_apply_inverse(P, 0.5, dev(b), u, T.TS_BF16X1)
+    e_inv = rel(host(u), O.apply_inverse(Po, 0.5, b))
+    psi = S.complex_normal(3, Po.N)
+    out = dev(np.zeros(2 * Po.N))
+    T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C128, T.TS_BF16X1)
+    e_exp = rel(host(out), O.apply_exp(Po, 0.01, psi))
+    T.ts_device_status()
+    assert 1e-4 < e_inv < 2e-2, e_inv
+    assert 1e-4 < e_exp < 2e-2, e_exp
+
+
+@pytest.mark.parametrize("n", [(64, 64, 64), (128, 96, 48), (40, 24, 8)])
+def test_schedule_reaches_target(T, n):
+    """A precision per apply: BF16X3, a BF16X3 refinement and a BF16X1 refinement end below
+    1e-10 (the error contracts by each apply's relative error); BF16X1 alone needs about
+    six applies for the same; the all-BF16X3 schedule equals ts_solve_refined bit for bit."""
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK1)
+    b = S.normal(2, Po.N)
+    want = O.apply_inverse(Po, 0.5, b)
+    bt = dev(b)
+    X1, X3 = T.TS_BF16X1, T.TS_BF16X3
+    errs = {}
+    for name, sched in {"331": [X3, X3, X1], "1x6": [X1] * 6, "33": [X3, X3], "333": [X3, X3, X3]}.items():
+        u = dev(np.zeros(Po.N))
+        T.ts_solve_schedule(P, 0.5, bt, u, sched)
+        errs[name] = rel(host(u), want)
+        if name == "333":
+            ur = dev(np.zeros(Po.N))
+            T.ts_solve_refined(P, 0.5, bt, ur, X3, 2)
+            assert np.array_equal(host(u), host(ur))
+    assert errs["331"] < 1e-10, errs
+    assert errs["1x6"] < 1e-9, errs
+    assert errs["331"] < errs["33"], errs
+
+
+def test_schedule_rejects_bad_entries(T):
+    n = (16, 16, 16)
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)  # BF16X1 not in the mask
+    b = dev(np.ones(Po.N))
+    u = dev(np.zeros(Po.N))
+    for sched in ([], [T.TS_FP64], [T.TS_BF16X3, T.TS_FP32], [T.TS_BF16X3, T.TS_BF16X1], [T.TS_BF16X3] * 18):
+        with pytest.raises(T.TsError) as e:
+            T.ts_solve_schedule(P, 0.5, b, u, sched)
+        assert e.value.status in (T.TS_ERR_INVALID_ARG, T.TS_ERR_UNSUPPORTED)
+    T.ts_solve_schedule(P, 0.5, b, u, [T.TS_BF16X3, T.TS_BF16X6])
