@@ -180,9 +180,23 @@ def run_profile_case(args):
     """Small fixed case for profiler captures (a few GB on the device): the refined solve
     of the n = 512 workload only (with --profile-n m: on an m^3 grid of the same box and
     potential), or, with --workload 6d_n24_strang / 9d_n8_strang, the complex64 FP32 Strang
-    steps only; warmup + steps times, nothing else."""
+    steps only, or, with --workload 3d_n256_pcg, one BF16X3-preconditioned shifted inverse
+    iteration; warmup + steps times (not the inverse iteration), nothing else."""
     import torch
     from paper_2605_20491_b300 import tschrod as T
+    if args.workload == "3d_n256_pcg":
+        # the BF16X3-preconditioned shifted inverse iteration only
+        w = synth.WORKLOADS[args.workload]
+        n, L = w["n"], w["L"]
+        P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << T.TS_BF16X3)
+        V2h = synth.v2_cos_bumps(n, L, seed=w["v2_seed"])
+        V2 = torch.from_numpy(V2h).cuda()
+        shift = sum(T.ts_plan_eigs(P, k)[0] for k in range(3)) + V2h.min() - 1.0
+        u = torch.zeros(P.N, dtype=torch.float64, device="cuda")
+        T.ts_inverse_iteration(P, shift, V2, u, True, w["lambda_tol"], 400, w["pcg_tol"], 500, T.TS_BF16X3)
+        torch.cuda.synchronize()
+        print("profile case done", flush=True)
+        return 0
     if args.workload in ("6d_n24_strang", "9d_n8_strang"):
         w = synth.WORKLOADS[args.workload]
         n, L = w["n"], w["L"]

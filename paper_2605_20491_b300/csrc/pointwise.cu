@@ -510,7 +510,9 @@ __global__ void k_sum_partials(const double* partial, int nblk, double* out) {
 __global__ void k_pcg_xr(const double* rz, const double* pq, double* alpha_out, double* __restrict__ x,
                          double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q,
                          long long N, double* partial) {
-  double alpha = rz[0] / pq[0];
+  // a zero p.q only arises after exact convergence (p = 0): then no step (also for the
+  // extra iteration that the lagged stopping test may run)
+  double alpha = pq[0] != 0.0 ? rz[0] / pq[0] : 0.0;
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
@@ -530,7 +532,7 @@ __global__ void k_pcg_xr(const double* rz, const double* pq, double* alpha_out, 
 // p = z + beta p with the flexible beta = -alpha (z_{k+1}.q_k) / (z_k.r_k); first: p = z.
 __global__ void k_pcg_p(const double* alpha, const double* zq, const double* rz_old, int first,
                         double* __restrict__ p, const double* __restrict__ z, long long N) {
-  double beta = first ? 0.0 : -alpha[0] * zq[0] / rz_old[0];
+  double beta = first || rz_old[0] == 0.0 ? 0.0 : -alpha[0] * zq[0] / rz_old[0];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x)
     p[i] = first ? z[i] : fma(beta, p[i], z[i]);

@@ -40,6 +40,33 @@ ts_status read_scalars(const double* dev, double* host, int count, cudaStream_t 
   return TS_OK;
 }
 
+// Pinned two-slot mailbox for the PCG stopping test: iteration k copies its r.r into slot
+// k % 2 and records an event, and the host reads slot (k - 1) % 2 while iteration k runs.
+struct RrMailbox {
+  double* host = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  ~RrMailbox() {
+    if (host) cudaFreeHost(host);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  ts_status init() {
+    TS_CHECK_CUDA(cudaMallocHost(&host, 2 * sizeof(double)));
+    for (cudaEvent_t& e : ev) TS_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return TS_OK;
+  }
+  ts_status post(const double* dev, int k, cudaStream_t s) {
+    TS_CHECK_CUDA(cudaMemcpyAsync(host + (k & 1), dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TS_CHECK_CUDA(cudaEventRecord(ev[k & 1], s));
+    return TS_OK;
+  }
+  ts_status take(int k, double* out) {
+    TS_CHECK_CUDA(cudaEventSynchronize(ev[k & 1]));
+    *out = host[k & 1];
+    return TS_OK;
+  }
+};
+
 }  // namespace
 
 ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double* V2, const double* b, double* x,
@@ -66,24 +93,67 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
     TS_TRY(dot2(N, r, z, nullptr, nullptr, partial, sc + 2, s));     // sc[2] = r.z
     TS_TRY(pcg_update_p(nullptr, nullptr, nullptr, 1, pv, z, N, s)); // p = z
   }
+  // The stopping test lags one iteration: iteration k posts its r.r, and the host reads
+  // iteration k - 1's while the GPU runs iteration k, so the GPU never waits for the host.
+  // The solve therefore stops one iteration after the first one below tol (a smaller
+  // residual, reported with its own iteration count).
+  RrMailbox mb;
+  if (!converged) TS_TRY(mb.init());
+  double rr_last = 0.0, rr_prev = 0.0;  // the two most recent tested r.r
+  auto check = [&](int k, bool* stop) -> ts_status {
+    double rr = 0.0;
+    TS_TRY(mb.take(k, &rr));
+    if (!std::isfinite(rr)) {
+      set_error("PCG breakdown: non-finite residual at iteration %d", k);
+      if (iters_out) *iters_out = it;
+      return TS_ERR_NOT_CONVERGED;
+    }
+    rr_prev = rr_last;
+    rr_last = rr;
+    *stop = std::sqrt(rr) / bnorm < tol;
+    return TS_OK;
+  };
+  int last_checked = 0;
   while (!converged && it < maxit) {
     TS_TRY(stencil_apply(p, V2, sigma, pv, q, partial, sc + 4, s));                     // q = A p; sc[4] = p.q
     TS_TRY(pcg_update_xr(sc + 2, sc + 4, sc + 6, x, r, pv, q, N, partial, sc + 8, s));  // sc[6] = alpha, sc[8] = r.r
     ++it;
-    TS_TRY(read_scalars(sc + 8, h, 1, s));
-    if (!std::isfinite(h[0])) {
-      set_error("PCG breakdown: non-finite residual at iteration %d", it);
-      if (iters_out) *iters_out = it;
-      return TS_ERR_NOT_CONVERGED;
+    TS_TRY(mb.post(sc + 8, it, s));
+    // the first iteration is tested at once (an exact preconditioner converges in one),
+    // later ones one iteration behind
+    const int ck = it == 1 ? 1 : it - 1;
+    if (ck > last_checked) {
+      bool stop = false;
+      TS_TRY(check(ck, &stop));
+      last_checked = ck;
+      if (stop) {  // iteration ck converged: stop with iterate it (ck or ck + 1)
+        converged = true;
+        break;
+      }
+      // When the contraction of the last two tested residuals predicts that iteration it
+      // already meets tol, test it now instead of running one more iteration behind it.
+      if (ck < it && rr_prev > 0.0) {
+        const double predicted = rr_last * (rr_last / rr_prev);
+        if (std::sqrt(predicted) / bnorm < tol) {
+          TS_TRY(check(it, &stop));
+          last_checked = it;
+          if (stop) {
+            converged = true;
+            break;
+          }
+        }
+      }
     }
-    if (std::sqrt(h[0]) / bnorm < tol) {
-      converged = true;
-      break;
-    }
+    if (it == maxit) break;
     TS_TRY(apply_inverse_impl(p, sigma_P, r, z, prec, s));          // z = P r
     TS_TRY(dot2(N, r, z, z, q, partial, sc + 10, s));               // sc[10] = r.z, sc[11] = z.q
     TS_TRY(pcg_update_p(sc + 6, sc + 11, sc + 2, 0, pv, z, N, s));  // p = z + beta p
     TS_TRY(copy_scalar(sc + 10, sc + 2, s));
+  }
+  if (!converged && it > last_checked) {  // the last iteration's own test
+    bool stop = false;
+    TS_TRY(check(it, &stop));
+    converged = stop;
   }
   // true residual at exit
   TS_TRY(stencil_residual(p, V2, sigma, x, b, r, partial, sc + 12, s));
