@@ -168,6 +168,27 @@ ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void
                        ts_dtype dtype, ts_precision prec, void* stream);
 
 /*
+ * Many independent applies in one call (no counterpart in the paper; the serving
+ * subsystem's batched launch): items[q] asks for ts_apply_inverse (dtype TS_R64, param =
+ * sigma) or ts_apply_exp (dtype TS_C128 / TS_C64, param = tau) of its own plan, input and
+ * output, in a split precision (TS_BF16X1 / TS_BF16X3 / TS_BF16X6, in the plan's mask).
+ * Instead of 2d + 1 launches per item, every stage of all items runs in one launch:
+ * one input split over all items, then for each pass s one tensor-core launch per group
+ * of items with the same precision and data kind, walking the tiles of all of them (a
+ * work list of up to 40 (item, pass) entries per launch).  Results equal the per-item
+ * calls bit for bit.  Items must not share outputs; inputs are not modified.
+ */
+typedef struct {
+  const ts_plan* plan;
+  ts_dtype dtype;      /* TS_R64: inverse; TS_C128 / TS_C64: exp                         */
+  ts_precision prec;   /* split precision                                                 */
+  double param;        /* sigma (inverse) or tau (exp)                                    */
+  const void* in;      /* device input (N doubles, or N complex values of dtype)          */
+  void* out;           /* device output, same layout                                      */
+} ts_batch_item;
+ts_status ts_apply_batch(const ts_batch_item* items, int count, void* stream);
+
+/*
  * y = (-Delta_h + V1 + V2 + sigma) x by the 2d+1 point stencil of eq. general_system
  * (zero Dirichlet ghosts).  V2: N doubles or NULL.  x, y: N doubles, must not alias.
  */

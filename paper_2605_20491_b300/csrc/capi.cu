@@ -3,6 +3,8 @@
 #include <cstdarg>
 #include <cstring>
 
+#include <vector>
+
 #include "common.cuh"
 #include "mixed.cuh"
 #include "pointwise.cuh"
@@ -180,6 +182,33 @@ ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void
   TS_REQUIRE(dtype == TS_C128 || dtype == TS_C64, "dtype must be TS_C128 or TS_C64");
   TS_TRY(check_prec(plan, prec));
   return apply_exp_impl(plan, tau, psi_in, psi_out, dtype, prec, (cudaStream_t)stream);
+}
+
+ts_status ts_apply_batch(const ts_batch_item* items, int count, void* stream) {
+  clear_error();
+  TS_REQUIRE(count >= 0, "count must be >= 0");
+  TS_REQUIRE(items || count == 0, "items is NULL");
+  if (count == 0) return TS_OK;
+  std::vector<BatchApply> q(count);
+  int device = -1;
+  for (int i = 0; i < count; ++i) {
+    const ts_batch_item& it = items[i];
+    TS_REQUIRE(it.plan, "items[%d].plan is NULL", i);
+    TS_REQUIRE(it.in && it.out, "items[%d]: in and out must be non-NULL", i);
+    TS_REQUIRE(it.dtype == TS_R64 || it.dtype == TS_C128 || it.dtype == TS_C64, "items[%d]: bad dtype", i);
+    TS_REQUIRE(bf16_planes(it.prec) > 0, "items[%d]: split precisions only", i);
+    TS_TRY(check_prec(it.plan, it.prec));
+    TS_REQUIRE(device < 0 || it.plan->device == device, "items[%d]: all plans must be on one device", i);
+    device = it.plan->device;
+    q[i] = BatchApply{it.plan, it.prec, it.dtype == TS_R64 ? MixedOp::Inverse : MixedOp::Exp, it.param, it.in,
+                      it.out, it.dtype};
+  }
+  DeviceGuard g(device);
+  if (!g.ok) {
+    set_error("cannot select device %d", device);
+    return TS_ERR_CUDA;
+  }
+  return mixed_apply_batch(q.data(), count, (cudaStream_t)stream);
 }
 
 ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2, const double* x, double* y,

@@ -37,6 +37,8 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "mixed.cuh"
 #include "pointwise.cuh"
@@ -121,6 +123,84 @@ __device__ __forceinline__ double f2d(float f) {
   const unsigned long long bits =
       ((unsigned long long)(u & 0x80000000u) << 32) | (e64 << 52) | (e == 0u ? 0ull : (m << 29));
   return __longlong_as_double((long long)bits);
+}
+
+// sigma + the row axes' eigenvalues (scale 1) or the product of their phases (scale 2) at
+// data row r of a pass, from the per-axis FP64 tables (the first row axis fastest).
+__device__ __forceinline__ void epi_row_factors(const EpiParams& ep, long long r, float* rowsum, float2* rowph) {
+  long long q = r;
+  double sacc = ep.sigma;
+  double pr = 1.0, pi = 0.0;
+  for (int k = 0; k < ep.rd; ++k) {
+    long long qq = q / ep.rn[k];
+    int i = (int)(q - qq * ep.rn[k]);
+    q = qq;
+    if (ep.scale_mode == 1) {
+      sacc += ep.rlam[k][i];
+    } else {
+      double2 ph = ep.rph[k][i];
+      double tr = pr * ph.x - pi * ph.y;
+      pi = pr * ph.y + pi * ph.x;
+      pr = tr;
+    }
+  }
+  *rowsum = (float)sacc;
+  *rowph = make_float2((float)pr, (float)pi);
+}
+
+// The epilogue for one 16-column chunk of one accumulator row: data row r, output columns
+// jbase..jbase+15 (those below ep.n), accumulator values v[component][column].  Applies the
+// fused pointwise step, then stores the bf16 planes of the next pass or the final result
+// (transposed: element r + R j); emx collects the largest biased exponent of FP64 stores.
+template <int NP, int NACC, bool PLANES_OUT>
+__device__ __forceinline__ void epi_chunk(const EpiParams& ep, const uint32_t (&v)[NACC][16], long long r, int jbase,
+                                          float rowsum, float2 rowph, int& emx) {
+  const int jn = ep.n - jbase < 16 ? ep.n - jbase : 16;
+  long long idx = r + ep.R * (long long)jbase;
+  double prev[16];
+  if (!PLANES_OUT && ep.out_mode == 4) {
+    // u += delta: issue all 16 loads of the chunk before any store, so they overlap
+    const double* uo = reinterpret_cast<const double*>(ep.out);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) prev[i] = i < jn ? uo[idx + ep.R * (long long)i] : 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i, idx += ep.R) {
+    if (i >= jn) break;
+    const int j = jbase + i;
+    float val[NACC];
+#pragma unroll
+    for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
+    if (ep.scale_mode == 1) {
+      val[0] = val[0] * (1.0f / (rowsum + ep.clam[j]));
+    } else if (ep.scale_mode == 2 && NACC == 2) {
+      const float2 cp = ep.cph[j];
+      const float cx = cp.x, cy = cp.y;
+      const float phx = rowph.x * cx - rowph.y * cy;
+      const float phy = rowph.x * cy + rowph.y * cx;
+      const float re = val[0] * phx - val[NACC - 1] * phy;
+      const float im = val[0] * phy + val[NACC - 1] * phx;
+      val[0] = re;
+      val[NACC - 1] = im;
+    }
+    if (PLANES_OUT) {
+      __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
+#pragma unroll
+      for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
+    } else if (ep.out_mode == 1) {
+      const double o = f2d(val[0]);
+      reinterpret_cast<double*>(ep.out)[idx] = o;
+      emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
+    } else if (ep.out_mode == 4) {
+      const double o = prev[i] + f2d(val[0]);
+      reinterpret_cast<double*>(ep.out)[idx] = o;
+      emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
+    } else if (ep.out_mode == 2) {
+      reinterpret_cast<double2*>(ep.out)[idx] = make_double2(f2d(val[0]), f2d(val[NACC - 1]));
+    } else {
+      reinterpret_cast<float2*>(ep.out)[idx] = make_float2(val[0], val[NACC - 1]);
+    }
+  }
 }
 
 // PAIR: CTA pairs (clusters of 2) share each MMA through tcgen05 cta_group::2.  A unit is
@@ -296,26 +376,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const bool row_ok = r < ep.R;
       float rowsum = 0.f;
       float2 rowph = make_float2(1.f, 0.f);
-      if (ep.scale_mode != 0 && row_ok) {
-        long long q = r;
-        double sacc = ep.sigma;
-        double pr = 1.0, pi = 0.0;
-        for (int k = 0; k < ep.rd; ++k) {
-          long long qq = q / ep.rn[k];
-          int i = (int)(q - qq * ep.rn[k]);
-          q = qq;
-          if (ep.scale_mode == 1) {
-            sacc += ep.rlam[k][i];
-          } else {
-            double2 ph = ep.rph[k][i];
-            double tr = pr * ph.x - pi * ph.y;
-            pi = pr * ph.y + pi * ph.x;
-            pr = tr;
-          }
-        }
-        rowsum = (float)sacc;
-        rowph = make_float2((float)pr, (float)pi);
-      }
+      if (ep.scale_mode != 0 && row_ok) epi_row_factors(ep, r, &rowsum, &rowph);
       const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
       for (int col0 = part * 16; col0 < BN; col0 += 16 * (EPI_WARPS / 4)) {
         uint32_t v[NACC][16];
@@ -323,53 +384,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
         tc::tmem_ld_wait();
         if (!row_ok) continue;
-        const int jbase = n0 + col0;
-        const int jn = ep.n - jbase < 16 ? ep.n - jbase : 16;
-        long long idx = r + ep.R * (long long)jbase;
-        double prev[16];
-        if (!PLANES_OUT && ep.out_mode == 4) {
-          // u += delta: issue all 16 loads of the chunk before any store, so they overlap
-          const double* uo = reinterpret_cast<const double*>(ep.out);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) prev[i] = i < jn ? uo[idx + ep.R * (long long)i] : 0.0;
-        }
-#pragma unroll
-        for (int i = 0; i < 16; ++i, idx += ep.R) {
-          if (i >= jn) break;
-          const int j = jbase + i;
-          float val[NACC];
-#pragma unroll
-          for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
-          if (ep.scale_mode == 1) {
-            val[0] = val[0] * (1.0f / (rowsum + ep.clam[j]));
-          } else if (ep.scale_mode == 2 && NACC == 2) {
-            const float2 cp = ep.cph[j];
-            const float cx = cp.x, cy = cp.y;
-            const float phx = rowph.x * cx - rowph.y * cy;
-            const float phy = rowph.x * cy + rowph.y * cx;
-            const float re = val[0] * phx - val[NACC - 1] * phy;
-            const float im = val[0] * phy + val[NACC - 1] * phx;
-            val[0] = re;
-            val[NACC - 1] = im;
-          }
-          if (PLANES_OUT) {
-            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
-#pragma unroll
-            for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
-          } else if (ep.out_mode == 1) {
-            const double o = f2d(val[0]);
-            reinterpret_cast<double*>(ep.out)[idx] = o;
-            emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
-          } else if (ep.out_mode == 4) {
-            const double o = prev[i] + f2d(val[0]);
-            reinterpret_cast<double*>(ep.out)[idx] = o;
-            emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
-          } else if (ep.out_mode == 2) {
-            reinterpret_cast<double2*>(ep.out)[idx] = make_double2(f2d(val[0]), f2d(val[NACC - 1]));
-          } else {
-            reinterpret_cast<float2*>(ep.out)[idx] = make_float2(val[0], val[NACC - 1]);
-          }
-        }
+        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, r, n0 + col0, rowsum, rowph, emx);
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -395,6 +410,186 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------- work-list pass ----
+//
+// One launch over a work list of (request, pass) items, e.g. pass s of every request of a
+// serving batch: the tiles of all items form one unit space (item by item, N tile fastest
+// within an item) that persistent single CTAs walk exactly like k_rot_tc walks one pass.
+// Items share the template parameters (planes, components, output kind) but each has its
+// own tensor maps, contracted extent n, rows R, N tile and epilogue (all in the kernel's
+// parameter space); shared memory and TMEM are sized for the widest N tile of the list.
+constexpr int TC_LIST_MAX = 40;
+struct TcItem {
+  CUtensorMap tmA;       // data planes [NACC * NP][R][n], 128-row boxes
+  CUtensorMap tmB;       // S_k planes [NP][n][n], ep.bn-row boxes
+  EpiParams ep;          // ep.bn: this item's N tile
+  long long unit_begin;  // first unit of the item in the launch's unit space
+  int mtiles, ntiles, nk;
+};
+struct TcItemList {
+  TcItem item[TC_LIST_MAX];
+  int count;
+  long long total;  // units of all items
+  int bn_max;       // rows of the B tile slots in shared memory
+  int nstages;
+};
+static_assert(sizeof(TcItemList) < 32000, "the work list travels in the kernel's parameter space");
+
+template <int NP, int NACC, int BKT, bool PLANES_OUT>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_rot_tc_list(const __grid_constant__ TcItemList L) {
+  constexpr int SW = BKT * 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int BNM = L.bn_max;
+  const int NS = L.nstages;
+  const uint32_t A_TILE = BM * BKT * 2;
+  const uint32_t B_TILE = (uint32_t)BNM * BKT * 2;  // slot size; an item fills ep.bn rows of it
+  const uint32_t A_STAGE = NACC * NP * A_TILE;
+  const uint32_t B_STAGE = NP * B_TILE;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + (size_t)NS * A_STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NS * (A_STAGE + B_STAGE));
+  uint64_t* full = bars;
+  uint64_t* empty = bars + MAX_STAGES;
+  uint64_t* accf = bars + 2 * MAX_STAGES;
+  uint64_t* acce = bars + 2 * MAX_STAGES + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAX_STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t acc_cols = NACC * BNM;
+  uint32_t ncols = 32;
+  while (ncols < 2 * acc_cols) ncols <<= 1;
+  // item of unit t: the items' unit ranges are consecutive, and each role visits units in
+  // increasing order, so a cursor that only moves forward finds it
+  auto advance = [&](int& cur, long long t) {
+    while (cur + 1 < L.count && t >= L.item[cur + 1].unit_begin) ++cur;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], EPI_WARPS);
+    }
+    tc::fence_barrier_init();
+    tc::fence_proxy_async();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, ncols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int it = 0, cur = 0;
+      for (long long t = blockIdx.x; t < L.total; t += gridDim.x) {
+        advance(cur, t);
+        const TcItem& I = L.item[cur];
+        const long long u = t - I.unit_begin;
+        const int m0 = (int)(u / I.ntiles) * BM, n0 = (int)(u % I.ntiles) * I.ep.bn;
+        const uint32_t bytes = A_STAGE + (uint32_t)NP * I.ep.bn * BKT * 2;
+        for (int kc = 0; kc < I.nk; ++kc, ++it) {
+          const int s = it % NS, round = it / NS;
+          if (round > 0) tc::mbar_wait(&empty[s], (round - 1) & 1, &g_tc_error, 1);
+          tc::mbar_arrive_expect_tx(&full[s], bytes);
+          for (int c = 0; c < NACC; ++c)
+            for (int p = 0; p < NP; ++p)
+              tc::tma_load_3d(sA + (size_t)s * A_STAGE + (c * NP + p) * A_TILE, &I.tmA, kc * BKT, m0, c * NP + p,
+                              &full[s]);
+          for (int p = 0; p < NP; ++p)
+            tc::tma_load_3d(sB + (size_t)s * B_STAGE + p * B_TILE, &I.tmB, kc * BKT, n0, p, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int it = 0, tl = 0, cur = 0;
+      for (long long t = blockIdx.x; t < L.total; t += gridDim.x, ++tl) {
+        advance(cur, t);
+        const TcItem& I = L.item[cur];
+        const int BN = I.ep.bn;
+        const uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+        const int ab = tl & 1, use = tl >> 1;
+        if (use > 0) tc::mbar_wait(&acce[ab], (use - 1) & 1, &g_tc_error, 4);
+        tc::tc_fence_after();
+        const uint32_t dbase = tmem + (uint32_t)(ab * acc_cols);
+        for (int kc = 0; kc < I.nk; ++kc, ++it) {
+          const int s = it % NS, round = it / NS;
+          tc::mbar_wait(&full[s], round & 1, &g_tc_error, 2);
+          tc::tc_fence_after();
+          const uint32_t a0 = tc::smem_u32(sA + (size_t)s * A_STAGE);
+          const uint32_t b0 = tc::smem_u32(sB + (size_t)s * B_STAGE);
+#pragma unroll
+          for (int ks = 0; ks < BKT / UMMA_K; ++ks) {
+#pragma unroll
+            for (int q = 0; q < Products<NP>::count; ++q) {
+              const uint64_t bdesc = tc::desc_sw<SW>(b0 + Products<NP>::b(q) * B_TILE + ks * 32);
+#pragma unroll
+              for (int c = 0; c < NACC; ++c) {
+                const uint64_t adesc = tc::desc_sw<SW>(a0 + (c * NP + Products<NP>::a(q)) * A_TILE + ks * 32);
+                tc::mma_bf16(dbase + (uint32_t)(c * BN), adesc, bdesc, idesc, (kc | ks | q) != 0);
+              }
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(&accf[ab]);
+      }
+    }
+  } else {
+    // ---------------- epilogue (as in k_rot_tc, per item)
+    const int g = warp & 3;
+    const int part = (warp - 2) >> 2;
+    int emx = 0, tl = 0, cur = 0;
+    for (long long t = blockIdx.x; t < L.total; t += gridDim.x, ++tl) {
+      advance(cur, t);
+      const TcItem& I = L.item[cur];
+      const EpiParams& ep = I.ep;
+      const int BN = ep.bn;
+      const long long u = t - I.unit_begin;
+      const long long m0 = (u / I.ntiles) * BM;
+      const int n0 = (int)(u % I.ntiles) * BN;
+      const int ab = tl & 1, use = tl >> 1;
+      tc::mbar_wait(&accf[ab], use & 1, &g_tc_error, 3);
+      __syncwarp();
+      tc::tc_fence_after();
+      const long long r = m0 + g * 32 + lane;
+      const bool row_ok = r < ep.R;
+      float rowsum = 0.f;
+      float2 rowph = make_float2(1.f, 0.f);
+      if (ep.scale_mode != 0 && row_ok) epi_row_factors(ep, r, &rowsum, &rowph);
+      const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
+      for (int col0 = part * 16; col0 < BN; col0 += 16 * (EPI_WARPS / 4)) {
+        uint32_t v[NACC][16];
+#pragma unroll
+        for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
+        tc::tmem_ld_wait();
+        if (!row_ok) continue;
+        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, r, n0 + col0, rowsum, rowph, emx);
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[ab]);
+    }
+    (void)emx;  // the exponent collection of the refined solve is not used by list passes
+  }
+  __syncwarp();
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, ncols);
+  }
+}
+
 // ------------------------------------------------------------ pointwise ----
 
 // FP64 / complex input -> planar bf16 planes [c][p][N]; x rounded to FP32 first (the
@@ -417,6 +612,46 @@ __global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N
       v[1] = z.y;
     }
     for (int c = 0; c < NC; ++c) split_store<NP>(v[c], planes + (long long)c * NP * N, N, i);
+  }
+}
+
+// The input split of many items in one launch: item q owns blocks [block_begin_q,
+// block_begin_{q+1}) and runs k_split_input's loop over its N values with them.
+struct SplitItem {
+  const void* in;
+  __nv_bfloat16* planes;
+  long long N;
+  int mode;  // 0: real FP64, 1: complex128, 2: complex64
+  int block_begin;
+};
+struct SplitList {
+  SplitItem item[TC_LIST_MAX];
+  int count;
+};
+
+template <int NP>
+__global__ void k_split_list(const __grid_constant__ SplitList L) {
+  int cur = 0;
+  while (cur + 1 < L.count && (int)blockIdx.x >= L.item[cur + 1].block_begin) ++cur;
+  const SplitItem& I = L.item[cur];
+  const int nb = (cur + 1 < L.count ? L.item[cur + 1].block_begin : (int)gridDim.x) - I.block_begin;
+  const int nc = I.mode == 0 ? 1 : 2;
+  for (long long i = (long long)(blockIdx.x - I.block_begin) * blockDim.x + threadIdx.x; i < I.N;
+       i += (long long)nb * blockDim.x) {
+    float v[2];
+    if (I.mode == 0) {
+      v[0] = (float)reinterpret_cast<const double*>(I.in)[i];
+      v[1] = 0.f;
+    } else if (I.mode == 1) {
+      const double2 z = reinterpret_cast<const double2*>(I.in)[i];
+      v[0] = (float)z.x;
+      v[1] = (float)z.y;
+    } else {
+      const float2 z = reinterpret_cast<const float2*>(I.in)[i];
+      v[0] = z.x;
+      v[1] = z.y;
+    }
+    for (int c = 0; c < nc; ++c) split_store<NP>(v[c], I.planes + (long long)c * NP * I.N, I.N, i);
   }
 }
 
@@ -806,6 +1041,198 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
   return st;
 }
 
+namespace {
+
+template <int NP, int NACC, int BKT, bool PO>
+ts_status launch_list_t(const TcItemList& L, int smem, cudaStream_t s) {
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc_list<NP, NACC, BKT, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_LIMIT));
+    attr_set = true;
+  }
+  if (g_num_sms == 0) {
+    int dev = 0;
+    TS_CHECK_CUDA(cudaGetDevice(&dev));
+    TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const unsigned grid = (unsigned)(L.total < g_num_sms ? L.total : g_num_sms);
+  k_rot_tc_list<NP, NACC, BKT, PO><<<grid, TC_THREADS, smem, s>>>(L);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
+ts_status launch_list(int np, int nacc, int bk, bool po, const TcItemList& L, int smem, cudaStream_t s) {
+#define TS_LIST_CASE(NP, NACC)                                                                            \
+  if (np == NP && nacc == NACC) {                                                                         \
+    if (bk == 64) return po ? launch_list_t<NP, NACC, 64, true>(L, smem, s) : launch_list_t<NP, NACC, 64, false>(L, smem, s); \
+    return po ? launch_list_t<NP, NACC, 32, true>(L, smem, s) : launch_list_t<NP, NACC, 32, false>(L, smem, s);               \
+  }
+  TS_LIST_CASE(1, 1) TS_LIST_CASE(1, 2) TS_LIST_CASE(2, 1) TS_LIST_CASE(2, 2) TS_LIST_CASE(3, 1) TS_LIST_CASE(3, 2)
+#undef TS_LIST_CASE
+  set_error("no work-list kernel for %d planes, %d components", np, nacc);
+  return TS_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+ts_status mixed_apply_batch(const BatchApply* q, int count, cudaStream_t s) {
+  for (int i = 0; i < count; ++i) TS_TRY(check_mixed(q[i].p, q[i].prec));
+  struct Work {
+    __nv_bfloat16* buf[2] = {nullptr, nullptr};
+    void* tabs = nullptr;
+    int tab_off[MAXD] = {};
+    int tab_total = 0;
+    int np = 0, nc = 1;
+  };
+  std::vector<Work> w(count);
+  ts_status st = TS_OK;
+  int dmax = 0;
+  // per item: plane buffers and (exp) phase tables
+  for (int i = 0; i < count && st == TS_OK; ++i) {
+    const ts_plan* p = q[i].p;
+    w[i].np = bf16_planes(q[i].prec);
+    w[i].nc = q[i].op == MixedOp::Exp ? 2 : 1;
+    dmax = p->d > dmax ? p->d : dmax;
+    const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)w[i].nc * w[i].np * p->N;
+    for (int b = 0; b < 2 && st == TS_OK; ++b) st = scratch_alloc((void**)&w[i].buf[b], plane_bytes, s);
+    if (st == TS_OK && q[i].op == MixedOp::Exp) {
+      int tot = 0;
+      for (int k = 0; k < p->d; ++k) {
+        w[i].tab_off[k] = tot;
+        tot += p->n[k];
+      }
+      w[i].tab_total = tot;
+      st = scratch_alloc(&w[i].tabs, (sizeof(double2) + sizeof(float2)) * tot, s);
+      for (int k = 0; k < p->d && st == TS_OK; ++k) {
+        k_phase_table<<<(p->n[k] + 127) / 128, 128, 0, s>>>(p->lam[k], q[i].param,
+                                                            (double2*)w[i].tabs + w[i].tab_off[k],
+                                                            (float2*)((double2*)w[i].tabs + tot) + w[i].tab_off[k],
+                                                            p->n[k]);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) {
+          set_error("phase table launch failed");
+          st = TS_ERR_CUDA;
+        }
+      }
+    }
+  }
+  // input split: one launch per plane count over all its items
+  for (int np = 1; np <= 3 && st == TS_OK; ++np) {
+    std::vector<int> idx;
+    for (int i = 0; i < count; ++i)
+      if (w[i].np == np) idx.push_back(i);
+    for (size_t c0 = 0; c0 < idx.size() && st == TS_OK; c0 += TC_LIST_MAX) {
+      SplitList L{};
+      int blocks = 0;
+      for (size_t c = c0; c < idx.size() && c < c0 + TC_LIST_MAX; ++c) {
+        const int i = idx[c];
+        SplitItem& it = L.item[L.count++];
+        it.in = q[i].in;
+        it.planes = w[i].buf[0];
+        it.N = q[i].p->N;
+        it.mode = q[i].dt == TS_R64 ? 0 : (q[i].dt == TS_C128 ? 1 : 2);
+        it.block_begin = blocks;
+        long long nb = (it.N + 255) / 256;
+        blocks += (int)(nb < 148 * 4 ? nb : 148 * 4);
+      }
+      if (np == 1) k_split_list<1><<<blocks, 256, 0, s>>>(L);
+      else if (np == 2) k_split_list<2><<<blocks, 256, 0, s>>>(L);
+      else k_split_list<3><<<blocks, 256, 0, s>>>(L);
+      TS_LAUNCHED(1);
+    }
+  }
+  // the 2d passes: pass st of every item that has one, one launch per (planes, components,
+  // planes-out) group and up to TC_LIST_MAX items
+  const int reserve = 1024 + 8 * (2 * MAX_STAGES + 6);
+  for (int stage = 0; stage < 2 * dmax && st == TS_OK; ++stage) {
+    std::map<std::tuple<int, int, bool>, std::vector<int>> groups;
+    for (int i = 0; i < count; ++i) {
+      const int d = q[i].p->d;
+      if (stage < 2 * d) groups[std::make_tuple(w[i].np, w[i].nc, stage != 2 * d - 1)].push_back(i);
+    }
+    for (auto& gkv : groups) {
+      const int np = std::get<0>(gkv.first), nacc = std::get<1>(gkv.first);
+      const bool po = std::get<2>(gkv.first);
+      const std::vector<int>& idx = gkv.second;
+      for (size_t c0 = 0; c0 < idx.size() && st == TS_OK; c0 += TC_LIST_MAX) {
+        const size_t c1 = idx.size() < c0 + TC_LIST_MAX ? idx.size() : c0 + TC_LIST_MAX;
+        const int cap = nacc == 1 ? 256 : 128;  // two accumulator buffers fit in TMEM
+        int bn_max = 16;
+        for (size_t c = c0; c < c1; ++c) {
+          const ts_plan* p = q[idx[c]].p;
+          int bn = ((p->n[stage % p->d] + 15) / 16) * 16;
+          bn = bn > cap ? cap : bn;
+          bn_max = bn > bn_max ? bn : bn_max;
+        }
+        int bk = 64;
+        auto stage_bytes = [&](int b) { return nacc * np * BM * b * 2 + np * bn_max * b * 2; };
+        if ((SMEM_LIMIT - reserve) / stage_bytes(64) < 2) bk = 32;
+        int ns = (SMEM_LIMIT - reserve) / stage_bytes(bk);
+        ns = ns > MAX_STAGES ? MAX_STAGES : ns;
+        if (ns < 2) {
+          set_error("work-list tile does not fit in shared memory");
+          st = TS_ERR_UNSUPPORTED;
+          break;
+        }
+        TcItemList L{};
+        L.bn_max = bn_max;
+        L.nstages = ns;
+        long long units = 0;
+        for (size_t c = c0; c < c1 && st == TS_OK; ++c) {
+          const int i = idx[c];
+          const ts_plan* p = q[i].p;
+          const int d = p->d, k = stage % d;
+          const bool fwd = stage < d, last = stage == 2 * d - 1;
+          const int n = p->n[k];
+          const long long R = p->N / n;
+          TcItem& it = L.item[L.count++];
+          EpiParams& ep = it.ep;
+          ep = EpiParams{};
+          ep.out_mode = last ? (q[i].dt == TS_R64 ? 1 : (q[i].dt == TS_C128 ? 2 : 3)) : 0;
+          ep.out = last ? q[i].out : (void*)w[i].buf[(stage + 1) & 1];
+          if (stage == d - 1) {
+            ep.scale_mode = q[i].op == MixedOp::Inverse ? 1 : 2;
+            ep.sigma = q[i].op == MixedOp::Inverse ? q[i].param : 0.0;
+            ep.rd = d - 1;
+            for (int j = 0; j < d - 1; ++j) {
+              ep.rn[j] = p->n[j];
+              ep.rlam[j] = p->lam[j];
+              ep.rph[j] = w[i].tabs ? (const double2*)w[i].tabs + w[i].tab_off[j] : nullptr;
+            }
+            ep.clam = p->lamf[k];
+            ep.cph = w[i].tabs ? (const float2*)((const double2*)w[i].tabs + w[i].tab_total) + w[i].tab_off[k]
+                               : nullptr;
+          }
+          int bn = ((n + 15) / 16) * 16;
+          bn = bn > cap ? cap : bn;
+          ep.R = R;
+          ep.n = n;
+          ep.N = p->N;
+          ep.bn = bn;
+          ep.nstages = ns;
+          const __nv_bfloat16* B = fwd ? p->Bf[q[i].prec][k] : p->Bb[q[i].prec][k];
+          st = make_map(&it.tmA, w[i].buf[stage & 1], n, R, nacc * np, bk, BM);
+          if (st == TS_OK) st = make_map(&it.tmB, B, n, n, np, bk, bn);
+          it.mtiles = (int)((R + BM - 1) / BM);
+          it.ntiles = (n + bn - 1) / bn;
+          it.nk = (n + bk - 1) / bk;
+          it.unit_begin = units;
+          units += (long long)it.mtiles * it.ntiles;
+        }
+        L.total = units;
+        if (st == TS_OK) st = launch_list(np, nacc, bk, po, L, ns * stage_bytes(bk) + reserve, s);
+      }
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    scratch_free(w[i].buf[0], s);
+    scratch_free(w[i].buf[1], s);
+    scratch_free(w[i].tabs, s);
+  }
+  return st;
+}
+
 ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
                                 __nv_bfloat16* w0, __nv_bfloat16* w1, cudaStream_t s) {
   TS_TRY(check_mixed(p, prec));
@@ -892,6 +1319,13 @@ ts_status tc_prepare_kernels() {
   TS_PREP(3, 2, 64, true); TS_PREP(3, 2, 64, false); TS_PREP(3, 2, 32, true); TS_PREP(3, 2, 32, false);
 #undef TS_PREP1
 #undef TS_PREP
+#define TS_PREPL(NP, NACC)                                                                                     \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc_list<NP, NACC, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT)); \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc_list<NP, NACC, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT)); \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc_list<NP, NACC, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT)); \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc_list<NP, NACC, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT))
+  TS_PREPL(1, 1); TS_PREPL(1, 2); TS_PREPL(2, 1); TS_PREPL(2, 2); TS_PREPL(3, 1); TS_PREPL(3, 2);
+#undef TS_PREPL
   if (g_num_sms == 0) {
     int dev = 0;
     TS_CHECK_CUDA(cudaGetDevice(&dev));

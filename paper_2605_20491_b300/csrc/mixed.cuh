@@ -14,6 +14,19 @@ int bf16_planes(ts_precision prec);
 ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double param, const void* in, void* out,
                       ts_dtype dt, cudaStream_t s);
 
+// Many independent split-precision applies; every stage of all of them runs in one launch
+// (work-list tensor-core passes).
+struct BatchApply {
+  const ts_plan* p;
+  ts_precision prec;
+  MixedOp op;
+  double param;  // sigma (Inverse) or tau (Exp)
+  const void* in;
+  void* out;
+  ts_dtype dt;
+};
+ts_status mixed_apply_batch(const BatchApply* q, int count, cudaStream_t s);
+
 // Split-precision inverse apply with caller-provided plane buffers w0, w1 of
 // bf16_planes(prec) * N bf16 each (no allocation).
 ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,

@@ -10,8 +10,10 @@
 //     (n_k, L_k, f_k compared bit for bit); the per-axis eigendecompositions underneath
 //     are shared process-wide, so requests on a few distinct 1D operators rarely solve one;
 //   * batching: the inverse / exp requests admitted in one scheduling round are captured
-//     into ONE CUDA graph (the capture stream forks one stream per request, so their
-//     kernels overlap on the device) and launched; the graph's completion event completes
+//     into ONE CUDA graph and launched.  Split-precision requests run as one batched apply
+//     (mixed_apply_batch: one input-split launch and, for each of the 2d passes, one
+//     work-list tensor-core launch over the tiles of all of them); FP64 requests run on
+//     their own forked streams, so their kernels overlap; the graph's completion event completes
 //     every request of the batch;
 //   * PCG requests read one scalar back per iteration, so they cannot live in a graph: each
 //     runs on a pooled host thread with its own stream, overlapping with everything else.
@@ -312,7 +314,25 @@ void worker_loop(ts_server* sv) {
       std::vector<cudaEvent_t> joins(batch.size(), nullptr);
       if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = TS_ERR_CUDA;
       if (st == TS_OK) cudaEventRecord(fork, cs);
+      // split-precision requests: every stage of all of them in one work-list launch
+      // (mixed_apply_batch) on the capture stream; FP64 requests on their own forked streams
+      std::vector<BatchApply> grouped;
+      for (auto& jp : batch)
+        if (bf16_planes(jp->req.prec) > 0) {
+          const ts_request& r = jp->req;
+          grouped.push_back(BatchApply{jp->plan, r.prec,
+                                       r.kind == TS_REQ_INVERSE ? MixedOp::Inverse : MixedOp::Exp,
+                                       r.kind == TS_REQ_INVERSE ? r.sigma : r.tau, r.in, r.out,
+                                       r.kind == TS_REQ_INVERSE ? TS_R64 : r.dtype});
+        }
+      if (st == TS_OK && !grouped.empty()) {
+        st = mixed_apply_batch(grouped.data(), (int)grouped.size(), cs);
+        if (st != TS_OK)
+          for (auto& jp : batch)
+            if (bf16_planes(jp->req.prec) > 0) snprintf(jp->msg, sizeof(jp->msg), "%s", ts_last_error());
+      }
       for (size_t q = 0; q < batch.size() && st == TS_OK; ++q) {
+        if (bf16_planes(batch[q]->req.prec) > 0) continue;
         cudaStream_t s = sv->streams[batch[q]->stream_slot];
         cudaStreamWaitEvent(s, fork, 0);
         st = enqueue_async(*batch[q], s);

@@ -28,7 +28,7 @@ TS_MAX_DIM = 12
 #: Every extern "C" symbol that include/tschrod.h declares.
 EXPORTS = [
     "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
-    "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_solve_schedule", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
+    "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_solve_schedule", "ts_apply_batch", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
     "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_selftest_wait_timeout", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
@@ -68,6 +68,11 @@ class _ServingStats(C.Structure):
 TS_TC_PAIR = -2  # ts_tc_config_set cluster value: CTA pairs sharing each MMA
 TS_REQ_INVERSE, TS_REQ_EXP, TS_REQ_PCG = range(3)
 
+
+class _BatchItem(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("dtype", C.c_int), ("prec", C.c_int), ("param", C.c_double),
+                ("in_", C.c_void_p), ("out", C.c_void_p)]
+
 _lib = None
 
 
@@ -90,6 +95,7 @@ def lib() -> C.CDLL:
     L.ts_apply_exp.argtypes = [vp, dp, vp, vp, ip, ip, vp]
     L.ts_solve_refined.argtypes = [vp, dp, vp, vp, ip, ip, vp]
     L.ts_solve_schedule.argtypes = [vp, dp, vp, vp, C.POINTER(ip), ip, vp]
+    L.ts_apply_batch.argtypes = [C.POINTER(_BatchItem), ip, vp]
     L.ts_apply_inverse_noalloc.argtypes = [vp, dp, vp, vp, ip, vp]
     L.ts_apply_operator.argtypes = [vp, dp, vp, vp, vp, vp]
     L.ts_pcg.argtypes = [vp, dp, dp, vp, vp, vp, dp, ip, ip, C.POINTER(ip), C.POINTER(dp), vp]
@@ -229,6 +235,15 @@ def ts_solve_schedule(plan: Plan, sigma: float, b, u, schedule, stream=None):
     arr = (C.c_int * len(schedule))(*schedule)
     _check(lib().ts_solve_schedule(plan.handle, sigma, _ptr(b), _ptr(u), arr, len(schedule), _stream(stream)),
            "ts_solve_schedule")
+
+
+def ts_apply_batch(items, stream=None):
+    """items: (plan, dtype, prec, param, in, out) tuples; TS_R64 = inverse (param sigma),
+    TS_C128 / TS_C64 = exp (param tau).  One launch per stage over all items."""
+    arr = (_BatchItem * max(1, len(items)))()
+    for k, (plan, dtype, prec, param, xin, xout) in enumerate(items):
+        arr[k] = _BatchItem(plan.handle, dtype, prec, param, _ptr(xin), _ptr(xout))
+    _check(lib().ts_apply_batch(arr, len(items), _stream(stream)), "ts_apply_batch")
 
 
 def ts_apply_exp(plan: Plan, tau: float, psi_in, psi_out, dtype: int, prec: int = TS_FP64, stream=None):

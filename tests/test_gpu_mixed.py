@@ -277,3 +277,53 @@ def test_schedule_rejects_bad_entries(T):
             T.ts_solve_schedule(P, 0.5, b, u, sched)
         assert e.value.status in (T.TS_ERR_INVALID_ARG, T.TS_ERR_UNSUPPORTED)
     T.ts_solve_schedule(P, 0.5, b, u, [T.TS_BF16X3, T.TS_BF16X6])
+
+
+BATCH_CASES = [((32, 48, 64), "inv", 1), ((64, 64, 64), "inv", 1), ((40, 24, 8), "c128", 1), ((96, 32, 48), "c64", 6),
+               ((16, 16, 16, 16), "inv", 2), ((264, 16), "inv", 1), ((256, 16, 16), "inv", 1), ((48, 48, 48), "c128", 2),
+               ((24, 40, 56), "inv", 6)]
+
+
+def test_apply_batch_equals_single_calls(T):
+    """ts_apply_batch runs every stage of all items in one launch per (precision, data kind)
+    group (work-list tensor-core passes over heterogeneous grids: d = 2, 3, 4, ragged n,
+    real and complex, BF16X1/X3/X6); each item's result equals its own single call bit for
+    bit, and one of them matches the oracle."""
+    import torch
+    items, singles = [], []
+    for q, (n, kind, prec) in enumerate(BATCH_CASES):
+        L, f = harmonic_case(n)
+        P, Po = plans(n, L, f, MASK1)
+        if kind == "inv":
+            x = dev(S.normal(10 + q, Po.N))
+            out = dev(np.zeros(Po.N))
+            ref = dev(np.zeros(Po.N))
+            T.ts_apply_inverse(P, 0.5, x, ref, prec)
+            items.append((P, T.TS_R64, prec, 0.5, x, out))
+        else:
+            dt = T.TS_C128 if kind == "c128" else T.TS_C64
+            z = S.complex_normal(10 + q, Po.N)
+            x = dev(z) if kind == "c128" else dev(z.astype(np.complex64).view(np.float32))
+            out = torch.zeros_like(x)
+            ref = torch.zeros_like(x)
+            T.ts_apply_exp(P, 0.01, x, ref, dt, prec)
+            items.append((P, dt, prec, 0.01, x, out))
+        singles.append((ref, Po, kind))
+    T.ts_apply_batch(items)
+    T.ts_device_status()
+    for (P, dt, prec, param, x, out), (ref, Po, kind) in zip(items, singles):
+        assert np.array_equal(host(out), host(ref)), (Po.n, kind, prec)
+    P, dt, prec, param, x, out = items[1]
+    assert rel(host(out), O.apply_inverse(singles[1][1], 0.5, host(x))) < TOL[1]
+    T.ts_apply_batch([])
+
+
+def test_apply_batch_rejects_bad_items(T):
+    n = (16, 16, 16)
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)
+    x = dev(np.ones(Po.N))
+    y = dev(np.zeros(Po.N))
+    for bad in [(P, T.TS_R64, T.TS_FP64, 0.5, x, y), (P, T.TS_R64, T.TS_BF16X1, 0.5, x, y), (P, 7, T.TS_BF16X3, 0.5, x, y)]:
+        with pytest.raises(T.TsError):
+            T.ts_apply_batch([(P, T.TS_R64, T.TS_BF16X3, 0.5, x, y), bad])
