@@ -335,13 +335,19 @@ constexpr int MX = 32, MY = 16, MZ = 32;
 constexpr int RD = 4;           // ring depth (groups in flight: RD - 1)
 constexpr int RING_VALUES = 5;  // per thread and group: x(z+1) of both cells, halo x(z+1), b(z) of both cells
 constexpr int RING_BYTES = RD * RING_VALUES * 256 * 8;
-template <int NP, int P, bool QF>
+// APPLY (with QF): the operator itself for PCG, y = A x = c_s L + V2 x, where b carries
+//   V2 (NULL: none) and y is written in FP64 to `yout`; each block adds x.y into
+//   partial[2 blockIdx], partial[2 blockIdx + 1] = 0 (summed in a fixed order afterwards).
+template <int NP, int P, bool QF, bool APPLY = false>
 __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double sigma, const long long* __restrict__ Q,
                                                          int F, const double* __restrict__ x,
                                                          const double* __restrict__ b,
                                                          __nv_bfloat16* __restrict__ planes, long long N,
-                                                         const int* __restrict__ emax_ptr) {
+                                                         const int* __restrict__ emax_ptr, double* yout = nullptr,
+                                                         double* partial = nullptr) {
+  static_assert(!APPLY || QF, "the operator form folds the separable diagonal");
   constexpr int H = 53 + P;
+  double dot = 0.0;
   __shared__ long long sU[2][MY + 2][MX + 2];
   const int emax = *emax_ptr;
   const double cs = ldexp(a.ih2[0], emax - 1022 - H);
@@ -388,8 +394,8 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
   const double* sxa = x + (va ? oa + (long long)(z0 + 1) * s2 : 0);
   const double* sxb = x + (vb ? ob + (long long)(z0 + 1) * s2 : 0);
   const double* sxh = x + (hv ? oh + (long long)(z0 + 1) * s2 : 0);
-  const double* sba = b + (va ? oa + (long long)z0 * s2 : 0);
-  const double* sbb = b + (vb ? ob + (long long)z0 * s2 : 0);
+  const double* sba = b ? b + (va ? oa + (long long)z0 * s2 : 0) : nullptr;
+  const double* sbb = b ? b + (vb ? ob + (long long)z0 * s2 : 0) : nullptr;
   const long long sa_step = va ? s2 : 0, sb_step = vb ? s2 : 0, sh_step = hv ? s2 : 0;
   auto issue = [&](int z) {
     if (z < z1) {
@@ -398,13 +404,15 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
       cp_async8_zfill(dst, va && xn ? sxa : x, va && xn);  // past the last plane: no address
       cp_async8_zfill(dst + 256, vb && xn ? sxb : x, vb && xn);
       if (ly < 3) cp_async8_zfill(dst + 512, hn ? sxh : x, hn);
-      cp_async8_zfill(dst + 768, sba, va);
-      cp_async8_zfill(dst + 1024, sbb, vb);
+      cp_async8_zfill(dst + 768, b && va ? sba : x, b && va);
+      cp_async8_zfill(dst + 1024, b && vb ? sbb : x, b && vb);
       sxa += sa_step;
       sxb += sb_step;
       sxh += sh_step;
-      sba += sa_step;
-      sbb += sb_step;
+      if (b) {
+        sba += sa_step;
+        sbb += sb_step;
+      }
     }
     cp_async_commit();  // an empty group past the end keeps the group count uniform
   };
@@ -440,7 +448,20 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
     const long long La = 6 * Uca - Upa - Una - T[ly + 1][lx] - T[ly + 1][lx + 2] - T[ly][lx + 1] - T[ly + 2][lx + 1];
     const long long Lb = 6 * Ucb - Upb - Unb - T[ly + 9][lx] - T[ly + 9][lx + 2] - T[ly + 8][lx + 1] -
                          T[ly + 10][lx + 1];
-    if (QF) {
+    if (APPLY) {
+      const long long qz = q2[z];
+      const long long zoff = (long long)z * s2;
+      if (va) {
+        const double y = fma(b_a, xa, cs * __ll2double_rn(La + mul_shift(qa + qz, Uca, F)));
+        yout[oa + zoff] = y;
+        dot = fma(xa, y, dot);
+      }
+      if (vb) {
+        const double y = fma(b_b, xb, cs * __ll2double_rn(Lb + mul_shift(qb + qz, Ucb, F)));
+        yout[ob + zoff] = y;
+        dot = fma(xb, y, dot);
+      }
+    } else if (QF) {
       const long long qz = q2[z];
       if (va) {
         const double r = fma(-cs, __ll2double_rn(La + mul_shift(qa + qz, Uca, F)), b_a);
@@ -471,6 +492,13 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
     Uca = Una;
     Ucb = Unb;
     buf ^= 1;
+  }
+  if (APPLY) {
+    dot = block_sum(dot);
+    if (threadIdx.x == 0) {
+      partial[2 * blockIdx.x] = dot;
+      partial[2 * blockIdx.x + 1] = 0.0;
+    }
   }
 }
 
@@ -530,12 +558,21 @@ __global__ void k_pcg_xr(const double* rz, const double* pq, double* alpha_out, 
 }
 
 // p = z + beta p with the flexible beta = -alpha (z_{k+1}.q_k) / (z_k.r_k); first: p = z.
+// emax_out (may be NULL): raised to the largest biased exponent of the new p.
 __global__ void k_pcg_p(const double* alpha, const double* zq, const double* rz_old, int first,
-                        double* __restrict__ p, const double* __restrict__ z, long long N) {
+                        double* __restrict__ p, const double* __restrict__ z, long long N, int* emax_out) {
   double beta = first || rz_old[0] == 0.0 ? 0.0 : -alpha[0] * zq[0] / rz_old[0];
+  int emx = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x)
-    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = first ? z[i] : fma(beta, p[i], z[i]);
+    p[i] = v;
+    emx = max(emx, (__double2hiint(v) >> 20) & 0x7FF);
+  }
+  if (emax_out) {
+    for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(emax_out, emx);
+  }
 }
 
 __global__ void k_copy_scalar(const double* src, double* dst) { *dst = *src; }
@@ -675,18 +712,47 @@ ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, 
 }
 
 namespace {
-template <int NP, int P, bool QF>
+template <int NP, int P, bool QF, bool APPLY = false>
 ts_status launch_march3(long long blocks, const AxisParams& a, double sigma, const long long* Q, int F,
                         const double* x, const double* b, __nv_bfloat16* planes, long long N, const int* emax_dev,
-                        cudaStream_t s) {
+                        cudaStream_t s, double* yout = nullptr, double* partial = nullptr) {
   static bool attr_set = false;  // per instantiation: the ring is dynamic shared memory
   if (!attr_set) {
-    TS_CHECK_CUDA(cudaFuncSetAttribute(k_residual_march3<NP, P, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       RING_BYTES));
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_residual_march3<NP, P, QF, APPLY>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, RING_BYTES));
     attr_set = true;
   }
-  k_residual_march3<NP, P, QF><<<(unsigned)blocks, 256, RING_BYTES, s>>>(a, sigma, Q, F, x, b, planes, N, emax_dev);
+  k_residual_march3<NP, P, QF, APPLY>
+      <<<(unsigned)blocks, 256, RING_BYTES, s>>>(a, sigma, Q, F, x, b, planes, N, emax_dev, yout, partial);
   return TS_OK;
+}
+
+// Fixed-point headroom H and fraction bits F of the folded diagonal for sigma + V1
+// (d = 3, one spacing): q_max bounds |sigma + V1| / h^-2; H leaves room for
+// (4d + q_max + 1) 2^H <= 2^62 and F for q_max 2^F < 2^62.  False when fewer than 53 bits
+// of headroom would remain.
+bool fold_params(const ts_plan* p, double sigma, int* Hq_out, int* F_out) {
+  if (p->d != 3 || !isotropic_h(p)) return false;
+  double fmax = std::fabs(sigma);
+  for (int k = 0; k < 3; ++k) {
+    double m = 0.0;
+    for (double v : p->axis[k]->f) m = std::fmax(m, std::fabs(v));
+    fmax += m;
+  }
+  const double h = 2.0 * p->L[0] / (p->n[0] + 1);
+  const double qmax = fmax / (1.0 / (h * h));
+  if (!std::isfinite(qmax)) return false;
+  int Hq = 58;
+  while (Hq >= 53 && std::ldexp(4.0 * p->d + qmax + 1.0, Hq) > std::ldexp(1.0, 62)) --Hq;
+  int F = 62;
+  while (F > Hq && std::ldexp(qmax + 1.0, F) >= std::ldexp(1.0, 62)) --F;
+  *Hq_out = Hq;
+  *F_out = F;
+  return Hq >= 53 && F >= Hq;
+}
+
+long long march_blocks(const ts_plan* p) {
+  return (long long)((p->n[0] + MX - 1) / MX) * ((p->n[1] + MY - 1) / MY) * ((p->n[2] + MZ - 1) / MZ);
 }
 
 ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const double* x, const double* b,
@@ -698,20 +764,9 @@ ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const doub
   if (p->d == 3) {
     const long long blocks = (long long)((p->n[0] + MX - 1) / MX) * ((p->n[1] + MY - 1) / MY) *
                              ((p->n[2] + MZ - 1) / MZ);
-    // Folded diagonal: q_max bounds |sigma + V1| / h^-2; H leaves room for
-    // (4d + q_max + 1) 2^H <= 2^62, F for q_max 2^F < 2^62; needs H >= 53.
-    double fmax = std::fabs(sigma);
-    for (int k = 0; k < 3; ++k) {
-      double m = 0.0;
-      for (double v : p->axis[k]->f) m = std::fmax(m, std::fabs(v));
-      fmax += m;
-    }
-    const double qmax = fmax / a.ih2[0];
-    int Hq = 58;
-    while (Hq >= 53 && std::ldexp(4.0 * p->d + qmax + 1.0, Hq) > std::ldexp(1.0, 62)) --Hq;
-    int F = 62;
-    while (F > Hq && std::ldexp(qmax + 1.0, F) >= std::ldexp(1.0, 62)) --F;
-    if (qtab && Hq >= 53 && F >= Hq && std::isfinite(qmax)) {
+    int Hq = 0, F = 0;
+    const bool fold = fold_params(p, sigma, &Hq, &F);
+    if (qtab && fold) {
       const int total = qtable_count(p);
       k_qtables<<<(total + 127) / 128, 128, 0, s>>>(p->f[0], p->n[0], p->f[1], p->n[1], p->f[2], p->n[2], sigma,
                                                     a.ih2[0], F, qtab);
@@ -753,6 +808,43 @@ ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const doub
 }
 }  // namespace
 
+ts_status fixed_operator_prepare(const ts_plan* p, double sigma, long long* qtab, FixedOperator* fo,
+                                 cudaStream_t s) {
+  fo->ok = false;
+  if (!fold_params(p, sigma, &fo->H, &fo->F)) return TS_OK;
+  const AxisParams a = axis_params(p, false);
+  const int total = qtable_count(p);
+  k_qtables<<<(total + 127) / 128, 128, 0, s>>>(p->f[0], p->n[0], p->f[1], p->n[1], p->f[2], p->n[2], sigma,
+                                                a.ih2[0], fo->F, qtab);
+  TS_LAUNCHED(1);
+  fo->qtab = qtab;
+  fo->sigma = sigma;
+  fo->blocks = march_blocks(p);
+  fo->ok = true;
+  return TS_OK;
+}
+
+ts_status operator_apply_fixed(const ts_plan* p, const FixedOperator& fo, const double* V2, const double* x, double* y,
+                               const int* emax_dev, double* partial, double* out2, cudaStream_t s) {
+  const AxisParams a = axis_params(p, false);
+#define TS_OP_CASE(PP)                                                                                     \
+  case PP:                                                                                                 \
+    TS_TRY((launch_march3<1, PP, true, true>(fo.blocks, a, fo.sigma, fo.qtab, fo.F, x, V2, nullptr, p->N, emax_dev, \
+                                             s, y, partial)));                                             \
+    break;
+  switch (fo.H - 53) {
+    TS_OP_CASE(0) TS_OP_CASE(1) TS_OP_CASE(2) TS_OP_CASE(3) TS_OP_CASE(4)
+    default: TS_OP_CASE(5)
+  }
+#undef TS_OP_CASE
+  TS_LAUNCHED(1);
+  if (out2) {
+    k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)fo.blocks, out2);
+    TS_LAUNCHED(1);
+  }
+  return TS_OK;
+}
+
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s) {
   unsigned g = grid_for(N);
@@ -775,8 +867,9 @@ ts_status pcg_update_xr(const double* rz, const double* pq, double* alpha_out, d
 }
 
 ts_status pcg_update_p(const double* alpha, const double* zq, const double* rz_old, int first, double* p,
-                       const double* z, long long N, cudaStream_t s) {
-  k_pcg_p<<<grid_for(N), 256, 0, s>>>(alpha, zq, rz_old, first, p, z, N);
+                       const double* z, long long N, cudaStream_t s, int* emax_out) {
+  if (emax_out) TS_CHECK_CUDA(cudaMemsetAsync(emax_out, 0, sizeof(int), s));
+  k_pcg_p<<<grid_for(N), 256, 0, s>>>(alpha, zq, rz_old, first, p, z, N, emax_out);
   TS_LAUNCHED(1);
   return TS_OK;
 }

@@ -29,6 +29,23 @@ bool isotropic_h(const ts_plan* p);
 ts_status residual_split_fixed(const ts_plan* p, double sigma, const double* x, const double* b,
                                __nv_bfloat16* planes, int np, const int* emax_dev, long long* qtab, cudaStream_t s);
 int qtable_count(const ts_plan* p);
+
+// The operator apply of PCG in exact fixed point (d = 3, one spacing): y = A x with the
+// Laplacian and sigma + V1 folded into the integer sum and V2 x in FP64, plus x.y into
+// out2[0] (fixed-order reduction over `blocks` partials; partial holds 2 * blocks doubles).
+// *emax_dev must hold the largest biased exponent of x.  fixed_operator_prepare fills the
+// Q tables for sigma (qtab: qtable_count(p) int64) and leaves ok = false when the form does
+// not apply (then use stencil_apply).
+struct FixedOperator {
+  bool ok = false;
+  int H = 0, F = 0;
+  double sigma = 0.0;
+  const long long* qtab = nullptr;
+  long long blocks = 0;
+};
+ts_status fixed_operator_prepare(const ts_plan* p, double sigma, long long* qtab, FixedOperator* fo, cudaStream_t s);
+ts_status operator_apply_fixed(const ts_plan* p, const FixedOperator& fo, const double* V2, const double* x, double* y,
+                               const int* emax_dev, double* partial, double* out2, cudaStream_t s);
 // out2[0] = a.b (b == NULL: sum of a), out2[1] = c.d (c, d may be NULL).
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s);
@@ -38,7 +55,7 @@ ts_status pcg_update_xr(const double* rz, const double* pq, double* alpha_out, d
                         cudaStream_t s);
 // p = z + beta p, beta = -alpha zq / rz_old (first: p = z).
 ts_status pcg_update_p(const double* alpha, const double* zq, const double* rz_old, int first, double* p,
-                       const double* z, long long N, cudaStream_t s);
+                       const double* z, long long N, cudaStream_t s, int* emax_out = nullptr);
 ts_status copy_scalar(const double* src, double* dst, cudaStream_t s);
 // u = tensor product of the per-axis ground eigenvectors (column 0 of each S_k).
 ts_status tensor_ground(const ts_plan* p, double* u, cudaStream_t s);

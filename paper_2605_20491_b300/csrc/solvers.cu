@@ -73,13 +73,27 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
                    double tol, int maxit, ts_precision prec, int* iters_out, double* relres_out, cudaStream_t s) {
   const long long N = p->N;
   Scratch sc_mem(s);
-  double *r, *z, *pv, *q, *partial, *sc;
+  double *r, *z, *pv, *q, *partial, *sc, *qtab, *opart;
   TS_TRY(sc_mem.get(&r, N));
   TS_TRY(sc_mem.get(&z, N));
   TS_TRY(sc_mem.get(&pv, N));
   TS_TRY(sc_mem.get(&q, N));
   TS_TRY(sc_mem.get(&partial, 2 * RED_BLOCKS));
   TS_TRY(sc_mem.get(&sc, 16));
+  // On grids with one spacing (d = 3) the operator apply q = A p runs in exact fixed point
+  // (Laplacian and sigma + V1 folded into an integer sum, V2 p in FP64); its scale is the
+  // largest exponent of p, which the update of p reports into sc[15]'s int slot.
+  FixedOperator fo;
+  int* emax = reinterpret_cast<int*>(sc + 15);
+  if (qtable_count(p) > 0) {
+    TS_TRY(sc_mem.get(&qtab, (size_t)qtable_count(p)));
+    TS_TRY(fixed_operator_prepare(p, sigma, reinterpret_cast<long long*>(qtab), &fo, s));
+    if (fo.ok) TS_TRY(sc_mem.get(&opart, 2 * (size_t)fo.blocks));
+  }
+  auto apply_A = [&](double* out2) -> ts_status {  // q = A p; out2[0] = p.q
+    if (fo.ok) return operator_apply_fixed(p, fo, V2, pv, q, emax, opart, out2, s);
+    return stencil_apply(p, V2, sigma, pv, q, partial, out2, s);
+  };
   double h[2];
   // r = b - A x;  sc[0] = r.r, sc[1] = b.b
   TS_TRY(stencil_residual(p, V2, sigma, x, b, r, partial, sc + 0, s));
@@ -91,7 +105,7 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
   if (!converged) {
     TS_TRY(apply_inverse_impl(p, sigma_P, r, z, prec, s));           // z = P r
     TS_TRY(dot2(N, r, z, nullptr, nullptr, partial, sc + 2, s));     // sc[2] = r.z
-    TS_TRY(pcg_update_p(nullptr, nullptr, nullptr, 1, pv, z, N, s)); // p = z
+    TS_TRY(pcg_update_p(nullptr, nullptr, nullptr, 1, pv, z, N, s, fo.ok ? emax : nullptr));  // p = z
   }
   // The stopping test lags one iteration: iteration k posts its r.r, and the host reads
   // iteration k - 1's while the GPU runs iteration k, so the GPU never waits for the host.
@@ -115,7 +129,7 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
   };
   int last_checked = 0;
   while (!converged && it < maxit) {
-    TS_TRY(stencil_apply(p, V2, sigma, pv, q, partial, sc + 4, s));                     // q = A p; sc[4] = p.q
+    TS_TRY(apply_A(sc + 4));                                                            // q = A p; sc[4] = p.q
     TS_TRY(pcg_update_xr(sc + 2, sc + 4, sc + 6, x, r, pv, q, N, partial, sc + 8, s));  // sc[6] = alpha, sc[8] = r.r
     ++it;
     TS_TRY(mb.post(sc + 8, it, s));
@@ -147,7 +161,7 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
     if (it == maxit) break;
     TS_TRY(apply_inverse_impl(p, sigma_P, r, z, prec, s));          // z = P r
     TS_TRY(dot2(N, r, z, z, q, partial, sc + 10, s));               // sc[10] = r.z, sc[11] = z.q
-    TS_TRY(pcg_update_p(sc + 6, sc + 11, sc + 2, 0, pv, z, N, s));  // p = z + beta p
+    TS_TRY(pcg_update_p(sc + 6, sc + 11, sc + 2, 0, pv, z, N, s, fo.ok ? emax : nullptr));  // p = z + beta p
     TS_TRY(copy_scalar(sc + 10, sc + 2, s));
   }
   if (!converged && it > last_checked) {  // the last iteration's own test

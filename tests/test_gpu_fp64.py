@@ -155,3 +155,24 @@ def test_strang_vs_oracle(T, n, dtype):
         t = dev(psi.astype(np.float32))
         T.ts_split_step(P, 0.01, 10, dev(V2), t, T.TS_C64)
         assert rel(host(t), want) < 1e-6
+
+
+@pytest.mark.parametrize("n", [(40, 24, 56), (33, 33, 33), (64, 16, 40)])
+def test_pcg_fixed_point_operator_vs_oracle(T, n):
+    """On grids with one spacing h (d = 3) PCG applies A in exact fixed point (Laplacian and
+    sigma + V1 as one integer sum, V2 x in FP64): same iterate as the oracle's textbook PCG,
+    on ragged tiles, with a mixed (BF16X3) preconditioner too."""
+    L = tuple((k + 1) / 4.0 for k in n)
+    f = S.harmonic(n, L, (1.0, 1.2, 0.8))
+    P = T.ts_plan_create(n, L, f, 1 << T.TS_BF16X3)
+    Po = O.plan(n, L, f)
+    V2 = S.v2_cos_bumps(n, L, seed=1) + 5.0
+    b = S.uniform(0, Po.N)
+    xo, ito, _ = O.pcg(Po, b, sigma=0.3, V2=V2, tol=1e-12)
+    for prec in (T.TS_FP64, T.TS_BF16X3) if all(k % 8 == 0 for k in n) else (T.TS_FP64,):
+        x = dev(np.zeros(Po.N))
+        st, it, relres = T.ts_pcg(P, 0.3, 0.3, dev(V2), dev(b), x, 1e-12, 200, prec)
+        assert relres < 1e-11
+        assert rel(host(x), xo) < 1e-10
+        if prec == T.TS_FP64:
+            assert abs(it - ito) <= 1
