@@ -191,6 +191,9 @@ ts_status ts_apply_batch(const ts_batch_item* items, int count, void* stream);
 /*
  * y = (-Delta_h + V1 + V2 + sigma) x by the 2d+1 point stencil of eq. general_system
  * (zero Dirichlet ghosts).  V2: N doubles or NULL.  x, y: N doubles, must not alias.
+ * For d = 3 with one spacing h on all axes (and sigma + V1 not too large against h^-2)
+ * the Laplacian and sigma + V1 are summed exactly in 64-bit fixed point scaled by the
+ * largest exponent of x (V2 x in FP64); otherwise in FP64.
  */
 ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2,
                             const double* x, double* y, void* stream);

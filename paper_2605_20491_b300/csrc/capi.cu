@@ -215,12 +215,7 @@ ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2,
                             void* stream) {
   TS_API_BEGIN(plan);
   TS_REQUIRE(x && y && x != y, "x and y must be non-NULL and distinct");
-  double* partial = nullptr;
-  cudaStream_t s = (cudaStream_t)stream;
-  TS_TRY(scratch_alloc((void**)&partial, sizeof(double) * 2 * RED_BLOCKS, s));
-  ts_status st = stencil_apply(plan, V2, sigma, x, y, partial, nullptr, s);
-  scratch_free(partial, s);
-  return st;
+  return operator_apply(plan, V2, sigma, x, y, (cudaStream_t)stream);
 }
 
 ts_status ts_pcg(const ts_plan* plan, double sigma, double sigma_P, const double* V2, const double* b, double* x,

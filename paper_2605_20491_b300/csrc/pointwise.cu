@@ -808,6 +808,52 @@ ts_status residual_split_fixed_launch(const ts_plan* p, double sigma, const doub
 }
 }  // namespace
 
+namespace {
+// Largest biased exponent over x (integer max of the exponent bits; order-independent).
+__global__ void k_max_exponent(const double* __restrict__ x, long long N, int* out) {
+  int m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, (__double2hiint(x[i]) >> 20) & 0x7FF);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+}  // namespace
+
+ts_status operator_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
+                         cudaStream_t s) {
+  int H = 0, F = 0;
+  if (!fold_params(p, sigma, &H, &F)) {
+    void* partial = nullptr;
+    TS_TRY(scratch_alloc(&partial, sizeof(double) * 2 * RED_BLOCKS, s));
+    const ts_status st = stencil_apply(p, V2, sigma, x, y, (double*)partial, nullptr, s);
+    scratch_free(partial, s);
+    return st;
+  }
+  const long long blocks = march_blocks(p);
+  // one allocation: the exponent, the Q tables, the per-block partials
+  const size_t qbytes = sizeof(long long) * (size_t)qtable_count(p);
+  void* work = nullptr;
+  TS_TRY(scratch_alloc(&work, 256 + qbytes + sizeof(double) * 2 * (size_t)blocks, s));
+  char* w = static_cast<char*>(work);
+  int* emax = reinterpret_cast<int*>(w);
+  long long* qtab = reinterpret_cast<long long*>(w + 256);
+  double* partial = reinterpret_cast<double*>(w + 256 + qbytes);
+  ts_status st = TS_OK;
+  if (cudaMemsetAsync(emax, 0, sizeof(int), s) != cudaSuccess) {
+    set_error("memset failed");
+    st = TS_ERR_CUDA;
+  }
+  if (st == TS_OK) {
+    k_max_exponent<<<grid_for(p->N), 256, 0, s>>>(x, p->N, emax);
+    count_launches(1);
+    FixedOperator fo;
+    st = fixed_operator_prepare(p, sigma, qtab, &fo, s);
+    if (st == TS_OK) st = operator_apply_fixed(p, fo, V2, x, y, emax, partial, nullptr, s);
+  }
+  scratch_free(work, s);
+  return st;
+}
+
 ts_status fixed_operator_prepare(const ts_plan* p, double sigma, long long* qtab, FixedOperator* fo,
                                  cudaStream_t s) {
   fo->ok = false;

@@ -36,6 +36,10 @@ int qtable_count(const ts_plan* p);
 // *emax_dev must hold the largest biased exponent of x.  fixed_operator_prepare fills the
 // Q tables for sigma (qtab: qtable_count(p) int64) and leaves ok = false when the form does
 // not apply (then use stencil_apply).
+// y = A x for any plan: the exact fixed-point form where it applies (a max-exponent pass
+// over x first), else the FP64 stencil.
+ts_status operator_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
+                         cudaStream_t s);
 struct FixedOperator {
   bool ok = false;
   int H = 0, F = 0;

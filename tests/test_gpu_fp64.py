@@ -176,3 +176,18 @@ def test_pcg_fixed_point_operator_vs_oracle(T, n):
         assert rel(host(x), xo) < 1e-10
         if prec == T.TS_FP64:
             assert abs(it - ito) <= 1
+
+
+@pytest.mark.parametrize("n", [(40, 24, 56), (33, 33, 33)])
+def test_operator_fixed_point_vs_oracle(T, n):
+    """ts_apply_operator on grids with one spacing (d = 3): the exact fixed-point form agrees
+    with the oracle's FP64 stencil to rounding, also for x spanning eleven decades."""
+    L = tuple((k + 1) / 4.0 for k in n)
+    f = S.harmonic(n, L, (1.0, 1.2, 0.8))
+    P = T.ts_plan_create(n, L, f, 0)
+    Po = O.plan(n, L, f)
+    V2 = S.uniform(2, Po.N, 0, 3)
+    for x in (S.normal(1, Po.N), S.normal(1, Po.N) * np.exp(S.uniform(3, Po.N, -12.0, 13.0))):
+        y = dev(np.zeros(Po.N))
+        T.ts_apply_operator(P, 0.3, dev(V2), dev(x), y)
+        assert rel(host(y), O.stencil(Po, x, 0.3, V2)) < 1e-14
