@@ -111,6 +111,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
 
 
+def max_over_ranks(ms, dist=None, device=None):
+    """The slowest rank's time (all-reduce MAX over the process group; `dist` None: this
+    process alone).  Every rank gets the same value."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(world, dof_per_rank, ms):
+    """GDoF/s of `world` independent replicas of dof_per_rank each, timed by the slowest."""
+    return world * dof_per_rank / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -437,12 +453,8 @@ def run_ours(args):
     x1_launches, x1_ms, x1_flops, x1_bytes = T.ts_profile_end(T.PROF_TC_PASS_X1)
     launches = T.ts_launch_count() - launches0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
-    value = world * N / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    value = whole_job_rate(world, N, ms)
 
     # End to end through the public API with host buffers: every step copies its right-hand
     # side from pinned host memory, solves, and copies its solution back.  Steps are
