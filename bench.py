@@ -236,10 +236,12 @@ def run_profile_case(args):
     return 0
 
 
-def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None):
+def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, overload_factor=2.0):
     """The serving workload: `count` requests (3D grids with n_k from {32, 48, 64, 96, 128},
     30% PCG / 50% inverse / 20% exp), first submitted all at once (saturated throughput),
-    then again with Poisson arrivals at rate_factor x that throughput; returns the stats."""
+    then again with Poisson arrivals at rate_factor x that throughput, and once more at
+    overload_factor x it (an overloaded server: the queue grows while arrivals last);
+    returns the stats of each phase."""
     import torch
     prec = T.TS_BF16X3 if prec is None else prec
     specs = synth.serving_requests(count, seed=seed, omega_set=omega_set)
@@ -264,7 +266,8 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None):
     torch.cuda.synchronize()
     server = T.Server(max_inflight=16)
     out = {}
-    for phase in ("saturated", "poisson"):
+    phases = ("saturated", "poisson") + (("overload",) if overload_factor else ())
+    for phase in phases:
         for kw in reqs:
             if kw["kind"] == T.TS_REQ_PCG:
                 kw["out"].zero_()
@@ -273,7 +276,8 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None):
         if phase == "saturated":
             tickets = [server.submit(**kw) for kw in reqs]
         else:
-            rate = rate_factor * out["saturated"]["completed"] / (out["saturated"]["makespan_ms"] * 1e-3)
+            factor = rate_factor if phase == "poisson" else overload_factor
+            rate = factor * out["saturated"]["completed"] / (out["saturated"]["makespan_ms"] * 1e-3)
             u = synth.uniform(seed + 17, count, 1e-12, 1.0)
             gaps = -np.log(u) / rate
             tickets = []
@@ -290,15 +294,17 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None):
             fails += st != T.TS_OK
         stats = server.stats()
         stats["failed"] = fails
-        if phase == "poisson":
+        if phase != "saturated":
             stats["arrival_rate_per_s"] = rate
+            stats["rate_factor"] = factor
         out[phase] = stats
     server.close()
     out["requests"] = count
     out["mix"] = "30% PCG (V2 = 5 cos cos cos + 8 Gaussian bumps, tol 1e-10) / 50% inverse / 20% exp (tau 0.01)"
     out["grids"] = "3D, n_k iid from {32, 48, 64, 96, 128}"
     out["omega"] = "U[0.5, 2) per axis" if omega_set is None else f"from {list(omega_set)}"
-    out["precision"] = "BF16X3 (PCG: BF16X3 preconditioner, FP64 recurrence)"
+    out["precision"] = ("BF16X3 (PCG: BF16X3 preconditioner, FP64 recurrence)" if prec == T.TS_BF16X3
+                        else "FP64 (all applies and the PCG preconditioner)")
     return out
 
 
@@ -354,6 +360,7 @@ def run_secondary(args):
     elif name == "serving":
         line["continuous_omega"] = serving_run(T, args.requests)
         line["discrete_omega"] = serving_run(T, args.requests, omega_set=(0.5, 1.0, 1.5, 2.0))
+        line["fp64"] = serving_run(T, args.requests, prec=T.TS_FP64)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -441,12 +448,20 @@ def run_ours(args):
     t_wall0 = time.time()
     launches0 = T.ts_launch_count()
     T.ts_profile_begin()
+    # One event between consecutive steps as well (recording an event costs no GPU time):
+    # the whole region gives the mean, the per-step intervals the median.
+    ev_steps = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps - 1)]
     e0.record()
-    for _ in range(args.steps):
+    for i in range(args.steps):
         step()
+        if i < args.steps - 1:
+            ev_steps[i].record()
     e1.record()
     torch.cuda.synchronize()
     clocks.mark(t_wall0, time.time())
+    marks = [e0] + ev_steps + [e1]
+    step_ms = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps))
+    median_ms = step_ms[len(step_ms) // 2] if len(step_ms) % 2 else 0.5 * sum(step_ms[len(step_ms) // 2 - 1:len(step_ms) // 2 + 1])
     barrier()
     tc_launches, tc_ms, tc_flops, tc_bytes = T.ts_profile_end(T.PROF_TC_PASS)
     res_launches, res_ms, _, res_bytes = T.ts_profile_end(T.PROF_RESIDUAL)
@@ -509,6 +524,7 @@ def run_ours(args):
                 "share_of_step": tc_ms / (ms * args.steps)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step_median": median_ms, "ms_per_step_min": step_ms[0], "ms_per_step_max": step_ms[-1],
             "vs_baseline": None, "dtype": "bf16 splits (x3, x1) + f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": list(n), "L": list(L), "omega": list(w["omega"]), "sigma": sigma,
                        "rhs": "iid N(0,1), SplitMix64 seed 2",
