@@ -74,18 +74,38 @@ typedef struct {
   int d;                   /* dimension, 1 <= d <= TS_MAX_DIM                          */
   const int* n;            /* n[k] interior nodes on axis k, 1 <= n[k] <= 4096          */
   const double* L;         /* L[k] > 0: axis k spans [-L[k], L[k]]                     */
-  const double* const* f;  /* f[k][i] = f_k(x_{k,i+1}), i = 0..n[k]-1 (V1 samples)      */
+  const double* const* f;  /* f[k][i] = f_k(x_{k,i}), i = 0..n[k]-1, at the interior nodes
+                              of axis k (ts_grid_nodes) (V1 samples)                     */
   int bc;                  /* boundary condition: 0 = homogeneous Dirichlet (only one) */
+  int order;               /* the k of Q^k (Sec. 2): 0 or 1 = Q^1, the second-order
+                              finite-difference scheme on the uniform nodes
+                              x_i = -L + (i+1) h, h = 2L/(n+1); 2..32 = Q^k spectral
+                              elements with GLL quadrature, (n[k] + 1) / order elements
+                              per axis ((n[k] + 1) % order == 0 on every axis)          */
 } ts_plan_desc;
 
 /*
- * Step 1 of Sec. 2.1 (eq. eigen_decomp): assemble H_k = h_k^-2 tridiag(-1,2,-1) + diag f_k
- * for every axis, eigendecompose each in FP64 on the GPU (axes with identical (n, L, f)
- * share one decomposition) and keep S_k, S_k^T, lambda_k and, for every precision bit
- * set in precision_mask (bit p = 1u << ts_precision p; TS_FP64 is always built), the
- * split low-precision copies of S_k resident on the current device.  The work runs on
- * `stream` and is complete when the call returns.  *out receives the plan; on error it
- * is set to NULL.
+ * Interior nodes of one axis (Sec. 2): for order 0 or 1 the uniform x_i = -L + (i+1) h,
+ * h = 2L/(n+1); for order k >= 2 the Gauss-Lobatto-Legendre points of degree k mapped onto
+ * the c = (n+1)/k equal elements of [-L, L], end points shared, the two boundary nodes
+ * dropped.  x (n doubles, HOST) receives the coordinates; m (n doubles, HOST, may be NULL)
+ * the lumped mass, i.e. the diagonal of the GLL mass matrix M (h for order 1).  Needs no
+ * GPU.  TS_ERR_INVALID_ARG if n < 1, L <= 0, order > 32 or (n+1) % order != 0.
+ */
+ts_status ts_grid_nodes(int n, double L, int order, double* x, double* m);
+
+/*
+ * Step 1 of Sec. 2.1 (eq. eigen_decomp): for every axis assemble H_k = M_k^{-1} Stiff_k + F_k
+ * (Q^1: h_k^-2 tridiag(-1,2,-1) + diag f_k), eigendecompose the symmetric
+ * M_k^{-1/2} Stiff_k M_k^{-1/2} + F_k = Q_k Lambda_k Q_k^T in FP64 on the GPU (axes with
+ * identical (n, L, f, order) share one decomposition) and keep T_k^{-1} = Q_k^T M_k^{1/2},
+ * T_k = M_k^{-1/2} Q_k, lambda_k and, for every precision bit set in precision_mask
+ * (bit p = 1u << ts_precision p; TS_FP64 is always built), their split low-precision
+ * copies resident on the current device.  For Q^1, M_k = h_k I and T_k = Q_k is
+ * orthogonal.  For Q^k, k >= 2, the plan also keeps the orthogonal Q_k and the banded
+ * M^{-1} Stiff and M^{-1/2} Stiff M^{-1/2} that PCG and inverse iteration use.  The work
+ * runs on `stream` and is complete when the call returns.  *out receives the plan; on
+ * error it is set to NULL.
  */
 ts_status ts_plan_create(const ts_plan_desc* desc, unsigned precision_mask, void* stream,
                          ts_plan** out);
@@ -96,7 +116,9 @@ ts_status ts_plan_destroy(ts_plan* plan);
 /* Copies lambda_axis (ascending, n[axis] doubles) into HOST memory lambda_host. */
 ts_status ts_plan_eigs(const ts_plan* plan, int axis, double* lambda_host);
 
-/* Copies S_axis (row-major n x n, column j = eigenvector of lambda_j) into HOST memory. */
+/* Copies T_axis (row-major n x n, column j = eigenvector of H_axis for lambda_j; for
+ * Q^1 the orthonormal S_axis, for Q^k T = M^{-1/2} Q, M-orthonormal columns) into HOST
+ * memory. */
 ts_status ts_plan_eigvecs(const ts_plan* plan, int axis, double* S_host);
 
 /* Plan geometry: *d, n[0..d-1] (n may be NULL) and *N (may be NULL). */
@@ -110,7 +132,8 @@ ts_status ts_plan_bytes(const ts_plan* plan, long long* bytes);
  * b, u: N doubles (real, FP64).  b and u may alias.  sigma must keep the operator
  * nonsingular (sigma != -lambda_min sum); the call does not check definiteness.
  * prec selects the contraction arithmetic (TS_FP64, TS_BF16X3, TS_BF16X6); a split
- * precision needs its bit in the plan's precision_mask and every n_k a multiple of 8.
+ * precision needs its bit in the plan's precision_mask (any n_k: its bf16 planes store each
+ * pass's contracted axis in rows padded to a multiple of 8 elements).
  */
 ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, double* u,
                            ts_precision prec, void* stream);
@@ -189,11 +212,12 @@ typedef struct {
 ts_status ts_apply_batch(const ts_batch_item* items, int count, void* stream);
 
 /*
- * y = (-Delta_h + V1 + V2 + sigma) x by the 2d+1 point stencil of eq. general_system
- * (zero Dirichlet ghosts).  V2: N doubles or NULL.  x, y: N doubles, must not alias.
- * For d = 3 with one spacing h on all axes (and sigma + V1 not too large against h^-2)
+ * y = (-Delta_h + V1 + V2 + sigma) x (eq. general_system, zero Dirichlet ghosts).
+ * V2: N doubles or NULL.  x, y: N doubles, must not alias.  Q^1: the 2d+1 point stencil;
+ * for d = 3 with one spacing h on all axes (and sigma + V1 not too large against h^-2)
  * the Laplacian and sigma + V1 are summed exactly in 64-bit fixed point scaled by the
- * largest exponent of x (V2 x in FP64); otherwise in FP64.
+ * largest exponent of x (V2 x in FP64); otherwise in FP64.  Q^k, k >= 2: the per-axis
+ * banded product with K_k = M_k^{-1} Stiff_k (bandwidth 2k + 1) in FP64.
  */
 ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2,
                             const double* x, double* y, void* stream);
@@ -208,6 +232,10 @@ ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2,
  * recurrence residual, or after maxit iterations (then TS_ERR_NOT_CONVERGED, x holds
  * the last iterate).  *iters (may be NULL) = iterations taken; *relres (may be NULL) =
  * TRUE relative residual ||b - A x|| / ||b|| recomputed at exit.  Synchronises stream.
+ * Q^k, k >= 2: A and P are self-adjoint in the M-inner product <u, v>_M = sum M u v
+ * (M = prod_k M_k, the lumped mass), not in the plain one; the iteration runs in
+ * x~ = M^{1/2} x on the symmetric M^{1/2} A M^{-1/2}, so every inner product and norm
+ * above is the M-weighted one (for Q^1, M = prod h_k I and the two coincide).
  */
 ts_status ts_pcg(const ts_plan* plan, double sigma, double sigma_P, const double* V2,
                  const double* b, double* x, double tol, int maxit, ts_precision precond,
@@ -223,7 +251,8 @@ ts_status ts_pcg(const ts_plan* plan, double sigma, double sigma_P, const double
  *           lambda_{k+1} = (u_{k+1}, H u_{k+1})
  *   until |lambda_{k+1} - lambda_k| / |lambda_{k+1}| < tol_lambda or maxit.
  * u: N doubles (in/out).  The sign is fixed so that sum(u) > 0.  *lambda, *outer_iters,
- * *pcg_iters may be NULL.  Synchronises stream.
+ * *pcg_iters may be NULL.  Synchronises stream.  Q^k, k >= 2: inner products and norms
+ * are M-weighted as in ts_pcg, so the returned u has ||u||_M = 1.
  */
 ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* V2, double* u,
                                int init_from_plan, double tol_lambda, int maxit, double pcg_tol,

@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "mixed.cuh"
 #include "pointwise.cuh"
+#include "sem_axis.cuh"
 #include "solvers.cuh"
 
 namespace ts {
@@ -97,6 +98,9 @@ ts_status ts_plan_create(const ts_plan_desc* desc, unsigned precision_mask, void
     TS_REQUIRE(desc->n[k] >= 1 && desc->n[k] <= 4096, "n[%d] = %d out of range [1, 4096]", k, desc->n[k]);
     TS_REQUIRE(desc->L[k] > 0.0, "L[%d] must be positive", k);
     TS_REQUIRE(desc->f[k], "f[%d] is NULL", k);
+    TS_REQUIRE(desc->order >= 0 && desc->order <= 32, "order = %d out of range [0, 32]", desc->order);
+    TS_REQUIRE(desc->order < 2 || (desc->n[k] + 1) % desc->order == 0,
+               "Q^%d: n[%d] + 1 = %d is not a multiple of %d", desc->order, k, desc->n[k] + 1, desc->order);
     N *= desc->n[k];
     TS_REQUIRE(N <= (1LL << 40), "grid too large");
   }
@@ -108,6 +112,27 @@ ts_status ts_plan_destroy(ts_plan* plan) {
   if (!plan) return TS_OK;
   DeviceGuard g(plan->device);
   plan_free(plan);
+  return TS_OK;
+}
+
+ts_status ts_grid_nodes(int n, double L, int order, double* x, double* m) {
+  clear_error();
+  TS_REQUIRE(x, "x is NULL");
+  TS_REQUIRE(n >= 1 && n <= 4096, "n = %d out of range [1, 4096]", n);
+  TS_REQUIRE(L > 0.0, "L must be positive");
+  TS_REQUIRE(order >= 0 && order <= 32, "order = %d out of range [0, 32]", order);
+  if (order < 2) {
+    const double h = 2.0 * L / (n + 1);
+    for (int i = 0; i < n; ++i) {
+      x[i] = -L + (i + 1) * h;
+      if (m) m[i] = h;
+    }
+    return TS_OK;
+  }
+  SemAxis ax;
+  TS_TRY(sem_axis_build(n, L, order, &ax));
+  std::memcpy(x, ax.x.data(), sizeof(double) * n);
+  if (m) std::memcpy(m, ax.m.data(), sizeof(double) * n);
   return TS_OK;
 }
 
@@ -224,7 +249,7 @@ ts_status ts_pcg(const ts_plan* plan, double sigma, double sigma_P, const double
   TS_REQUIRE(b && x && b != x, "b and x must be non-NULL and distinct");
   TS_REQUIRE(tol > 0.0 && maxit >= 0, "tol must be > 0 and maxit >= 0");
   TS_TRY(check_prec(plan, precond));
-  return pcg_impl(plan, sigma, sigma_P, V2, b, x, tol, maxit, precond, iters, relres, (cudaStream_t)stream);
+  return pcg_solve(plan, sigma, sigma_P, V2, b, x, tol, maxit, precond, iters, relres, (cudaStream_t)stream);
 }
 
 ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* V2, double* u, int init_from_plan,
@@ -234,7 +259,7 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
   TS_REQUIRE(u, "u must be non-NULL");
   TS_REQUIRE(tol_lambda > 0.0 && pcg_tol > 0.0 && maxit >= 1 && pcg_maxit >= 1, "bad tolerances or caps");
   TS_TRY(check_prec(plan, precond));
-  return inverse_iteration_impl(plan, shift, V2, u, init_from_plan, tol_lambda, maxit, pcg_tol, pcg_maxit, precond,
+  return inverse_iteration_solve(plan, shift, V2, u, init_from_plan, tol_lambda, maxit, pcg_tol, pcg_maxit, precond,
                                 lambda, outer_iters, pcg_iters, (cudaStream_t)stream);
 }
 

@@ -81,17 +81,25 @@ struct AxisParams {
 
 namespace ts {
 
-// Device tables of one axis: the eigendecomposition of H_k = h^-2 tridiag(-1,2,-1) + diag f
-// and the copies derived from it.  Shared by every plan (and every request) whose axis has
-// the same (n, L, f) on the same device; freed when the last user lets go of it.
+// Device tables of one axis: the eigendecomposition of H_k = M^{-1} Stiff + diag f (Q^1:
+// h^-2 tridiag(-1,2,-1) + diag f) and the copies derived from it.  Shared by every plan (and
+// every request) whose axis has the same (n, L, f, order, frame) on the same device; freed
+// when the last user lets go of it.
+//
+// S and St are the operands of the forward and backward contractions in the rotating form
+// Y = X^T B (y_j = sum_i B[i][j] x_i): S = (T^{-1})^T = M^{1/2} Q and St = T^T = Q^T M^{-1/2}.
+// For Q^1 (M = h I, the h^{+-1/2} cancel) and in the symmetric frame (the frame of PCG for
+// Q^k, where the unknown is M^{1/2} u) they are Q and Q^T.
 struct AxisTables {
   int device = 0;
   int n = 0;
   double L = 0.0;
+  int order = 1;                     // the k of Q^k
+  int frame = 0;                     // Q^k: 0 = the plan's own unknowns, 1 = M^{1/2} u
   std::vector<double> f;             // host copy of the samples (cache key)
-  void* block = nullptr;             // one allocation: S, St, lam, f, lamf
-  double* S = nullptr;               // row-major S[i][j], column j = eigenvector j
-  double* St = nullptr;              // S^T
+  void* block = nullptr;             // one allocation: S, St, lam, f, lamf (+ band, mh, mhi)
+  double* S = nullptr;               // forward operand S[i][j], see above
+  double* St = nullptr;              // backward operand
   double* lam = nullptr;             // eigenvalues, ascending
   double* fdev = nullptr;            // potential samples
   float* lamf = nullptr;             // eigenvalues rounded to FP32
@@ -101,7 +109,13 @@ struct AxisTables {
   __nv_bfloat16* Bb[NPREC] = {};
   float* Sf32 = nullptr;             // S and S^T rounded to FP32 (small-n path)
   float* Stf32 = nullptr;
-  std::vector<double> lam_host, S_host;
+  // Q^k, k >= 2: the 1D Laplacian as a band, band[i * (2k+1) + o] = K[i][i + o - k] (zero
+  // outside [0, n)), with K = M^{-1} Stiff (frame 0) or M^{-1/2} Stiff M^{-1/2} (frame 1);
+  // mh = M^{1/2} and mhi = M^{-1/2} (diagonals).
+  double* band = nullptr;
+  double* mh = nullptr;
+  double* mhi = nullptr;
+  std::vector<double> lam_host, S_host;  // S_host: T = M^{-1/2} Q, the eigenvectors of H_k
   long long bytes = 0;
   std::mutex mu;                     // guards the lazily built precision copies
   ~AxisTables();
@@ -129,6 +143,16 @@ struct ts_plan {
   __nv_bfloat16* Bf[ts::NPREC][TS_MAX_DIM] = {};
   __nv_bfloat16* Bb[ts::NPREC][TS_MAX_DIM] = {};
   long long bytes = 0;
+  // Q^k, k >= 2 (order 1 leaves these empty)
+  int order = 1;
+  const double* band[TS_MAX_DIM] = {};  // banded K_k of this plan's frame, 2 * order + 1 per row
+  const double* mh[TS_MAX_DIM] = {};    // M_k^{1/2}
+  const double* mhi[TS_MAX_DIM] = {};   // M_k^{-1/2}
+  ts_plan* sym = nullptr;               // the same grid in the frame M^{1/2} u (owned), or NULL
+  ts_plan() = default;
+  ts_plan(const ts_plan&) = delete;
+  ts_plan& operator=(const ts_plan&) = delete;
+  ~ts_plan();
 };
 
 namespace ts {

@@ -47,6 +47,15 @@
 
 namespace ts {
 
+long long mixed_plane_elems(const ts_plan* p) {
+  long long m = 0;
+  for (int k = 0; k < p->d; ++k) {
+    const long long e = (p->N / p->n[k]) * ((p->n[k] + 7) & ~7);
+    m = e > m ? e : m;
+  }
+  return m;
+}
+
 int bf16_planes(ts_precision prec) {
   if (prec == TS_BF16X1) return 1;
   if (prec == TS_BF16X3) return 2;
@@ -70,6 +79,12 @@ struct EpiParams {
   long long R;     // rows of the pass
   int n;           // contracted (= output column) extent
   long long N;     // elements per plane (R * n)
+  // Where output (row r, column j) goes: r_o + Ro j, planes No elements apart, with
+  // r_o = (r / on) old + r % on.  Plane outputs are the next pass's input, whose fastest
+  // axis (extent on) is stored in rows of old = on rounded up to a multiple of 8 (TMA rows
+  // are 16-byte aligned); FP64 / complex results are unpadded (on = old = 1, Ro = R).
+  long long Ro, No;
+  int on, old;
   void* out;
   int nstages;
   int bn;
@@ -148,6 +163,13 @@ __device__ __forceinline__ void epi_row_factors(const EpiParams& ep, long long r
   *rowph = make_float2((float)pr, (float)pi);
 }
 
+// Output row of data row r (see EpiParams::on).
+__device__ __forceinline__ long long epi_out_row(const EpiParams& ep, long long r) {
+  if (ep.on == ep.old) return r;
+  const long long q = r / ep.on;
+  return q * ep.old + (r - q * ep.on);
+}
+
 // The epilogue for one 16-column chunk of one accumulator row: data row r, output columns
 // jbase..jbase+15 (those below ep.n), accumulator values v[component][column].  Applies the
 // fused pointwise step, then stores the bf16 planes of the next pass or the final result
@@ -156,16 +178,16 @@ template <int NP, int NACC, bool PLANES_OUT>
 __device__ __forceinline__ void epi_chunk(const EpiParams& ep, const uint32_t (&v)[NACC][16], long long r, int jbase,
                                           float rowsum, float2 rowph, int& emx) {
   const int jn = ep.n - jbase < 16 ? ep.n - jbase : 16;
-  long long idx = r + ep.R * (long long)jbase;
+  long long idx = r + ep.Ro * (long long)jbase;  // r: the output row (mapped by the caller)
   double prev[16];
   if (!PLANES_OUT && ep.out_mode == 4) {
     // u += delta: issue all 16 loads of the chunk before any store, so they overlap
     const double* uo = reinterpret_cast<const double*>(ep.out);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) prev[i] = i < jn ? uo[idx + ep.R * (long long)i] : 0.0;
+    for (int i = 0; i < 16; ++i) prev[i] = i < jn ? uo[idx + ep.Ro * (long long)i] : 0.0;
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i, idx += ep.R) {
+  for (int i = 0; i < 16; ++i, idx += ep.Ro) {
     if (i >= jn) break;
     const int j = jbase + i;
     float val[NACC];
@@ -186,7 +208,7 @@ __device__ __forceinline__ void epi_chunk(const EpiParams& ep, const uint32_t (&
     if (PLANES_OUT) {
       __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out);
 #pragma unroll
-      for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.N, ep.N, idx);
+      for (int c = 0; c < NACC; ++c) split_store<NP>(val[c], o + (long long)c * NP * ep.No, ep.No, idx);
     } else if (ep.out_mode == 1) {
       const double o = f2d(val[0]);
       reinterpret_cast<double*>(ep.out)[idx] = o;
@@ -377,6 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       float rowsum = 0.f;
       float2 rowph = make_float2(1.f, 0.f);
       if (ep.scale_mode != 0 && row_ok) epi_row_factors(ep, r, &rowsum, &rowph);
+      const long long ro = row_ok ? epi_out_row(ep, r) : 0;
       const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
       for (int col0 = part * 16; col0 < BN; col0 += 16 * (EPI_WARPS / 4)) {
         uint32_t v[NACC][16];
@@ -384,7 +407,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
         tc::tmem_ld_wait();
         if (!row_ok) continue;
-        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, r, n0 + col0, rowsum, rowph, emx);
+        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, ro, n0 + col0, rowsum, rowph, emx);
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -566,6 +589,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rot_tc_list(const __grid_cons
       float rowsum = 0.f;
       float2 rowph = make_float2(1.f, 0.f);
       if (ep.scale_mode != 0 && row_ok) epi_row_factors(ep, r, &rowsum, &rowph);
+      const long long ro = row_ok ? epi_out_row(ep, r) : 0;
       const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
       for (int col0 = part * 16; col0 < BN; col0 += 16 * (EPI_WARPS / 4)) {
         uint32_t v[NACC][16];
@@ -573,7 +597,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rot_tc_list(const __grid_cons
         for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
         tc::tmem_ld_wait();
         if (!row_ok) continue;
-        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, r, n0 + col0, rowsum, rowph, emx);
+        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, ro, n0 + col0, rowsum, rowph, emx);
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -592,13 +616,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rot_tc_list(const __grid_cons
 
 // ------------------------------------------------------------ pointwise ----
 
-// FP64 / complex input -> planar bf16 planes [c][p][N]; x rounded to FP32 first (the
-// planes carry at most 24 bits), then split exactly in FP32.
+// FP64 / complex input -> planar bf16 planes [c][p][rows][ld0] (rows of axis 1, padded to
+// ld0 = n0 rounded up to a multiple of 8); x rounded to FP32 first (the planes carry at most
+// 24 bits), then split exactly in FP32.
 template <int NP, int MODE>  // MODE 0: real FP64, 1: complex128, 2: complex64
-__global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N) {
+__global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N, int n0) {
   const int NC = MODE == 0 ? 1 : 2;
+  const int ld0 = (n0 + 7) & ~7;                // padded row (axis 1) of the planes
+  const long long Np = (N / n0) * ld0;          // plane stride
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / n0;
+    const long long ip = row * ld0 + (i - row * n0);
     float v[2];
     if (MODE == 0) {
       v[0] = (float)reinterpret_cast<const double*>(in)[i];
@@ -611,7 +640,7 @@ __global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N
       v[0] = z.x;
       v[1] = z.y;
     }
-    for (int c = 0; c < NC; ++c) split_store<NP>(v[c], planes + (long long)c * NP * N, N, i);
+    for (int c = 0; c < NC; ++c) split_store<NP>(v[c], planes + (long long)c * NP * Np, Np, ip);
   }
 }
 
@@ -621,6 +650,7 @@ struct SplitItem {
   const void* in;
   __nv_bfloat16* planes;
   long long N;
+  int n0;    // extent of axis 1 (plane rows are padded to a multiple of 8)
   int mode;  // 0: real FP64, 1: complex128, 2: complex64
   int block_begin;
 };
@@ -636,8 +666,12 @@ __global__ void k_split_list(const __grid_constant__ SplitList L) {
   const SplitItem& I = L.item[cur];
   const int nb = (cur + 1 < L.count ? L.item[cur + 1].block_begin : (int)gridDim.x) - I.block_begin;
   const int nc = I.mode == 0 ? 1 : 2;
+  const int ld0 = (I.n0 + 7) & ~7;
+  const long long Np = (I.N / I.n0) * ld0;
   for (long long i = (long long)(blockIdx.x - I.block_begin) * blockDim.x + threadIdx.x; i < I.N;
        i += (long long)nb * blockDim.x) {
+    const long long row = i / I.n0;
+    const long long ip = row * ld0 + (i - row * I.n0);
     float v[2];
     if (I.mode == 0) {
       v[0] = (float)reinterpret_cast<const double*>(I.in)[i];
@@ -651,18 +685,26 @@ __global__ void k_split_list(const __grid_constant__ SplitList L) {
       v[0] = z.x;
       v[1] = z.y;
     }
-    for (int c = 0; c < nc; ++c) split_store<NP>(v[c], I.planes + (long long)c * NP * I.N, I.N, i);
+    for (int c = 0; c < nc; ++c) split_store<NP>(v[c], I.planes + (long long)c * NP * Np, Np, ip);
   }
 }
 
 // FP64 table -> NP bf16 planes (FP64 arithmetic; tables are tiny).
-__global__ void k_split_table(const double* src, __nv_bfloat16* dst, long long count, int np) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-       i += (long long)gridDim.x * blockDim.x) {
-    double x = src[i];
+// dst[p][j][i] = plane p of the split of src[i][j] (n x n): the transpose, so that the
+// contracted index of the operand is contiguous (K-major); rows of ld = n rounded up to a
+// multiple of 8 (16-byte TMA rows), planes n * ld apart.  The padding is left as it is
+// (the caller zeroes it; TMA never reads past column n of the declared extent anyway).
+__global__ void k_split_table_t(const double* src, __nv_bfloat16* dst, int n, int np) {
+  const long long count = (long long)n * n;
+  const int ld = (n + 7) & ~7;
+  const long long pstride = (long long)n * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e - i * n;
+    double x = src[e];
     for (int p = 0; p < np; ++p) {
       __nv_bfloat16 h = __double2bfloat16(x);
-      dst[p * count + i] = h;
+      dst[p * pstride + j * ld + i] = h;
       x -= (double)__bfloat162float(h);
     }
   }
@@ -695,9 +737,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 3D bf16 tensor map over planes [planes][rows][cols] (cols contiguous), box
+// 3D bf16 tensor map over planes [planes][rows][cols] (cols contiguous, rows of
+// ld = cols rounded up to a multiple of 8, planes ld * rows apart), box
 // {box_cols cols, box_rows rows, 1 plane}, swizzle = 2 * box_cols bytes (128 or 64),
-// zero fill out of bounds.
+// zero fill out of bounds (so a row's padding and the K tail read as zeros).
 ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long rows, int planes, int box_cols,
                    int box_rows) {
   auto enc = get_encode();
@@ -706,7 +749,8 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
     return TS_ERR_CUDA;
   }
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)(cols * 2), (cuuint64_t)(cols * rows * 2)};
+  const long long ld = (cols + 7) & ~7LL;
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(ld * rows * 2)};
   cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
@@ -755,6 +799,11 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   ep.R = R;
   ep.n = n;
   ep.N = R * n;
+  if (ep.Ro == 0) {  // unpadded output (callers set the layout of plane outputs)
+    ep.Ro = R;
+    ep.No = R * n;
+    ep.on = ep.old = 1;
+  }
   ep.bn = bn;
   ep.nstages = ns;
   static bool attr_set = false;  // per instantiation
@@ -908,17 +957,21 @@ ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(t->mu);
     if (!t->Bf[prec]) {
       const long long cnt = (long long)t->n * t->n;
+      const long long padded = (long long)t->n * ((t->n + 7) & ~7);  // rows padded to 16 bytes
       __nv_bfloat16 *bf = nullptr, *bb = nullptr;
-      TS_CHECK_CUDA(cudaMalloc(&bf, sizeof(__nv_bfloat16) * np * cnt));
-      TS_CHECK_CUDA(cudaMalloc(&bb, sizeof(__nv_bfloat16) * np * cnt));
-      // Forward operand B[j][i] = S[i][j] is the row-major S^T; backward B[i][j] = S[i][j].
-      k_split_table<<<grid_1d(cnt), 256, 0, s>>>(t->St, bf, cnt, np);
-      k_split_table<<<grid_1d(cnt), 256, 0, s>>>(t->S, bb, cnt, np);
+      TS_CHECK_CUDA(cudaMalloc(&bf, sizeof(__nv_bfloat16) * np * padded));
+      TS_CHECK_CUDA(cudaMalloc(&bb, sizeof(__nv_bfloat16) * np * padded));
+      TS_CHECK_CUDA(cudaMemsetAsync(bf, 0, sizeof(__nv_bfloat16) * np * padded, s));
+      TS_CHECK_CUDA(cudaMemsetAsync(bb, 0, sizeof(__nv_bfloat16) * np * padded, s));
+      // Forward: y_j = sum_i S[i][j] x_i, K-major operand B[j][i] = S[i][j]; backward:
+      // y_i = sum_j St[j][i] x_j, operand B[i][j] = St[j][i] (for orthogonal tables St = S^T).
+      k_split_table_t<<<grid_1d(cnt), 256, 0, s>>>(t->S, bf, t->n, np);
+      k_split_table_t<<<grid_1d(cnt), 256, 0, s>>>(t->St, bb, t->n, np);
       TS_LAUNCHED(2);
       TS_CHECK_CUDA(cudaStreamSynchronize(s));  // published to other plans only once complete
       t->Bf[prec] = bf;
       t->Bb[prec] = bb;
-      t->bytes += 2LL * np * cnt * (long long)sizeof(__nv_bfloat16);
+      t->bytes += 2LL * np * padded * (long long)sizeof(__nv_bfloat16);
     }
     p->Bf[prec][k] = t->Bf[prec];
     p->Bb[prec][k] = t->Bb[prec];
@@ -934,13 +987,29 @@ ts_status check_mixed(const ts_plan* p, ts_precision prec) {
     return TS_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < p->d; ++k) {
-    if (p->n[k] % 8 != 0 || p->N / p->n[k] >= (1LL << 31)) {
-      set_error("split-precision path needs every n_k to be a multiple of 8 and N/n_k < 2^31 (axis %d: n = %d)", k,
-                p->n[k]);
+    if (p->N / p->n[k] >= (1LL << 31)) {
+      set_error("split-precision path needs N/n_k < 2^31 (axis %d: n = %d)", k, p->n[k]);
       return TS_ERR_UNSUPPORTED;
     }
   }
   return TS_OK;
+}
+
+// Layout of a pass's plane output = the next pass's input (see EpiParams::on): rows of the
+// next contracted axis, padded to a multiple of 8 elements.
+void set_plane_output(EpiParams& ep, const ts_plan* p, int k) {
+  if (p->d == 1) {  // one row: output column j is element j of the next input row
+    ep.Ro = 1;
+    ep.No = (p->n[0] + 7) & ~7;
+    ep.on = ep.old = 1;
+    return;
+  }
+  const int kn = (k + 1) % p->d;
+  const long long R = p->N / p->n[k];
+  ep.on = p->n[kn];
+  ep.old = (p->n[kn] + 7) & ~7;
+  ep.Ro = (R / ep.on) * ep.old;
+  ep.No = (p->N / ep.on) * ep.old;
 }
 
 // The 2d contraction passes of one apply: planes in buf[0] -> ... -> `out` (out_mode of the
@@ -975,17 +1044,19 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
       ep.clam = p->lamf[k];
       ep.cph = tabsf ? tabsf + tab_off[k] : nullptr;
     }
+    if (!last) set_plane_output(ep, p, k);
     const __nv_bfloat16* B = fwd ? p->Bf[prec][k] : p->Bb[prec][k];
     st = pass(np, nc, buf[t & 1], B, p->N / p->n[k], p->n[k], ep, s);
   }
   return st;
 }
 
-ts_status split_input(int np, ts_dtype dt, const void* in, __nv_bfloat16* planes, long long N, cudaStream_t s) {
+ts_status split_input(int np, ts_dtype dt, const void* in, __nv_bfloat16* planes, long long N, int n0,
+                      cudaStream_t s) {
 #define TS_SPLIT(MODE)                                                   \
-  (np == 1   ? k_split_input<1, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N) \
-   : np == 2 ? k_split_input<2, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N) \
-             : k_split_input<3, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N))
+  (np == 1   ? k_split_input<1, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
+   : np == 2 ? k_split_input<2, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
+             : k_split_input<3, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0))
   if (dt == TS_R64)
     TS_SPLIT(0);
   else if (dt == TS_C128)
@@ -1005,7 +1076,7 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
   const int np = bf16_planes(prec);
   const int nc = op == MixedOp::Exp ? 2 : 1;
   const long long N = p->N;
-  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)nc * np * N;
+  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)nc * np * mixed_plane_elems(p);
   void *w0 = nullptr, *w1 = nullptr, *tabs = nullptr;
   TS_TRY(scratch_alloc(&w0, plane_bytes, s));
   ts_status st = scratch_alloc(&w1, plane_bytes, s);
@@ -1030,7 +1101,7 @@ ts_status mixed_apply(const ts_plan* p, ts_precision prec, MixedOp op, double pa
     }
   }
   __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
-  if (st == TS_OK) st = split_input(np, dt, in, buf[0], N, s);
+  if (st == TS_OK) st = split_input(np, dt, in, buf[0], N, p->n[0], s);
   if (st == TS_OK)
     st = run_passes(p, prec, op, param, buf, (const double2*)tabs,
                     tabs ? (const float2*)((const double2*)tabs + tab_total) : nullptr, tab_off, out,
@@ -1094,7 +1165,7 @@ ts_status mixed_apply_batch(const BatchApply* q, int count, cudaStream_t s) {
     w[i].np = bf16_planes(q[i].prec);
     w[i].nc = q[i].op == MixedOp::Exp ? 2 : 1;
     dmax = p->d > dmax ? p->d : dmax;
-    const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)w[i].nc * w[i].np * p->N;
+    const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)w[i].nc * w[i].np * mixed_plane_elems(p);
     for (int b = 0; b < 2 && st == TS_OK; ++b) st = scratch_alloc((void**)&w[i].buf[b], plane_bytes, s);
     if (st == TS_OK && q[i].op == MixedOp::Exp) {
       int tot = 0;
@@ -1131,6 +1202,7 @@ ts_status mixed_apply_batch(const BatchApply* q, int count, cudaStream_t s) {
         it.in = q[i].in;
         it.planes = w[i].buf[0];
         it.N = q[i].p->N;
+        it.n0 = q[i].p->n[0];
         it.mode = q[i].dt == TS_R64 ? 0 : (q[i].dt == TS_C128 ? 1 : 2);
         it.block_begin = blocks;
         long long nb = (it.N + 255) / 256;
@@ -1209,6 +1281,13 @@ ts_status mixed_apply_batch(const BatchApply* q, int count, cudaStream_t s) {
           ep.R = R;
           ep.n = n;
           ep.N = p->N;
+          if (last) {
+            ep.Ro = R;
+            ep.No = p->N;
+            ep.on = ep.old = 1;
+          } else {
+            set_plane_output(ep, p, k);
+          }
           ep.bn = bn;
           ep.nstages = ns;
           const __nv_bfloat16* B = fwd ? p->Bf[q[i].prec][k] : p->Bb[q[i].prec][k];
@@ -1237,7 +1316,7 @@ ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigm
                                 __nv_bfloat16* w0, __nv_bfloat16* w1, cudaStream_t s) {
   TS_TRY(check_mixed(p, prec));
   __nv_bfloat16* buf[2] = {w0, w1};
-  TS_TRY(split_input(bf16_planes(prec), TS_R64, b, buf[0], p->N, s));
+  TS_TRY(split_input(bf16_planes(prec), TS_R64, b, buf[0], p->N, p->n[0], s));
   return run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s);
 }
 
@@ -1257,7 +1336,7 @@ ts_status mixed_solve_schedule(const ts_plan* p, const ts_precision* sched, int 
   }
   const int refinements = count - 1;
   const long long N = p->N;
-  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)npmax * N;
+  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)npmax * mixed_plane_elems(p);
   void *w0 = nullptr, *w1 = nullptr, *partial = nullptr, *qtab = nullptr;
   TS_TRY(scratch_alloc(&w0, plane_bytes, s));
   ts_status st = scratch_alloc(&w1, plane_bytes, s);
@@ -1277,7 +1356,7 @@ ts_status mixed_solve_schedule(const ts_plan* p, const ts_precision* sched, int 
     return TS_OK;
   };
   // u_0 = P_0 b
-  if (st == TS_OK) st = split_input(bf16_planes(sched[0]), TS_R64, b, buf[0], N, s);
+  if (st == TS_OK) st = split_input(bf16_planes(sched[0]), TS_R64, b, buf[0], N, p->n[0], s);
   if (st == TS_OK && refinements > 0) st = zero_emax();
   if (st == TS_OK)
     st = run_passes(p, sched[0], MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s,

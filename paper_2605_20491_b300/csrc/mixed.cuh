@@ -8,6 +8,9 @@ enum class MixedOp { Inverse = 0, Exp = 1 };
 
 // Number of bf16 planes per value for a split precision (0 if not a bf16 split).
 int bf16_planes(ts_precision prec);
+// Elements of one bf16 plane of the split-precision passes: the grid with the contracted
+// (fastest) axis of each pass padded to a multiple of 8, maximised over the passes.
+long long mixed_plane_elems(const ts_plan* p);
 
 // Mixed-precision apply: op Inverse (real FP64 in/out, param = sigma) or Exp (complex
 // in/out of dtype dt, param = tau).
@@ -28,7 +31,7 @@ struct BatchApply {
 ts_status mixed_apply_batch(const BatchApply* q, int count, cudaStream_t s);
 
 // Split-precision inverse apply with caller-provided plane buffers w0, w1 of
-// bf16_planes(prec) * N bf16 each (no allocation).
+// bf16_planes(prec) * mixed_plane_elems(p) bf16 each (no allocation).
 ts_status mixed_inverse_buffers(const ts_plan* p, ts_precision prec, double sigma, const double* b, double* u,
                                 __nv_bfloat16* w0, __nv_bfloat16* w1, cudaStream_t s);
 

@@ -110,7 +110,7 @@ extern "C" ts_status ts_apply_inverse_noalloc(const ts_plan* plan, double sigma,
       set_error("precision %d was not requested in the plan's precision_mask", (int)prec);
       return TS_ERR_UNSUPPORTED;
     }
-    per_buffer = sizeof(__nv_bfloat16) * (size_t)np * (size_t)N;
+    per_buffer = sizeof(__nv_bfloat16) * (size_t)np * (size_t)mixed_plane_elems(plan);
   }
   per_buffer = (per_buffer + 255) & ~size_t(255);
   if (2 * per_buffer > NOALLOC_SCRATCH_BYTES) {

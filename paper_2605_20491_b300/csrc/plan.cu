@@ -2,9 +2,13 @@
 //
 // For the Q^1 discretisation the mass matrix is M_k = h_k I, so
 //     H_k = M_k^{-1} Stiff_k + F_k = h_k^{-2} tridiag(-1, 2, -1) + diag f_k(x_{k,i})
-// is symmetric and T_k = S_k is orthogonal (T_k^{-1} = S_k^T).  Each H_k is
-// eigendecomposed in FP64 on the GPU (cuSOLVER syevd: eigenvalues ascending,
-// eigenvectors as columns); the tables stay resident on the device for every later apply.
+// is symmetric and T_k = S_k is orthogonal (T_k^{-1} = S_k^T).  For Q^k, k >= 2, M_k is the
+// diagonal GLL mass and H_k is similar to the symmetric M^{-1/2} Stiff M^{-1/2} + F_k =
+// Q Lambda Q^T, so T_k = M^{-1/2} Q and T_k^{-1} = Q^T M^{1/2}; the diagonal factors are
+// folded into the contraction operands, so every apply kernel runs unchanged.  Each
+// symmetric matrix is eigendecomposed in FP64 on the GPU (cuSOLVER syevd: eigenvalues
+// ascending, eigenvectors as columns); the tables stay resident on the device for every
+// later apply.
 //
 // Axis tables are cached process-wide by (device, n, L, f): plans whose axes coincide
 // -- within one plan (isotropic grids) or across plans (a server's stream of requests on
@@ -19,6 +23,7 @@
 
 #include "common.cuh"
 #include "mixed.cuh"
+#include "sem_axis.cuh"
 #include "small_n.cuh"
 
 namespace ts {
@@ -115,9 +120,12 @@ struct AxisKey {
   int device, n;
   double L;
   std::vector<double> f;
+  int order, frame;
   bool operator<(const AxisKey& o) const {
     if (device != o.device) return device < o.device;
     if (n != o.n) return n < o.n;
+    if (order != o.order) return order < o.order;
+    if (frame != o.frame) return frame < o.frame;
     const int c = std::memcmp(&L, &o.L, sizeof(double));
     if (c != 0) return c < 0;
     return std::memcmp(f.data(), o.f.data(), sizeof(double) * f.size()) < 0;
@@ -139,23 +147,60 @@ ts_status build_axis(const AxisKey& key, cudaStream_t s, std::shared_ptr<AxisTab
   t->n = n;
   t->L = key.L;
   t->f = key.f;
-  const double h = 2.0 * key.L / (n + 1);
-  const double ih2 = 1.0 / (h * h);
+  t->order = key.order;
+  t->frame = key.frame;
+  const bool sem = key.order >= 2;
   std::vector<double> H((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) {
-    H[(size_t)i * n + i] = 2.0 * ih2 + key.f[i];
-    if (i > 0) H[(size_t)i * n + i - 1] = -ih2;
-    if (i + 1 < n) H[(size_t)i * n + i + 1] = -ih2;
+  SemAxis ax;
+  std::vector<double> rh(n, 1.0), rhi(n, 1.0);  // M^{1/2}, M^{-1/2} (Q^k only)
+  if (!sem) {
+    const double h = 2.0 * key.L / (n + 1);
+    const double ih2 = 1.0 / (h * h);
+    for (int i = 0; i < n; ++i) {
+      H[(size_t)i * n + i] = 2.0 * ih2 + key.f[i];
+      if (i > 0) H[(size_t)i * n + i - 1] = -ih2;
+      if (i + 1 < n) H[(size_t)i * n + i + 1] = -ih2;
+    }
+  } else {
+    TS_TRY(sem_axis_build(n, key.L, key.order, &ax));
+    for (int i = 0; i < n; ++i) {
+      rh[i] = std::sqrt(ax.m[i]);
+      rhi[i] = 1.0 / rh[i];
+    }
+    // M^{-1/2} Stiff M^{-1/2} + diag f; the assembled Stiff is symmetric, so is this
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        H[(size_t)i * n + j] = rhi[i] * ax.stiff[(size_t)i * n + j] * rhi[j] + (i == j ? key.f[i] : 0.0);
   }
   std::vector<double> Qcol;
   TS_TRY(eig_on_device(n, H, t->lam_host, Qcol, s));
-  // Qcol is column-major: Qcol[i + n j] = S[i][j], i.e. the row-major S^T.
+  // Qcol is column-major: Qcol[i + n j] = Q[i][j].  Forward operand S[i][j] = M^{1/2}_i Q[i][j],
+  // backward operand St[j][i] = Q[i][j] M^{-1/2}_i; in frame 1 (and for Q^1) Q and Q^T.
+  const bool fold = sem && key.frame == 0;
+  std::vector<double> Sh((size_t)n * n), Sth((size_t)n * n);
   t->S_host.resize((size_t)n * n);
   for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) t->S_host[(size_t)i * n + j] = Qcol[(size_t)i + (size_t)n * j];
+    for (int j = 0; j < n; ++j) {
+      const double q = Qcol[(size_t)i + (size_t)n * j];
+      Sh[(size_t)i * n + j] = fold ? rh[i] * q : q;
+      Sth[(size_t)j * n + i] = fold ? rhi[i] * q : q;
+      t->S_host[(size_t)i * n + j] = key.frame == 0 ? rhi[i] * q : q;
+    }
+  // Q^k: the band of K = M^{-1} Stiff (frame 0) or M^{-1/2} Stiff M^{-1/2} (frame 1)
+  const int bw = sem ? 2 * key.order + 1 : 0;
+  std::vector<double> band((size_t)n * bw, 0.0);
+  for (int i = 0; i < n && sem; ++i)
+    for (int o = 0; o < bw; ++o) {
+      const int j = i + o - key.order;
+      if (j < 0 || j >= n) continue;
+      const double a = ax.stiff[(size_t)i * n + j];
+      band[(size_t)i * bw + o] = key.frame == 0 ? a / ax.m[i] : rhi[i] * a * rhi[j];
+    }
   std::vector<float> lf(t->lam_host.begin(), t->lam_host.end());
   const size_t oS = 0, oSt = align256(oS + 8ull * n * n), oLam = align256(oSt + 8ull * n * n),
-               oF = align256(oLam + 8ull * n), oLf = align256(oF + 8ull * n), total = align256(oLf + 4ull * n);
+               oF = align256(oLam + 8ull * n), oLf = align256(oF + 8ull * n), oBand = align256(oLf + 4ull * n),
+               oMh = align256(oBand + 8ull * n * bw), oMhi = align256(oMh + (sem ? 8ull * n : 0)),
+               total = align256(oMhi + (sem ? 8ull * n : 0));
   TS_CHECK_CUDA(cudaMalloc(&t->block, total));
   t->bytes = (long long)total;
   char* b = (char*)t->block;
@@ -164,18 +209,27 @@ ts_status build_axis(const AxisKey& key, cudaStream_t s, std::shared_ptr<AxisTab
   t->lam = (double*)(b + oLam);
   t->fdev = (double*)(b + oF);
   t->lamf = (float*)(b + oLf);
-  TS_CHECK_CUDA(cudaMemcpyAsync(t->S, t->S_host.data(), 8ull * n * n, cudaMemcpyHostToDevice, s));
-  TS_CHECK_CUDA(cudaMemcpyAsync(t->St, Qcol.data(), 8ull * n * n, cudaMemcpyHostToDevice, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(t->S, Sh.data(), 8ull * n * n, cudaMemcpyHostToDevice, s));
+  TS_CHECK_CUDA(cudaMemcpyAsync(t->St, Sth.data(), 8ull * n * n, cudaMemcpyHostToDevice, s));
   TS_CHECK_CUDA(cudaMemcpyAsync(t->lam, t->lam_host.data(), 8ull * n, cudaMemcpyHostToDevice, s));
   TS_CHECK_CUDA(cudaMemcpyAsync(t->fdev, key.f.data(), 8ull * n, cudaMemcpyHostToDevice, s));
   TS_CHECK_CUDA(cudaMemcpyAsync(t->lamf, lf.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+  if (sem) {
+    t->band = (double*)(b + oBand);
+    t->mh = (double*)(b + oMh);
+    t->mhi = (double*)(b + oMhi);
+    TS_CHECK_CUDA(cudaMemcpyAsync(t->band, band.data(), 8ull * n * bw, cudaMemcpyHostToDevice, s));
+    TS_CHECK_CUDA(cudaMemcpyAsync(t->mh, rh.data(), 8ull * n, cudaMemcpyHostToDevice, s));
+    TS_CHECK_CUDA(cudaMemcpyAsync(t->mhi, rhi.data(), 8ull * n, cudaMemcpyHostToDevice, s));
+  }
   TS_CHECK_CUDA(cudaStreamSynchronize(s));  // host staging vectors go out of scope
   *out = t;
   return TS_OK;
 }
 
-ts_status get_axis(int device, int n, double L, const double* f, cudaStream_t s, std::shared_ptr<AxisTables>* out) {
-  AxisKey key{device, n, L, std::vector<double>(f, f + n)};
+ts_status get_axis(int device, int n, double L, const double* f, int order, int frame, cudaStream_t s,
+                   std::shared_ptr<AxisTables>* out) {
+  AxisKey key{device, n, L, std::vector<double>(f, f + n), order, frame};
   {
     std::lock_guard<std::mutex> lk(g_axis_mu);
     auto it = g_axis_map.find(key);
@@ -217,7 +271,26 @@ void axis_cache_counters(long long* hits, long long* builds) {
 
 void plan_free(ts_plan* p) { delete p; }
 
+namespace {
+ts_status plan_create_frame(const ts_plan_desc* desc, unsigned mask, int frame, cudaStream_t s, ts_plan** out);
+}
+
 ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, ts_plan** out) {
+  TS_TRY(plan_create_frame(desc, mask, 0, s, out));
+  if ((*out)->order >= 2) {  // the symmetric frame used by PCG and inverse iteration
+    const ts_status st = plan_create_frame(desc, mask, 1, s, &(*out)->sym);
+    if (st != TS_OK) {
+      plan_free(*out);
+      *out = nullptr;
+      return st;
+    }
+    (*out)->bytes += (*out)->sym->bytes;
+  }
+  return TS_OK;
+}
+
+namespace {
+ts_status plan_create_frame(const ts_plan_desc* desc, unsigned mask, int frame, cudaStream_t s, ts_plan** out) {
   ts_plan* p = new ts_plan();
   ts_status st = TS_OK;
   cudaError_t e = cudaGetDevice(&p->device);
@@ -228,6 +301,7 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
   p->d = desc->d;
   p->N = 1;
   p->precision_mask = mask | 1u;
+  p->order = desc->order >= 2 ? desc->order : 1;
   for (int k = 0; k < p->d; ++k) {
     p->n[k] = desc->n[k];
     p->L[k] = desc->L[k];
@@ -235,7 +309,7 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
     if (desc->n[k] > p->nmax) p->nmax = desc->n[k];
   }
   for (int k = 0; k < p->d && st == TS_OK; ++k) {
-    st = get_axis(p->device, p->n[k], p->L[k], desc->f[k], s, &p->axis[k]);
+    st = get_axis(p->device, p->n[k], p->L[k], desc->f[k], p->order, p->order >= 2 ? frame : 0, s, &p->axis[k]);
     if (st != TS_OK) break;
     AxisTables* t = p->axis[k].get();
     p->S[k] = t->S;
@@ -243,6 +317,9 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
     p->lam[k] = t->lam;
     p->lamf[k] = t->lamf;
     p->f[k] = t->fdev;
+    p->band[k] = t->band;
+    p->mh[k] = t->mh;
+    p->mhi[k] = t->mhi;
   }
   for (int q = 1; q < NPREC && st == TS_OK; ++q) {
     if (!(p->precision_mask & (1u << q))) continue;
@@ -261,5 +338,8 @@ ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, t
   *out = p;
   return TS_OK;
 }
+}  // namespace
 
 }  // namespace ts
+
+ts_plan::~ts_plan() { delete sym; }

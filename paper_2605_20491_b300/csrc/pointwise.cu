@@ -176,8 +176,8 @@ __global__ void k_stencil(AxisParams a, const double* __restrict__ V2, double si
         const double bi = b[idx];
         acc0 = fma(acc, acc, acc0);
         acc1 = fma(bi, bi, acc1);
-      } else {
-        split_store<NP>((float)acc, planes, N, idx);
+      } else {  // planes: rows of axis 1 padded to a multiple of 8
+        split_store<NP>((float)acc, planes, R * ((n0 + 7) & ~7), row * ((n0 + 7) & ~7) + i0);
       }
     }
   }
@@ -288,7 +288,7 @@ __global__ void k_residual_fixed(AxisParams a, double sigma, const double* __res
       }
       const double diag = drow + a.tab[0][i0];
       const double r = fma(-cs, __ll2double_rn(L), fma(-diag, xc, b[idx]));
-      split_store<NP>((float)r, planes, N, idx);
+      split_store<NP>((float)r, planes, R * ((n0 + 7) & ~7), row * ((n0 + 7) & ~7) + i0);
     }
   }
 }
@@ -417,9 +417,13 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
     cp_async_commit();  // an empty group past the end keeps the group count uniform
   };
   for (int k = 0; k < RD - 1; ++k) issue(z0 + k);
-  // output pointers of the two cells' plane-0 elements, advanced one plane per step
-  __nv_bfloat16* pa = planes + (va ? oa + (long long)z0 * s2 : 0);
-  __nv_bfloat16* pb = planes + (vb ? ob + (long long)z0 * s2 : 0);
+  // output pointers of the two cells' plane-0 elements, advanced one z-slab per step; the
+  // planes' rows (axis 1) are padded to ld0 elements, a multiple of 8
+  const int ld0 = (n0 + 7) & ~7;
+  const long long ps2 = (long long)ld0 * n1;
+  const long long Np = ps2 * n2;
+  __nv_bfloat16* pa = planes + (va ? (long long)ia * ld0 + i0 + (long long)z0 * ps2 : 0);
+  __nv_bfloat16* pb = planes + (vb ? (long long)ib * ld0 + i0 + (long long)z0 * ps2 : 0);
   auto ld = [&](bool v, const double* base, long long off, int z) -> double {
     return v ? base[off + z * s2] : 0.0;
   };
@@ -465,25 +469,25 @@ __global__ void __launch_bounds__(256) k_residual_march3(AxisParams a, double si
       const long long qz = q2[z];
       if (va) {
         const double r = fma(-cs, __ll2double_rn(La + mul_shift(qa + qz, Uca, F)), b_a);
-        split_store<NP>(f64_to_f32(r), pa, N, 0);
+        split_store<NP>(f64_to_f32(r), pa, Np, 0);
       }
       if (vb) {
         const double r = fma(-cs, __ll2double_rn(Lb + mul_shift(qb + qz, Ucb, F)), b_b);
-        split_store<NP>(f64_to_f32(r), pb, N, 0);
+        split_store<NP>(f64_to_f32(r), pb, Np, 0);
       }
     } else {
       const double fz = f2[z];
       if (va) {
         const double r = fma(-cs, i64_to_f64(La), fma(-(ca + fz), xa, b_a));
-        split_store<NP>(f64_to_f32(r), pa, N, 0);
+        split_store<NP>(f64_to_f32(r), pa, Np, 0);
       }
       if (vb) {
         const double r = fma(-cs, i64_to_f64(Lb), fma(-(cb + fz), xb, b_b));
-        split_store<NP>(f64_to_f32(r), pb, N, 0);
+        split_store<NP>(f64_to_f32(r), pb, Np, 0);
       }
     }
-    pa += sa_step;
-    pb += sb_step;
+    pa += va ? ps2 : 0;
+    pb += vb ? ps2 : 0;
     sU[buf ^ 1][ly + 1][lx + 1] = Una;
     sU[buf ^ 1][ly + 9][lx + 1] = Unb;
     if (ly < 3) sU[buf ^ 1][hy][hx] = Unh;
@@ -607,6 +611,104 @@ __global__ void k_scale_by_scalar(const double* num, const double* den, double* 
     y[i] = x[i] * f;
 }
 
+// Per-axis band tables of a Q^k plan (k >= 2), by value.
+struct BandParams {
+  int d, w;                   // dimension, half bandwidth (= k)
+  int n[MAXD];
+  long long stride[MAXD];
+  const double* band[MAXD];   // n[k] rows of 2w + 1: band[i][o] = K[i][i + o - w]
+  const double* f[MAXD];      // V1 samples
+};
+
+// The Q^k operator of eq. general_system, A x = sum_k K_k x (along axis k) + (sigma + V1 + V2) x,
+// with K_k banded (half bandwidth w = k; M^{-1} Stiff, or M^{-1/2} Stiff M^{-1/2} in the
+// symmetric frame), in the three forms of k_stencil (MODE 0: y = A x and x.y; MODE 1:
+// y = b - A x, y.y and b.b; MODE 2: split(b - A x) into bf16 planes).  Same mapping as
+// k_stencil: G lanes walk one grid row (axis 1) with unit stride, the multi-index of the row
+// is decomposed once per row and the band rows of the other axes are the same for the whole
+// row.  d (2w + 1) FP64 multiply-adds per point.
+template <int MODE, int NP>
+__global__ void k_banded(BandParams a, const double* __restrict__ V2, double sigma, const double* __restrict__ x,
+                         const double* __restrict__ b, double* __restrict__ y, __nv_bfloat16* __restrict__ planes,
+                         long long N, double* partial) {
+  const int n0 = a.n[0], w = a.w, bw = 2 * a.w + 1;
+  int G = 1;
+  while (G < n0 && G < 32) G <<= 1;
+  const int rows_per_warp = 32 / G;
+  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
+  const long long R = N / n0;
+  const long long warps_total = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  double acc0 = 0.0, acc1 = 0.0;
+  for (long long rb = wid * rows_per_warp; rb < R; rb += warps_total * rows_per_warp) {
+    const long long row = rb + sub;
+    if (row >= R) continue;
+    long long q = row;
+    double drow = sigma;
+    int ik[MAXD];
+    for (int k = 1; k < a.d; ++k) {
+      const long long qq = q / a.n[k];
+      ik[k] = (int)(q - qq * a.n[k]);
+      q = qq;
+      drow += a.f[k][ik[k]];
+    }
+    const long long base = row * n0;
+    for (int i0 = gl; i0 < n0; i0 += G) {
+      const long long idx = base + i0;
+      double diag = drow + a.f[0][i0];
+      if (V2) diag += V2[idx];
+      double ax = diag * x[idx];
+      {
+        const double* B = a.band[0] + (long long)i0 * bw;
+        const int lo = i0 - w < 0 ? w - i0 : 0, hi = i0 + w >= n0 ? w + n0 - 1 - i0 : 2 * w;
+        for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + o - w], ax);
+      }
+      for (int k = 1; k < a.d; ++k) {
+        const double* B = a.band[k] + (long long)ik[k] * bw;
+        const int lo = ik[k] - w < 0 ? w - ik[k] : 0, hi = ik[k] + w >= a.n[k] ? w + a.n[k] - 1 - ik[k] : 2 * w;
+        const long long st = a.stride[k];
+        for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + (o - w) * st], ax);
+      }
+      if (MODE == 0) {
+        y[idx] = ax;
+        acc0 = fma(x[idx], ax, acc0);
+      } else {
+        const double bi = b[idx];
+        const double r = bi - ax;
+        if (MODE == 1) {
+          y[idx] = r;
+          acc0 = fma(r, r, acc0);
+          acc1 = fma(bi, bi, acc1);
+        } else {  // planes: rows of axis 1 padded to a multiple of 8
+          split_store<NP>((float)r, planes, R * ((n0 + 7) & ~7), row * ((n0 + 7) & ~7) + i0);
+        }
+      }
+    }
+  }
+  if (MODE == 2) return;
+  double s0 = block_sum(acc0);
+  double s1 = block_sum(acc1);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// y = x * prod_k tab_k[i_k] (a separable diagonal, e.g. M^{1/2} or M^{-1/2}); x and y may alias.
+__global__ void k_scale_separable(AxisParams a, const double* x, double* y, long long N) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long q = idx;
+    double s = 1.0;
+    for (int k = 0; k < a.d; ++k) {
+      const long long qq = q / a.n[k];
+      s *= a.tab[k][(int)(q - qq * a.n[k])];
+      q = qq;
+    }
+    y[idx] = x[idx] * s;
+  }
+}
+
 }  // namespace
 
 int red_blocks() { return RED_BLOCKS; }
@@ -652,9 +754,37 @@ ts_status convert_c128_to_c64(long long N, const double* in, float* out, cudaStr
   return TS_OK;
 }
 
+namespace {
+BandParams band_params(const ts_plan* p) {
+  BandParams a{};
+  a.d = p->d;
+  a.w = p->order;
+  long long st = 1;
+  for (int k = 0; k < p->d; ++k) {
+    a.n[k] = p->n[k];
+    a.stride[k] = st;
+    st *= p->n[k];
+    a.band[k] = p->band[k];
+    a.f[k] = p->f[k];
+  }
+  return a;
+}
+}  // namespace
+
+ts_status scale_separable(const ts_plan* p, bool inverse, const double* x, double* y, cudaStream_t s) {
+  AxisParams a = axis_params(p, false);
+  for (int k = 0; k < p->d; ++k) a.tab[k] = inverse ? p->mhi[k] : p->mh[k];
+  k_scale_separable<<<grid_for(p->N), 256, 0, s>>>(a, x, y, p->N);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
 ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
                         double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
+  if (p->order >= 2)
+    k_banded<0, 2><<<g, 256, 0, s>>>(band_params(p), V2, sigma, x, nullptr, y, nullptr, p->N, partial);
+  else
   k_stencil<0, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, nullptr, y, nullptr, p->N, partial);
   TS_LAUNCHED(1);
   if (out2) {
@@ -667,7 +797,10 @@ ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const 
 ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, const double* x, const double* b,
                            double* r, double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  k_stencil<1, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, r, nullptr, p->N, partial);
+  if (p->order >= 2)
+    k_banded<1, 2><<<g, 256, 0, s>>>(band_params(p), V2, sigma, x, b, r, nullptr, p->N, partial);
+  else
+    k_stencil<1, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, r, nullptr, p->N, partial);
   TS_LAUNCHED(1);
   k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
   TS_LAUNCHED(1);
@@ -677,7 +810,15 @@ ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, con
 ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigma, const double* x,
                                  const double* b, __nv_bfloat16* planes, int np, double* partial, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  if (np == 1)
+  if (p->order >= 2) {
+    const BandParams a = band_params(p);
+    if (np == 1)
+      k_banded<2, 1><<<g, 256, 0, s>>>(a, V2, sigma, x, b, nullptr, planes, p->N, partial);
+    else if (np == 2)
+      k_banded<2, 2><<<g, 256, 0, s>>>(a, V2, sigma, x, b, nullptr, planes, p->N, partial);
+    else
+      k_banded<2, 3><<<g, 256, 0, s>>>(a, V2, sigma, x, b, nullptr, planes, p->N, partial);
+  } else if (np == 1)
     k_stencil<2, 1><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
   else if (np == 2)
     k_stencil<2, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, nullptr, planes, p->N, partial);
@@ -688,6 +829,7 @@ ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigm
 }
 
 bool isotropic_h(const ts_plan* p) {
+  if (p->order >= 2) return false;  // Q^k nodes are not equally spaced
   for (int k = 1; k < p->d; ++k)
     if (2.0 * p->L[k] / (p->n[k] + 1) != 2.0 * p->L[0] / (p->n[0] + 1)) return false;
   return true;

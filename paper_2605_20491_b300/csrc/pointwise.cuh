@@ -18,7 +18,11 @@ ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, con
 // planes (np bf16 planes of N values) = split(b - (A + V2 + sigma) x); partial sums only.
 ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigma, const double* x,
                                  const double* b, __nv_bfloat16* planes, int np, double* partial, cudaStream_t s);
-// True when every axis has the same grid spacing h.
+// Q^k plans (k >= 2): the three functions above evaluate the banded operator
+// sum_k K_k + V1 + V2 + sigma of the plan's frame instead of the stencil.
+// y = x * prod_k M_k^{1/2} (inverse: M_k^{-1/2}) for a Q^k plan; x and y may alias.
+ts_status scale_separable(const ts_plan* p, bool inverse, const double* x, double* y, cudaStream_t s);
+// True when every axis has the same grid spacing h (never for Q^k, k >= 2).
 bool isotropic_h(const ts_plan* p);
 // As stencil_residual_split without V2, for isotropic grids: the Laplacian part in exact
 // 64-bit fixed point, scaled by *emax_dev, which must hold the largest biased exponent of

@@ -45,11 +45,13 @@ using Clock = std::chrono::steady_clock;
 
 struct PlanKey {
   int d;
+  int order = 1;          // the k of Q^k
   std::vector<int> n;
   std::vector<double> L;
   std::vector<double> f;  // all axes' samples concatenated
   bool operator<(const PlanKey& o) const {
     if (d != o.d) return d < o.d;
+    if (order != o.order) return order < o.order;
     if (n != o.n) return n < o.n;
     if (L != o.L) return L < o.L;
     return std::lexicographical_compare(f.begin(), f.end(), o.f.begin(), o.f.end(), [](double a, double b) {
@@ -81,14 +83,16 @@ struct Job {
   char msg[256] = "";
 };
 
-size_t footprint_of(const ts_request& r, long long N) {
+// Np: elements of one bf16 plane (the grid with each pass's contracted axis padded to a
+// multiple of 8, maximised over the passes).
+size_t footprint_of(const ts_request& r, long long N, long long Np) {
   const int np = bf16_planes(r.prec);
   size_t apply_scratch;
   if (r.kind == TS_REQ_EXP) {
-    apply_scratch = np ? 2 * (size_t)2 * np * N * 2 : 2 * (size_t)2 * N * 8;
+    apply_scratch = np ? 2 * (size_t)2 * np * Np * 2 : 2 * (size_t)2 * N * 8;
     if (np == 0 && r.dtype == TS_C64) apply_scratch += (size_t)2 * N * 8;
   } else {
-    apply_scratch = np ? 2 * (size_t)np * N * 2 : 2 * (size_t)N * 8;
+    apply_scratch = np ? 2 * (size_t)np * Np * 2 : 2 * (size_t)N * 8;
   }
   if (r.kind == TS_REQ_PCG) apply_scratch += (size_t)4 * N * 8 + 16 * 1024;
   return apply_scratch + (1 << 20);
@@ -233,7 +237,7 @@ void run_pcg(ts_server* sv, std::shared_ptr<Job> jp) {
   cudaSetDevice(sv->device);
   const ts_request& r = j.req;
   int it = 0;
-  ts_status st = pcg_impl(j.plan, r.sigma, r.sigma, r.V2, (const double*)r.in, (double*)r.out, r.tol, r.maxit,
+  ts_status st = pcg_solve(j.plan, r.sigma, r.sigma, r.V2, (const double*)r.in, (double*)r.out, r.tol, r.maxit,
                           r.prec, &it, nullptr, sv->streams[j.stream_slot]);
   if (st != TS_OK) snprintf(j.msg, sizeof(j.msg), "%s", ts_last_error());
   std::lock_guard<std::mutex> lk(sv->mu);
@@ -430,6 +434,8 @@ ts_status ts_server_submit(ts_server* sv, const ts_request* r, long long* ticket
   auto jp = std::make_shared<Job>();
   jp->req = *r;
   jp->key.d = r->grid.d;
+  TS_REQUIRE(r->grid.order >= 0 && r->grid.order <= 32, "bad order %d", r->grid.order);
+  jp->key.order = r->grid.order >= 2 ? r->grid.order : 1;
   long long N = 1;
   for (int k = 0; k < r->grid.d; ++k) {
     TS_REQUIRE(r->grid.n[k] >= 1 && r->grid.n[k] <= 4096 && r->grid.L[k] > 0 && r->grid.f[k], "bad axis %d", k);
@@ -442,7 +448,12 @@ ts_status ts_server_submit(ts_server* sv, const ts_request* r, long long* ticket
   jp->req.grid.n = nullptr;  // the job keeps its own copies
   jp->req.grid.L = nullptr;
   jp->req.grid.f = nullptr;
-  jp->footprint = footprint_of(*r, N);
+  long long Np = 0;
+  for (int k = 0; k < r->grid.d; ++k) {
+    const long long e = (N / r->grid.n[k]) * ((r->grid.n[k] + 7) & ~7);
+    Np = e > Np ? e : Np;
+  }
+  jp->footprint = footprint_of(*r, N, Np);
   jp->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);

@@ -241,6 +241,37 @@ ts_status inverse_iteration_impl(const ts_plan* p, double shift, const double* V
   return TS_OK;
 }
 
+ts_status pcg_solve(const ts_plan* p, double sigma, double sigma_P, const double* V2, const double* b, double* x,
+                    double tol, int maxit, ts_precision prec, int* iters_out, double* relres_out, cudaStream_t s) {
+  if (!p->sym) return pcg_impl(p, sigma, sigma_P, V2, b, x, tol, maxit, prec, iters_out, relres_out, s);
+  // (M^{1/2} A M^{-1/2}) (M^{1/2} x) = M^{1/2} b; V2, V1 and sigma are diagonal and commute with M
+  Scratch sc_mem(s);
+  double* bt = nullptr;
+  TS_TRY(sc_mem.get(&bt, p->N));
+  TS_TRY(scale_separable(p, false, b, bt, s));
+  TS_TRY(scale_separable(p, false, x, x, s));
+  const ts_status st = pcg_impl(p->sym, sigma, sigma_P, V2, bt, x, tol, maxit, prec, iters_out, relres_out, s);
+  const ts_status st2 = scale_separable(p, true, x, x, s);  // the iterate, also when not converged
+  return st != TS_OK ? st : st2;
+}
+
+ts_status inverse_iteration_solve(const ts_plan* p, double shift, const double* V2, double* u, int init_from_plan,
+                                  double tol_lambda, int maxit, double pcg_tol, int pcg_maxit, ts_precision prec,
+                                  double* lambda_out, int* outer_out, long long* pcg_out, cudaStream_t s) {
+  if (!p->sym)
+    return inverse_iteration_impl(p, shift, V2, u, init_from_plan, tol_lambda, maxit, pcg_tol, pcg_maxit, prec,
+                                  lambda_out, outer_out, pcg_out, s);
+  if (!init_from_plan) TS_TRY(scale_separable(p, false, u, u, s));
+  const ts_status st = inverse_iteration_impl(p->sym, shift, V2, u, init_from_plan, tol_lambda, maxit, pcg_tol,
+                                              pcg_maxit, prec, lambda_out, outer_out, pcg_out, s);
+  const ts_status st2 = scale_separable(p, true, u, u, s);
+  if (st2 == TS_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("stream synchronisation failed");
+    return TS_ERR_CUDA;
+  }
+  return st != TS_OK ? st : st2;
+}
+
 ts_status split_step_impl(const ts_plan* p, double dt, int nsteps, const double* V2, void* psi, ts_dtype dtype,
                           ts_precision prec, cudaStream_t s) {
   if (nsteps <= 0) return TS_OK;

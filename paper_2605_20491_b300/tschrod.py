@@ -27,7 +27,7 @@ TS_MAX_DIM = 12
 
 #: Every extern "C" symbol that include/tschrod.h declares.
 EXPORTS = [
-    "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
+    "ts_grid_nodes", "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
     "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_solve_schedule", "ts_apply_batch", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
@@ -44,7 +44,7 @@ class TsError(RuntimeError):
 
 class _Desc(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.POINTER(C.c_int)), ("L", C.POINTER(C.c_double)),
-                ("f", C.POINTER(C.POINTER(C.c_double))), ("bc", C.c_int)]
+                ("f", C.POINTER(C.POINTER(C.c_double))), ("bc", C.c_int), ("order", C.c_int)]
 
 
 class _Request(C.Structure):
@@ -180,13 +180,24 @@ class Plan:
             pass
 
 
-def ts_plan_create(n, L, f, precision_mask: int = 0, stream=None, bc: int = 0) -> Plan:
+def ts_grid_nodes(n: int, L: float, order: int = 1):
+    """Interior nodes and lumped masses of one axis: (x, m), n doubles each (host)."""
+    x, m = np.empty(int(n)), np.empty(int(n))
+    _check(lib().ts_grid_nodes(C.c_int(int(n)), C.c_double(float(L)), C.c_int(int(order)),
+                               x.ctypes.data_as(C.POINTER(C.c_double)), m.ctypes.data_as(C.POINTER(C.c_double))),
+           "ts_grid_nodes")
+    return x, m
+
+
+def ts_plan_create(n, L, f, precision_mask: int = 0, stream=None, bc: int = 0, order: int = 1) -> Plan:
+    """order = k of Q^k (1: finite differences on uniform nodes; >= 2: spectral elements,
+    f sampled at ts_grid_nodes(n_k, L_k, order))."""
     d = len(n)
     f_arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in f]
     n_arr = (C.c_int * d)(*[int(v) for v in n])
     L_arr = (C.c_double * d)(*[float(v) for v in L])
     f_ptrs = (C.POINTER(C.c_double) * d)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in f_arrs])
-    desc = _Desc(d, n_arr, L_arr, f_ptrs, bc)
+    desc = _Desc(d, n_arr, L_arr, f_ptrs, bc, order)
     out = C.c_void_p()
     _check(lib().ts_plan_create(C.byref(desc), precision_mask, _stream(stream), C.byref(out)), "ts_plan_create")
     return Plan(out.value, n, L)
@@ -342,13 +353,13 @@ class Server:
         self._keep = {}
 
     def submit(self, kind: int, n, L, f, inp, out, sigma: float = 0.0, tau: float = 0.0, V2=None, tol: float = 1e-10,
-               maxit: int = 200, dtype: int = TS_R64, prec: int = TS_FP64) -> int:
+               maxit: int = 200, dtype: int = TS_R64, prec: int = TS_FP64, order: int = 1) -> int:
         d = len(n)
         f_arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in f]
         n_arr = (C.c_int * d)(*[int(v) for v in n])
         L_arr = (C.c_double * d)(*[float(v) for v in L])
         f_ptrs = (C.POINTER(C.c_double) * d)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in f_arrs])
-        req = _Request(kind, _Desc(d, n_arr, L_arr, f_ptrs, 0), sigma, tau, _ptr(V2), tol, maxit, _ptr(inp),
+        req = _Request(kind, _Desc(d, n_arr, L_arr, f_ptrs, 0, order), sigma, tau, _ptr(V2), tol, maxit, _ptr(inp),
                        _ptr(out), dtype, prec)
         ticket = C.c_longlong()
         _check(lib().ts_server_submit(self.handle, C.byref(req), C.byref(ticket)), "ts_server_submit")

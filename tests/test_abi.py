@@ -58,8 +58,30 @@ def test_invalid_arguments_rejected_on_host(built_lib):
     assert L.ts_plan_create(None, 0, None, C.byref(out)) == T.TS_ERR_INVALID_ARG
     assert "NULL" in T.ts_last_error()
     d = 13
-    desc = T._Desc(d, (C.c_int * d)(*([4] * d)), (C.c_double * d)(*([1.0] * d)), None, 0)
+    desc = T._Desc(d, (C.c_int * d)(*([4] * d)), (C.c_double * d)(*([1.0] * d)), None, 0, 1)
     assert L.ts_plan_create(C.byref(desc), 0, None, C.byref(out)) == T.TS_ERR_INVALID_ARG
     assert out.value is None
     assert L.ts_apply_inverse(None, 1.0, None, None, 0, None) == T.TS_ERR_INVALID_ARG
     assert L.ts_plan_destroy(None) == T.TS_OK
+
+
+def test_grid_nodes_on_host_match_the_oracle(built_lib):
+    """ts_grid_nodes needs no GPU: its GLL nodes and lumped masses (Newton on the Legendre
+    recurrence, barycentric derivative matrix) against the numpy oracle (Legendre roots,
+    Legendre Vandermonde); invalid Q^k grids are rejected."""
+    import ctypes as C
+    import numpy as np
+    from oracle import sem
+    from paper_2605_20491_b300 import tschrod as T
+    for n, L, k in ((99, 8.0, 20), (1099, 1.0, 2), (599, 8.0, 10), (31, 2.0, 32), (37, 3.5, 1), (37, 3.5, 0)):
+        x, m = T.ts_grid_nodes(n, L, k)
+        ax = sem.axis_1d(n, L, max(k, 1))
+        assert np.max(np.abs(x - ax.x)) < 1e-14 * L
+        assert np.max(np.abs(m / ax.m - 1)) < 1e-13
+    with pytest.raises(T.TsError):
+        T.ts_grid_nodes(100, 1.0, 3)
+    f = (C.POINTER(C.c_double) * 1)((C.c_double * 100)())
+    desc = T._Desc(1, (C.c_int * 1)(100), (C.c_double * 1)(1.0), f, 0, 3)
+    out = C.c_void_p()
+    assert T.lib().ts_plan_create(C.byref(desc), 0, None, C.byref(out)) == T.TS_ERR_INVALID_ARG
+    assert "multiple of 3" in T.ts_last_error()

@@ -169,7 +169,7 @@ def test_pcg_fixed_point_operator_vs_oracle(T, n):
     V2 = S.v2_cos_bumps(n, L, seed=1) + 5.0
     b = S.uniform(0, Po.N)
     xo, ito, _ = O.pcg(Po, b, sigma=0.3, V2=V2, tol=1e-12)
-    for prec in (T.TS_FP64, T.TS_BF16X3) if all(k % 8 == 0 for k in n) else (T.TS_FP64,):
+    for prec in (T.TS_FP64, T.TS_BF16X3):
         x = dev(np.zeros(Po.N))
         st, it, relres = T.ts_pcg(P, 0.3, 0.3, dev(V2), dev(b), x, 1e-12, 200, prec)
         assert relres < 1e-11

@@ -67,11 +67,7 @@ def test_exp_mixed_vs_oracle(T, n, prec, dtype):
 def test_mixed_rejects_unsupported(T):
     n = (12, 16)
     L, f = harmonic_case(n)
-    P, _ = plans(n, L, f, MASK)
-    b = dev(np.ones(P.N))
-    with pytest.raises(T.TsError) as e:
-        T.ts_apply_inverse(P, 1.0, b, b, T.TS_BF16X3)
-    assert e.value.status == T.TS_ERR_UNSUPPORTED
+    b = dev(np.ones(12 * 16))
     P2, _ = plans((16, 16), L, [f[1], f[1]], 0)
     with pytest.raises(T.TsError) as e:
         T.ts_apply_inverse(P2, 1.0, b[:256], b[:256], T.TS_BF16X3)
@@ -303,7 +299,7 @@ def test_apply_batch_equals_single_calls(T):
         else:
             dt = T.TS_C128 if kind == "c128" else T.TS_C64
             z = S.complex_normal(10 + q, Po.N)
-            x = dev(z) if kind == "c128" else dev(z.astype(np.complex64).view(np.float32))
+            x = dev(z) if kind == "c128" else dev(z.astype(np.float32))
             out = torch.zeros_like(x)
             ref = torch.zeros_like(x)
             T.ts_apply_exp(P, 0.01, x, ref, dt, prec)
@@ -327,3 +323,96 @@ def test_apply_batch_rejects_bad_items(T):
     for bad in [(P, T.TS_R64, T.TS_FP64, 0.5, x, y), (P, T.TS_R64, T.TS_BF16X1, 0.5, x, y), (P, 7, T.TS_BF16X3, 0.5, x, y)]:
         with pytest.raises(T.TsError):
             T.ts_apply_batch([(P, T.TS_R64, T.TS_BF16X3, 0.5, x, y), bad])
+
+
+# Any n: the planes and tables store each pass's contracted axis in rows padded to a
+# multiple of 8 (16-byte TMA rows); the writers of every plane (input split, pass
+# epilogues, the three residual kernels) and the final unpadded FP64 / complex stores.
+RAGGED = [(12, 16), (33, 9, 21), (99,), (5, 7, 3, 9), (100, 37, 51), (1, 17, 3), (129, 65)]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n", RAGGED)
+def test_inverse_any_n_vs_oracle(T, n, prec):
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)
+    b = S.normal(2, Po.N)
+    u = dev(np.zeros(Po.N))
+    T.ts_apply_inverse(P, 0.5, dev(b), u, prec)
+    T.ts_device_status()
+    assert rel(host(u), O.apply_inverse(Po, 0.5, b)) < TOL[prec]
+
+
+@pytest.mark.parametrize("n", [(33, 9, 21), (5, 7, 3, 9), (99,)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_exp_any_n_vs_oracle(T, n, dtype):
+    L, f = harmonic_case(n, L=4.0)
+    P, Po = plans(n, L, f, MASK)
+    psi = S.complex_normal(3, Po.N)
+    if dtype == "c128":
+        out = dev(np.zeros(2 * Po.N))
+        T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C128, T.TS_BF16X3)
+    else:
+        out = dev(np.zeros(2 * Po.N, dtype=np.float32))
+        T.ts_apply_exp(P, 0.01, dev(psi.astype(np.float32)), out, T.TS_C64, T.TS_BF16X3)
+    T.ts_device_status()
+    got = host(out).astype(np.float64)
+    assert rel(got, O.apply_exp(Po, 0.01, psi).view(np.float64)) < max(TOL[1], 1e-6)
+
+
+@pytest.mark.parametrize("n,iso", [((33, 33, 33), True), ((41, 19, 27), True), ((33, 9, 21), False),
+                                   ((5, 7, 3, 9), False), ((99, 45), True)])
+def test_refined_any_n_reaches_fp64(T, n, iso):
+    """Refinements with residuals split into padded planes: the exact fixed-point kernels
+    (equal spacing; d = 3 uses the marching form) and the FP64 stencil (unequal spacing)."""
+    L = tuple((k + 1) / 4.0 for k in n) if iso else tuple(1.0 + 0.5 * a for a in range(len(n)))
+    f = S.harmonic(n, L, tuple(1.0 + 0.2 * k for k in range(len(n))))
+    P, Po = plans(n, L, f, MASK | (1 << 6))
+    b = S.normal(6, Po.N)
+    want = O.apply_inverse(Po, 0.25, b)
+    u = dev(np.zeros(Po.N))
+    T.ts_solve_refined(P, 0.25, dev(b), u, T.TS_BF16X3, 2)
+    assert rel(host(u), want) < 1e-12
+    T.ts_solve_schedule(P, 0.25, dev(b), u, [T.TS_BF16X3, T.TS_BF16X3, T.TS_BF16X1])
+    assert rel(host(u), want) < 1e-10
+
+
+def test_apply_batch_any_n(T):
+    """Work-list passes over grids of unrelated ragged shapes equal their single calls."""
+    import torch
+    cases = [((33, 9, 21), "inv", T.TS_BF16X3), ((5, 7, 3, 9), "c128", T.TS_BF16X3), ((99,), "inv", T.TS_BF16X6),
+             ((12, 16), "c64", T.TS_BF16X3), ((40, 24, 8), "inv", T.TS_BF16X3)]
+    items, refs = [], []
+    for q, (n, kind, prec) in enumerate(cases):
+        L, f = harmonic_case(n)
+        P, Po = plans(n, L, f, MASK)
+        if kind == "inv":
+            x = dev(S.normal(20 + q, Po.N))
+            out, ref = dev(np.zeros(Po.N)), dev(np.zeros(Po.N))
+            T.ts_apply_inverse(P, 0.5, x, ref, prec)
+            items.append((P, T.TS_R64, prec, 0.5, x, out))
+        else:
+            dt = T.TS_C128 if kind == "c128" else T.TS_C64
+            z = S.complex_normal(20 + q, Po.N)  # interleaved (re, im)
+            x = dev(z) if kind == "c128" else dev(z.astype(np.float32))
+            out, ref = torch.zeros_like(x), torch.zeros_like(x)
+            T.ts_apply_exp(P, 0.01, x, ref, dt, prec)
+            items.append((P, dt, prec, 0.01, x, out))
+        refs.append(ref)
+    T.ts_apply_batch(items)
+    T.ts_device_status()
+    for it, ref in zip(items, refs):
+        assert np.array_equal(host(it[5]), host(ref))
+
+
+def test_noalloc_any_n(T):
+    n = (33, 9, 21)
+    L, f = harmonic_case(n)
+    P, Po = plans(n, L, f, MASK)
+    b = S.normal(7, Po.N)
+    u = dev(np.zeros(Po.N))
+    T.ts_apply_inverse_noalloc(P, 0.5, dev(b), u, T.TS_BF16X3)
+    u2 = dev(np.zeros(Po.N))
+    T.ts_apply_inverse(P, 0.5, dev(b), u2, T.TS_BF16X3)
+    assert np.array_equal(host(u), host(u2))
+    assert rel(host(u), O.apply_inverse(Po, 0.5, b)) < TOL[1]
