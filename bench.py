@@ -244,7 +244,10 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, ov
     returns the stats of each phase."""
     import torch
     prec = T.TS_BF16X3 if prec is None else prec
-    specs = synth.serving_requests(count, seed=seed, omega_set=omega_set)
+    phases = ("saturated", "poisson") + (("overload",) if overload_factor else ())
+    # every phase serves its own requests (drawn in one sequence, `count` per phase), so
+    # that the plan cache meets new potentials in each phase as a live server would
+    specs = synth.serving_requests(count * len(phases), seed=seed, omega_set=omega_set)
     reqs = []
     for sp in specs:
         n, L = sp["n"], sp["L"]
@@ -266,15 +269,12 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, ov
     torch.cuda.synchronize()
     server = T.Server(max_inflight=16)
     out = {}
-    phases = ("saturated", "poisson") + (("overload",) if overload_factor else ())
-    for phase in phases:
-        for kw in reqs:
-            if kw["kind"] == T.TS_REQ_PCG:
-                kw["out"].zero_()
+    for q, phase in enumerate(phases):
+        preqs = reqs[q * count:(q + 1) * count]
         torch.cuda.synchronize()
         server.reset_stats()
         if phase == "saturated":
-            tickets = [server.submit(**kw) for kw in reqs]
+            tickets = [server.submit(**kw) for kw in preqs]
         else:
             factor = rate_factor if phase == "poisson" else overload_factor
             rate = factor * out["saturated"]["completed"] / (out["saturated"]["makespan_ms"] * 1e-3)
@@ -283,7 +283,7 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, ov
             tickets = []
             t0 = time.perf_counter()
             t_next = 0.0
-            for kw, gap in zip(reqs, gaps):
+            for kw, gap in zip(preqs, gaps):
                 t_next += gap
                 while time.perf_counter() - t0 < t_next:
                     time.sleep(min(1e-4, max(0.0, t_next - (time.perf_counter() - t0))))
@@ -299,12 +299,56 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, ov
             stats["rate_factor"] = factor
         out[phase] = stats
     server.close()
-    out["requests"] = count
+    out["requests_per_phase"] = count
     out["mix"] = "30% PCG (V2 = 5 cos cos cos + 8 Gaussian bumps, tol 1e-10) / 50% inverse / 20% exp (tau 0.01)"
     out["grids"] = "3D, n_k iid from {32, 48, 64, 96, 128}"
     out["omega"] = "U[0.5, 2) per axis" if omega_set is None else f"from {list(omega_set)}"
     out["precision"] = ("BF16X3 (PCG: BF16X3 preconditioner, FP64 recurrence)" if prec == T.TS_BF16X3
                         else "FP64 (all applies and the PCG preconditioner)")
+    return out
+
+
+def table1_run(T, n=1099, k=2):
+    """The paper's Table 1 3D problem (eq. test_potential) on Q^k SEM: (-Delta + V) u = f on
+    [-1, 1]^3, V = 1600 sum sin^2(pi x_k / 4) + (x^2 + 2 y^2 + 3 z^2),
+    u* = sin(pi x) sin(2 pi y) sin(3 pi z), f = (14 pi^2 + V) u*, sampled at the GLL nodes.
+    Solves it with the FP64 apply and with the split-precision tensor-core applies (single
+    and refined) and reports time, GDoF/s and the l2 relative error against u*."""
+    import torch
+    x, _ = T.ts_grid_nodes(n, 1.0, k)
+    xs = torch.from_numpy(x).cuda()
+    fx = [1600 * torch.sin(math.pi * xs / 4) ** 2 + (a + 1) * xs ** 2 for a in range(3)]
+    P = T.ts_plan_create((n,) * 3, (1.0,) * 3, [v.cpu().numpy() for v in fx],
+                         (1 << T.TS_BF16X3) | (1 << T.TS_BF16X1), order=k)
+    us = (torch.sin(3 * math.pi * xs)[:, None, None] * torch.sin(2 * math.pi * xs)[None, :, None]
+          * torch.sin(math.pi * xs)[None, None, :])
+    b = (14 * math.pi ** 2 + fx[2][:, None, None] + fx[1][None, :, None] + fx[0][None, None, :]) * us
+    b = b.reshape(-1)
+    us = us.reshape(-1)
+    u = torch.empty_like(b)
+    nus = torch.linalg.vector_norm(us).item()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    N = P.N
+    out = {"n": n, "order": k, "dof": N, "data": "synthetic (the paper's manufactured solution)"}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        err = (torch.linalg.vector_norm(u - us) / nus).item()
+        return {"ms": ms, "gdofs": N / (ms * 1e-3) / 1e9, "err_vs_exact": err}
+
+    out["fp64"] = timed(lambda: T.ts_apply_inverse(P, 0.0, b, u, T.TS_FP64), 1)
+    out["bf16x3"] = timed(lambda: T.ts_apply_inverse(P, 0.0, b, u, T.TS_BF16X3), 5)
+    out["bf16x1"] = timed(lambda: T.ts_apply_inverse(P, 0.0, b, u, T.TS_BF16X1), 5)
+    sched = [T.TS_BF16X3, T.TS_BF16X3, T.TS_BF16X1]
+    out["refined_x3_x3_x1"] = timed(lambda: T.ts_solve_schedule(P, 0.0, b, u, sched), 5)
+    out["printed_err"] = {"Q1": 3.66e-6, "Q2": 1.93e-9, "Q10": 7.66e-13}
     return out
 
 
@@ -357,6 +401,8 @@ def run_secondary(args):
             line[label] = {"lambda": lam, "outer_iters": outer, "pcg_iters": pcg, "seconds": el,
                            "gdofs_per_pcg_iter": P.N * pcg / el / 1e9}
         line["shift"] = shift
+    elif name == "3d_q2_n1099_table1":
+        line.update(table1_run(T))
     elif name == "serving":
         line["continuous_omega"] = serving_run(T, args.requests)
         line["discrete_omega"] = serving_run(T, args.requests, omega_set=(0.5, 1.0, 1.5, 2.0))
@@ -596,7 +642,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving run")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "3d_n256_pcg", "6d_n24_strang", "9d_n8_strang", "serving"])
+                    choices=[WORKLOAD, "3d_n256_pcg", "6d_n24_strang", "9d_n8_strang", "serving",
+                             "3d_q2_n1099_table1"])
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
