@@ -259,6 +259,30 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
                                int pcg_maxit, ts_precision precond, double* lambda,
                                int* outer_iters, long long* pcg_iters, void* stream);
 
+/* Splitting schemes of Sec. 5.1 (ts_propagate). */
+typedef enum {
+  TS_STRANG = 0,   /* e^{-i B dt/2} e^{-i A dt} e^{-i B dt/2} (M is ignored)                 */
+  TS_QHOP = 1,     /* approximated qHOP, eq. qhop_product: e^{-iA dt} prod_k e^{-i w_k dt H_I(s_k)},
+                      H_I(s) = e^{iAs} B e^{-iAs}, M Gauss-Legendre nodes s_k in [0, dt] with
+                      weights w_k (sum 1); M = 1 runs the Strang step                       */
+  TS_MAGNUS2 = 2   /* approximated Magnus-2, eq. yoshida: P(g1 dt) P(g2 dt) P(g1 dt) with P the
+                      TS_QHOP step (M = 1: plain Yoshida over Strang),
+                      g1 = 1/(2 - 2^{1/3}), g2 = -2^{1/3}/(2 - 2^{1/3})                       */
+} ts_scheme;
+
+/*
+ * nsteps steps of size dt of `scheme` for i dpsi/dt = (A + B) psi with A = -Delta_h + V1
+ * (the plan's operator, applied by the exact propagator of Sec. 2.1) and B = diag(VB)
+ * (VB: N doubles on the device, e.g. V2, or V1 + V2 for a plan built with f = 0).
+ * Adjacent factors are merged as in Remark cost_naive_merged (A with A by the group
+ * property, B with B), also across steps and Yoshida sub-steps: qHOP costs about M
+ * A-propagations per step, Magnus-2 about 3M (3 for M = 1).  psi: TS_C128 or TS_C64, in
+ * place; prec: the propagator's precision (TS_FP32: fused small-n kernels, complex64).
+ * 1 <= M <= 64.  *a_propagations (may be NULL) = A-propagations applied.
+ */
+ts_status ts_propagate(const ts_plan* plan, ts_scheme scheme, int M, double dt, int nsteps, const double* VB,
+                       void* psi, ts_dtype dtype, ts_precision prec, int* a_propagations, void* stream);
+
 /*
  * nsteps Strang steps (Sec. 5.1, Remark cost_naive_merged with M = 1) of
  * i d psi/dt = (A + B) psi, A = -Delta_h + V1 (exact propagator), B = diag(V2):

@@ -295,4 +295,16 @@ ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double
   return split_step_impl(plan, dt, nsteps, V2, psi, dtype, prec, (cudaStream_t)stream);
 }
 
+ts_status ts_propagate(const ts_plan* plan, ts_scheme scheme, int M, double dt, int nsteps, const double* VB,
+                       void* psi, ts_dtype dtype, ts_precision prec, int* a_propagations, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(VB && psi, "VB and psi must be non-NULL");
+  TS_REQUIRE(scheme == TS_STRANG || scheme == TS_QHOP || scheme == TS_MAGNUS2, "unknown scheme %d", (int)scheme);
+  TS_REQUIRE(M >= 1 && M <= 64, "M = %d out of range [1, 64]", M);
+  TS_REQUIRE(dtype == TS_C128 || dtype == TS_C64, "dtype must be TS_C128 or TS_C64");
+  TS_REQUIRE(nsteps >= 0, "nsteps must be >= 0");
+  TS_TRY(check_prec(plan, prec));
+  return propagate_impl(plan, scheme, M, dt, nsteps, VB, psi, dtype, prec, a_propagations, (cudaStream_t)stream);
+}
+
 }  // extern "C"

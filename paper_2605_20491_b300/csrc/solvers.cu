@@ -272,6 +272,114 @@ ts_status inverse_iteration_solve(const ts_plan* p, double shift, const double* 
   return st != TS_OK ? st : st2;
 }
 
+namespace {
+
+// Gauss-Legendre rule of M points mapped onto [0, 1]: nodes c ascending, weights summing to
+// 1 (the normalised weights of Sec. 5.1).  Roots of P_M by Newton's method from the
+// asymptotic guesses cos(pi (j + 3/4) / (M + 1/2)), with P_M' = M (x P_M - P_{M-1}) / (x^2 - 1);
+// the weight of root x on [-1, 1] is 2 / ((1 - x^2) P_M'(x)^2).
+void gauss_legendre_01(int M, std::vector<double>* c, std::vector<double>* w) {
+  c->assign(M, 0.0);
+  w->assign(M, 0.0);
+  for (int j = 0; j < M; ++j) {
+    double x = std::cos(M_PI * (j + 0.75) / (M + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;  // P_0, P_1 -> P_{M-1}, P_M
+      for (int q = 1; q < M; ++q) {
+        const double p2 = ((2.0 * q + 1.0) * x * p1 - q * p0) / (q + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = M * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    // j = 0 is the largest root: store ascending on [0, 1]
+    (*c)[M - 1 - j] = 0.5 * (x + 1.0);
+    (*w)[M - 1 - j] = 1.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+struct SplitOp {
+  bool a;    // true: e^{-i t A} (exact propagator), false: e^{-i t B} (pointwise)
+  double t;
+};
+
+// Appends an operation, merging it into the previous one of the same kind (A with A: the
+// propagator's group property; B with B: both diagonal).
+void push_op(std::vector<SplitOp>& v, bool a, double t) {
+  if (!v.empty() && v.back().a == a)
+    v.back().t += t;
+  else
+    v.push_back({a, t});
+}
+
+// One step of size h of the scheme's base method: M = 1, Strang B(h/2) A(h) B(h/2); M >= 2,
+// approximated qHOP in its merged form (Remark cost_naive_merged):
+// A(c_1 h) B(w_1 h) A((c_2 - c_1) h) ... B(w_M h) A((1 - c_M) h), in the order of application.
+void push_base_step(std::vector<SplitOp>& v, int M, const std::vector<double>& c, const std::vector<double>& w,
+                    double h) {
+  if (M == 1) {
+    push_op(v, false, 0.5 * h);
+    push_op(v, true, h);
+    push_op(v, false, 0.5 * h);
+    return;
+  }
+  double prev = 0.0;
+  for (int k = 0; k < M; ++k) {
+    push_op(v, true, (c[k] - prev) * h);
+    push_op(v, false, w[k] * h);
+    prev = c[k];
+  }
+  push_op(v, true, (1.0 - prev) * h);
+}
+
+}  // namespace
+
+ts_status propagate_impl(const ts_plan* p, ts_scheme scheme, int M, double dt, int nsteps, const double* VB,
+                         void* psi, ts_dtype dtype, ts_precision prec, int* a_props, cudaStream_t s) {
+  if (a_props) *a_props = 0;
+  if (nsteps <= 0) return TS_OK;
+  const long long N = p->N;
+  if (prec == TS_FP64 && dtype == TS_C64) {  // FP64 arithmetic on complex64 data
+    Scratch sc_mem(s);
+    double* wbuf;
+    TS_TRY(sc_mem.get(&wbuf, 2 * N));
+    TS_TRY(convert_c64_to_c128(N, (const float*)psi, wbuf, s));
+    TS_TRY(propagate_impl(p, scheme, M, dt, nsteps, VB, wbuf, TS_C128, prec, a_props, s));
+    return convert_c128_to_c64(N, wbuf, (float*)psi, s);
+  }
+  const int Mb = scheme == TS_STRANG ? 1 : M;
+  std::vector<double> c, w;
+  if (Mb > 1) gauss_legendre_01(Mb, &c, &w);
+  // Yoshida's fourth-order composition (eq. yoshida): g1 + g2 + g1 = 1, 2 g1^3 + g2^3 = 0
+  const double g1 = 1.0 / (2.0 - std::cbrt(2.0)), g2 = -std::cbrt(2.0) / (2.0 - std::cbrt(2.0));
+  std::vector<SplitOp> ops;
+  for (int k = 0; k < nsteps; ++k) {
+    if (scheme == TS_MAGNUS2) {
+      push_base_step(ops, Mb, c, w, g1 * dt);
+      push_base_step(ops, Mb, c, w, g2 * dt);
+      push_base_step(ops, Mb, c, w, g1 * dt);
+    } else {
+      push_base_step(ops, Mb, c, w, dt);
+    }
+  }
+  int na = 0;
+  for (const SplitOp& op : ops) {
+    if (op.a) {
+      TS_TRY(apply_exp_impl(p, op.t, psi, psi, dtype, prec, s));
+      ++na;
+    } else if (dtype == TS_C128) {
+      TS_TRY(phase_v2_c128(N, VB, op.t, (double*)psi, s));
+    } else {
+      TS_TRY(phase_v2_c64(N, VB, op.t, (float*)psi, s));
+    }
+  }
+  if (a_props) *a_props = na;
+  return TS_OK;
+}
+
 ts_status split_step_impl(const ts_plan* p, double dt, int nsteps, const double* V2, void* psi, ts_dtype dtype,
                           ts_precision prec, cudaStream_t s) {
   if (nsteps <= 0) return TS_OK;

@@ -18,6 +18,11 @@ ts_status pcg_solve(const ts_plan* p, double sigma, double sigma_P, const double
 ts_status inverse_iteration_solve(const ts_plan* p, double shift, const double* V2, double* u, int init_from_plan,
                                   double tol_lambda, int maxit, double pcg_tol, int pcg_maxit, ts_precision prec,
                                   double* lambda_out, int* outer_out, long long* pcg_out, cudaStream_t s);
+// The splitting schemes of Sec. 5.1 for i dpsi/dt = (A + B) psi, A = the plan's operator
+// (exact propagator), B = diag(VB): Strang, approximated qHOP with M Gauss-Legendre nodes,
+// approximated Magnus-2 (Yoshida composition), all with adjacent propagations merged.
+ts_status propagate_impl(const ts_plan* p, ts_scheme scheme, int M, double dt, int nsteps, const double* VB,
+                         void* psi, ts_dtype dtype, ts_precision prec, int* a_props, cudaStream_t s);
 ts_status split_step_impl(const ts_plan* p, double dt, int nsteps, const double* V2, void* psi, ts_dtype dtype,
                           ts_precision prec, cudaStream_t s);
 

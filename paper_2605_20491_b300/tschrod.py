@@ -32,7 +32,7 @@ EXPORTS = [
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
     "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_selftest_wait_timeout", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
-    "ts_last_error", "ts_version",
+    "ts_propagate", "ts_last_error", "ts_version",
 ]
 
 
@@ -102,6 +102,8 @@ def lib() -> C.CDLL:
     L.ts_inverse_iteration.argtypes = [vp, dp, vp, vp, ip, dp, ip, dp, ip, ip, C.POINTER(dp), C.POINTER(ip),
                                        C.POINTER(C.c_longlong), vp]
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
+    L.ts_propagate.argtypes = [vp, ip, ip, dp, ip, vp, vp, ip, ip, C.POINTER(ip), vp]
+    L.ts_grid_nodes.argtypes = [ip, dp, ip, C.POINTER(dp), C.POINTER(dp)]
     L.ts_device_status.argtypes = [vp]
     L.ts_selftest_wait_timeout.argtypes = [C.c_longlong, vp]
     L.ts_server_create.argtypes = [C.POINTER(_ServerConfig), C.POINTER(vp)]
@@ -338,6 +340,18 @@ def ts_device_status(stream=None):
 def ts_split_step(plan: Plan, dt: float, nsteps: int, V2, psi, dtype: int, prec: int = TS_FP64, stream=None):
     _check(lib().ts_split_step(plan.handle, dt, nsteps, _ptr(V2), _ptr(psi), dtype, prec, _stream(stream)),
            "ts_split_step")
+
+
+TS_STRANG, TS_QHOP, TS_MAGNUS2 = range(3)
+
+
+def ts_propagate(plan: Plan, scheme: int, M: int, dt: float, nsteps: int, VB, psi, dtype: int, prec: int = TS_FP64,
+                 stream=None) -> int:
+    """Splitting steps of Sec. 5.1 in place on psi; returns the number of A-propagations."""
+    na = C.c_int(0)
+    _check(lib().ts_propagate(plan.handle, int(scheme), int(M), float(dt), int(nsteps), _ptr(VB), _ptr(psi), dtype,
+                              prec, C.byref(na), _stream(stream)), "ts_propagate")
+    return na.value
 
 
 class Server:
