@@ -352,6 +352,57 @@ def table1_run(T, n=1099, k=2):
     return out
 
 
+def splitting_run(T, n=499, k=10):
+    """Table splitting's setup (Q^10, n^3 on [-8, 8]^3, A = -Delta, B = V1 =
+    sum (x_k^2 + 100 sin^2(pi x_k / 4)), psi_0 = prod sin(pi (x_k + L) / 2L), T = 0.1): the
+    cost of one A-propagation per precision, and the Delta t = 0.1 errors of Strang,
+    qHOP (M = 3, 5, 7) and Magnus-2 (M = 1, 3) against the exact propagator."""
+    import torch
+    L = 8.0
+    x, _ = T.ts_grid_nodes(n, L, k)
+    v1 = x ** 2 + 100 * np.sin(np.pi * x / 4) ** 2
+    mask = (1 << T.TS_BF16X3) | (1 << T.TS_BF16X6)
+    PA = T.ts_plan_create((n,) * 3, (L,) * 3, [np.zeros(n)] * 3, mask, order=k)
+    PH = T.ts_plan_create((n,) * 3, (L,) * 3, [v1] * 3, 0, order=k)
+    xs = torch.from_numpy(x).cuda()
+    s1 = torch.sin(np.pi * (xs + L) / (2 * L))
+    psi0 = (s1[:, None, None] * s1[None, :, None] * s1[None, None, :]).reshape(-1)
+    psi0 = (psi0 / torch.linalg.vector_norm(psi0)).to(torch.complex128)
+    v = torch.from_numpy(v1).cuda()
+    VB = (v[:, None, None] + v[None, :, None] + v[None, None, :]).reshape(-1).contiguous()
+    ref = torch.empty_like(psi0)
+    T.ts_apply_exp(PH, 0.1, torch.view_as_real(psi0), torch.view_as_real(ref), T.TS_C128)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"n": n, "order": k, "dof": PA.N, "dtype": "c128"}
+    prop = {}
+    for label, prec, reps in (("fp64", T.TS_FP64, 1), ("bf16x6", T.TS_BF16X6, 5), ("bf16x3", T.TS_BF16X3, 5)):
+        psi = psi0.clone()
+        T.ts_apply_exp(PA, 0.01, torch.view_as_real(psi), torch.view_as_real(psi), T.TS_C128, prec)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            T.ts_apply_exp(PA, 0.01, torch.view_as_real(psi), torch.view_as_real(psi), T.TS_C128, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        prop[label] = {"ms_per_A_propagation": ms, "gdofs": PA.N / (ms * 1e-3) / 1e9}
+    out["A_propagation"] = prop
+    errs = {}
+    for name, scheme, M in (("strang", T.TS_STRANG, 1), ("qhop_M3", T.TS_QHOP, 3), ("qhop_M5", T.TS_QHOP, 5),
+                            ("qhop_M7", T.TS_QHOP, 7)):
+        psi = psi0.clone()
+        torch.cuda.synchronize()
+        e0.record()
+        na = T.ts_propagate(PA, scheme, M, 0.1, 1, VB, torch.view_as_real(psi), T.TS_C128)
+        e1.record()
+        torch.cuda.synchronize()
+        errs[name] = {"err_dt0.1": torch.linalg.vector_norm(psi - ref).item(), "A_propagations": na,
+                      "ms": e0.elapsed_time(e1)}
+    out["fp64_dt0.1"] = errs
+    out["printed_err_dt0.1"] = {"strang": 5.85e-1, "qhop_M3": 1.07e-1, "qhop_M5": 4.25e-2, "qhop_M7": 2.28e-2}
+    return out
+
+
 def run_secondary(args):
     """One JSON line for a workload other than the benchmark's: the 3D n = 256 PCG /
     shifted inverse iteration, the 6D / 9D Strang runs, or the serving workload."""
@@ -403,6 +454,8 @@ def run_secondary(args):
         line["shift"] = shift
     elif name == "3d_q2_n1099_table1":
         line.update(table1_run(T))
+    elif name == "3d_q10_n499_splitting":
+        line.update(splitting_run(T))
     elif name == "serving":
         line["continuous_omega"] = serving_run(T, args.requests)
         line["discrete_omega"] = serving_run(T, args.requests, omega_set=(0.5, 1.0, 1.5, 2.0))
@@ -643,7 +696,7 @@ def main():
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving run")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "3d_n256_pcg", "6d_n24_strang", "9d_n8_strang", "serving",
-                             "3d_q2_n1099_table1"])
+                             "3d_q2_n1099_table1", "3d_q10_n499_splitting"])
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
