@@ -259,6 +259,35 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
                                int pcg_maxit, ts_precision precond, double* lambda,
                                int* outer_iters, long long* pcg_iters, void* stream);
 
+/* Riemannian gradient flows of Sec. 4.2 (ts_gpe_ground_state). */
+typedef enum {
+  TS_GPE_H1 = 0,  /* modified H^1 flow, metric (grad w, grad z) + alpha (w, z) (eq. h1_metric)   */
+  TS_GPE_AU = 1   /* a_u flow, metric (grad w, grad z) + (w, V z) + beta (w, u^2 z) (eq. au_metric) */
+} ts_gpe_flow;
+
+/*
+ * Ground state of the Gross-Pitaevskii eigenproblem -Delta u + V u + beta u^3 = lambda u,
+ * ||u||_L2 = 1 (eq. gpe), V = V1 + V2 (V1: the plan's separable potential; V2: N doubles on
+ * the device or NULL), by the Riemannian gradient flow (eq. riemannian_update)
+ *     u <- (u - tau grad) / ||u - tau grad||,  grad = G H_u u - [(u, G H_u u)/(u, G u)] G u,
+ * H_u = -Delta + V + beta u^2, with L2 inner products by the grid's quadrature (h_k per axis
+ * for Q^1, the GLL masses for Q^k).  TS_GPE_H1: G = (-Delta + alpha)^{-1}, two direct solves
+ * per step on a plan of the same grid without potential (prec: TS_FP64, or a split
+ * precision with two FP64-residual refinements).  TS_GPE_AU: G = H_u^{-1}, one PCG solve per
+ * step with preconditioner (-Delta + V1)^{-1} in precision prec to relative residual
+ * pcg_tol, warm-started.  u: N doubles, in = initial guess (normalised first), out = the
+ * last iterate.  Stops when every criterion with a positive tolerance holds:
+ * |E_k - E_{k-1}| < tol_energy |E_k| (E: the energy of eq. gpe_energy; E converges as the
+ * square of the error of u) and ||H_u u - lambda u||_L2 / lambda < tol_residual (eq. gpe; this
+ * one bounds the error of u and lambda); with neither positive, or after maxit steps:
+ * TS_ERR_NOT_CONVERGED, outputs still written.  *energy, *lambda = (u, H_u u), *residual,
+ * *iters, *solves (direct solves, or PCG iterations) may be NULL.  Synchronises stream.
+ */
+ts_status ts_gpe_ground_state(const ts_plan* plan, const double* V2, double beta, ts_gpe_flow flow, double alpha,
+                              double tau, double* u, double tol_energy, double tol_residual, int maxit,
+                              ts_precision prec, double pcg_tol, double* energy, double* lambda, double* residual,
+                              int* iters, long long* solves, void* stream);
+
 /* Splitting schemes of Sec. 5.1 (ts_propagate). */
 typedef enum {
   TS_STRANG = 0,   /* e^{-i B dt/2} e^{-i A dt} e^{-i B dt/2} (M is ignored)                 */

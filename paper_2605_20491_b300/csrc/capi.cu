@@ -307,4 +307,19 @@ ts_status ts_propagate(const ts_plan* plan, ts_scheme scheme, int M, double dt, 
   return propagate_impl(plan, scheme, M, dt, nsteps, VB, psi, dtype, prec, a_propagations, (cudaStream_t)stream);
 }
 
+ts_status ts_gpe_ground_state(const ts_plan* plan, const double* V2, double beta, ts_gpe_flow flow, double alpha,
+                              double tau, double* u, double tol_energy, double tol_residual, int maxit,
+                              ts_precision prec, double pcg_tol, double* energy, double* lambda, double* residual,
+                              int* iters, long long* solves, void* stream) {
+  TS_API_BEGIN(plan);
+  TS_REQUIRE(u, "u must be non-NULL");
+  TS_REQUIRE(flow == TS_GPE_H1 || flow == TS_GPE_AU, "unknown flow %d", (int)flow);
+  TS_REQUIRE(beta >= 0.0 && tau > 0.0 && maxit >= 0, "need beta >= 0, tau > 0, maxit >= 0");
+  TS_REQUIRE(flow != TS_GPE_H1 || alpha > 0.0, "the modified H^1 flow needs alpha > 0");
+  TS_REQUIRE(flow != TS_GPE_AU || pcg_tol > 0.0, "the a_u flow needs pcg_tol > 0");
+  TS_TRY(check_prec(plan, prec));
+  return gpe_ground_state_impl(plan, V2, beta, flow, alpha, tau, u, tol_energy, tol_residual, maxit, prec, pcg_tol,
+                               energy, lambda, residual, iters, solves, (cudaStream_t)stream);
+}
+
 }  // extern "C"

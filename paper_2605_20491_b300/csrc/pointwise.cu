@@ -709,6 +709,87 @@ __global__ void k_scale_separable(AxisParams a, const double* x, double* y, long
   }
 }
 
+// Per-axis quadrature weights of the L2 inner product: w_k(i) = mh_k[i]^2 (Q^k: the GLL
+// lumped mass) or h_k (Q^1, mh_k == NULL); the d-dimensional weight is their product.
+struct WeightParams {
+  int d;
+  int n[MAXD];
+  const double* mh[MAXD];
+  double h[MAXD];
+};
+
+__device__ __forceinline__ double axis_weight(const WeightParams& w, int k, int i) {
+  if (w.mh[k]) {
+    const double m = w.mh[k][i];
+    return m * m;
+  }
+  return w.h[k];
+}
+
+// Weighted reductions over grid rows (axis 1): one warp per row, the weight of the row's
+// other axes computed once.  MODE 0: sums of W a b and W c d (c may be NULL); MODE 1: sums
+// of W a b and W a^4 (the GPE energy terms, a = u, b = H_u u); MODE 2: sum of W (b - s a)^2
+// (the Euler-Lagrange residual, s = lambda).
+template <int MODE>
+__global__ void k_wdot(WeightParams w, const double* __restrict__ a, const double* __restrict__ b,
+                       const double* __restrict__ c, const double* __restrict__ dv, long long N, double* partial,
+                       double sc = 0.0) {
+  const int n0 = w.n[0];
+  const long long R = N / n0;
+  const int lane = threadIdx.x & 31;
+  const long long warps_total = (long long)gridDim.x * (blockDim.x >> 5);
+  double s0 = 0.0, s1 = 0.0;
+  for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < R; row += warps_total) {
+    long long q = row;
+    double wr = 1.0;
+    for (int k = 1; k < w.d; ++k) {
+      const long long qq = q / w.n[k];
+      wr *= axis_weight(w, k, (int)(q - qq * w.n[k]));
+      q = qq;
+    }
+    const long long base = row * n0;
+    for (int i0 = lane; i0 < n0; i0 += 32) {
+      const long long idx = base + i0;
+      const double wt = wr * axis_weight(w, 0, i0);
+      const double av = a[idx];
+      if (MODE == 2) {
+        const double e = fma(-sc, av, b[idx]);
+        s0 = fma(wt * e, e, s0);
+        continue;
+      }
+      s0 = fma(wt * av, b[idx], s0);
+      if (MODE == 1) {
+        const double a2 = av * av;
+        s1 = fma(wt * a2, a2, s1);
+      } else if (c) {
+        s1 = fma(wt * c[idx], dv[idx], s1);
+      }
+    }
+  }
+  s0 = block_sum(s0);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// veff = V2 + beta u^2 (V2 may be NULL).
+__global__ void k_gpe_veff(const double* __restrict__ V2, double beta, const double* __restrict__ u,
+                           double* __restrict__ veff, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double ui = u[i];
+    veff[i] = fma(beta * ui, ui, V2 ? V2[i] : 0.0);
+  }
+}
+
+// u = u + a x + b y.
+__global__ void k_axpy2(double* __restrict__ u, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    u[i] = fma(b, y[i], fma(a, x[i], u[i]));
+}
+
 }  // namespace
 
 int red_blocks() { return RED_BLOCKS; }
@@ -770,6 +851,55 @@ BandParams band_params(const ts_plan* p) {
   return a;
 }
 }  // namespace
+
+namespace {
+WeightParams weight_params(const ts_plan* p) {
+  WeightParams w{};
+  w.d = p->d;
+  for (int k = 0; k < p->d; ++k) {
+    w.n[k] = p->n[k];
+    w.mh[k] = p->order >= 2 ? p->mh[k] : nullptr;
+    w.h[k] = 2.0 * p->L[k] / (p->n[k] + 1);
+  }
+  return w;
+}
+}  // namespace
+
+ts_status wdot2(const ts_plan* p, const double* a, const double* b, const double* c, const double* d,
+                double* partial, double* out2, cudaStream_t s) {
+  k_wdot<0><<<RED_BLOCKS, 256, 0, s>>>(weight_params(p), a, b, c, d, p->N, partial);
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, RED_BLOCKS, out2);
+  TS_LAUNCHED(2);
+  return TS_OK;
+}
+
+ts_status wdot_energy(const ts_plan* p, const double* u, const double* Hu, double* partial, double* out2,
+                      cudaStream_t s) {
+  k_wdot<1><<<RED_BLOCKS, 256, 0, s>>>(weight_params(p), u, Hu, nullptr, nullptr, p->N, partial);
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, RED_BLOCKS, out2);
+  TS_LAUNCHED(2);
+  return TS_OK;
+}
+
+ts_status wdot_residual(const ts_plan* p, const double* u, const double* Hu, double lambda, double* partial,
+                        double* out2, cudaStream_t s) {
+  k_wdot<2><<<RED_BLOCKS, 256, 0, s>>>(weight_params(p), u, Hu, nullptr, nullptr, p->N, partial, lambda);
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, RED_BLOCKS, out2);
+  TS_LAUNCHED(2);
+  return TS_OK;
+}
+
+ts_status gpe_veff(long long N, const double* V2, double beta, const double* u, double* veff, cudaStream_t s) {
+  k_gpe_veff<<<grid_for(N), 256, 0, s>>>(V2, beta, u, veff, N);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
+ts_status axpy2(long long N, double* u, double a, const double* x, double b, const double* y, cudaStream_t s) {
+  k_axpy2<<<grid_for(N), 256, 0, s>>>(u, a, x, b, y, N);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
 
 ts_status scale_separable(const ts_plan* p, bool inverse, const double* x, double* y, cudaStream_t s) {
   AxisParams a = axis_params(p, false);

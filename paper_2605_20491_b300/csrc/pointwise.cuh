@@ -22,6 +22,20 @@ ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigm
 // sum_k K_k + V1 + V2 + sigma of the plan's frame instead of the stencil.
 // y = x * prod_k M_k^{1/2} (inverse: M_k^{-1/2}) for a Q^k plan; x and y may alias.
 ts_status scale_separable(const ts_plan* p, bool inverse, const double* x, double* y, cudaStream_t s);
+// Weighted inner products of the L2 quadrature (W = prod_k M_k: GLL masses for Q^k, h_k for
+// Q^1): out2[0] = sum W a b, out2[1] = sum W c d (c, d may be NULL -> 0).
+ts_status wdot2(const ts_plan* p, const double* a, const double* b, const double* c, const double* d,
+                double* partial, double* out2, cudaStream_t s);
+// out2[0] = sum W u Hu, out2[1] = sum W u^4.
+ts_status wdot_energy(const ts_plan* p, const double* u, const double* Hu, double* partial, double* out2,
+                      cudaStream_t s);
+// out2[0] = sum W (Hu - lambda u)^2.
+ts_status wdot_residual(const ts_plan* p, const double* u, const double* Hu, double lambda, double* partial,
+                        double* out2, cudaStream_t s);
+// veff = V2 + beta u^2 (V2 may be NULL).
+ts_status gpe_veff(long long N, const double* V2, double beta, const double* u, double* veff, cudaStream_t s);
+// u += a x + b y.
+ts_status axpy2(long long N, double* u, double a, const double* x, double b, const double* y, cudaStream_t s);
 // True when every axis has the same grid spacing h (never for Q^k, k >= 2).
 bool isotropic_h(const ts_plan* p);
 // As stencil_residual_split without V2, for isotropic grids: the Laplacian part in exact

@@ -6,6 +6,7 @@
 // Every vector update and inner product is FP64 on the device; scalars live in device
 // memory and only the residual norm / eigenvalue crosses to the host once per iteration
 // for the stopping test.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -377,6 +378,125 @@ ts_status propagate_impl(const ts_plan* p, ts_scheme scheme, int M, double dt, i
     }
   }
   if (a_props) *a_props = na;
+  return TS_OK;
+}
+
+ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, ts_plan** out);
+void plan_free(ts_plan* p);
+
+// The GPE ground state by Riemannian gradient flows on the L2 sphere (Sec. 4.2-4.3):
+//   u <- (u - tau grad) / ||u - tau grad||,  grad = G H_u u - [(u, G H_u u) / (u, G u)] G u,
+// H_u = -Delta + V1 + V2 + beta u^2, inner products weighted by the quadrature (W = prod M_k).
+// Modified H^1 flow: G = (-Delta + alpha)^{-1}, two direct solves per step on a plan of the
+// same grid with f = 0 (split precisions: two refinements with the FP64 residual).  a_u flow:
+// G = H_u^{-1}, so G H_u u = u and G u is one PCG solve with the plan's (-Delta + V1)^{-1}
+// as preconditioner, warm-started from the previous step's solution.
+ts_status gpe_ground_state_impl(const ts_plan* p, const double* V2, double beta, ts_gpe_flow flow, double alpha,
+                                double tau, double* u, double tol_energy, double tol_residual, int maxit,
+                                ts_precision prec, double pcg_tol, double* energy_out, double* lambda_out,
+                                double* residual_out, int* iters_out, long long* solves_out, cudaStream_t s) {
+  const long long N = p->N;
+  Scratch sc_mem(s);
+  double *r, *w1, *w2, *veff, *partial, *sc;
+  TS_TRY(sc_mem.get(&r, N));
+  TS_TRY(sc_mem.get(&w1, N));
+  TS_TRY(sc_mem.get(&w2, N));
+  TS_TRY(sc_mem.get(&veff, N));
+  TS_TRY(sc_mem.get(&partial, 2 * RED_BLOCKS));
+  TS_TRY(sc_mem.get(&sc, 8));
+  ts_plan* p0 = nullptr;  // -Delta alone on the same grid (modified H^1 flow)
+  struct Owner {
+    ts_plan* q;
+    ~Owner() { if (q) plan_free(q); }
+  } own{nullptr};
+  if (flow == TS_GPE_H1) {
+    std::vector<std::vector<double>> zeros(p->d);
+    std::vector<const double*> fz(p->d);
+    for (int k = 0; k < p->d; ++k) {
+      zeros[k].assign(p->n[k], 0.0);
+      fz[k] = zeros[k].data();
+    }
+    ts_plan_desc desc{};
+    desc.d = p->d;
+    desc.n = p->n;
+    desc.L = p->L;
+    desc.f = fz.data();
+    desc.bc = 0;
+    desc.order = p->order;
+    TS_TRY(plan_create(&desc, p->precision_mask, s, &p0));
+    own.q = p0;
+  }
+  // A split-precision G carries two FP64-residual refinements: the flow's fixed point moves
+  // by about G's error over the spectral gap, and one refinement (~1e-10 for BF16X3)
+  // leaves the Euler-Lagrange residual near 1e-8.
+  const ts_precision sched[3] = {prec, prec, prec};
+  auto applyG = [&](const double* in, double* out) -> ts_status {
+    if (prec == TS_FP64) return apply_inverse_impl(p0, alpha, in, out, prec, s);
+    return mixed_solve_schedule(p0, sched, 3, alpha, in, out, s);
+  };
+  // u <- u / ||u||
+  TS_TRY(wdot2(p, u, u, nullptr, nullptr, partial, sc, s));
+  TS_TRY(scale_by_device_ratio(N, sc, nullptr, u, u, s));
+  TS_CHECK_CUDA(cudaMemsetAsync(w2, 0, sizeof(double) * N, s));
+  double E_prev = 0.0, E = 0.0, lam = 0.0, res = 0.0;
+  long long solves = 0;
+  int it = 0;
+  bool converged = false;
+  for (;; ++it) {
+    // H_u u, then E = 1/2 (u, H_u u) - beta/4 (u^2, u^2), lambda = (u, H_u u) and, when asked
+    // for, the Euler-Lagrange residual ||H_u u - lambda u|| / lambda
+    TS_TRY(gpe_veff(N, V2, beta, u, veff, s));
+    TS_TRY(stencil_apply(p, veff, 0.0, u, r, partial, nullptr, s));
+    TS_TRY(wdot_energy(p, u, r, partial, sc, s));
+    double h[2];
+    TS_TRY(read_scalars(sc, h, 2, s));
+    lam = h[0];
+    E = 0.5 * h[0] - 0.25 * beta * h[1];
+    if (tol_residual > 0.0 || residual_out) {
+      TS_TRY(wdot_residual(p, u, r, lam, partial, sc, s));
+      TS_TRY(read_scalars(sc, h, 1, s));
+      res = std::sqrt(std::max(h[0], 0.0)) / std::fabs(lam);
+    }
+    converged = (tol_energy > 0.0 || tol_residual > 0.0) &&
+                (tol_energy <= 0.0 || (it > 0 && std::fabs(E - E_prev) < tol_energy * std::fabs(E))) &&
+                (tol_residual <= 0.0 || res < tol_residual);
+    if (converged || it == maxit) break;
+    E_prev = E;
+    const double* g1;
+    if (flow == TS_GPE_H1) {
+      TS_TRY(applyG(r, w1));
+      TS_TRY(applyG(u, w2));
+      solves += 2;
+      g1 = w1;
+    } else {
+      int pit = 0;
+      const ts_status st = pcg_solve(p, 0.0, 0.0, veff, u, w2, pcg_tol, 10000, prec, &pit, nullptr, s);
+      if (st != TS_OK && st != TS_ERR_NOT_CONVERGED) return st;
+      solves += pit;
+      g1 = u;  // G H_u u = u
+    }
+    TS_TRY(wdot2(p, u, g1, u, w2, partial, sc, s));
+    TS_TRY(read_scalars(sc, h, 2, s));
+    const double gamma = h[0] / h[1];
+    // u <- u - tau (g1 - gamma w2), then normalise
+    if (g1 == u) {
+      TS_TRY(axpy2(N, u, -tau, u, tau * gamma, w2, s));
+    } else {
+      TS_TRY(axpy2(N, u, -tau, g1, tau * gamma, w2, s));
+    }
+    TS_TRY(wdot2(p, u, u, nullptr, nullptr, partial, sc, s));
+    TS_TRY(scale_by_device_ratio(N, sc, nullptr, u, u, s));
+  }
+  if (energy_out) *energy_out = E;
+  if (lambda_out) *lambda_out = lam;
+  if (residual_out) *residual_out = res;
+  if (iters_out) *iters_out = it;
+  if (solves_out) *solves_out = solves;
+  if (!converged) {
+    set_error("GPE flow: no convergence in %d iterations (|dE|/E = %.3e, residual %.3e)", maxit,
+              std::fabs(E - E_prev) / std::fabs(E), res);
+    return TS_ERR_NOT_CONVERGED;
+  }
   return TS_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
     "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_selftest_wait_timeout", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
-    "ts_propagate", "ts_last_error", "ts_version",
+    "ts_propagate", "ts_gpe_ground_state", "ts_last_error", "ts_version",
 ]
 
 
@@ -104,6 +104,8 @@ def lib() -> C.CDLL:
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
     L.ts_propagate.argtypes = [vp, ip, ip, dp, ip, vp, vp, ip, ip, C.POINTER(ip), vp]
     L.ts_grid_nodes.argtypes = [ip, dp, ip, C.POINTER(dp), C.POINTER(dp)]
+    L.ts_gpe_ground_state.argtypes = [vp, vp, dp, ip, dp, dp, vp, dp, dp, ip, ip, dp, C.POINTER(dp), C.POINTER(dp),
+                                      C.POINTER(dp), C.POINTER(ip), C.POINTER(C.c_longlong), vp]
     L.ts_device_status.argtypes = [vp]
     L.ts_selftest_wait_timeout.argtypes = [C.c_longlong, vp]
     L.ts_server_create.argtypes = [C.POINTER(_ServerConfig), C.POINTER(vp)]
@@ -352,6 +354,21 @@ def ts_propagate(plan: Plan, scheme: int, M: int, dt: float, nsteps: int, VB, ps
     _check(lib().ts_propagate(plan.handle, int(scheme), int(M), float(dt), int(nsteps), _ptr(VB), _ptr(psi), dtype,
                               prec, C.byref(na), _stream(stream)), "ts_propagate")
     return na.value
+
+
+TS_GPE_H1, TS_GPE_AU = range(2)
+
+
+def ts_gpe_ground_state(plan: Plan, V2, beta: float, flow: int, u, alpha: float = 20.0, tau: float = 0.1,
+                        tol_energy: float = 1e-14, tol_residual: float = 0.0, maxit: int = 5000, prec: int = TS_FP64,
+                        pcg_tol: float = 1e-12, stream=None, allow_not_converged: bool = False):
+    """Returns (energy, lambda, iterations, solves, residual); u is updated in place."""
+    E, lam, res, it, so = C.c_double(), C.c_double(), C.c_double(), C.c_int(), C.c_longlong()
+    st = lib().ts_gpe_ground_state(plan.handle, _ptr(V2), float(beta), int(flow), float(alpha), float(tau), _ptr(u),
+                                   float(tol_energy), float(tol_residual), int(maxit), int(prec), float(pcg_tol),
+                                   C.byref(E), C.byref(lam), C.byref(res), C.byref(it), C.byref(so), _stream(stream))
+    _check(st, "ts_gpe_ground_state", allow=(TS_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return E.value, lam.value, it.value, so.value, res.value
 
 
 class Server:
