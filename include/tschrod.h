@@ -259,6 +259,29 @@ ts_status ts_inverse_iteration(const ts_plan* plan, double shift, const double* 
                                int pcg_maxit, ts_precision precond, double* lambda,
                                int* outer_iters, long long* pcg_iters, void* stream);
 
+/*
+ * uf = tensor-product linear interpolation of uc from the grid of plan `coarse` to the grid
+ * of plan `fine` (Sec. 5.3.1): the same d and the same L per axis, any n and order on
+ * either side; per axis each fine node takes the linear interpolant between its two
+ * neighbouring coarse nodes, the walls x = -L, L carrying the Dirichlet zero.  uc, uf:
+ * device arrays of the two grids' N doubles, must not alias.  Synchronises stream.
+ */
+ts_status ts_interpolate(const ts_plan* coarse, const double* uc, const ts_plan* fine, double* uf, void* stream);
+
+/*
+ * Multi-level shifted inverse iteration (Sec. 5.3.1, Table multilevel): ts_inverse_iteration
+ * on plans[0] from the tensor product of its per-axis ground states, then on plans[1], ...
+ * each from the previous level's eigenvector interpolated by ts_interpolate.  V2[l]: the
+ * non-separable potential sampled on level l's grid (V2 itself or V2[l] may be NULL).
+ * shift, tolerances and precond as in ts_inverse_iteration, the same for every level.
+ * u: the finest grid's N doubles (out).  outer[l], pcg[l] (levels entries each, may be
+ * NULL): the per-level outer and total PCG iterations.  Synchronises stream.
+ */
+ts_status ts_inverse_iteration_multilevel(const ts_plan* const* plans, const double* const* V2, int levels,
+                                          double shift, double* u, double tol_lambda, int maxit, double pcg_tol,
+                                          int pcg_maxit, ts_precision precond, double* lambda, int* outer,
+                                          long long* pcg, void* stream);
+
 /* Riemannian gradient flows of Sec. 4.2 (ts_gpe_ground_state). */
 typedef enum {
   TS_GPE_H1 = 0,  /* modified H^1 flow, metric (grad w, grad z) + alpha (w, z) (eq. h1_metric)   */

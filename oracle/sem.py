@@ -329,3 +329,21 @@ def inverse_iteration(P: SemPlan, shift: float, V2=None, u0=None, tol_lambda: fl
         if done:
             return lam, u, it, total
     return lam, u, maxit, total
+
+
+# -------------------------------------------------------------- multi-level transfer -----
+
+def interpolate(Pc: SemPlan, uc, Pf: SemPlan) -> np.ndarray:
+    """Tensor-product linear interpolation of the coarse grid function uc onto the fine grid
+    (Sec. 5.3.1), as successive 1D piecewise-linear interpolations along each axis; the
+    walls x = -L, L carry the Dirichlet zero."""
+    X = np.asarray(uc, dtype=np.float64).reshape(Pc.shape())
+    for a in range(Pc.d):
+        xc = np.concatenate(([-Pc.L[a]], Pc.axes[a].x, [Pc.L[a]]))
+        xf = Pf.axes[a].x
+        ax = Pc.d - 1 - a
+        Xe = np.moveaxis(X, ax, -1)
+        Xe = np.concatenate((np.zeros(Xe.shape[:-1] + (1,)), Xe, np.zeros(Xe.shape[:-1] + (1,))), axis=-1)
+        Y = np.apply_along_axis(lambda v: np.interp(xf, xc, v), -1, Xe)
+        X = np.moveaxis(Y, -1, ax)
+    return X.reshape(-1)

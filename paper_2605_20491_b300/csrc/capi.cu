@@ -121,19 +121,7 @@ ts_status ts_grid_nodes(int n, double L, int order, double* x, double* m) {
   TS_REQUIRE(n >= 1 && n <= 4096, "n = %d out of range [1, 4096]", n);
   TS_REQUIRE(L > 0.0, "L must be positive");
   TS_REQUIRE(order >= 0 && order <= 32, "order = %d out of range [0, 32]", order);
-  if (order < 2) {
-    const double h = 2.0 * L / (n + 1);
-    for (int i = 0; i < n; ++i) {
-      x[i] = -L + (i + 1) * h;
-      if (m) m[i] = h;
-    }
-    return TS_OK;
-  }
-  SemAxis ax;
-  TS_TRY(sem_axis_build(n, L, order, &ax));
-  std::memcpy(x, ax.x.data(), sizeof(double) * n);
-  if (m) std::memcpy(m, ax.m.data(), sizeof(double) * n);
-  return TS_OK;
+  return grid_nodes_host(n, L, order, x, m);
 }
 
 ts_status ts_plan_eigs(const ts_plan* plan, int axis, double* lambda_host) {
@@ -320,6 +308,35 @@ ts_status ts_gpe_ground_state(const ts_plan* plan, const double* V2, double beta
   TS_TRY(check_prec(plan, prec));
   return gpe_ground_state_impl(plan, V2, beta, flow, alpha, tau, u, tol_energy, tol_residual, maxit, prec, pcg_tol,
                                energy, lambda, residual, iters, solves, (cudaStream_t)stream);
+}
+
+ts_status ts_interpolate(const ts_plan* coarse, const double* uc, const ts_plan* fine, double* uf, void* stream) {
+  TS_API_BEGIN(fine);
+  TS_REQUIRE(coarse && uc && uf && uc != uf, "coarse, uc, uf must be non-NULL and uc != uf");
+  TS_REQUIRE(coarse->device == fine->device, "both plans must be on one device");
+  return interpolate(coarse, uc, fine, uf, (cudaStream_t)stream);
+}
+
+ts_status ts_inverse_iteration_multilevel(const ts_plan* const* plans, const double* const* V2, int levels,
+                                          double shift, double* u, double tol_lambda, int maxit, double pcg_tol,
+                                          int pcg_maxit, ts_precision precond, double* lambda, int* outer,
+                                          long long* pcg, void* stream) {
+  clear_error();
+  TS_REQUIRE(plans && levels >= 1 && u, "need plans, levels >= 1 and u");
+  for (int l = 0; l < levels; ++l) {
+    TS_REQUIRE(plans[l], "plans[%d] is NULL", l);
+    TS_REQUIRE(plans[l]->device == plans[0]->device && plans[l]->d == plans[0]->d,
+               "all levels must share the device and the dimension");
+    TS_TRY(check_prec(plans[l], precond));
+  }
+  TS_REQUIRE(maxit >= 1 && pcg_maxit >= 1, "maxit and pcg_maxit must be >= 1");
+  DeviceGuard g(plans[0]->device);
+  if (!g.ok) {
+    set_error("cannot select device %d", plans[0]->device);
+    return TS_ERR_CUDA;
+  }
+  return inverse_iteration_multilevel_impl(plans, V2, levels, shift, u, tol_lambda, maxit, pcg_tol, pcg_maxit, precond,
+                                           lambda, outer, pcg, (cudaStream_t)stream);
 }
 
 }  // extern "C"

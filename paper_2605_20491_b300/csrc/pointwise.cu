@@ -7,9 +7,13 @@
 // (148 SMs x 4) CTAs so that reductions see a fixed partition of the index space and
 // return bit-identical sums on every call (two-level reduction: per-CTA partials in a
 // fixed order, then one CTA sums the partials in a fixed order).
+#include <algorithm>
+#include <vector>
+
 #include "async_copy.cuh"
 #include "common.cuh"
 #include "pointwise.cuh"
+#include "sem_axis.cuh"
 #include "split.cuh"
 
 namespace ts {
@@ -790,6 +794,48 @@ __global__ void k_axpy2(double* __restrict__ u, double a, const double* __restri
     u[i] = fma(b, y[i], fma(a, x[i], u[i]));
 }
 
+// Tensor-product linear interpolation from a coarse to a fine grid of the same box: per
+// axis, fine node i lies between coarse nodes lo[i] and lo[i] + 1 at fraction t[i]
+// (lo = -1 and lo + 1 = n_c stand for the walls, where the Dirichlet value is 0).
+struct InterpParams {
+  int d;
+  int nf[MAXD], nc[MAXD];
+  long long cstride[MAXD];
+  const int* lo[MAXD];
+  const double* t[MAXD];
+};
+
+__global__ void k_interp(InterpParams ip, const double* __restrict__ uc, double* __restrict__ uf, long long Nf) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < Nf;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int l[MAXD];
+    double t[MAXD];
+    long long q = idx;
+    for (int k = 0; k < ip.d; ++k) {
+      const long long qq = q / ip.nf[k];
+      const int i = (int)(q - qq * ip.nf[k]);
+      q = qq;
+      l[k] = ip.lo[k][i];
+      t[k] = ip.t[k][i];
+    }
+    double acc = 0.0;
+    for (int corner = 0; corner < (1 << ip.d); ++corner) {
+      double w = 1.0;
+      long long off = 0;
+      bool inside = true;
+      for (int k = 0; k < ip.d; ++k) {
+        const int b = (corner >> k) & 1;
+        const int j = l[k] + b;
+        w *= b ? t[k] : 1.0 - t[k];
+        inside = inside && j >= 0 && j < ip.nc[k];
+        off += (long long)j * ip.cstride[k];
+      }
+      if (inside && w != 0.0) acc = fma(w, uc[off], acc);
+    }
+    uf[idx] = acc;
+  }
+}
+
 }  // namespace
 
 int red_blocks() { return RED_BLOCKS; }
@@ -899,6 +945,67 @@ ts_status axpy2(long long N, double* u, double a, const double* x, double b, con
   k_axpy2<<<grid_for(N), 256, 0, s>>>(u, a, x, b, y, N);
   TS_LAUNCHED(1);
   return TS_OK;
+}
+
+ts_status interpolate(const ts_plan* pc, const double* uc, const ts_plan* pf, double* uf, cudaStream_t s) {
+  TS_REQUIRE(pc->d == pf->d, "interpolation needs grids of one dimension (%d, %d)", pc->d, pf->d);
+  const int d = pc->d;
+  for (int k = 0; k < d; ++k)
+    TS_REQUIRE(pc->L[k] == pf->L[k], "interpolation needs the same box (axis %d: L = %g, %g)", k, pc->L[k], pf->L[k]);
+  // per axis: coarse nodes with the two walls, and the bracket of every fine node
+  std::vector<int> lo_h;
+  std::vector<double> t_h;
+  std::vector<size_t> off(d);
+  for (int k = 0; k < d; ++k) {
+    std::vector<double> xc(pc->n[k]), xf(pf->n[k]);
+    TS_TRY(grid_nodes_host(pc->n[k], pc->L[k], pc->order, xc.data(), nullptr));
+    TS_TRY(grid_nodes_host(pf->n[k], pf->L[k], pf->order, xf.data(), nullptr));
+    std::vector<double> ext(pc->n[k] + 2);
+    ext[0] = -pc->L[k];
+    for (int i = 0; i < pc->n[k]; ++i) ext[i + 1] = xc[i];
+    ext[pc->n[k] + 1] = pc->L[k];
+    off[k] = lo_h.size();
+    for (int i = 0; i < pf->n[k]; ++i) {
+      const double x = xf[i];
+      int j = (int)(std::upper_bound(ext.begin(), ext.end(), x) - ext.begin()) - 1;  // ext[j] <= x < ext[j+1]
+      j = j < 0 ? 0 : (j > pc->n[k] ? pc->n[k] : j);
+      lo_h.push_back(j - 1);
+      t_h.push_back((x - ext[j]) / (ext[j + 1] - ext[j]));
+    }
+  }
+  void* tab = nullptr;
+  const size_t nl = lo_h.size();
+  TS_TRY(scratch_alloc(&tab, sizeof(double) * nl + sizeof(int) * nl + 256, s));
+  double* t_d = static_cast<double*>(tab);
+  int* lo_d = reinterpret_cast<int*>(t_d + nl);
+  ts_status st = TS_OK;
+  if (cudaMemcpyAsync(t_d, t_h.data(), sizeof(double) * nl, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(lo_d, lo_h.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    set_error("interpolation tables: copy failed");
+    st = TS_ERR_CUDA;
+  }
+  if (st == TS_OK) {
+    InterpParams ip{};
+    ip.d = d;
+    long long cs = 1;
+    for (int k = 0; k < d; ++k) {
+      ip.nf[k] = pf->n[k];
+      ip.nc[k] = pc->n[k];
+      ip.cstride[k] = cs;
+      cs *= pc->n[k];
+      ip.lo[k] = lo_d + off[k];
+      ip.t[k] = t_d + off[k];
+    }
+    k_interp<<<grid_for(pf->N), 256, 0, s>>>(ip, uc, uf, pf->N);
+    TS_LAUNCHED(1);
+    // the host vectors go out of scope: wait for the copies
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("interpolation failed");
+      st = TS_ERR_CUDA;
+    }
+  }
+  scratch_free(tab, s);
+  return st;
 }
 
 ts_status scale_separable(const ts_plan* p, bool inverse, const double* x, double* y, cudaStream_t s) {

@@ -29,6 +29,9 @@ ts_status wdot2(const ts_plan* p, const double* a, const double* b, const double
 // out2[0] = sum W u Hu, out2[1] = sum W u^4.
 ts_status wdot_energy(const ts_plan* p, const double* u, const double* Hu, double* partial, double* out2,
                       cudaStream_t s);
+// uf (fine grid pf) = tensor-product linear interpolation of uc (coarse grid pc, same d and
+// box), the walls carrying the Dirichlet zero.  Synchronises s.
+ts_status interpolate(const ts_plan* pc, const double* uc, const ts_plan* pf, double* uf, cudaStream_t s);
 // out2[0] = sum W (Hu - lambda u)^2.
 ts_status wdot_residual(const ts_plan* p, const double* u, const double* Hu, double lambda, double* partial,
                         double* out2, cudaStream_t s);

@@ -132,4 +132,31 @@ ts_status sem_axis_build(int n, double L, int k, SemAxis* out) {
   return TS_OK;
 }
 
+ts_status grid_nodes_host(int n, double L, int order, double* x, double* m) {
+  if (order < 2) {
+    const double h = 2.0 * L / (n + 1);
+    for (int i = 0; i < n; ++i) {
+      x[i] = -L + (i + 1) * h;
+      if (m) m[i] = h;
+    }
+    return TS_OK;
+  }
+  const int k = order;
+  if ((n + 1) % k != 0) {
+    set_error("Q^%d needs n + 1 to be a multiple of %d (n = %d)", k, k, n);
+    return TS_ERR_INVALID_ARG;
+  }
+  const int c = (n + 1) / k;
+  const double he = 2.0 * L / c;
+  std::vector<double> xi, w;
+  gll_rule(k, &xi, &w);
+  // interior node i is global node g = i + 1 = e k + a (a = 0 only for shared element ends)
+  for (int i = 0; i < n; ++i) {
+    const int g = i + 1, e = g / k, a = g % k;
+    x[i] = -L + e * he + 0.5 * (xi[a] + 1.0) * he;
+    if (m) m[i] = a == 0 ? 0.5 * he * (w[0] + w[k]) : 0.5 * he * w[a];
+  }
+  return TS_OK;
+}
+
 }  // namespace ts

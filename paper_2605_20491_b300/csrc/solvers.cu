@@ -381,6 +381,40 @@ ts_status propagate_impl(const ts_plan* p, ts_scheme scheme, int M, double dt, i
   return TS_OK;
 }
 
+// Multi-level shifted inverse iteration (Sec. 5.3.1): inverse iteration on plans[0] from the
+// tensor product of its per-axis ground states, then on each finer plan from the previous
+// level's eigenvector carried over by tensor-product linear interpolation.  u receives the
+// finest level's eigenvector; outer[l] and pcg[l] the per-level iteration counts.
+ts_status inverse_iteration_multilevel_impl(const ts_plan* const* plans, const double* const* V2, int levels,
+                                            double shift, double* u, double tol_lambda, int maxit, double pcg_tol,
+                                            int pcg_maxit, ts_precision prec, double* lambda_out, int* outer,
+                                            long long* pcg, cudaStream_t s) {
+  Scratch sc_mem(s);
+  double* prev = nullptr;
+  const ts_plan* prev_plan = nullptr;
+  double lambda = 0.0;
+  for (int l = 0; l < levels; ++l) {
+    const ts_plan* p = plans[l];
+    double* ul = u;
+    if (l + 1 < levels) TS_TRY(sc_mem.get(&ul, p->N));
+    if (l > 0) TS_TRY(interpolate(prev_plan, prev, p, ul, s));
+    int it = 0;
+    long long pit = 0;
+    const ts_status st = inverse_iteration_solve(p, shift, V2 ? V2[l] : nullptr, ul, l == 0, tol_lambda, maxit,
+                                                 pcg_tol, pcg_maxit, prec, &lambda, &it, &pit, s);
+    if (outer) outer[l] = it;
+    if (pcg) pcg[l] = pit;
+    if (st != TS_OK && !(st == TS_ERR_NOT_CONVERGED && l + 1 < levels)) {
+      if (lambda_out) *lambda_out = lambda;
+      return st;
+    }
+    prev = ul;
+    prev_plan = p;
+  }
+  if (lambda_out) *lambda_out = lambda;
+  return TS_OK;
+}
+
 ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, ts_plan** out);
 void plan_free(ts_plan* p);
 

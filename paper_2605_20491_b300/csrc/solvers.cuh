@@ -23,6 +23,10 @@ ts_status inverse_iteration_solve(const ts_plan* p, double shift, const double* 
 // approximated Magnus-2 (Yoshida composition), all with adjacent propagations merged.
 ts_status propagate_impl(const ts_plan* p, ts_scheme scheme, int M, double dt, int nsteps, const double* VB,
                          void* psi, ts_dtype dtype, ts_precision prec, int* a_props, cudaStream_t s);
+ts_status inverse_iteration_multilevel_impl(const ts_plan* const* plans, const double* const* V2, int levels,
+                                            double shift, double* u, double tol_lambda, int maxit, double pcg_tol,
+                                            int pcg_maxit, ts_precision prec, double* lambda_out, int* outer,
+                                            long long* pcg, cudaStream_t s);
 ts_status gpe_ground_state_impl(const ts_plan* p, const double* V2, double beta, ts_gpe_flow flow, double alpha,
                                 double tau, double* u, double tol_energy, double tol_residual, int maxit,
                                 ts_precision prec, double pcg_tol, double* energy_out, double* lambda_out,

@@ -32,7 +32,8 @@ EXPORTS = [
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
     "ts_tc_config_set", "ts_autotune", "ts_device_status", "ts_selftest_wait_timeout", "ts_launch_count", "ts_profile_begin", "ts_profile_end",
-    "ts_propagate", "ts_gpe_ground_state", "ts_last_error", "ts_version",
+    "ts_propagate", "ts_gpe_ground_state", "ts_interpolate", "ts_inverse_iteration_multilevel",
+    "ts_last_error", "ts_version",
 ]
 
 
@@ -104,6 +105,9 @@ def lib() -> C.CDLL:
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
     L.ts_propagate.argtypes = [vp, ip, ip, dp, ip, vp, vp, ip, ip, C.POINTER(ip), vp]
     L.ts_grid_nodes.argtypes = [ip, dp, ip, C.POINTER(dp), C.POINTER(dp)]
+    L.ts_interpolate.argtypes = [vp, vp, vp, vp, vp]
+    L.ts_inverse_iteration_multilevel.argtypes = [C.POINTER(vp), C.POINTER(vp), ip, dp, vp, dp, ip, dp, ip, ip,
+                                                  C.POINTER(dp), C.POINTER(ip), C.POINTER(C.c_longlong), vp]
     L.ts_gpe_ground_state.argtypes = [vp, vp, dp, ip, dp, dp, vp, dp, dp, ip, ip, dp, C.POINTER(dp), C.POINTER(dp),
                                       C.POINTER(dp), C.POINTER(ip), C.POINTER(C.c_longlong), vp]
     L.ts_device_status.argtypes = [vp]
@@ -354,6 +358,27 @@ def ts_propagate(plan: Plan, scheme: int, M: int, dt: float, nsteps: int, VB, ps
     _check(lib().ts_propagate(plan.handle, int(scheme), int(M), float(dt), int(nsteps), _ptr(VB), _ptr(psi), dtype,
                               prec, C.byref(na), _stream(stream)), "ts_propagate")
     return na.value
+
+
+def ts_interpolate(coarse: Plan, uc, fine: Plan, uf, stream=None):
+    _check(lib().ts_interpolate(coarse.handle, _ptr(uc), fine.handle, _ptr(uf), _stream(stream)), "ts_interpolate")
+
+
+def ts_inverse_iteration_multilevel(plans, V2s, shift: float, u, tol_lambda: float = 1e-12, maxit: int = 200,
+                                    pcg_tol: float = 1e-12, pcg_maxit: int = 500, precond: int = TS_FP64,
+                                    stream=None):
+    """Returns (lambda, [outer iterations per level], [PCG iterations per level]); u (finest
+    grid) receives the eigenvector."""
+    lv = len(plans)
+    P = (C.c_void_p * lv)(*[p.handle.value if isinstance(p.handle, C.c_void_p) else p.handle for p in plans])
+    V = (C.c_void_p * lv)(*[None if v is None else v.data_ptr() for v in (V2s if V2s is not None else [None] * lv)])
+    lam = C.c_double()
+    outer = (C.c_int * lv)()
+    pcg = (C.c_longlong * lv)()
+    _check(lib().ts_inverse_iteration_multilevel(P, V, lv, float(shift), _ptr(u), float(tol_lambda), int(maxit),
+                                                 float(pcg_tol), int(pcg_maxit), int(precond), C.byref(lam), outer,
+                                                 pcg, _stream(stream)), "ts_inverse_iteration_multilevel")
+    return lam.value, list(outer), list(pcg)
 
 
 TS_GPE_H1, TS_GPE_AU = range(2)

@@ -228,3 +228,22 @@ def test_pcg_and_inverse_iteration_equal_dense(n, k, L):
     assert abs(lam - ev[0]) < 1e-10 * abs(ev[0])
     Hu = sem.operator(P, u, 0.0, V2)
     assert np.linalg.norm(Hu - lam * u) < 1e-6 * np.linalg.norm(Hu)
+
+
+def test_interpolation_identity_and_multilinear_exactness():
+    """Tensor-product linear interpolation is the identity onto the same grid, and exact
+    for functions linear in each variable at fine nodes between interior coarse nodes."""
+    Pc = sem.plan((9, 14), (2.0, 3.0), [np.zeros(9), np.zeros(14)], 5)
+    Pf = sem.plan((39, 23), (2.0, 3.0), [np.zeros(39), np.zeros(23)], 2)
+    xc, yc = Pc.axes[0].x, Pc.axes[1].x
+    Uc = (1.0 + 0.3 * xc[None, :]) * (2.0 - 0.7 * yc[:, None])
+    np.testing.assert_allclose(sem.interpolate(Pc, Uc.reshape(-1), Pc), Uc.reshape(-1), rtol=0, atol=1e-15)
+    Uf = sem.interpolate(Pc, Uc.reshape(-1), Pf).reshape(23, 39)
+    xf, yf = Pf.axes[0].x, Pf.axes[1].x
+    ix = (xf >= xc[0]) & (xf <= xc[-1])
+    iy = (yf >= yc[0]) & (yf <= yc[-1])
+    want = (1.0 + 0.3 * xf[None, :]) * (2.0 - 0.7 * yf[:, None])
+    np.testing.assert_allclose(Uf[np.ix_(iy, ix)], want[np.ix_(iy, ix)], rtol=1e-14, atol=1e-14)
+    # beyond the outermost coarse nodes the interpolant falls linearly to the wall's zero
+    j = np.argmax(~ix)
+    assert abs(Uf[np.argmax(iy), j]) < abs(want[np.argmax(iy), j])
