@@ -81,16 +81,22 @@ typedef struct {
                               finite-difference scheme on the uniform nodes
                               x_i = -L + (i+1) h, h = 2L/(n+1); 2..32 = Q^k spectral
                               elements with GLL quadrature, (n[k] + 1) / order elements
-                              per axis ((n[k] + 1) % order == 0 on every axis)          */
+                              per axis ((n[k] + 1) % order == 0 on every axis);
+                              -1 = the Hermite spectral method on R (Appendix app:hermite):
+                              n[k] <= 2048 Gauss-Hermite nodes, L[k] unused (must be > 0),
+                              the operator dense per axis; no interpolation               */
 } ts_plan_desc;
 
 /*
- * Interior nodes of one axis (Sec. 2): for order 0 or 1 the uniform x_i = -L + (i+1) h,
+ * Nodes of one axis (Sec. 2): for order 0 or 1 the uniform x_i = -L + (i+1) h,
  * h = 2L/(n+1); for order k >= 2 the Gauss-Lobatto-Legendre points of degree k mapped onto
  * the c = (n+1)/k equal elements of [-L, L], end points shared, the two boundary nodes
- * dropped.  x (n doubles, HOST) receives the coordinates; m (n doubles, HOST, may be NULL)
- * the lumped mass, i.e. the diagonal of the GLL mass matrix M (h for order 1).  Needs no
- * GPU.  TS_ERR_INVALID_ARG if n < 1, L <= 0, order > 32 or (n+1) % order != 0.
+ * dropped; for order -1 the n Gauss-Hermite nodes (eigenvalues of the Jacobi matrix with
+ * off-diagonal sqrt(k/2), by Sturm bisection).  x (n doubles, HOST) receives the
+ * coordinates; m (n doubles, HOST, may be NULL) the quadrature weights: the lumped mass,
+ * i.e. the diagonal of the GLL mass matrix M (h for order 1), or for order -1 the Gauss
+ * weights of Hermite functions 1/(n psi_{n-1}(x_j)^2).  Needs no GPU.  TS_ERR_INVALID_ARG if
+ * n < 1, L <= 0, order outside [-1, 32], (n+1) % order != 0, or order -1 with n > 2048.
  */
 ts_status ts_grid_nodes(int n, double L, int order, double* x, double* m);
 

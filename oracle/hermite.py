@@ -15,8 +15,9 @@ Per axis, with n nodes:
 D is similar to the skew matrix B_ij = s_i s_j / (x_i - x_j) (s = sign psi_{n-1}(x_j)) by the
 diagonal W^{1/2}, W_j = 1 / (n psi_{n-1}(x_j)^2) (the Gauss weights of Hermite functions):
 -D^2 + F = W^{-1/2} (-B^2 + F) W^{1/2}, so K is diagonalised through the symmetric
--B^2 + F = Q Lambda Q^T with T = W^{-1/2} Q, T^{-1} = Q^T W^{1/2}.  W spans e^{x^2}, so it is
-carried as log W (exponents stay below 709 for n up to ~700).
+-B^2 + F = Q Lambda Q^T with T = W^{-1/2} Q, T^{-1} = Q^T W^{1/2}.  psi_{n-1} is evaluated in
+log form (the plain recurrence underflows with e^{-x^2/2} from n ~ 745); W itself stays
+moderate, since every node lies where psi_{n-1} oscillates.
 """
 from __future__ import annotations
 

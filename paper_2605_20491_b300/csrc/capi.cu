@@ -98,9 +98,10 @@ ts_status ts_plan_create(const ts_plan_desc* desc, unsigned precision_mask, void
     TS_REQUIRE(desc->n[k] >= 1 && desc->n[k] <= 4096, "n[%d] = %d out of range [1, 4096]", k, desc->n[k]);
     TS_REQUIRE(desc->L[k] > 0.0, "L[%d] must be positive", k);
     TS_REQUIRE(desc->f[k], "f[%d] is NULL", k);
-    TS_REQUIRE(desc->order >= 0 && desc->order <= 32, "order = %d out of range [0, 32]", desc->order);
+    TS_REQUIRE(desc->order >= -1 && desc->order <= 32, "order = %d out of range [-1, 32]", desc->order);
     TS_REQUIRE(desc->order < 2 || (desc->n[k] + 1) % desc->order == 0,
                "Q^%d: n[%d] + 1 = %d is not a multiple of %d", desc->order, k, desc->n[k] + 1, desc->order);
+    TS_REQUIRE(desc->order != -1 || desc->n[k] <= 2048, "Hermite axis %d: n = %d above 2048", k, desc->n[k]);
     N *= desc->n[k];
     TS_REQUIRE(N <= (1LL << 40), "grid too large");
   }
@@ -120,7 +121,7 @@ ts_status ts_grid_nodes(int n, double L, int order, double* x, double* m) {
   TS_REQUIRE(x, "x is NULL");
   TS_REQUIRE(n >= 1 && n <= 4096, "n = %d out of range [1, 4096]", n);
   TS_REQUIRE(L > 0.0, "L must be positive");
-  TS_REQUIRE(order >= 0 && order <= 32, "order = %d out of range [0, 32]", order);
+  TS_REQUIRE(order >= -1 && order <= 32, "order = %d out of range [-1, 32]", order);
   return grid_nodes_host(n, L, order, x, m);
 }
 

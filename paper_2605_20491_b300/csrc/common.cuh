@@ -157,6 +157,12 @@ struct ts_plan {
 
 namespace ts {
 
+// Plans whose 1D operators are not the Q^1 tridiagonal: Q^k (k >= 2) and Hermite (order -1).
+// They carry a band table, M^{+-1/2} and a symmetric twin.
+inline bool banded_plan(const ts_plan* p) { return p->order >= 2 || p->order == -1; }
+// Half-width of axis k's band: k of Q^k, n_k - 1 (dense) for Hermite.
+inline int band_halfwidth(const ts_plan* p, int k) { return p->order == -1 ? p->n[k] - 1 : p->order; }
+
 // Device-side helpers implemented in the .cu files.
 AxisParams axis_params(const ts_plan* p, bool eig_tables);
 

@@ -149,11 +149,21 @@ ts_status build_axis(const AxisKey& key, cudaStream_t s, std::shared_ptr<AxisTab
   t->f = key.f;
   t->order = key.order;
   t->frame = key.frame;
-  const bool sem = key.order >= 2;
+  const bool hermite = key.order == ORDER_HERMITE;
+  const bool sem = key.order >= 2 || hermite;  // a diagonal M other than h I, and a band table
   std::vector<double> H((size_t)n * n, 0.0);
   SemAxis ax;
-  std::vector<double> rh(n, 1.0), rhi(n, 1.0);  // M^{1/2}, M^{-1/2} (Q^k only)
-  if (!sem) {
+  HermiteAxis hx;
+  std::vector<double> rh(n, 1.0), rhi(n, 1.0);  // M^{1/2}, M^{-1/2} (Q^k, Hermite)
+  if (hermite) {
+    // -D^2 + F = W^{-1/2} (-B^2 + F) W^{1/2} (W: the Gauss weights of Hermite functions)
+    TS_TRY(hermite_axis_build(n, &hx));
+    for (int i = 0; i < n; ++i) {
+      rh[i] = std::exp(0.5 * hx.log_w[i]);
+      rhi[i] = std::exp(-0.5 * hx.log_w[i]);
+      for (int j = 0; j < n; ++j) H[(size_t)i * n + j] = hx.hs0[(size_t)i * n + j] + (i == j ? key.f[i] : 0.0);
+    }
+  } else if (!sem) {
     const double h = 2.0 * key.L / (n + 1);
     const double ih2 = 1.0 / (h * h);
     for (int i = 0; i < n; ++i) {
@@ -186,13 +196,20 @@ ts_status build_axis(const AxisKey& key, cudaStream_t s, std::shared_ptr<AxisTab
       Sth[(size_t)j * n + i] = fold ? rhi[i] * q : q;
       t->S_host[(size_t)i * n + j] = key.frame == 0 ? rhi[i] * q : q;
     }
-  // Q^k: the band of K = M^{-1} Stiff (frame 0) or M^{-1/2} Stiff M^{-1/2} (frame 1)
-  const int bw = sem ? 2 * key.order + 1 : 0;
+  // the band of K = M^{-1} Stiff (frame 0) or M^{-1/2} Stiff M^{-1/2} (frame 1); Hermite: K is
+  // dense (half-width n - 1), -D^2 = W^{-1/2} (-B^2) W^{1/2} in frame 0 and -B^2 in frame 1
+  const int hw = hermite ? n - 1 : key.order;
+  const int bw = sem ? 2 * hw + 1 : 0;
   std::vector<double> band((size_t)n * bw, 0.0);
   for (int i = 0; i < n && sem; ++i)
     for (int o = 0; o < bw; ++o) {
-      const int j = i + o - key.order;
+      const int j = i + o - hw;
       if (j < 0 || j >= n) continue;
+      if (hermite) {
+        const double a = hx.hs0[(size_t)i * n + j];
+        band[(size_t)i * bw + o] = key.frame == 0 ? std::exp(0.5 * (hx.log_w[j] - hx.log_w[i])) * a : a;
+        continue;
+      }
       const double a = ax.stiff[(size_t)i * n + j];
       band[(size_t)i * bw + o] = key.frame == 0 ? a / ax.m[i] : rhi[i] * a * rhi[j];
     }
@@ -277,7 +294,7 @@ ts_status plan_create_frame(const ts_plan_desc* desc, unsigned mask, int frame, 
 
 ts_status plan_create(const ts_plan_desc* desc, unsigned mask, cudaStream_t s, ts_plan** out) {
   TS_TRY(plan_create_frame(desc, mask, 0, s, out));
-  if ((*out)->order >= 2) {  // the symmetric frame used by PCG and inverse iteration
+  if (banded_plan(*out)) {  // the symmetric frame used by PCG and inverse iteration
     const ts_status st = plan_create_frame(desc, mask, 1, s, &(*out)->sym);
     if (st != TS_OK) {
       plan_free(*out);
@@ -301,7 +318,7 @@ ts_status plan_create_frame(const ts_plan_desc* desc, unsigned mask, int frame, 
   p->d = desc->d;
   p->N = 1;
   p->precision_mask = mask | 1u;
-  p->order = desc->order >= 2 ? desc->order : 1;
+  p->order = desc->order >= 2 || desc->order == ORDER_HERMITE ? desc->order : 1;
   for (int k = 0; k < p->d; ++k) {
     p->n[k] = desc->n[k];
     p->L[k] = desc->L[k];
@@ -309,7 +326,7 @@ ts_status plan_create_frame(const ts_plan_desc* desc, unsigned mask, int frame, 
     if (desc->n[k] > p->nmax) p->nmax = desc->n[k];
   }
   for (int k = 0; k < p->d && st == TS_OK; ++k) {
-    st = get_axis(p->device, p->n[k], p->L[k], desc->f[k], p->order, p->order >= 2 ? frame : 0, s, &p->axis[k]);
+    st = get_axis(p->device, p->n[k], p->L[k], desc->f[k], p->order, banded_plan(p) ? frame : 0, s, &p->axis[k]);
     if (st != TS_OK) break;
     AxisTables* t = p->axis[k].get();
     p->S[k] = t->S;

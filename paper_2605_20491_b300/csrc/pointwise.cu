@@ -617,7 +617,8 @@ __global__ void k_scale_by_scalar(const double* num, const double* den, double* 
 
 // Per-axis band tables of a Q^k plan (k >= 2), by value.
 struct BandParams {
-  int d, w;                   // dimension, half bandwidth (= k)
+  int d;
+  int w[MAXD];                // half bandwidth per axis (k of Q^k; n - 1 for Hermite)
   int n[MAXD];
   long long stride[MAXD];
   const double* band[MAXD];   // n[k] rows of 2w + 1: band[i][o] = K[i][i + o - w]
@@ -635,7 +636,7 @@ template <int MODE, int NP>
 __global__ void k_banded(BandParams a, const double* __restrict__ V2, double sigma, const double* __restrict__ x,
                          const double* __restrict__ b, double* __restrict__ y, __nv_bfloat16* __restrict__ planes,
                          long long N, double* partial) {
-  const int n0 = a.n[0], w = a.w, bw = 2 * a.w + 1;
+  const int n0 = a.n[0], w = a.w[0], bw = 2 * a.w[0] + 1;
   int G = 1;
   while (G < n0 && G < 32) G <<= 1;
   const int rows_per_warp = 32 / G;
@@ -668,10 +669,11 @@ __global__ void k_banded(BandParams a, const double* __restrict__ V2, double sig
         for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + o - w], ax);
       }
       for (int k = 1; k < a.d; ++k) {
-        const double* B = a.band[k] + (long long)ik[k] * bw;
-        const int lo = ik[k] - w < 0 ? w - ik[k] : 0, hi = ik[k] + w >= a.n[k] ? w + a.n[k] - 1 - ik[k] : 2 * w;
+        const int wk = a.w[k];
+        const double* B = a.band[k] + (long long)ik[k] * (2 * wk + 1);
+        const int lo = ik[k] - wk < 0 ? wk - ik[k] : 0, hi = ik[k] + wk >= a.n[k] ? wk + a.n[k] - 1 - ik[k] : 2 * wk;
         const long long st = a.stride[k];
-        for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + (o - w) * st], ax);
+        for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + (o - wk) * st], ax);
       }
       if (MODE == 0) {
         y[idx] = ax;
@@ -885,9 +887,9 @@ namespace {
 BandParams band_params(const ts_plan* p) {
   BandParams a{};
   a.d = p->d;
-  a.w = p->order;
   long long st = 1;
   for (int k = 0; k < p->d; ++k) {
+    a.w[k] = band_halfwidth(p, k);
     a.n[k] = p->n[k];
     a.stride[k] = st;
     st *= p->n[k];
@@ -949,6 +951,10 @@ ts_status axpy2(long long N, double* u, double a, const double* x, double b, con
 
 ts_status interpolate(const ts_plan* pc, const double* uc, const ts_plan* pf, double* uf, cudaStream_t s) {
   TS_REQUIRE(pc->d == pf->d, "interpolation needs grids of one dimension (%d, %d)", pc->d, pf->d);
+  if (pc->order == -1 || pf->order == -1) {
+    set_error("interpolation between grids of bounded boxes only (not Hermite grids on R^d)");
+    return TS_ERR_UNSUPPORTED;
+  }
   const int d = pc->d;
   for (int k = 0; k < d; ++k)
     TS_REQUIRE(pc->L[k] == pf->L[k], "interpolation needs the same box (axis %d: L = %g, %g)", k, pc->L[k], pf->L[k]);
@@ -1019,7 +1025,7 @@ ts_status scale_separable(const ts_plan* p, bool inverse, const double* x, doubl
 ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
                         double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  if (p->order >= 2)
+  if (banded_plan(p))
     k_banded<0, 2><<<g, 256, 0, s>>>(band_params(p), V2, sigma, x, nullptr, y, nullptr, p->N, partial);
   else
   k_stencil<0, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, nullptr, y, nullptr, p->N, partial);
@@ -1034,7 +1040,7 @@ ts_status stencil_apply(const ts_plan* p, const double* V2, double sigma, const 
 ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, const double* x, const double* b,
                            double* r, double* partial, double* out2, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  if (p->order >= 2)
+  if (banded_plan(p))
     k_banded<1, 2><<<g, 256, 0, s>>>(band_params(p), V2, sigma, x, b, r, nullptr, p->N, partial);
   else
     k_stencil<1, 2><<<g, 256, 0, s>>>(axis_params(p, false), V2, sigma, x, b, r, nullptr, p->N, partial);
@@ -1047,7 +1053,7 @@ ts_status stencil_residual(const ts_plan* p, const double* V2, double sigma, con
 ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigma, const double* x,
                                  const double* b, __nv_bfloat16* planes, int np, double* partial, cudaStream_t s) {
   unsigned g = grid_for(p->N);
-  if (p->order >= 2) {
+  if (banded_plan(p)) {
     const BandParams a = band_params(p);
     if (np == 1)
       k_banded<2, 1><<<g, 256, 0, s>>>(a, V2, sigma, x, b, nullptr, planes, p->N, partial);
@@ -1066,7 +1072,7 @@ ts_status stencil_residual_split(const ts_plan* p, const double* V2, double sigm
 }
 
 bool isotropic_h(const ts_plan* p) {
-  if (p->order >= 2) return false;  // Q^k nodes are not equally spaced
+  if (banded_plan(p)) return false;  // Q^k and Hermite nodes are not equally spaced
   for (int k = 1; k < p->d; ++k)
     if (2.0 * p->L[k] / (p->n[k] + 1) != 2.0 * p->L[0] / (p->n[0] + 1)) return false;
   return true;

@@ -132,7 +132,100 @@ ts_status sem_axis_build(int n, double L, int k, SemAxis* out) {
   return TS_OK;
 }
 
+// ---------------------------------------------------------------- Hermite functions ------
+
+// Eigenvalues of the symmetric tridiagonal Jacobi matrix of the Hermite functions
+// (J_kk = 0, J_{k,k+1} = sqrt(k/2)): the Gauss-Hermite nodes (Golub-Welsch), found by
+// bisection on the Sturm-sequence count (Golub & Van Loan, Matrix Computations, Sec. 8.4):
+// the number of eigenvalues below t is the number of negative terms of
+// q_1 = -t, q_k = -t - b_{k-1}^2 / q_{k-1}.
+void hermite_nodes(int n, double* x) {
+  auto count_below = [n](double t) {
+    int c = 0;
+    double q = 1.0;
+    for (int k = 0; k < n; ++k) {
+      const double b2 = k == 0 ? 0.0 : 0.5 * k;  // b_k^2 = k / 2
+      q = -t - (k == 0 ? 0.0 : b2 / q);
+      if (q == 0.0) q = -1e-300;
+      c += q < 0.0;
+    }
+    return c;
+  };
+  const double R = std::sqrt(2.0 * n + 1.0) + 1.0;  // Gershgorin-type bound on |x|
+  for (int j = 0; j < n; ++j) {
+    double lo = -R, hi = R;  // count_below(lo) <= j < count_below(hi)
+    for (int it = 0; it < 200 && hi - lo > 4e-16 * (std::fabs(lo) + std::fabs(hi)) + 1e-300; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (count_below(mid) > j)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    x[j] = 0.5 * (lo + hi);
+  }
+}
+
+ts_status hermite_axis_build(int n, HermiteAxis* out) {
+  if (n < 1 || n > HERMITE_MAX_N) {
+    set_error("Hermite axis: n = %d out of range [1, %d]", n, HERMITE_MAX_N);
+    return TS_ERR_INVALID_ARG;
+  }
+  out->n = n;
+  out->x.resize(n);
+  hermite_nodes(n, out->x.data());
+  // log |psi_{n-1}(x_j)| and its sign: psi_m = p_m e^{-x^2/2} with the normalised recurrence
+  // p_0 = pi^{-1/4}, p_1 = sqrt(2) x p_0, p_{m+1} = sqrt(2/(m+1)) x p_m - sqrt(m/(m+1)) p_{m-1},
+  // rescaled whenever |p| exceeds 1e100, so that neither p nor e^{-x^2/2} (which underflows
+  // for |x| > ~38, i.e. from n ~ 745 in the plain recurrence) leaves the FP64 range.
+  std::vector<double> sg(n);
+  out->log_w.resize(n);
+  for (int j = 0; j < n; ++j) {
+    const double xj = out->x[j];
+    double p0 = std::pow(M_PI, -0.25), p1 = std::sqrt(2.0) * xj * p0, lg = 0.0;
+    if (n == 1) p1 = p0;
+    for (int m = 1; m < n - 1; ++m) {
+      const double p2 = std::sqrt(2.0 / (m + 1)) * xj * p1 - std::sqrt(m / (m + 1.0)) * p0;
+      p0 = p1;
+      p1 = p2;
+      if (std::fabs(p1) > 1e100) {
+        p0 *= 1e-100;
+        p1 *= 1e-100;
+        lg += 100.0 * std::log(10.0);
+      }
+    }
+    const double log_psi = std::log(std::fabs(p1)) + lg - 0.5 * xj * xj;
+    sg[j] = p1 < 0.0 ? -1.0 : 1.0;
+    out->log_w[j] = -std::log((double)n) - 2.0 * log_psi;  // W_j = 1 / (n psi_{n-1}(x_j)^2)
+  }
+  // the skew B_ij = s_i s_j / (x_i - x_j) with W^{1/2} D W^{-1/2} = B, and -B^2
+  std::vector<double> B((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (i != j) B[(size_t)i * n + j] = sg[i] * sg[j] / (out->x[i] - out->x[j]);
+  out->hs0.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j) {
+      double acc = 0.0;
+      for (int q = 0; q < n; ++q) acc -= B[(size_t)i * n + q] * B[(size_t)q * n + j];
+      out->hs0[(size_t)i * n + j] = out->hs0[(size_t)j * n + i] = acc;
+    }
+  return TS_OK;
+}
+
 ts_status grid_nodes_host(int n, double L, int order, double* x, double* m) {
+  if (order == ORDER_HERMITE) {
+    if (n < 1 || n > HERMITE_MAX_N) {
+      set_error("Hermite axis: n = %d out of range [1, %d]", n, HERMITE_MAX_N);
+      return TS_ERR_INVALID_ARG;
+    }
+    hermite_nodes(n, x);
+    if (m) {
+      HermiteAxis ax;
+      TS_TRY(hermite_axis_build(n, &ax));
+      for (int i = 0; i < n; ++i) m[i] = std::exp(ax.log_w[i]);
+    }
+    return TS_OK;
+  }
   if (order < 2) {
     const double h = 2.0 * L / (n + 1);
     for (int i = 0; i < n; ++i) {

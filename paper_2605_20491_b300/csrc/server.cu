@@ -434,8 +434,8 @@ ts_status ts_server_submit(ts_server* sv, const ts_request* r, long long* ticket
   auto jp = std::make_shared<Job>();
   jp->req = *r;
   jp->key.d = r->grid.d;
-  TS_REQUIRE(r->grid.order >= 0 && r->grid.order <= 32, "bad order %d", r->grid.order);
-  jp->key.order = r->grid.order >= 2 ? r->grid.order : 1;
+  TS_REQUIRE(r->grid.order >= -1 && r->grid.order <= 32, "bad order %d", r->grid.order);
+  jp->key.order = r->grid.order >= 2 || r->grid.order == -1 ? r->grid.order : 1;
   long long N = 1;
   for (int k = 0; k < r->grid.d; ++k) {
     TS_REQUIRE(r->grid.n[k] >= 1 && r->grid.n[k] <= 4096 && r->grid.L[k] > 0 && r->grid.f[k], "bad axis %d", k);
