@@ -104,3 +104,29 @@ def test_paper_table_h1_flow(T, beta, E_printed, lam_printed, prec):
     E, lam, it2, _, res = T.ts_gpe_ground_state(P, None, beta, T.TS_GPE_H1, u, 20.0, 0.1, 0.0, 1e-11, 20000, p)
     print(f"beta {beta}: lambda {lam!r} after {it2} more steps, residual {res:.2e}")
     assert abs(E - E_printed) < 1e-9 and abs(lam - lam_printed) < 1e-8
+
+
+@pytest.mark.parametrize("flow,tau,steps_printed,solves_printed", [("au", 1.0, 66, 790), ("h1", 0.1, 272, 544)])
+def test_paper_table_au_vs_h1_beta1600(T, flow, tau, steps_printed, solves_printed):
+    """Table au_vs_h1: beta = 1600, constant initial guess, Q^20 on [-8, 8]^3, V1 of eq.
+    separable_V1, alpha = 20; a_u with tau = 1 and PCG (preconditioner (-Delta + V1)^{-1},
+    tolerance 1e-12), modified H^1 with tau = 0.1, both until |E_k - E*| / E* < 1e-12 with
+    E* = 33.80227900547423 (the table's criterion).  n = 199 (the table: 599) already reaches
+    E* to that tolerance; the step and linear-solve counts agree with the table's within
+    15% (a_u: 66 steps, 790 PCG iterations; H^1: 272 steps, 544 direct solves)."""
+    import torch
+    Estar = 33.80227900547423
+    P, _ = _paper_grid(T, 199, 1 << T.TS_BF16X3)
+    u = torch.ones(P.N, dtype=torch.float64, device="cuda")
+    f = T.TS_GPE_AU if flow == "au" else T.TS_GPE_H1
+    steps = solves = 0
+    while True:  # in chunks of 5 steps, to apply the table's criterion with E* known
+        E, lam, it, so, _ = T.ts_gpe_ground_state(P, None, 1600.0, f, u, 20.0, tau, 0.0, 0.0, 5, T.TS_BF16X3,
+                                                  pcg_tol=1e-12, allow_not_converged=True)
+        steps, solves = steps + it, solves + so
+        if abs(E - Estar) < 1e-12 * Estar or steps > 2000:
+            break
+    print(f"{flow}: {steps} steps, {solves} solves, E = {E!r}")
+    assert abs(E - Estar) < 1e-12 * Estar
+    assert abs(steps - steps_printed) <= 0.15 * steps_printed
+    assert abs(solves - solves_printed) <= 0.15 * solves_printed
