@@ -618,6 +618,7 @@ __global__ void k_scale_by_scalar(const double* num, const double* den, double* 
 // Per-axis band tables of a Q^k plan (k >= 2), by value.
 struct BandParams {
   int d;
+  int order;                  // k of Q^k (>= 2), or -1 (Hermite: dense rows)
   int w[MAXD];                // half bandwidth per axis (k of Q^k; n - 1 for Hermite)
   int n[MAXD];
   long long stride[MAXD];
@@ -669,9 +670,20 @@ __global__ void k_banded(BandParams a, const double* __restrict__ V2, double sig
         for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + o - w], ax);
       }
       for (int k = 1; k < a.d; ++k) {
+        // the row index is the same for all lanes here, so the element structure of Q^k is
+        // used to skip the band's structural zeros: node g = i + 1 at position p = g mod k of
+        // its element couples to that element's k + 1 nodes only (o in [k - p, 2k - p]) unless
+        // it is a shared element end (p = 0: both elements, the full band)
         const int wk = a.w[k];
         const double* B = a.band[k] + (long long)ik[k] * (2 * wk + 1);
-        const int lo = ik[k] - wk < 0 ? wk - ik[k] : 0, hi = ik[k] + wk >= a.n[k] ? wk + a.n[k] - 1 - ik[k] : 2 * wk;
+        int lo = ik[k] - wk < 0 ? wk - ik[k] : 0, hi = ik[k] + wk >= a.n[k] ? wk + a.n[k] - 1 - ik[k] : 2 * wk;
+        if (a.order >= 2) {
+          const int pos = (ik[k] + 1) % a.order;
+          if (pos != 0) {
+            lo = max(lo, a.order - pos);
+            hi = min(hi, 2 * a.order - pos);
+          }
+        }
         const long long st = a.stride[k];
         for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + (o - wk) * st], ax);
       }
@@ -887,6 +899,7 @@ namespace {
 BandParams band_params(const ts_plan* p) {
   BandParams a{};
   a.d = p->d;
+  a.order = p->order;
   long long st = 1;
   for (int k = 0; k < p->d; ++k) {
     a.w[k] = band_halfwidth(p, k);
