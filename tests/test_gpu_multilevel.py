@@ -95,3 +95,16 @@ def test_paper_coulomb_ground_state_4d(T, delta, lam_printed):
                                                         500, T.TS_BF16X3)
     print(f"coulomb delta {delta}: lambda {lam!r}, outer {outer}, pcg {pcg}")
     assert abs(lam - lam_printed) < 1e-11
+
+
+def test_paper_pcg_precond_iterations(T):
+    """Table pcg_precond: PCG on (-Delta + V1 + V2) u = f, the 4D Coulomb system with
+    delta = 0.01 on 49^4 Q^10, random f, tolerance 1e-12, FP64, preconditioner
+    (-Delta + V1)^{-1}: 24 iterations (the comparison preconditioners are other methods)."""
+    import torch
+    P, V2 = _coulomb_level(T, 49, 0.01)
+    f = torch.from_numpy(np.random.default_rng(7).standard_normal(P.N)).cuda()
+    x = torch.zeros_like(f)
+    _, it, relres = T.ts_pcg(P, 0.0, 0.0, V2, f, x, 1e-12, 500, T.TS_FP64)
+    print(f"pcg_precond: {it} iterations, relres {relres:.2e}")
+    assert relres < 1e-11 and abs(it - 24) <= 3

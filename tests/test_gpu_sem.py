@@ -192,6 +192,13 @@ def test_paper_inverse_iteration_eigenvalue_q10(T):
     u = dev(np.zeros(n ** 3))
     lam, outer, _ = T.ts_inverse_iteration(P, 0.9 * _lam_min(T, P, 3), None, u, True, 1e-12, 100, 1e-12, 50)
     assert abs(lam - 23.2878438176) < 5e-11
+    assert outer == 1  # from the tensor product of the axes' ground states, exact for separable V1
+    # from a constant start (the table's iteration count, 9 on every grid)
+    u = dev(np.ones(n ** 3))
+    lam, outer, _ = T.ts_inverse_iteration(P, 0.9 * _lam_min(T, P, 3), None, u, False, 1e-12, 100, 1e-12, 50)
+    print(f"inverse_iter from a constant: {outer} outer iterations (table: 9)")
+    assert abs(lam - 23.2878438176) < 5e-11
+    assert abs(outer - 9) <= 1
 
 
 def test_paper_multilevel_eigenvalue_stirrer_q20(T):
