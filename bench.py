@@ -213,6 +213,18 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         print("profile case done", flush=True)
         return 0
+    if args.workload == "3d_q2_n1099_table1":
+        # the Q^k banded operator (k_banded) alone: Q^20 on 299^3 (213 MB per vector)
+        n, k = args.profile_n or 299, 20
+        x, _ = T.ts_grid_nodes(n, 8.0, k)
+        P = T.ts_plan_create((n,) * 3, (8.0,) * 3, [x ** 2] * 3, 0, order=k)
+        u = torch.from_numpy(synth.normal(2, P.N)).cuda()
+        y = torch.empty_like(u)
+        for _ in range(args.warmup + args.steps):
+            T.ts_apply_operator(P, 0.5, None, u, y)
+        torch.cuda.synchronize()
+        print("profile case done", flush=True)
+        return 0
     if args.workload in ("6d_n24_strang", "9d_n8_strang"):
         w = synth.WORKLOADS[args.workload]
         n, L = w["n"], w["L"]
@@ -674,11 +686,11 @@ def run_ours(args):
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu captures in
-# profiles/k_rot_tc_bf16x3_n512.md (CTA-pair kernel): 1.0313e9 for a bf16-plane pass,
-# 1.5573e9 for the FP64-store pass of u_0 and 2.6363e9 for a u += delta pass, weighted
-# 10 : 1 : 1 as the BF16X3 passes occur in one solve of the schedule (the BF16X1 passes
-# of the last refinement are reported separately).
-TRAFFIC_PER_LAUNCH = (10 * 1.0313e9 + 1 * 1.5573e9 + 1 * 2.6363e9) / 12
+# profiles/k_rot_tc_bf16x3_n512.md (CTA-pair kernel, padded-row layout): 1.0275e9 for a
+# bf16-plane pass, 1.5571e9 for the FP64-store pass of u_0 and 2.6323e9 for a u += delta
+# pass, weighted 10 : 1 : 1 as the BF16X3 passes occur in one solve of the schedule (the
+# BF16X1 passes of the last refinement are reported separately).
+TRAFFIC_PER_LAUNCH = (10 * 1.0275e9 + 1 * 1.5571e9 + 1 * 2.6323e9) / 12
 
 
 def main():

@@ -619,15 +619,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rot_tc_list(const __grid_cons
 // FP64 / complex input -> planar bf16 planes [c][p][rows][ld0] (rows of axis 1, padded to
 // ld0 = n0 rounded up to a multiple of 8); x rounded to FP32 first (the planes carry at most
 // 24 bits), then split exactly in FP32.
-template <int NP, int MODE>  // MODE 0: real FP64, 1: complex128, 2: complex64
+// PADDED = false: rows need no padding (n0 % 8 == 0), element i goes to i.
+template <int NP, int MODE, bool PADDED>  // MODE 0: real FP64, 1: complex128, 2: complex64
 __global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N, int n0) {
   const int NC = MODE == 0 ? 1 : 2;
-  const int ld0 = (n0 + 7) & ~7;                // padded row (axis 1) of the planes
-  const long long Np = (N / n0) * ld0;          // plane stride
+  const int ld0 = PADDED ? (n0 + 7) & ~7 : n0;  // padded row (axis 1) of the planes
+  const long long Np = PADDED ? (N / n0) * ld0 : N;  // plane stride
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long row = i / n0;
-    const long long ip = row * ld0 + (i - row * n0);
+    long long ip = i;
+    if (PADDED) {
+      const long long row = i / n0;
+      ip = row * ld0 + (i - row * n0);
+    }
     float v[2];
     if (MODE == 0) {
       v[0] = (float)reinterpret_cast<const double*>(in)[i];
@@ -670,8 +674,11 @@ __global__ void k_split_list(const __grid_constant__ SplitList L) {
   const long long Np = (I.N / I.n0) * ld0;
   for (long long i = (long long)(blockIdx.x - I.block_begin) * blockDim.x + threadIdx.x; i < I.N;
        i += (long long)nb * blockDim.x) {
-    const long long row = i / I.n0;
-    const long long ip = row * ld0 + (i - row * I.n0);
+    long long ip = i;
+    if (ld0 != I.n0) {
+      const long long row = i / I.n0;
+      ip = row * ld0 + (i - row * I.n0);
+    }
     float v[2];
     if (I.mode == 0) {
       v[0] = (float)reinterpret_cast<const double*>(I.in)[i];
@@ -1053,10 +1060,11 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
 
 ts_status split_input(int np, ts_dtype dt, const void* in, __nv_bfloat16* planes, long long N, int n0,
                       cudaStream_t s) {
-#define TS_SPLIT(MODE)                                                   \
-  (np == 1   ? k_split_input<1, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
-   : np == 2 ? k_split_input<2, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
-             : k_split_input<3, MODE><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0))
+#define TS_SPLIT2(MODE, PAD)                                                        \
+  (np == 1   ? k_split_input<1, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
+   : np == 2 ? k_split_input<2, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
+             : k_split_input<3, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0))
+#define TS_SPLIT(MODE) (n0 % 8 == 0 ? TS_SPLIT2(MODE, false) : TS_SPLIT2(MODE, true))
   if (dt == TS_R64)
     TS_SPLIT(0);
   else if (dt == TS_C128)
@@ -1064,6 +1072,7 @@ ts_status split_input(int np, ts_dtype dt, const void* in, __nv_bfloat16* planes
   else
     TS_SPLIT(2);
 #undef TS_SPLIT
+#undef TS_SPLIT2
   TS_LAUNCHED(1);
   return TS_OK;
 }
