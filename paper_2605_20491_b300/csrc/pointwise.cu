@@ -601,10 +601,12 @@ __global__ void k_tensor_ground(AxisParams a, double* u, long long N) {
   }
 }
 
+// y = a x + b y; with b == 0, y is not read (BLAS convention): it may hold anything, e.g. a
+// recycled scratch buffer whose stale bits form NaNs.
 __global__ void k_axpby(double a, const double* x, double b, double* y, long long N) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
+    y[i] = b == 0.0 ? a * x[i] : fma(b, y[i], a * x[i]);
 }
 
 __global__ void k_scale_by_scalar(const double* num, const double* den, double* y, const double* x, long long N) {
@@ -632,7 +634,8 @@ struct BandParams {
 // y = b - A x, y.y and b.b; MODE 2: split(b - A x) into bf16 planes).  Same mapping as
 // k_stencil: G lanes walk one grid row (axis 1) with unit stride, the multi-index of the row
 // is decomposed once per row and the band rows of the other axes are the same for the whole
-// row.  d (2w + 1) FP64 multiply-adds per point.
+// row.  Structural zeros of Q^k rows are skipped on every axis: about d (k + 2) FP64
+// multiply-adds per point instead of d (2k + 1).
 template <int MODE, int NP>
 __global__ void k_banded(BandParams a, const double* __restrict__ V2, double sigma, const double* __restrict__ x,
                          const double* __restrict__ b, double* __restrict__ y, __nv_bfloat16* __restrict__ planes,
@@ -659,14 +662,15 @@ __global__ void k_banded(BandParams a, const double* __restrict__ V2, double sig
       drow += a.f[k][ik[k]];
     }
     const long long base = row * n0;
-    for (int i0 = gl; i0 < n0; i0 += G) {
+    // one node: axis-1 band entries olo..ohi (clipped to the row), then the other axes
+    auto node = [&](int i0, int olo, int ohi) {
       const long long idx = base + i0;
       double diag = drow + a.f[0][i0];
       if (V2) diag += V2[idx];
       double ax = diag * x[idx];
       {
         const double* B = a.band[0] + (long long)i0 * bw;
-        const int lo = i0 - w < 0 ? w - i0 : 0, hi = i0 + w >= n0 ? w + n0 - 1 - i0 : 2 * w;
+        const int lo = max(olo, i0 - w < 0 ? w - i0 : 0), hi = min(ohi, i0 + w >= n0 ? w + n0 - 1 - i0 : 2 * w);
         for (int o = lo; o <= hi; ++o) ax = fma(B[o], x[idx + o - w], ax);
       }
       for (int k = 1; k < a.d; ++k) {
@@ -701,6 +705,22 @@ __global__ void k_banded(BandParams a, const double* __restrict__ V2, double sig
           split_store<NP>((float)r, planes, R * ((n0 + 7) & ~7), row * ((n0 + 7) & ~7) + i0);
         }
       }
+    };
+    if (a.order >= 2) {
+      // Q^k rows in two uniform loops, so that lanes do not wait on each other: the
+      // element-interior nodes (k - 1 per element, node g = i0 + 1 at position p = g mod k)
+      // couple to their element's k + 1 nodes, band entries k - p .. 2k - p; the shared
+      // element ends (p = 0, every k-th node) to both elements, the full band.
+      const int kq = a.order;
+      const int nb = (n0 + 1) / kq - 1;  // shared element ends in the row
+      for (int j = gl; j < n0 - nb; j += G) {
+        const int i0 = j + j / (kq - 1);
+        const int pos = (i0 + 1) % kq;
+        node(i0, kq - pos, 2 * kq - pos);
+      }
+      for (int m = gl; m < nb; m += G) node((m + 1) * kq - 1, 0, 2 * w);
+    } else {
+      for (int i0 = gl; i0 < n0; i0 += G) node(i0, 0, 2 * w);
     }
   }
   if (MODE == 2) return;

@@ -137,6 +137,25 @@ def test_inverse_iteration_vs_oracle(T):
     assert np.linalg.norm(host(u) - uo) < 1e-5
 
 
+def test_inverse_iteration_on_poisoned_scratch(T):
+    """Scratch buffers come back from the pool with whatever the last user left in them:
+    here the pool is filled with NaNs by an FP64 apply of a NaN right-hand side first.  The
+    warm start w_0 = u / (lambda - s) must not read the old contents of w (0 * NaN = NaN)."""
+    n = (24, 24, 24)
+    L, f = harmonic_case(n, omega=(1, 1, 1))
+    P, Po = plans(n, L, f)
+    junk = dev(np.full(Po.N, np.nan))
+    out = dev(np.zeros(Po.N))
+    for _ in range(3):
+        T.ts_apply_inverse(P, 0.5, junk, out)  # leaves NaN in the pool's buffers
+    V2 = S.v2_cos_bumps(n, L, seed=1)
+    s = sum(l[0] for l in Po.lam) + V2.min() - 1.0
+    u = dev(np.zeros(Po.N))
+    lam, outer, tot = T.ts_inverse_iteration(P, s, dev(V2), u, True, 1e-12, 300, 1e-10, 500)
+    uo, lamo, ito, toto = O.inverse_iteration(Po, s, V2, tol_lambda=1e-12, maxit=300, pcg_tol=1e-10)
+    assert np.isfinite(lam) and abs(lam - lamo) / abs(lamo) < 1e-11
+
+
 @pytest.mark.parametrize("n,dtype", [((6,) * 6, "c128"), ((3,) * 9, "c128"), ((6,) * 6, "c64")])
 def test_strang_vs_oracle(T, n, dtype):
     d = len(n)
