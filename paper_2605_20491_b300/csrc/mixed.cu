@@ -413,9 +413,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __syncwarp();
       if (lane == 0) {
         if (PAIR)
-          tc::mbar_arrive_cluster(tc::mapa_shared(&acce[ab], 0));  // the leader reuses the buffer
+          tc::mbar_arrive_cluster_relaxed(tc::mapa_shared(&acce[ab], 0));  // the leader reuses the buffer
         else
-          tc::mbar_arrive(&acce[ab]);
+          tc::mbar_arrive_relaxed(&acce[ab]);
       }
     }
     if (!PLANES_OUT && ep.emax_out) {
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rot_tc_list(const __grid_cons
       }
       tc::tc_fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&acce[ab]);
+      if (lane == 0) tc::mbar_arrive_relaxed(&acce[ab]);
     }
     (void)emx;  // the exponent collection of the refined solve is not used by list passes
   }
