@@ -177,9 +177,7 @@ class Plan:
         return len(self.n)
 
     def close(self):
-        if self.handle:
-            ts_plan_destroy(self)
-            self.handle = C.c_void_p(None)
+        ts_plan_destroy(self)
 
     def __del__(self):
         try:
@@ -212,7 +210,11 @@ def ts_plan_create(n, L, f, precision_mask: int = 0, stream=None, bc: int = 0, o
 
 
 def ts_plan_destroy(plan: Plan):
-    _check(lib().ts_plan_destroy(plan.handle), "ts_plan_destroy")
+    """Frees the plan once: the handle is cleared first, so a later close() or garbage
+    collection of the same object does nothing."""
+    h, plan.handle = plan.handle, C.c_void_p(None)
+    if h:
+        _check(lib().ts_plan_destroy(h), "ts_plan_destroy")
 
 
 def ts_plan_eigs(plan: Plan, axis: int) -> np.ndarray:

@@ -85,3 +85,29 @@ def test_grid_nodes_on_host_match_the_oracle(built_lib):
     out = C.c_void_p()
     assert T.lib().ts_plan_create(C.byref(desc), 0, None, C.byref(out)) == T.TS_ERR_INVALID_ARG
     assert "multiple of 3" in T.ts_last_error()
+
+
+def test_plan_handle_is_freed_once(monkeypatch):
+    """ts_plan_destroy clears the Python handle, so a later close() or garbage collection of
+    the same Plan does not free the native plan a second time (a double free of the host
+    object)."""
+    import gc
+    from paper_2605_20491_b300 import tschrod as T
+    freed = []
+
+    class FakeLib:
+        def ts_plan_destroy(self, h):
+            freed.append(h.value)
+            return T.TS_OK
+
+    monkeypatch.setattr(T, "lib", lambda: FakeLib())
+    P = T.Plan(0x1234, (4, 4), (1.0, 1.0))
+    T.ts_plan_destroy(P)
+    P.close()
+    T.ts_plan_destroy(P)
+    del P
+    gc.collect()
+    Q = T.Plan(0x5678, (4,), (1.0,))
+    del Q
+    gc.collect()
+    assert freed == [0x1234, 0x5678]
