@@ -101,9 +101,23 @@ typedef struct {
 ts_status ts_grid_nodes(int n, double L, int order, double* x, double* m);
 
 /*
+ * Step 1 of Sec. 2.1 (eq. eigen_decomp) for a symmetric tridiagonal matrix, such as the Q^1
+ * operator h^-2 tridiag(-1, 2, -1) + diag f: T = Z diag(lambda) Z^T by implicit symmetric
+ * QR steps with the Wilkinson shift on the host, every rotation accumulated into Z (Golub &
+ * Van Loan, Sec. 8.3).  diag (n doubles), offdiag (n - 1 doubles; may be NULL for n = 1),
+ * lambda_host (n doubles, receives the eigenvalues ascending) and Z_host (n x n doubles,
+ * column-major: Z_host[i + n j] is component i of the unit eigenvector for lambda_j) are
+ * HOST arrays owned by the caller.  ts_plan_create uses it for Q^1 axes with n <= 192.
+ * Needs no GPU.  TS_ERR_INVALID_ARG for n < 1, NULL arrays or non-finite entries;
+ * TS_ERR_NOT_CONVERGED after 30 n + 30 QR steps.
+ */
+ts_status ts_tridiag_eig(int n, const double* diag, const double* offdiag, double* lambda_host, double* Z_host);
+
+/*
  * Step 1 of Sec. 2.1 (eq. eigen_decomp): for every axis assemble H_k = M_k^{-1} Stiff_k + F_k
  * (Q^1: h_k^-2 tridiag(-1,2,-1) + diag f_k), eigendecompose the symmetric
- * M_k^{-1/2} Stiff_k M_k^{-1/2} + F_k = Q_k Lambda_k Q_k^T in FP64 on the GPU (axes with
+ * M_k^{-1/2} Stiff_k M_k^{-1/2} + F_k = Q_k Lambda_k Q_k^T in FP64 (Q^1 axes with n <= 192:
+ * ts_tridiag_eig on the host; otherwise a dense solver on the GPU) (axes with
  * identical (n, L, f, order) share one decomposition) and keep T_k^{-1} = Q_k^T M_k^{1/2},
  * T_k = M_k^{-1/2} Q_k, lambda_k and, for every precision bit set in precision_mask
  * (bit p = 1u << ts_precision p; TS_FP64 is always built), their split low-precision
@@ -116,7 +130,10 @@ ts_status ts_grid_nodes(int n, double L, int order, double* x, double* m);
 ts_status ts_plan_create(const ts_plan_desc* desc, unsigned precision_mask, void* stream,
                          ts_plan** out);
 
-/* Frees the plan's device tables.  NULL is accepted.  No call may be using the plan. */
+/* Releases the plan.  NULL is accepted.  No call may be using the plan, and every kernel
+ * enqueued with it must have completed (synchronise the streams that used it first): its
+ * tables go back to the library's device pool, reusable at once, without a device-wide
+ * synchronisation.  Tables shared with other plans stay until the last of them is gone. */
 ts_status ts_plan_destroy(ts_plan* plan);
 
 /* Copies lambda_axis (ascending, n[axis] doubles) into HOST memory lambda_host. */

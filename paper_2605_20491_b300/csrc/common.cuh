@@ -170,6 +170,19 @@ AxisParams axis_params(const ts_plan* p, bool eig_tables);
 ts_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t s);
 void scratch_free(void* ptr, cudaStream_t s);
 
+// Device memory of the resident per-axis tables: stream-ordered allocations from a
+// per-device pool that keeps its memory mapped (release threshold unbounded), so that
+// creating and evicting tables never synchronises the device (cudaMalloc/cudaFree would
+// wait for every kernel in flight, serialising plan builders against the GPU work of
+// earlier requests).  table_free requires that no enqueued work still reads the block.
+ts_status table_alloc(void** ptr, size_t bytes, cudaStream_t s);
+void table_free(void* ptr, int device);
+
+// Eigendecomposition of a symmetric tridiagonal matrix on the host (implicit QR with the
+// Wilkinson shift): lam ascending, Z column-major n x n.  False if it did not converge.
+bool tridiag_eig_host(int n, const double* diag, const double* offdiag, double* lam, double* Z);
+constexpr int TRIDIAG_HOST_MAX = 192;  // Q^1 axes up to this length use it in plan builds
+
 // FP64 contraction pass (rotating form): see mode_fp64.cu.
 ts_status rot_pass_fp64(const double* X, double* Y, const double* B, long long R, int n, int ncomp,
                         cudaStream_t s);

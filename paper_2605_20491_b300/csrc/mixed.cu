@@ -966,8 +966,12 @@ ts_status build_split_tables(ts_plan* p, ts_precision prec, cudaStream_t s) {
       const long long cnt = (long long)t->n * t->n;
       const long long padded = (long long)t->n * ((t->n + 7) & ~7);  // rows padded to 16 bytes
       __nv_bfloat16 *bf = nullptr, *bb = nullptr;
-      TS_CHECK_CUDA(cudaMalloc(&bf, sizeof(__nv_bfloat16) * np * padded));
-      TS_CHECK_CUDA(cudaMalloc(&bb, sizeof(__nv_bfloat16) * np * padded));
+      TS_TRY(table_alloc((void**)&bf, sizeof(__nv_bfloat16) * np * padded, s));
+      const ts_status st = table_alloc((void**)&bb, sizeof(__nv_bfloat16) * np * padded, s);
+      if (st != TS_OK) {
+        table_free(bf, t->device);
+        return st;
+      }
       TS_CHECK_CUDA(cudaMemsetAsync(bf, 0, sizeof(__nv_bfloat16) * np * padded, s));
       TS_CHECK_CUDA(cudaMemsetAsync(bb, 0, sizeof(__nv_bfloat16) * np * padded, s));
       // Forward: y_j = sum_i S[i][j] x_i, K-major operand B[j][i] = S[i][j]; backward:

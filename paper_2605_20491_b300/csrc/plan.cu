@@ -6,9 +6,11 @@
 // diagonal GLL mass and H_k is similar to the symmetric M^{-1/2} Stiff M^{-1/2} + F_k =
 // Q Lambda Q^T, so T_k = M^{-1/2} Q and T_k^{-1} = Q^T M^{1/2}; the diagonal factors are
 // folded into the contraction operands, so every apply kernel runs unchanged.  Each
-// symmetric matrix is eigendecomposed in FP64 on the GPU (cuSOLVER syevd: eigenvalues
-// ascending, eigenvectors as columns); the tables stay resident on the device for every
-// later apply.
+// symmetric matrix is eigendecomposed in FP64 (eigenvalues ascending, eigenvectors as
+// columns): the tridiagonal Q^1 operator up to TRIDIAG_HOST_MAX nodes on the host by
+// implicit QR (no device synchronisation, so plan builders overlap the GPU work of others),
+// every other one on the GPU (cuSOLVER syevd).  The tables stay resident on the device for
+// every later apply, in the stream-ordered table pool.
 //
 // Axis tables are cached process-wide by (device, n, L, f): plans whose axes coincide
 // -- within one plan (isotropic grids) or across plans (a server's stream of requests on
@@ -29,16 +31,12 @@
 namespace ts {
 
 AxisTables::~AxisTables() {
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != device) cudaSetDevice(device);
-  cudaFree(block);
+  table_free(block, device);
   for (int q = 0; q < NPREC; ++q) {
-    cudaFree(Bf[q]);
-    cudaFree(Bb[q]);
+    table_free(Bf[q], device);
+    table_free(Bb[q], device);
   }
-  cudaFree(Sf32);
-  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  table_free(Sf32, device);
 }
 
 namespace {
@@ -183,7 +181,17 @@ ts_status build_axis(const AxisKey& key, cudaStream_t s, std::shared_ptr<AxisTab
         H[(size_t)i * n + j] = rhi[i] * ax.stiff[(size_t)i * n + j] * rhi[j] + (i == j ? key.f[i] : 0.0);
   }
   std::vector<double> Qcol;
-  TS_TRY(eig_on_device(n, H, t->lam_host, Qcol, s));
+  if (!sem && n <= TRIDIAG_HOST_MAX) {  // Q^1: H is tridiagonal already
+    std::vector<double> dg(n), od(n > 1 ? n - 1 : 1, 0.0);
+    for (int i = 0; i < n; ++i) dg[i] = H[(size_t)i * n + i];
+    for (int i = 0; i + 1 < n; ++i) od[i] = H[(size_t)i * n + i + 1];
+    t->lam_host.resize(n);
+    Qcol.resize((size_t)n * n);
+    if (!tridiag_eig_host(n, dg.data(), od.data(), t->lam_host.data(), Qcol.data()))
+      TS_TRY(eig_on_device(n, H, t->lam_host, Qcol, s));
+  } else {
+    TS_TRY(eig_on_device(n, H, t->lam_host, Qcol, s));
+  }
   // Qcol is column-major: Qcol[i + n j] = Q[i][j].  Forward operand S[i][j] = M^{1/2}_i Q[i][j],
   // backward operand St[j][i] = Q[i][j] M^{-1/2}_i; in frame 1 (and for Q^1) Q and Q^T.
   const bool fold = sem && key.frame == 0;
@@ -218,7 +226,7 @@ ts_status build_axis(const AxisKey& key, cudaStream_t s, std::shared_ptr<AxisTab
                oF = align256(oLam + 8ull * n), oLf = align256(oF + 8ull * n), oBand = align256(oLf + 4ull * n),
                oMh = align256(oBand + 8ull * n * bw), oMhi = align256(oMh + (sem ? 8ull * n : 0)),
                total = align256(oMhi + (sem ? 8ull * n : 0));
-  TS_CHECK_CUDA(cudaMalloc(&t->block, total));
+  TS_TRY(table_alloc(&t->block, total, s));
   t->bytes = (long long)total;
   char* b = (char*)t->block;
   t->S = (double*)(b + oS);
@@ -260,6 +268,7 @@ ts_status get_axis(int device, int n, double L, const double* f, int order, int 
   }
   std::shared_ptr<AxisTables> built;
   TS_TRY(build_axis(key, s, &built));
+  std::vector<std::shared_ptr<AxisTables>> evicted;  // destroyed after the lock is released
   std::lock_guard<std::mutex> lk(g_axis_mu);
   auto it = g_axis_map.find(key);
   if (it != g_axis_map.end()) {
@@ -271,7 +280,10 @@ ts_status get_axis(int device, int n, double L, const double* f, int order, int 
   ++g_axis_builds;
   g_axis_map[key] = built;
   g_axis_keep.push_back(built);
-  while (g_axis_keep.size() > AXIS_KEEP) g_axis_keep.pop_front();
+  while (g_axis_keep.size() > AXIS_KEEP) {
+    evicted.push_back(std::move(g_axis_keep.front()));
+    g_axis_keep.pop_front();
+  }
   for (auto m = g_axis_map.begin(); m != g_axis_map.end();)  // drop dead entries
     m = m->second.expired() ? g_axis_map.erase(m) : std::next(m);
   *out = built;

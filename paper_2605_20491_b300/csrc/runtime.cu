@@ -1,7 +1,8 @@
-// Process-wide runtime services: the kernel launch counter and live per-kernel timing
-// with CUDA events (used by the benchmark to measure the contraction kernels inside its
-// timed region without a profiler).
+// Process-wide runtime services: the kernel launch counter, live per-kernel timing with
+// CUDA events (used by the benchmark to measure the contraction kernels inside its timed
+// region without a profiler), and the device memory pool of the resident axis tables.
 #include <atomic>
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -52,6 +53,67 @@ void prof_end_launch(cudaStream_t s, void* token, int kind, double flops, double
   cudaEvent_t e1 = take_event();
   cudaEventRecord(e1, s);
   g_records.push_back({(cudaEvent_t)token, e1, kind, flops, bytes});
+}
+
+namespace {
+struct TablePools {
+  std::mutex mu;
+  std::map<int, cudaMemPool_t> pool;
+  std::map<int, cudaStream_t> release;  // an otherwise idle stream: frees complete at once
+};
+// Never destroyed: tables cached process-wide are released during static destruction.
+TablePools& table_pools() {
+  static TablePools* t = new TablePools;
+  return *t;
+}
+}  // namespace
+
+ts_status table_alloc(void** ptr, size_t bytes, cudaStream_t s) {
+  *ptr = nullptr;
+  int dev = 0;
+  TS_CHECK_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool = nullptr;
+  {
+    TablePools& tp = table_pools();
+    std::lock_guard<std::mutex> lk(tp.mu);
+    auto it = tp.pool.find(dev);
+    if (it == tp.pool.end()) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      TS_CHECK_CUDA(cudaMemPoolCreate(&pool, &props));
+      uint64_t keep = UINT64_MAX;
+      TS_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+      cudaStream_t rs = nullptr;
+      TS_CHECK_CUDA(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+      tp.pool[dev] = pool;
+      tp.release[dev] = rs;
+    } else {
+      pool = it->second;
+    }
+  }
+  const cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes > 0 ? bytes : 1, pool, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("table allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    *ptr = nullptr;
+    return TS_ERR_NO_MEMORY;
+  }
+  return TS_OK;
+}
+
+void table_free(void* ptr, int device) {
+  if (!ptr) return;
+  cudaStream_t rs = nullptr;
+  {
+    TablePools& tp = table_pools();
+    std::lock_guard<std::mutex> lk(tp.mu);
+    auto it = tp.release.find(device);
+    if (it != tp.release.end()) rs = it->second;
+  }
+  if (rs && cudaFreeAsync(ptr, rs) != cudaSuccess) cudaGetLastError();  // at exit the runtime may be gone
 }
 
 }  // namespace ts

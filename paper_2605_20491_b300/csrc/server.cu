@@ -5,8 +5,9 @@
 //     and their scratch footprint fits the device-memory budget (requests that can never
 //     fit fail with TS_ERR_NO_MEMORY); requests that arrive while others run are admitted
 //     as slots and memory free up;
-//   * plans: planner threads build each request's plan ahead of admission (overlapping the
-//     GPU work of earlier requests), from a plan cache keyed by the grid and the sampled V1
+//   * plans: four planner threads build each request's plan ahead of admission, overlapping
+//     the GPU work of earlier requests (for Q^1 axes of up to 192 nodes no step of a build
+//     synchronises the device), from a plan cache keyed by the grid and the sampled V1
 //     (n_k, L_k, f_k compared bit for bit); the per-axis eigendecompositions underneath
 //     are shared process-wide, so requests on a few distinct 1D operators rarely solve one;
 //   * batching: the inverse / exp requests admitted in one scheduling round are captured
@@ -410,9 +411,15 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   for (auto& s : sv->streams) TS_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   TS_CHECK_CUDA(cudaStreamCreateWithFlags(&sv->capture_stream, cudaStreamNonBlocking));
   TS_TRY(tc_prepare_kernels());
-  const int nplanners = 2;
+  // Planners build plans on host threads (Q^1 eigendecompositions on the host, table
+  // uploads and splits on their own streams); their streams take the highest priority, so
+  // the few small kernels of a build are scheduled ahead of queued batch work.
+  const int nplanners = 4;
+  int prio_least = 0, prio_greatest = 0;
+  TS_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
   sv->planner_streams.resize(nplanners);
-  for (auto& s : sv->planner_streams) TS_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  for (auto& s : sv->planner_streams)
+    TS_CHECK_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio_greatest));
   for (int i = 0; i < nplanners; ++i) sv->planners.emplace_back(planner_loop, sv, i);
   sv->worker = std::thread(worker_loop, sv);
   *out = sv;

@@ -379,7 +379,7 @@ ts_status build_small_tables(ts_plan* p, cudaStream_t s) {
     if (!t->Sf32) {
       const int cnt = t->n * t->n;
       float* buf = nullptr;
-      TS_CHECK_CUDA(cudaMalloc(&buf, sizeof(float) * 2 * cnt));
+      TS_TRY(table_alloc((void**)&buf, sizeof(float) * 2 * cnt, s));
       k_to_f32_table<<<(cnt + 255) / 256, 256, 0, s>>>(t->S, t->St, buf, buf + cnt, cnt);
       TS_LAUNCHED(1);
       TS_CHECK_CUDA(cudaStreamSynchronize(s));

@@ -439,10 +439,15 @@ ts_status gpe_ground_state_impl(const ts_plan* p, const double* V2, double beta,
   TS_TRY(sc_mem.get(&partial, 2 * RED_BLOCKS));
   TS_TRY(sc_mem.get(&sc, 8));
   ts_plan* p0 = nullptr;  // -Delta alone on the same grid (modified H^1 flow)
-  struct Owner {
+  struct Owner {  // the internal plan outlives every kernel that reads its tables
     ts_plan* q;
-    ~Owner() { if (q) plan_free(q); }
-  } own{nullptr};
+    cudaStream_t s;
+    ~Owner() {
+      if (!q) return;
+      cudaStreamSynchronize(s);
+      plan_free(q);
+    }
+  } own{nullptr, s};
   if (flow == TS_GPE_H1) {
     std::vector<std::vector<double>> zeros(p->d);
     std::vector<const double*> fz(p->d);

@@ -27,7 +27,7 @@ TS_MAX_DIM = 12
 
 #: Every extern "C" symbol that include/tschrod.h declares.
 EXPORTS = [
-    "ts_grid_nodes", "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
+    "ts_grid_nodes", "ts_tridiag_eig", "ts_plan_create", "ts_plan_destroy", "ts_plan_eigs", "ts_plan_eigvecs", "ts_plan_shape", "ts_plan_bytes",
     "ts_apply_inverse", "ts_apply_inverse_noalloc", "ts_solve_refined", "ts_solve_schedule", "ts_apply_batch", "ts_apply_exp", "ts_apply_operator", "ts_pcg", "ts_inverse_iteration", "ts_split_step",
     "ts_server_create", "ts_server_submit", "ts_server_wait", "ts_server_drain", "ts_server_stats",
     "ts_server_reset_stats", "ts_server_destroy",
@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
     L.ts_split_step.argtypes = [vp, dp, ip, vp, vp, ip, ip, vp]
     L.ts_propagate.argtypes = [vp, ip, ip, dp, ip, vp, vp, ip, ip, C.POINTER(ip), vp]
     L.ts_grid_nodes.argtypes = [ip, dp, ip, C.POINTER(dp), C.POINTER(dp)]
+    L.ts_tridiag_eig.argtypes = [ip, C.POINTER(dp), C.POINTER(dp), C.POINTER(dp), C.POINTER(dp)]
     L.ts_interpolate.argtypes = [vp, vp, vp, vp, vp]
     L.ts_inverse_iteration_multilevel.argtypes = [C.POINTER(vp), C.POINTER(vp), ip, dp, vp, dp, ip, dp, ip, ip,
                                                   C.POINTER(dp), C.POINTER(ip), C.POINTER(C.c_longlong), vp]
@@ -195,6 +196,19 @@ def ts_grid_nodes(n: int, L: float, order: int = 1):
     return x, m
 
 
+def ts_tridiag_eig(diag, offdiag):
+    """Eigenvalues (ascending) and unit eigenvectors (columns) of the symmetric tridiagonal
+    matrix with this diagonal and off-diagonal, on the host: (lam, Z) with T = Z diag(lam) Z^T."""
+    a = np.ascontiguousarray(np.asarray(diag, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(offdiag, dtype=np.float64))
+    n = a.size
+    lam, Zc = np.empty(n), np.empty((n, n))  # Zc[j] = eigenvector j (column-major Z)
+    P = C.POINTER(C.c_double)
+    _check(lib().ts_tridiag_eig(C.c_int(n), a.ctypes.data_as(P), b.ctypes.data_as(P) if b.size else None,
+                                lam.ctypes.data_as(P), Zc.ctypes.data_as(P)), "ts_tridiag_eig")
+    return lam, Zc.T.copy()
+
+
 def ts_plan_create(n, L, f, precision_mask: int = 0, stream=None, bc: int = 0, order: int = 1) -> Plan:
     """order = k of Q^k (1: finite differences on uniform nodes; >= 2: spectral elements,
     f sampled at ts_grid_nodes(n_k, L_k, order))."""
@@ -211,9 +225,13 @@ def ts_plan_create(n, L, f, precision_mask: int = 0, stream=None, bc: int = 0, o
 
 def ts_plan_destroy(plan: Plan):
     """Frees the plan once: the handle is cleared first, so a later close() or garbage
-    collection of the same object does nothing."""
+    collection of the same object does nothing.  The device is synchronised first, since a
+    Python object may be collected while kernels that read its tables are still queued."""
     h, plan.handle = plan.handle, C.c_void_p(None)
     if h:
+        import torch
+        if torch.cuda.is_initialized():
+            torch.cuda.synchronize()
         _check(lib().ts_plan_destroy(h), "ts_plan_destroy")
 
 

@@ -46,6 +46,7 @@ def test_binding_lists_every_declared_symbol():
 def test_version_and_error_string_without_gpu(built_lib):
     from paper_2605_20491_b300 import tschrod
     assert "sm_103a" in tschrod.ts_version()
+    assert tschrod.lib().ts_plan_destroy(None) == tschrod.TS_OK  # a successful call clears the message
     assert tschrod.ts_last_error() == ""
 
 
