@@ -210,3 +210,36 @@ def test_operator_fixed_point_vs_oracle(T, n):
         y = dev(np.zeros(Po.N))
         T.ts_apply_operator(P, 0.3, dev(V2), dev(x), y)
         assert rel(host(y), O.stencil(Po, x, 0.3, V2)) < 1e-14
+
+
+def test_axis_tables_evicted_and_reused(T):
+    """More distinct axes than the process-wide axis cache keeps (128): 60 plans of three
+    fresh axes each (Q^1, host tridiagonal QR), each destroyed after use, so evicted tables
+    go back to the table pool and later plans reuse their memory.  Every plan's FP64 and
+    BF16X3 inverse still matches the oracle, and two plans built on identical axes (one
+    before and one after the evictions) give identical results."""
+    n, L = (12, 9, 7), (8.0, 8.0, 8.0)
+    rng = np.random.default_rng(11)
+    b = S.normal(3, int(np.prod(n)))
+    f_first = None
+    u_first = None
+    for i in range(60):
+        om = tuple(rng.uniform(0.5, 2.0, 3))
+        f = S.harmonic(n, L, om)
+        if i == 0:
+            f_first = f
+        P, Po = plans(n, L, f, 1 << T.TS_BF16X3)
+        u = dev(np.zeros(Po.N))
+        T.ts_apply_inverse(P, 0.7, dev(b), u)
+        if i == 0:
+            u_first = host(u)
+        if i % 6 == 0:
+            ref = O.apply_inverse(Po, 0.7, b)
+            assert rel(host(u), ref) < TOL
+            T.ts_apply_inverse(P, 0.7, dev(b), u, T.TS_BF16X3)
+            assert rel(host(u), ref) < 1e-4
+        T.ts_plan_destroy(P)
+    P = T.ts_plan_create(n, L, f_first, 0)
+    u = dev(np.zeros(int(np.prod(n))))
+    T.ts_apply_inverse(P, 0.7, dev(b), u)
+    assert np.array_equal(host(u), u_first)
