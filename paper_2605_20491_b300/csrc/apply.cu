@@ -1,6 +1,9 @@
 // Apply drivers: the direct inverse (steps 2-4 of Sec. 2.1) and the exact propagator
 // (eq. exact_prop), composed of d rotating contraction passes forward, the pointwise
 // eigenvalue scale or phase, and d passes backward.
+#include <mutex>
+#include <set>
+
 #include "common.cuh"
 #include "mixed.cuh"
 #include "pointwise.cuh"
@@ -8,9 +11,31 @@
 
 namespace ts {
 
+namespace {
+// The device's default pool serves the work buffers.  By default it hands freed memory
+// back at every synchronisation, so a solver that synchronises between calls (one PCG
+// solve per outer step of inverse iteration) maps its buffers afresh each time; keeping up
+// to 4 GiB of freed buffers in the pool avoids that.
+void keep_scratch_mapped() {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done.insert(dev).second) return;
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = 4ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+}
+}  // namespace
+
 ts_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t s) {
   *ptr = nullptr;
   if (bytes == 0) return TS_OK;
+  keep_scratch_mapped();
   cudaError_t e = cudaMallocAsync(ptr, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -527,6 +527,25 @@ __global__ void k_dot2(const double* __restrict__ a, const double* __restrict__ 
   }
 }
 
+// r = b - y (y = A x already in r) with partial sums of r.r and b.b.
+__global__ void k_sub_dot(const double* __restrict__ b, double* __restrict__ r, long long N, double* partial) {
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double v = bi - r[i];
+    r[i] = v;
+    s0 += v * v;
+    s1 += bi * bi;
+  }
+  s0 = block_sum(s0);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
 // Sum the partials in a fixed order; out[0], out[1] = the two sums.
 __global__ void k_sum_partials(const double* partial, int nblk, double* out) {
   double s0 = 0.0, s1 = 0.0;
@@ -1236,6 +1255,25 @@ __global__ void k_max_exponent(const double* __restrict__ x, long long N, int* o
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 }  // namespace
+
+ts_status max_exponent(const double* x, long long N, int* emax, cudaStream_t s) {
+  TS_CHECK_CUDA(cudaMemsetAsync(emax, 0, sizeof(int), s));
+  k_max_exponent<<<grid_for(N), 256, 0, s>>>(x, N, emax);
+  TS_LAUNCHED(1);
+  return TS_OK;
+}
+
+ts_status residual_fixed(const ts_plan* p, const FixedOperator& fo, const double* V2, const double* x,
+                         const double* b, double* r, int* emax, double* opart, double* partial, double* out2,
+                         cudaStream_t s) {
+  TS_TRY(max_exponent(x, p->N, emax, s));
+  TS_TRY(operator_apply_fixed(p, fo, V2, x, r, emax, opart, nullptr, s));  // r = A x
+  const unsigned g = grid_for(p->N);
+  k_sub_dot<<<g, 256, 0, s>>>(b, r, p->N, partial);
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)g, out2);
+  TS_LAUNCHED(2);
+  return TS_OK;
+}
 
 ts_status operator_apply(const ts_plan* p, const double* V2, double sigma, const double* x, double* y,
                          cudaStream_t s) {

@@ -71,6 +71,14 @@ struct FixedOperator {
 ts_status fixed_operator_prepare(const ts_plan* p, double sigma, long long* qtab, FixedOperator* fo, cudaStream_t s);
 ts_status operator_apply_fixed(const ts_plan* p, const FixedOperator& fo, const double* V2, const double* x, double* y,
                                const int* emax_dev, double* partial, double* out2, cudaStream_t s);
+// *emax = the largest biased exponent over x (reset first).
+ts_status max_exponent(const double* x, long long N, int* emax, cudaStream_t s);
+// r = b - A x through the fixed-point operator (its exponent pass included), with
+// out2[0] = r.r and out2[1] = b.b; opart holds 2 * fo.blocks doubles, partial
+// 2 * RED_BLOCKS.  The same quantities as stencil_residual, with A x exact.
+ts_status residual_fixed(const ts_plan* p, const FixedOperator& fo, const double* V2, const double* x,
+                         const double* b, double* r, int* emax, double* opart, double* partial, double* out2,
+                         cudaStream_t s);
 // out2[0] = a.b (b == NULL: sum of a), out2[1] = c.d (c, d may be NULL).
 ts_status dot2(long long N, const double* a, const double* b, const double* c, const double* d, double* partial,
                double* out2, cudaStream_t s);

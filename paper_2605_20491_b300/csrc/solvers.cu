@@ -43,17 +43,30 @@ ts_status read_scalars(const double* dev, double* host, int count, cudaStream_t 
 
 // Pinned two-slot mailbox for the PCG stopping test: iteration k copies its r.r into slot
 // k % 2 and records an event, and the host reads slot (k - 1) % 2 while iteration k runs.
+// One per host thread and device, kept for the thread's lifetime: a pinned allocation and
+// its release cost about a millisecond, once per PCG solve otherwise (inverse iteration
+// runs one solve per outer step).
 struct RrMailbox {
+  int device = -1;
   double* host = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  ~RrMailbox() {
+  ~RrMailbox() { release(); }
+  void release() {
     if (host) cudaFreeHost(host);
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);
+    host = nullptr;
+    ev[0] = ev[1] = nullptr;
+    device = -1;
   }
   ts_status init() {
+    int dev = 0;
+    TS_CHECK_CUDA(cudaGetDevice(&dev));
+    if (host && device == dev) return TS_OK;
+    release();
     TS_CHECK_CUDA(cudaMallocHost(&host, 2 * sizeof(double)));
     for (cudaEvent_t& e : ev) TS_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    device = dev;
     return TS_OK;
   }
   ts_status post(const double* dev, int k, cudaStream_t s) {
@@ -95,9 +108,12 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
     if (fo.ok) return operator_apply_fixed(p, fo, V2, pv, q, emax, opart, out2, s);
     return stencil_apply(p, V2, sigma, pv, q, partial, out2, s);
   };
+  auto residual = [&](double* out2) -> ts_status {  // r = b - A x; out2[0] = r.r, out2[1] = b.b
+    if (fo.ok) return residual_fixed(p, fo, V2, x, b, r, emax, opart, partial, out2, s);
+    return stencil_residual(p, V2, sigma, x, b, r, partial, out2, s);
+  };
   double h[2];
-  // r = b - A x;  sc[0] = r.r, sc[1] = b.b
-  TS_TRY(stencil_residual(p, V2, sigma, x, b, r, partial, sc + 0, s));
+  TS_TRY(residual(sc + 0));
   TS_TRY(read_scalars(sc, h, 2, s));
   double bnorm = std::sqrt(h[1]);
   if (bnorm == 0.0) bnorm = 1.0;
@@ -112,7 +128,7 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
   // iteration k - 1's while the GPU runs iteration k, so the GPU never waits for the host.
   // The solve therefore stops one iteration after the first one below tol (a smaller
   // residual, reported with its own iteration count).
-  RrMailbox mb;
+  thread_local RrMailbox mb;
   if (!converged) TS_TRY(mb.init());
   double rr_last = 0.0, rr_prev = 0.0;  // the two most recent tested r.r
   auto check = [&](int k, bool* stop) -> ts_status {
@@ -171,7 +187,7 @@ ts_status pcg_impl(const ts_plan* p, double sigma, double sigma_P, const double*
     converged = stop;
   }
   // true residual at exit
-  TS_TRY(stencil_residual(p, V2, sigma, x, b, r, partial, sc + 12, s));
+  TS_TRY(residual(sc + 12));
   TS_TRY(read_scalars(sc + 12, h, 1, s));
   if (iters_out) *iters_out = it;
   if (relres_out) *relres_out = std::sqrt(h[0]) / bnorm;
@@ -192,11 +208,27 @@ ts_status inverse_iteration_impl(const ts_plan* p, double shift, const double* V
   TS_TRY(sc_mem.get(&Hu, N));
   TS_TRY(sc_mem.get(&partial, 2 * RED_BLOCKS));
   TS_TRY(sc_mem.get(&sc, 8));
+  // H u for the Rayleigh quotient, in exact fixed point where the form applies (its
+  // exponent pass in sc[7]'s int slot), else by the FP64 stencil; out[0] = (u, H u)
+  FixedOperator fo0;
+  double* opart0 = nullptr;
+  int* emax0 = reinterpret_cast<int*>(sc + 7);
+  if (qtable_count(p) > 0) {
+    double* qt = nullptr;
+    TS_TRY(sc_mem.get(&qt, (size_t)qtable_count(p)));
+    TS_TRY(fixed_operator_prepare(p, 0.0, reinterpret_cast<long long*>(qt), &fo0, s));
+    if (fo0.ok) TS_TRY(sc_mem.get(&opart0, 2 * (size_t)fo0.blocks));
+  }
+  auto apply_H = [&](double* out) -> ts_status {
+    if (!fo0.ok) return stencil_apply(p, V2, 0.0, u, Hu, partial, out, s);
+    TS_TRY(max_exponent(u, N, emax0, s));
+    return operator_apply_fixed(p, fo0, V2, u, Hu, emax0, opart0, out, s);
+  };
   if (init_from_plan) TS_TRY(tensor_ground(p, u, s));
   // u <- u / ||u||; lambda = (u, H u)
   TS_TRY(dot2(N, u, u, nullptr, nullptr, partial, sc, s));
   TS_TRY(scale_by_device_ratio(N, sc, nullptr, u, u, s));
-  TS_TRY(stencil_apply(p, V2, 0.0, u, Hu, partial, sc + 2, s));
+  TS_TRY(apply_H(sc + 2));
   double h[2];
   TS_TRY(read_scalars(sc + 2, h, 1, s));
   double lambda = h[0];
@@ -217,7 +249,7 @@ ts_status inverse_iteration_impl(const ts_plan* p, double shift, const double* V
     if (st != TS_OK && st != TS_ERR_NOT_CONVERGED) return st;
     TS_TRY(dot2(N, w, w, nullptr, nullptr, partial, sc, s));
     TS_TRY(scale_by_device_ratio(N, sc, nullptr, w, u, s));  // u = w / ||w||
-    TS_TRY(stencil_apply(p, V2, 0.0, u, Hu, partial, sc + 2, s));
+    TS_TRY(apply_H(sc + 2));
     TS_TRY(read_scalars(sc + 2, h, 1, s));
     ++it;
     double change = std::fabs(h[0] - lambda) / std::fabs(h[0]);
