@@ -155,10 +155,37 @@ def cpu_oracle_sample(target_seconds: float = 15.0):
             break
     per = el / reps
     rate = P.N / per / 1e9 * (n_s / 512.0)
-    return {"value": rate, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+    cores = O.num_threads()
+    # the same oracle on one core, on a 3D n = 128 sample (a few seconds)
+    n_1 = 128
+    f1 = synth.harmonic((n_1,) * 3, w["L"], w["omega"])
+    P1 = O.plan((n_1,) * 3, w["L"], f1)
+    b1 = synth.normal(w["seed"], P1.N)
+    O.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.apply_inverse(P1, w["sigma"], b1)
+        per1 = time.perf_counter() - t0
+    finally:
+        O.set_num_threads(cores)
+    rate1 = P1.N / per1 / 1e9 * (n_1 / 512.0)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"oracle FP64 4-step apply (plain C loops, OpenMP) on 3D n={n_s} ({P.N} DoF), "
                       f"{reps} run(s) of {per:.2f} s each; rate scaled by {n_s}/512 to n=512 "
-                      f"(oracle cost per DoF grows like n)"}
+                      f"(oracle cost per DoF grows like n)",
+            "one_core": {"value": rate1, "unit": UNIT,
+                         "sample": f"the same on 1 thread, 3D n={n_1}, one run of {per1:.2f} s, scaled by {n_1}/512"}}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_reference(args):
@@ -186,7 +213,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": [512, 512, 512], "sample_n": n_s},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

@@ -62,6 +62,7 @@ def lib():
         L.or_inverse_iteration.restype = C.c_int
         L.or_strang.argtypes = [C.c_int, _ip, C.POINTER(_dp), C.POINTER(_dp), _dp, C.c_double, C.c_int, _dp]
         L.or_num_threads.restype = C.c_int
+        L.or_set_num_threads.argtypes = [C.c_int]
     return _lib
 
 
@@ -80,6 +81,10 @@ def _ptr_array(arrs):
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(t: int) -> None:
+    lib().or_set_num_threads(int(t))
 
 
 def grid(n: int, L: float) -> np.ndarray:

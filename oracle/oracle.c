@@ -546,3 +546,12 @@ int or_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops that follow (timing on one core or on all of them). */
+void or_set_num_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
