@@ -31,12 +31,16 @@
 namespace ts {
 
 AxisTables::~AxisTables() {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
   table_free(block, device);
   for (int q = 0; q < NPREC; ++q) {
     table_free(Bf[q], device);
     table_free(Bb[q], device);
   }
   table_free(Sf32, device);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
 }
 
 namespace {
