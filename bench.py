@@ -648,6 +648,22 @@ def run_ours(args):
     e2e_ms = (time.perf_counter() - t0) / n_e2e * 1e3
     e2e_err = float(np.linalg.norm(u_host[last].numpy() - u64.cpu().numpy()) / nrm)
 
+    # The floor of that pipeline: the same uploads and downloads with no solve, the two
+    # directions concurrent on their own streams (the host link, not the GPU, bounds it).
+    def copies_only(n_steps):
+        for k in range(n_steps):
+            j = k % 2
+            with torch.cuda.stream(s_h2d):
+                bd[j].copy_(b_host, non_blocking=True)
+            with torch.cuda.stream(s_d2h):
+                u_host[j].copy_(xd[j], non_blocking=True)
+        torch.cuda.synchronize()
+
+    copies_only(1)
+    t0 = time.perf_counter()
+    copies_only(n_e2e)
+    copy_ms = (time.perf_counter() - t0) / n_e2e * 1e3
+
     peaks, peaks_src = load_peaks()
     avg_launch_ms = tc_ms / max(1, tc_launches)
     achieved = (tc_flops / max(1, tc_launches)) / (avg_launch_ms * 1e-3) / 1e12 if tc_launches else None
@@ -696,7 +712,8 @@ def run_ours(args):
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N, "err_vs_fp64": e2e_err,
-                    "pipelining": "2 buffer sets, 3 streams: upload k+1 and download k-1 overlap solve k"}}
+                    "pipelining": "2 buffer sets, 3 streams: upload k+1 and download k-1 overlap solve k",
+                    "copy_floor_ms_per_step": copy_ms, "frac_of_copy_floor": copy_ms / e2e_ms}}
     if rank == 0 and not args.no_serving:
         sv = serving_run(T, args.requests)
         line["serving"] = sv
