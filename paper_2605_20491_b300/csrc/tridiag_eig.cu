@@ -58,11 +58,15 @@ void qr_step(int n, int lo, int hi, double* a, double* b, double* Z, RotateFn ro
   const double mu = den != 0.0 ? a[hi] - e * e / den : a[hi] - std::fabs(e);
   double x = a[lo] - mu, z = b[lo];
   for (int k = lo; k < hi; ++k) {
-    const double rho = std::hypot(x, z);
+    // |(x, z)|: the plain square root where x^2 + z^2 can neither overflow nor underflow
+    // (hypot's rescaling costs more than the rest of the step), hypot outside that range
+    const double m = std::fmax(std::fabs(x), std::fabs(z));
+    const double rho = (m > 1e-150 && m < 1e150) ? std::sqrt(x * x + z * z) : std::hypot(x, z);
     double c = 1.0, s = 0.0;
     if (rho != 0.0) {
-      c = x / rho;
-      s = z / rho;
+      const double inv = 1.0 / rho;
+      c = x * inv;
+      s = z * inv;
     }
     if (k > lo) b[k - 1] = rho;
     const double p = a[k], q = a[k + 1], r = b[k];
