@@ -1,6 +1,6 @@
 // cp.async (global -> shared, Ampere-style asynchronous copies) wrappers shared by the
 // small-n contraction and the refinement residual: 8-byte copies, optionally zero-filled,
-// grouped with commit_group / wait_group.
+// and 16-byte copies, grouped with commit_group / wait_group.
 #pragma once
 #include <cstdint>
 
@@ -8,6 +8,13 @@ namespace ts {
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gmem_src)
+               : "memory");
+}
+
+// 16-byte copy: both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
                "l"(gmem_src)
                : "memory");
 }

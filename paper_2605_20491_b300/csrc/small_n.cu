@@ -49,6 +49,9 @@ struct GroupParams {
   // potential phase e^{-i theta V2}: applied on load (theta_pre) / on store (theta_post)
   const float* V2;
   float theta_pre, theta_post;
+  // 1: lo > 1 with an even tile count T and 16-byte aligned X and Y, so elements (t, t + 1)
+  // for even t are adjacent in HBM and in shared memory: copies move them as one 16-byte pair
+  int pairs;
 };
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -156,7 +159,7 @@ __device__ __forceinline__ void tile_origin(long long b, int lgTlo, int Thi, con
 template <int N>
 __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, float2* Y, const GroupParams p,
                                                                long long ntiles) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int lgT = 31 - __clz(p.T);
   const int lgTlo = p.lo > 1 ? lgT : 0;
   const int Tlo = 1 << lgTlo;
@@ -177,10 +180,18 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
     long long l0, h0;
     tile_origin(b, lgTlo, Thi, p, &l0, &h0);
     const long long gbase = l0 + p.lo * p.G * h0;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      int g, th;
-      const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-      cp_async8(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th));
+    if (p.pairs) {
+      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) {
+        int g, th;
+        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+        cp_async16(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th));
+      }
+    } else {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int g, th;
+        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+        cp_async8(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th));
+      }
     }
     cp_async_commit();
   };
@@ -228,11 +239,12 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
         rowph[t] = ph;
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int step_e = p.pairs ? 2 : 1;  // pairs: (t, t + 1) share the group's phase
+      for (int e = step_e * threadIdx.x; e < cnt; e += step_e * blockDim.x) {
         const int t = e & (Tlo - 1);
         int r = e >> lgTlo;
         int sidx = t, mul = Tlo;
-        float2 ph = rowph[t];
+        float2 ph = make_float2(1.f, 0.f);
         for (int j = 0; j < p.nm; ++j) {
           const int ij = r % N;
           r /= N;
@@ -241,7 +253,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
           ph = cmulf(ph, p.ph[p.k0 + j][ij]);
         }
         sidx += r * mul;
-        tile[sidx] = cmulf(tile[sidx], ph);
+        tile[sidx] = cmulf(tile[sidx], cmulf(rowph[t], ph));
+        if (p.pairs) tile[sidx + 1] = cmulf(tile[sidx + 1], cmulf(rowph[t + 1], ph));
       }
       __syncthreads();
     }
@@ -251,13 +264,28 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
         __syncthreads();
       }
     }
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      int g, th;
-      const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-      const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
-      float2 v = tile[sidx];
-      if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, p.V2[gidx]);
-      Y[gidx] = v;
+    if (p.pairs) {
+      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) {
+        int g, th;
+        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
+        const float4 w = *reinterpret_cast<const float4*>(tile + sidx);
+        float2 v0 = make_float2(w.x, w.y), v1 = make_float2(w.z, w.w);
+        if (p.V2 && p.theta_post != 0.f) {
+          v0 = vphase(v0, p.theta_post, p.V2[gidx]);
+          v1 = vphase(v1, p.theta_post, p.V2[gidx + 1]);
+        }
+        *reinterpret_cast<float4*>(Y + gidx) = make_float4(v0.x, v0.y, v1.x, v1.y);
+      }
+    } else {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int g, th;
+        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
+        float2 v = tile[sidx];
+        if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, p.V2[gidx]);
+        Y[gidx] = v;
+      }
     }
     __syncthreads();  // the buffer is refilled two iterations later
   }
@@ -464,6 +492,8 @@ ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, floa
       gp.theta_pre = (V2 && first) ? (float)(step == 0 ? 0.5 * dt : 0.0) : 0.f;
       gp.theta_post = (V2 && last) ? (float)(step == nsteps - 1 ? 0.5 * dt : dt) : 0.f;
       const float2* src = (step == 0 && first) ? in : out;
+      gp.pairs = gp.lo > 1 && gp.T % 2 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
+                 reinterpret_cast<uintptr_t>(out) % 16 == 0;
       st = group_pass(p->n[g.k0], src, out, gp, s);
     }
   }
