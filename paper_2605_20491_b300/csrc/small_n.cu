@@ -49,8 +49,13 @@ struct GroupParams {
   // potential phase e^{-i theta V2}: applied on load (theta_pre) / on store (theta_post)
   const float* V2;
   float theta_pre, theta_post;
+  // Element pairs in the copies between HBM and the tile (index arithmetic once per pair):
   // 1: lo > 1 with an even tile count T and 16-byte aligned X and Y, so elements (t, t + 1)
-  // for even t are adjacent in HBM and in shared memory: copies move them as one 16-byte pair
+  //    for even t are adjacent in HBM and in shared memory: one 16-byte copy each way;
+  // 2: lo == 1 with an even first extent and 16-byte aligned Y: elements (i, i + 1) of the
+  //    first group axis, i even, are adjacent in HBM and in shared memory, where the padded
+  //    rows leave them 8-byte aligned: two 8-byte copies in, one 16-byte store out;
+  // 0: one element at a time.
   int pairs;
 };
 
@@ -180,11 +185,19 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
     long long l0, h0;
     tile_origin(b, lgTlo, Thi, p, &l0, &h0);
     const long long gbase = l0 + p.lo * p.G * h0;
-    if (p.pairs) {
+    if (p.pairs == 1) {
       for (int e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) {
         int g, th;
         const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
         cp_async16(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th));
+      }
+    } else if (p.pairs == 2) {
+      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) {
+        int g, th;
+        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
+        const float2* src = X + gbase + p.lo * ((long long)g + p.G * th);
+        cp_async8(dst + sidx, src);
+        cp_async8(dst + sidx + 1, src + 1);
       }
     } else {
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -212,11 +225,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
     tile_origin(b, lgTlo, Thi, p, &l0, &h0);
     const long long gbase = l0 + p.lo * p.G * h0;
     if (p.V2 && p.theta_pre != 0.f) {
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int step_e = p.pairs ? 2 : 1;  // both pair kinds: (e, e + 1) at (sidx, sidx + 1)
+      for (int e = step_e * threadIdx.x; e < cnt; e += step_e * blockDim.x) {
         int g, th;
         const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
         const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
         tile[sidx] = vphase(tile[sidx], p.theta_pre, p.V2[gidx]);
+        if (p.pairs) tile[sidx + 1] = vphase(tile[sidx + 1], p.theta_pre, p.V2[gidx + 1]);
       }
       __syncthreads();
     }
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
         rowph[t] = ph;
       }
       __syncthreads();
-      const int step_e = p.pairs ? 2 : 1;  // pairs: (t, t + 1) share the group's phase
+      const int step_e = p.pairs == 1 ? 2 : 1;  // pairs along t share the group's phase
       for (int e = step_e * threadIdx.x; e < cnt; e += step_e * blockDim.x) {
         const int t = e & (Tlo - 1);
         int r = e >> lgTlo;
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
         }
         sidx += r * mul;
         tile[sidx] = cmulf(tile[sidx], cmulf(rowph[t], ph));
-        if (p.pairs) tile[sidx + 1] = cmulf(tile[sidx + 1], cmulf(rowph[t + 1], ph));
+        if (p.pairs == 1) tile[sidx + 1] = cmulf(tile[sidx + 1], cmulf(rowph[t + 1], ph));
       }
       __syncthreads();
     }
@@ -269,8 +284,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
         int g, th;
         const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
         const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
-        const float4 w = *reinterpret_cast<const float4*>(tile + sidx);
-        float2 v0 = make_float2(w.x, w.y), v1 = make_float2(w.z, w.w);
+        float2 v0 = tile[sidx], v1 = tile[sidx + 1];
         if (p.V2 && p.theta_post != 0.f) {
           v0 = vphase(v0, p.theta_post, p.V2[gidx]);
           v1 = vphase(v1, p.theta_post, p.V2[gidx + 1]);
@@ -492,8 +506,8 @@ ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, floa
       gp.theta_pre = (V2 && first) ? (float)(step == 0 ? 0.5 * dt : 0.0) : 0.f;
       gp.theta_post = (V2 && last) ? (float)(step == nsteps - 1 ? 0.5 * dt : dt) : 0.f;
       const float2* src = (step == 0 && first) ? in : out;
-      gp.pairs = gp.lo > 1 && gp.T % 2 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
-                 reinterpret_cast<uintptr_t>(out) % 16 == 0;
+      const bool src16 = reinterpret_cast<uintptr_t>(src) % 16 == 0, out16 = reinterpret_cast<uintptr_t>(out) % 16 == 0;
+      gp.pairs = gp.lo > 1 ? (gp.T % 2 == 0 && src16 && out16 ? 1 : 0) : (p->n[g.k0] % 2 == 0 && out16 ? 2 : 0);
       st = group_pass(p->n[g.k0], src, out, gp, s);
     }
   }
