@@ -255,6 +255,8 @@ ts_status ts_apply_operator(const ts_plan* plan, double sigma, const double* V2,
  * recurrence residual, or after maxit iterations (then TS_ERR_NOT_CONVERGED, x holds
  * the last iterate).  *iters (may be NULL) = iterations taken; *relres (may be NULL) =
  * TRUE relative residual ||b - A x|| / ||b|| recomputed at exit.  Synchronises stream.
+ * Every product A x (the iteration's and the residuals at entry and exit) is formed as
+ * ts_apply_operator forms it, in exact fixed point where that form applies.
  * Q^k, k >= 2: A and P are self-adjoint in the M-inner product <u, v>_M = sum M u v
  * (M = prod_k M_k, the lumped mass), not in the plain one; the iteration runs in
  * x~ = M^{1/2} x on the symmetric M^{1/2} A M^{-1/2}, so every inner product and norm
