@@ -375,13 +375,13 @@ ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double
  * the paper; set by the autotuner).  For real (complex_data = 0) or complex data and a
  * contracted axis of length n (n = 0: the default for all lengths): K chunk bk (64 =
  * 128-byte swizzled rows, 32 = 64-byte), the cap bn_cap (multiple of 16, <= 256) on the
- * N tile, and `cluster`: 1, 2 or 4 = the number of CTAs of a thread-block cluster that
- * share every S_k tile through TMA multicast, each loading 1/cluster of it; TS_TC_PAIR =
+ * N tile, and `cluster`: 1 = single CTAs, each staging its whole S_k tile; TS_TC_PAIR =
  * CTA pairs that share each tensor-core instruction (tcgen05 cta_group::2: 256-row units,
  * each CTA staging its own 128 rows and half of the S_k tile; the built-in choice for real
- * data on axes of 256 points or more).  bk = bn_cap = cluster = 0 forgets the entry for
- * (complex_data, n), restoring the built-in choice.  Process-wide; takes effect for calls
- * issued afterwards.
+ * data on axes of 256 points or more).  Every other cluster value returns
+ * TS_ERR_INVALID_ARG: no tile is ever shared by a multicast load.  bk = bn_cap = cluster = 0
+ * forgets the entry for (complex_data, n), restoring the built-in choice.  Process-wide;
+ * takes effect for calls issued afterwards.
  */
 #define TS_TC_PAIR (-2)
 ts_status ts_tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster);
@@ -455,9 +455,8 @@ ts_status ts_server_destroy(ts_server* server);
  * Autotuner of the split-precision contraction (no counterpart in the paper).  For every
  * distinct axis length n of the plan and the data kind (dtype TS_R64: real data of
  * ts_apply_inverse; TS_C128: complex data of ts_apply_exp) it times the tile
- * configurations (K chunk 64 / 32, N-tile cap 256 / 128 / 64, cluster 1 / 2 / 4 / TS_TC_PAIR) on whole
- * applies with CUDA
- * events on `stream`, keeps the fastest with ts_tc_config_set, and appends it to the text
+ * configurations (K chunk 64 / 32, N-tile cap 256 / 128 / 64, cluster 1 / TS_TC_PAIR) on
+ * whole applies with CUDA events on `stream`, keeps the fastest with ts_tc_config_set, and appends it to the text
  * file cache_path (NULL or "" = no file).  Entries already in the file are applied without
  * timing.  *tuned (may be NULL) = number of axis lengths searched.  Synchronises stream.
  */

@@ -1,10 +1,10 @@
 // Autotuner of the split-precision tensor-core pass: for each distinct contracted extent
 // n of a plan and the data kind (real / complex), time the candidate tile configurations
-// (K chunk 64 or 32; N-tile cap 256, 128 or 64; 1, 2 or 4 CTAs per multicast cluster, or CTA
-// pairs sharing each MMA) on a
-// whole apply with CUDA events, keep the fastest through tc_config_set, and remember it in
-// a plain-text cache file so later processes skip the search.
-// Cache line: "<complex> <n> <prec> <bk> <bn_cap> <cluster> <ms>".
+// (K chunk 64 or 32; N-tile cap 256, 128 or 64; single CTAs or CTA pairs sharing each MMA)
+// on a whole apply with CUDA events, keep the fastest through tc_config_set, and remember
+// it in a plain-text cache file so later processes skip the search.
+// Cache line: "<complex> <n> <prec> <bk> <bn_cap> <cluster> <ms>", cluster 1 (single CTAs)
+// or TS_TC_PAIR; lines with any other cluster value are ignored.
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -19,7 +19,7 @@ namespace ts {
 namespace {
 
 struct Entry {
-  int cplx, n, prec, bk, bn, cm;
+  int cplx, n, prec, bk, bn, cluster;
   double ms;
 };
 
@@ -31,7 +31,9 @@ std::vector<Entry> read_cache(const char* path) {
   while (std::getline(in, line)) {
     std::istringstream ss(line);
     Entry e{};
-    if (ss >> e.cplx >> e.n >> e.prec >> e.bk >> e.bn >> e.cm >> e.ms) out.push_back(e);
+    if (ss >> e.cplx >> e.n >> e.prec >> e.bk >> e.bn >> e.cluster >> e.ms &&
+        (e.cluster == 1 || e.cluster == TS_TC_PAIR))
+      out.push_back(e);
   }
   return out;
 }
@@ -39,7 +41,7 @@ std::vector<Entry> read_cache(const char* path) {
 void append_cache(const char* path, const Entry& e) {
   if (!path || !*path) return;
   std::ofstream out(path, std::ios::app);
-  out << e.cplx << " " << e.n << " " << e.prec << " " << e.bk << " " << e.bn << " " << e.cm << " " << e.ms << "\n";
+  out << e.cplx << " " << e.n << " " << e.prec << " " << e.bk << " " << e.bn << " " << e.cluster << " " << e.ms << "\n";
 }
 
 ts_status time_apply(const ts_plan* p, ts_precision prec, bool cplx, void* in, void* out, cudaStream_t s,
@@ -104,7 +106,7 @@ extern "C" ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precisi
     for (const Entry& e : cache)
       if (e.cplx == cval && e.n == n && e.prec == (int)prec) hit = &e;
     if (hit) {
-      st = tc_config_set(cval, n, hit->bk, hit->bn, hit->cm);
+      st = tc_config_set(cval, n, hit->bk, hit->bn, hit->cluster);
       continue;
     }
     if (!in) {
@@ -120,24 +122,24 @@ extern "C" ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precisi
     Entry best{cval, n, (int)prec, 64, 256, 1, 1e30};
     const int bks[2] = {64, 32};
     const int bns[3] = {256, 128, 64};
-    const int cms[4] = {1, 2, 4, TS_TC_PAIR};
+    const int clusters[2] = {1, TS_TC_PAIR};
     for (int bk : bks)
       for (int bn : bns)
-        for (int cm : cms) {
+        for (int cl : clusters) {
           if (st != TS_OK) break;
           if (2 * (cplx ? 2 : 1) * bn > 512) continue;
-          st = tc_config_set(cval, n, bk, bn, cm);
+          st = tc_config_set(cval, n, bk, bn, cl);
           double ms = 0.0;
           if (st == TS_OK) st = time_apply(plan, prec, cplx, in, out, s, 3, &ms);
           if (st == TS_OK && ms < best.ms) {
             best.bk = bk;
             best.bn = bn;
-            best.cm = cm;
+            best.cluster = cl;
             best.ms = ms;
           }
         }
     if (st == TS_OK) {
-      st = tc_config_set(cval, n, best.bk, best.bn, best.cm);
+      st = tc_config_set(cval, n, best.bk, best.bn, best.cluster);
       append_cache(cache_path, best);
       ++searched;
     }

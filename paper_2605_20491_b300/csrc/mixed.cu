@@ -233,12 +233,11 @@ __device__ __forceinline__ void epi_chunk(const EpiParams& ep, const uint32_t (&
 // Both CTAs' TMA loads complete on the leader's stage barrier (the leader alone expects
 // their bytes); commits are multicast to both CTAs; both epilogues arrive on the leader's
 // accumulator-drained barrier.
-template <int NP, int NACC, int BKT, bool PLANES_OUT, int CM, bool PAIR>
+template <int NP, int NACC, int BKT, bool PLANES_OUT, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_rot_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const EpiParams ep) {
-  static_assert(!PAIR || CM == 1, "CTA pairs do not combine with B multicast");
   constexpr int SW = BKT * 2;  // bytes per smem row = swizzle width
-  constexpr int CL = PAIR ? 2 : CM;  // CTAs per cluster
+  constexpr int CL = PAIR ? 2 : 1;  // CTAs per cluster
   constexpr int CG = PAIR ? 2 : 1;   // tcgen05 CTA group
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -261,10 +260,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int nk = (ep.n + BKT - 1) / BKT;
   const int mtiles = (int)((ep.R + BM - 1) / BM);
   const int ntiles = (ep.n + BN - 1) / BN;
-  // Work units: with clusters of CL CTAs, unit t covers M tiles (t / ntiles) * CL + rank
-  // (one per CTA of the cluster) and N tile t % ntiles.  Multicast clusters (CM > 1) share
-  // every B tile through TMA multicast, each CTA loading BN / CM of its rows; pairs split the
-  // B tile between their two CTAs.
+  // Work units: with CTA pairs, unit t covers M tiles (t / ntiles) * 2 + rank (one per CTA
+  // of the pair) and N tile t % ntiles, and the pair splits the B tile between its two CTAs.
+  // Every TMA load lands in the issuing CTA's own shared memory.
   const int rank = CL > 1 ? (int)tc::cluster_ctarank() : 0;
   const int unit0 = CL > 1 ? (int)tc::cluster_id_x() : (int)blockIdx.x;
   const int unit_step = CL > 1 ? (int)tc::cluster_count_x() : (int)gridDim.x;
@@ -277,7 +275,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], PAIR ? 1 : CM);  // one commit per MMA-issuing CTA of the cluster
+      tc::mbar_init(&empty[s], 1);  // one commit by the MMA-issuing CTA
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&accf[b], 1);
@@ -302,7 +300,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       // ---------------- TMA producer: a ring of NS stages that runs across tiles
       int it = 0;
-      const int bslice = BN / CM;
       for (int t = unit0; t < total; t += unit_step) {
         const int m0 = ((t / ntiles) * CL + rank) * BM, n0 = (t % ntiles) * BN;
         for (int kc = 0; kc < nk; ++kc, ++it) {
@@ -326,13 +323,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int p = 0; p < NP; ++p)
               tc::tma_load_3d(sA + (size_t)s * A_STAGE + (c * NP + p) * A_TILE, &tmA, kc * BKT, m0, c * NP + p,
                               &full[s]);
-          for (int p = 0; p < NP; ++p) {
-            if (CM == 1)
-              tc::tma_load_3d(sB + (size_t)s * B_STAGE + p * B_TILE, &tmB, kc * BKT, n0, p, &full[s]);
-            else
-              tc::tma_load_3d_mc(sB + (size_t)s * B_STAGE + p * B_TILE + rank * bslice * SW, &tmB, kc * BKT,
-                                 n0 + rank * bslice, p, &full[s], cta_mask);
-          }
+          for (int p = 0; p < NP; ++p)
+            tc::tma_load_3d(sB + (size_t)s * B_STAGE + p * B_TILE, &tmB, kc * BKT, n0, p, &full[s]);
         }
       }
     }
@@ -368,14 +360,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
           }
           if (PAIR)
-            tc::mma_commit_pair_mc(&empty[s], cta_mask);  // both CTAs' halves of the stage are free
-          else if (CM == 1)
-            tc::mma_commit(&empty[s]);
+            tc::mma_commit_pair(&empty[s], cta_mask);  // both CTAs' halves of the stage are free
           else
-            tc::mma_commit_mc(&empty[s], cta_mask);  // the stage is free once every CTA is done with it
+            tc::mma_commit(&empty[s]);
         }
         if (PAIR)
-          tc::mma_commit_pair_mc(&accf[ab], cta_mask);  // each CTA's TMEM holds its 128 rows
+          tc::mma_commit_pair(&accf[ab], cta_mask);  // each CTA's TMEM holds its 128 rows
         else
           tc::mma_commit(&accf[ab]);
       }
@@ -774,20 +764,16 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
 
 int g_num_sms = 0;
 
-template <int NP, int NACC, int BKT, bool PO, int CM, bool PAIR>
+template <int NP, int NACC, int BKT, bool PO, bool PAIR>
 ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
                         int bn_cap, cudaStream_t s) {
-  constexpr int CL = PAIR ? 2 : CM;
+  constexpr int CL = PAIR ? 2 : 1;
   // pairs: N tiles in multiples of 32 (every such N is a valid M = 256 shape)
   const int bq = PAIR ? 32 : 16;
   int bn = ((n + bq - 1) / bq) * bq;
   if (bn > bn_cap) bn = bn_cap;
   if (PAIR && bn % 32 != 0) {
     set_error("CTA pairs need an N-tile cap that is a multiple of 32 (got %d)", bn_cap);
-    return TS_ERR_UNSUPPORTED;
-  }
-  if (CM > 1 && (bn % (8 * CM) != 0)) {
-    set_error("N tile %d cannot be split into %d multicast slices of whole 8-row atoms", bn, CM);
     return TS_ERR_UNSUPPORTED;
   }
   const int b_rows = PAIR ? bn / 2 : bn;  // rows of the S_k tile staged per CTA (bn % 16 == 0)
@@ -802,7 +788,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   const int smem = ns * stage + reserve;
   CUtensorMap ma, mb;
   TS_TRY(make_map(&ma, A, n, R, NACC * NP, BKT, BM));
-  TS_TRY(make_map(&mb, B, n, n, NP, BKT, PAIR ? bn / 2 : bn / CM));
+  TS_TRY(make_map(&mb, B, n, n, NP, BKT, PAIR ? bn / 2 : bn));
   ep.R = R;
   ep.n = n;
   ep.N = R * n;
@@ -816,7 +802,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     TS_CHECK_CUDA(
-        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              SMEM_LIMIT));
     attr_set = true;
   }
@@ -833,7 +819,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   void* tok = nullptr;
   if (prof_enabled()) prof_begin_launch(s, &tok);
   if (CL == 1) {
-    k_rot_tc<NP, NACC, BKT, PO, 1, false><<<grid, TC_THREADS, smem, s>>>(ma, mb, ep);
+    k_rot_tc<NP, NACC, BKT, PO, false><<<grid, TC_THREADS, smem, s>>>(ma, mb, ep);
   } else {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -847,7 +833,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    TS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_rot_tc<NP, NACC, BKT, PO, CM, PAIR>, ma, mb, ep));
+    TS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_rot_tc<NP, NACC, BKT, PO, PAIR>, ma, mb, ep));
   }
   TS_LAUNCHED(1);
   if (tok) {
@@ -865,8 +851,7 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
 struct TcConfig {
   int bk = 64;
   int bn_cap = 256;
-  int cm = 1;         // CTAs per cluster sharing each B tile by multicast (1, 2 or 4)
-  bool pair = false;  // CTA pairs sharing each MMA (cta_group::2, 256-row units); cm is then 1
+  bool pair = false;  // CTA pairs sharing each MMA (cta_group::2, 256-row units)
 };
 
 std::mutex g_cfg_mu;
@@ -881,7 +866,6 @@ TcConfig lookup_config(int nacc, int n) {
   TcConfig c;
   c.bk = 64;
   c.bn_cap = nacc == 1 ? 256 : 128;
-  c.cm = 1;
   // real data on long axes: CTA pairs (each SM stages half of the S_k tile); measured on the
   // BF16X3 plane passes at n = 512: 0.299 ms against 0.321 ms for single CTAs
   c.pair = nacc == 1 && n >= 256;
@@ -893,12 +877,6 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
                       cudaStream_t s) {
   TcConfig c = lookup_config(NACC, n);
   if (2 * NACC * c.bn_cap > 512) c.bn_cap = 256 / NACC;  // two accumulator buffers must fit in TMEM
-  {
-    int bn = ((n + 15) / 16) * 16;
-    if (bn > c.bn_cap) bn = c.bn_cap;
-    while (c.cm > 1 && bn % (8 * c.cm) != 0) c.cm /= 2;  // multicast slices are whole 8-row atoms
-  }
-  if (c.pair) c.cm = 1;
   if (c.bn_cap % 32 != 0) c.pair = false;
   // Fall back to a narrower K chunk, then a narrower N tile, until two stages fit.
   const int reserve = 1024 + 8 * (2 * MAX_STAGES + 6);
@@ -917,22 +895,18 @@ ts_status launch_pass(const __nv_bfloat16* A, const __nv_bfloat16* B, long long 
     if (c.bn_cap % 32 != 0) c.pair = false;
   }
   if (ep.out_mode == 0) {
-  // one statement (a braced block), so that `if (c.bk == 32) TS_CM_DISPATCH(32, ..)` guards all of it
-  #define TS_CM_DISPATCH(BKT, PO)                                                                   \
+  // one statement (a braced block), so that `if (c.bk == 32) TS_PAIR_DISPATCH(32, ..)` guards all of it
+  #define TS_PAIR_DISPATCH(BKT, PO)                                                                 \
   {                                                                                                \
-    if (c.pair) return launch_pass_t<NP, NACC, BKT, PO, 1, true>(A, B, R, n, ep, c.bn_cap, s);    \
-    switch (c.cm) {                                                                                \
-      case 2: return launch_pass_t<NP, NACC, BKT, PO, 2, false>(A, B, R, n, ep, c.bn_cap, s);      \
-      case 4: return launch_pass_t<NP, NACC, BKT, PO, 4, false>(A, B, R, n, ep, c.bn_cap, s);      \
-      default: return launch_pass_t<NP, NACC, BKT, PO, 1, false>(A, B, R, n, ep, c.bn_cap, s);     \
-    }                                                                                              \
+    if (c.pair) return launch_pass_t<NP, NACC, BKT, PO, true>(A, B, R, n, ep, c.bn_cap, s);       \
+    return launch_pass_t<NP, NACC, BKT, PO, false>(A, B, R, n, ep, c.bn_cap, s);                  \
   }
-    if (c.bk == 32) TS_CM_DISPATCH(32, true);
-    TS_CM_DISPATCH(64, true);
+    if (c.bk == 32) TS_PAIR_DISPATCH(32, true);
+    TS_PAIR_DISPATCH(64, true);
   }
-  if (c.bk == 32) TS_CM_DISPATCH(32, false);
-  TS_CM_DISPATCH(64, false);
-#undef TS_CM_DISPATCH
+  if (c.bk == 32) TS_PAIR_DISPATCH(32, false);
+  TS_PAIR_DISPATCH(64, false);
+#undef TS_PAIR_DISPATCH
 }
 
 ts_status pass(int np, int nacc, const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n,
@@ -1397,12 +1371,10 @@ ts_status mixed_solve_schedule(const ts_plan* p, const ts_precision* sched, int 
 
 ts_status tc_prepare_kernels() {
   // Shared-memory opt-in for every instantiation, outside any stream capture.
-#define TS_PREP1(NP, NACC, BKT, PO, CM, PAIR)                                                          \
-  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, CM, PAIR>,                            \
+#define TS_PREP1(NP, NACC, BKT, PO, PAIR)                                                              \
+  TS_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc<NP, NACC, BKT, PO, PAIR>,                                \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT))
-#define TS_PREP(NP, NACC, BKT, PO)                                                                     \
-  TS_PREP1(NP, NACC, BKT, PO, 1, false); TS_PREP1(NP, NACC, BKT, PO, 2, false);                         \
-  TS_PREP1(NP, NACC, BKT, PO, 4, false); TS_PREP1(NP, NACC, BKT, PO, 1, true)
+#define TS_PREP(NP, NACC, BKT, PO) TS_PREP1(NP, NACC, BKT, PO, false); TS_PREP1(NP, NACC, BKT, PO, true)
   TS_PREP(1, 1, 64, true); TS_PREP(1, 1, 64, false); TS_PREP(1, 1, 32, true); TS_PREP(1, 1, 32, false);
   TS_PREP(1, 2, 64, true); TS_PREP(1, 2, 64, false); TS_PREP(1, 2, 32, true); TS_PREP(1, 2, 32, false);
   TS_PREP(2, 1, 64, true); TS_PREP(2, 1, 64, false); TS_PREP(2, 1, 32, true); TS_PREP(2, 1, 32, false);
@@ -1433,8 +1405,9 @@ ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster
     return TS_OK;
   }
   if ((bk != 32 && bk != 64) || bn_cap < 16 || bn_cap > 256 || bn_cap % 16 != 0 || n < 0 ||
-      (cluster != 1 && cluster != 2 && cluster != 4 && cluster != TS_TC_PAIR)) {
-    set_error("invalid tensor-core tile configuration (bk %d, bn_cap %d, cluster %d)", bk, bn_cap, cluster);
+      (cluster != 1 && cluster != TS_TC_PAIR)) {
+    set_error("invalid tensor-core tile configuration (bk %d, bn_cap %d, cluster %d; cluster is 1 or TS_TC_PAIR)",
+              bk, bn_cap, cluster);
     return TS_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lk(g_cfg_mu);
@@ -1442,7 +1415,6 @@ ts_status tc_config_set(int complex_data, int n, int bk, int bn_cap, int cluster
   c.bk = bk;
   c.bn_cap = bn_cap;
   c.pair = cluster == TS_TC_PAIR;
-  c.cm = c.pair ? 1 : cluster;
   g_cfg[{complex_data ? 2 : 1, n}] = c;
   return TS_OK;
 }

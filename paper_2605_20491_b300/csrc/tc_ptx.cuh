@@ -68,18 +68,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// The same load, multicast: the box lands at the same shared-memory offset in every CTA of
-// the cluster named in cta_mask, and completes tx bytes on the barrier at the same offset
-// in each of them.
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
-                                               uint64_t* bar, uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(cta_mask)
-      : "memory");
-}
-
 // The same load for a CTA pair (tcgen05 cta_group::2): the box lands in this CTA's shared
 // memory and completes tx bytes on the barrier at the shared::cluster address mbar_cluster,
 // which may be the peer CTA's (the pair's leader, which issues the MMAs).
@@ -229,8 +217,9 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, u
 }
 
 // Arrive on the barrier at `bar`'s offset in both CTAs of the pair (cta_mask) once the
-// leader's previously issued pair MMAs have completed.
-__device__ __forceinline__ void mma_commit_pair_mc(uint64_t* bar, uint16_t cta_mask) {
+// leader's previously issued pair MMAs have completed.  This is a barrier signal to the two
+// CTAs of the pair, not a data load.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t cta_mask) {
   asm volatile(
       "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
           smem_u32(bar)),
@@ -242,16 +231,6 @@ __device__ __forceinline__ void mma_commit_pair_mc(uint64_t* bar, uint16_t cta_m
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-
-// Arrive on the barrier at `bar`'s offset in every CTA of cta_mask once this thread's
-// previously issued tcgen05.mma have completed.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(cta_mask)
-      : "memory");
 }
 
 // Each thread of the warp reads 16 consecutive 32-bit columns of its own TMEM lane.

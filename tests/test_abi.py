@@ -112,3 +112,16 @@ def test_plan_handle_is_freed_once(monkeypatch):
     del Q
     gc.collect()
     assert freed == [0x1234, 0x5678]
+
+
+def test_tile_config_refuses_clusters_other_than_single_and_pairs(built_lib):
+    """ts_tc_config_set accepts cluster 1 (single CTAs) and TS_TC_PAIR only: no tile of the
+    contraction is shared through a multicast load.  The check is host-side (no GPU)."""
+    from paper_2605_20491_b300 import tschrod as T
+    L = T.lib()
+    for cluster in (2, 4, 8, 0, -1, 3):
+        assert L.ts_tc_config_set(0, 64, 64, 128, cluster) == T.TS_ERR_INVALID_ARG, cluster
+        assert "cluster" in T.ts_last_error()
+    for cluster in (1, T.TS_TC_PAIR):
+        assert L.ts_tc_config_set(0, 64, 64, 128, cluster) == T.TS_OK
+        assert L.ts_tc_config_set(0, 64, 0, 0, 0) == T.TS_OK  # forget it again

@@ -189,31 +189,6 @@ def test_cta_pairs_match_single_cta(T, n, caps):
     assert np.array_equal(out_pair, out_one)
 
 
-@pytest.mark.parametrize("cluster", [2, 4])
-@pytest.mark.parametrize("n", [(64, 64, 64), (40, 24, 8), (264, 16), (128, 96, 48)])
-def test_multicast_clusters_match_oracle(T, n, cluster):
-    """The S_k tile shared by TMA multicast across a cluster of 2 or 4 CTAs gives the
-    same parity as the unclustered pass (ragged M tails leave some CTAs of a cluster with
-    rows beyond the tensor: they load zeros and store nothing)."""
-    L, f = harmonic_case(n)
-    P, Po = plans(n, L, f, MASK)
-    b = S.normal(2, Po.N)
-    psi = S.complex_normal(3, Po.N)
-    try:
-        T.ts_tc_config_set(False, 0, 64, 256, cluster)
-        T.ts_tc_config_set(True, 0, 64, 128, cluster)
-        u = dev(np.zeros(Po.N))
-        T.ts_apply_inverse(P, 0.5, dev(b), u, T.TS_BF16X3)
-        out = dev(np.zeros(2 * Po.N))
-        T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C128, T.TS_BF16X6)
-        T.ts_device_status()
-    finally:
-        T.ts_tc_config_reset(False)
-        T.ts_tc_config_reset(True)
-    assert rel(host(u), O.apply_inverse(Po, 0.5, b)) < TOL[1]
-    assert rel(host(out), O.apply_exp(Po, 0.01, psi)) < TOL[2]
-
-
 MASK1 = MASK | (1 << 6)  # TS_BF16X1
 
 
