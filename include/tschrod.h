@@ -167,14 +167,20 @@ ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, d
  * e.g. an application that gives the whole device to its own allocator at start-up, or
  * a latency-critical loop that cannot pay for cudaMalloc/cudaFree (cudaFree synchronises
  * the device) or for growing a memory pool.  Same arguments and result as
- * ts_apply_inverse (prec TS_FP64, TS_BF16X3 or TS_BF16X6; b and u may alias); the two
- * intermediate buffers come from a fixed 32 MiB array inside the library, which every GPU
- * that loads the library holds until the process exits.  Limit: 2 * N * 8 bytes (TS_FP64),
- * 2 * N * 4 (TS_BF16X3) or 2 * N * 6 (TS_BF16X6) must fit in 32 MiB, i.e. N <= 2,097,152,
- * 4,194,304 or 2,796,202; larger N returns TS_ERR_INVALID_ARG with the limit in the message.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it.  All calls share the array and it keeps the last call's contents; calls
- * that overlap on the GPU (other streams or threads) race on it, so serialise them.
+ * ts_apply_inverse (prec TS_FP64, TS_BF16X1, TS_BF16X3 or TS_BF16X6, checked as there;
+ * b and u may alias); the two intermediate buffers come from a fixed 32 MiB array inside
+ * the library, which every GPU that loads the library holds until the process exits.
+ * Limit: two buffers of N doubles (TS_FP64) or of the bf16 planes of the widest pass
+ * (2, 4 or 6 bytes per value for TS_BF16X1 / X3 / X6, each pass's contracted axis padded to
+ * a multiple of 8) must fit in 32 MiB: N <= 2,097,152 (FP64), 8,388,608 (BF16X1), 4,194,304
+ * (BF16X3) or 2,796,202 (BF16X6) when every n_k is a multiple of 8, less otherwise; a plan
+ * above it returns TS_ERR_INVALID_ARG with its own requirement in the message.  Set-up: the
+ * first call in each CUDA context of a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for that context; a device whose context has been
+ * replaced (e.g. after cudaDeviceReset) is looked up again.  Make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's contents
+ * (nothing needs to start at zero); calls that overlap on the GPU (other streams or
+ * threads) race on it, so serialise them.
  */
 ts_status ts_apply_inverse_noalloc(const ts_plan* plan, double sigma, const double* b, double* u,
                                    ts_precision prec, void* stream);

@@ -14,7 +14,7 @@ import pytest
 
 import oracle as O
 from paper_2605_20491_b300 import synth as S
-from gpu_util import dev, harmonic_case, host, plans, rel
+from gpu_util import MAXNORM_FACTOR, dev, harmonic_case, host, maxrel, plans, rel
 
 pytestmark = pytest.mark.gpu
 TOL = {1: 5e-5, 2: 1e-5}   # TS_BF16X3, TS_BF16X6
@@ -39,8 +39,10 @@ def test_inverse_mixed_vs_oracle(T, n, prec):
     u = dev(np.zeros(Po.N))
     T.ts_apply_inverse(P, 0.5, dev(b), u, prec)
     T.ts_device_status()
-    err = rel(host(u), O.apply_inverse(Po, 0.5, b))
+    want = O.apply_inverse(Po, 0.5, b)
+    err = rel(host(u), want)
     assert err < TOL[prec], err
+    assert maxrel(host(u), want) < MAXNORM_FACTOR * TOL[prec]
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -60,8 +62,11 @@ def test_exp_mixed_vs_oracle(T, n, prec, dtype):
         T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C64, prec)
         tol = max(TOL[prec], 1e-6)
     T.ts_device_status()
-    err = rel(host(out), O.apply_exp(Po, 0.01, psi.astype(np.float64)))
+    got = host(out).astype(np.float64)
+    want = O.apply_exp(Po, 0.01, psi.astype(np.float64))
+    err = rel(got, want)
     assert err < tol, err
+    assert maxrel(got, want) < MAXNORM_FACTOR * tol
 
 
 def test_mixed_rejects_unsupported(T):

@@ -79,24 +79,6 @@ def _coulomb_level(T, n, delta):
     return P, V2.reshape(-1).contiguous()
 
 
-@pytest.mark.parametrize("delta,lam_printed", [(0.1, 5.060514417326), (0.01, 5.221829172892)])
-def test_paper_coulomb_ground_state_4d(T, delta, lam_printed):
-    """Table coulomb_ground_99: two particles in 2D with traps |x|^2 and the soft Coulomb
-    repulsion 1 / sqrt(|x_1 - x_2|^2 + delta^2) on [-8, 8]^4, Q^10; shifted inverse iteration
-    with PCG (preconditioner (-Delta + V_trap)^{-1}, tolerance 1e-9, warm-started), shift
-    lambda_min(-Delta + V_trap) - 1e-4 = 3.9999, multi-level from 49^4 to the table's 99^4
-    (9.6e7 DoFs): lambda_1 to the printed 13 digits."""
-    import torch
-    levels = [_coulomb_level(T, 49, delta), _coulomb_level(T, 99, delta)]
-    plans = [p for p, _ in levels]
-    shift = sum(T.ts_plan_eigs(plans[-1], a)[0] for a in range(4)) - 1e-4
-    u = torch.empty(plans[-1].N, dtype=torch.float64, device="cuda")
-    lam, outer, pcg = T.ts_inverse_iteration_multilevel(plans, [v for _, v in levels], shift, u, 1e-13, 200, 1e-9,
-                                                        500, T.TS_BF16X3)
-    print(f"coulomb delta {delta}: lambda {lam!r}, outer {outer}, pcg {pcg}")
-    assert abs(lam - lam_printed) < 1e-11
-
-
 def test_paper_pcg_precond_iterations(T):
     """Table pcg_precond: PCG on (-Delta + V1 + V2) u = f, the 4D Coulomb system with
     delta = 0.01 on 49^4 Q^10, random f, tolerance 1e-12, FP64, preconditioner

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 from paper_2605_20491_b300 import synth as S
-from gpu_util import dev, host, plans, rel
+from gpu_util import MAXNORM_FACTOR, dev, host, maxrel, plans, rel
 
 pytestmark = pytest.mark.gpu
 FP32_MASK = 1 << 5
@@ -29,8 +29,11 @@ def test_fp32_exp_vs_oracle(T, n):
     psi = S.complex_normal(3, Po.N).astype(np.float32)
     out = dev(np.zeros(2 * Po.N, dtype=np.float32))
     T.ts_apply_exp(P, 0.01, dev(psi), out, T.TS_C64, T.TS_FP32)
-    err = rel(host(out), O.apply_exp(Po, 0.01, psi.astype(np.float64)))
+    got = host(out).astype(np.float64)
+    want = O.apply_exp(Po, 0.01, psi.astype(np.float64))
+    err = rel(got, want)
     assert err < 2e-6, err
+    assert maxrel(got, want) < MAXNORM_FACTOR * 2e-6
     # in place
     x = dev(psi)
     T.ts_apply_exp(P, 0.01, x, x, T.TS_C64, T.TS_FP32)
@@ -49,7 +52,9 @@ def test_fp32_strang_vs_oracle(T, n, Lv):
     want = O.strang(Po, V2, 0.01, steps, psi)
     t = dev(psi.astype(np.float32))
     T.ts_split_step(P, 0.01, steps, dev(V2), t, T.TS_C64, T.TS_FP32)
-    assert rel(host(t), want) < 1e-5
+    got = host(t).astype(np.float64)
+    assert rel(got, want) < 1e-5
+    assert maxrel(got, want) < MAXNORM_FACTOR * 1e-5
 
 
 @pytest.mark.parametrize("name", ["6d_n24_strang", "9d_n8_strang"])

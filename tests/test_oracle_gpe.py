@@ -78,3 +78,35 @@ def test_two_flows_reach_the_same_minimiser():
     assert abs(E - E1) < 1e-13 * E1 and abs(l2 - l1) < 1e-10 * l1
     assert np.linalg.norm(u - u1) < 1e-9 * np.linalg.norm(u1)
     assert it < it1 / 5  # the a_u metric needs far fewer steps (Sec. 4.3)
+
+
+@pytest.mark.parametrize("beta", [0.0, 10.0, 100.0])
+def test_energy_gradient_is_the_nonlinear_operator(beta):
+    """eq. gpe is the Euler-Lagrange equation of eq. gpe_energy: the first variation of
+    E(u) = 1/2 (u, (-Delta + V) u) + beta/4 (u^2, u^2) in a direction v is (H_u u, v) with
+    H_u = -Delta + V + beta u^2, all inner products weighted by the quadrature masses.
+    E(u + eps v) is a quartic in eps, so the central difference
+    (E(u + eps v) - E(u - eps v)) / (2 eps) = (H_u u, v) + eps^2 beta (u, v^3) exactly;
+    the eps^2 term is removed by taking two eps.  A wrong coefficient of the quartic term
+    (beta/2 instead of beta/4), a missing 1/2 or unweighted sums all fail this."""
+    P0, PV, V = _grid()
+    rng = np.random.default_rng(5)
+    u = gpe.normalize(P0, 1.0 + 0.3 * rng.standard_normal(P0.N))
+    v = rng.standard_normal(P0.N)
+
+    def cdiff(eps):
+        return (gpe.energy(P0, V, beta, u + eps * v) - gpe.energy(P0, V, beta, u - eps * v)) / (2 * eps)
+
+    e1, e2 = 1e-3, 5e-4
+    d1, d2 = cdiff(e1), cdiff(e2)
+    deriv = (d2 * e1 ** 2 - d1 * e2 ** 2) / (e1 ** 2 - e2 ** 2)  # eps^2 term eliminated
+    Hu = sem.operator(P0, u, 0.0, V + beta * u * u)
+    want = gpe.inner(P0, Hu, v)
+    assert abs(deriv - want) < 1e-8 * abs(want)
+    # the quartic term alone: (E_beta - E_0) is beta/4 (u^2, u^2), whose variation is beta (u^3, v)
+    if beta > 0:
+        q = lambda w: gpe.energy(P0, V, beta, w) - gpe.energy(P0, V, 0.0, w)
+        cq = lambda eps: (q(u + eps * v) - q(u - eps * v)) / (2 * eps)
+        dq = (cq(e2) * e1 ** 2 - cq(e1) * e2 ** 2) / (e1 ** 2 - e2 ** 2)
+        want_q = beta * gpe.inner(P0, u ** 3, v)
+        assert abs(dq - want_q) < 1e-8 * abs(want_q)
