@@ -475,9 +475,11 @@ ts_status ts_autotune(const ts_plan* plan, ts_dtype dtype, ts_precision prec, co
  * ts_profile_begin: start recording a CUDA event pair around every launch of the
  *   contraction kernels (on the launching stream); clears earlier records.
  * ts_profile_end: stop recording and sum the records of one kernel kind
- *   (0 = split-precision tensor-core pass with 2 or 3 bf16 planes, 1 = FP64 pass, 2 = small-n
- *   fused pass, 3 = refinement residual with the exact fixed-point Laplacian, 4 = tensor-core
- *   pass with one bf16 plane):
+ *   (0 = split-precision tensor-core pass writing 2 or 3 bf16 planes, 1 = FP64 pass,
+ *   2 = small-n fused pass, 3 = refinement residual with the exact fixed-point Laplacian,
+ *   4 = tensor-core pass writing one bf16 plane, 5 = tensor-core pass writing the FP64 or
+ *   complex result (the last pass of an apply, any plane count), 6 = work-list tensor-core
+ *   pass of a batched apply; launches captured into a CUDA graph are not recorded):
  *   launches, total device time in ms, algorithmic FLOPs and algorithmic HBM bytes.
  *   Synchronises on the recorded events.  Any pointer may be NULL.
  */

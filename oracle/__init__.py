@@ -45,6 +45,7 @@ def lib():
         L.or_jacobi_eigh.restype = C.c_int
         L.or_mode_forward.argtypes = [C.c_int, _ip, C.c_int, _dp, C.c_int, _dp, _dp]
         L.or_mode_backward.argtypes = [C.c_int, _ip, C.c_int, _dp, C.c_int, _dp, _dp]
+        L.or_mode_fibers.argtypes = [C.c_int, _ip, C.c_int, _dp, C.c_int, _dp, _dp, C.c_long, C.c_long]
         L.or_apply_inverse.argtypes = [C.c_int, _ip, C.POINTER(_dp), C.POINTER(_dp), C.c_double, _dp, _dp]
         L.or_apply_exp.argtypes = [C.c_int, _ip, C.POINTER(_dp), C.POINTER(_dp), C.c_double, _dp, _dp]
         L.or_dense_operator.argtypes = [C.c_int, _ip, C.POINTER(_dp), _dp, C.c_double, _dp]
@@ -156,6 +157,12 @@ def mode_backward(P: Plan, k: int, X, ncomp: int = 1) -> np.ndarray:
     Y = np.empty_like(X)
     lib().or_mode_backward(P.d, P._n(), k, _p(P.S[k]), ncomp, _p(X), _p(Y))
     return Y
+
+
+def mode_fibers(P: Plan, k: int, X, Y, backward: bool, f0: int, f1: int) -> None:
+    """Timing sample: the forward (or backward) transform along axis k of real X, written
+    into Y, for the fibers with flat index in [f0, f1) only (see or_mode_fibers)."""
+    lib().or_mode_fibers(P.d, P._n(), k, _p(P.S[k]), int(backward), _p(X), _p(Y), int(f0), int(f1))
 
 
 def apply_inverse(P: Plan, sigma: float, b) -> np.ndarray:

@@ -189,6 +189,32 @@ void or_mode_backward(int d, const int* n, int k, const double* S, int ncomp,
         }
 }
 
+/*
+ * Timing sample of the two transforms above (real data): the same loops restricted to the
+ * axis-k fibers with flat index f = l + lo * h in [f0, f1) (0 <= f0 <= f1 <= lo * hi);
+ * backward = 0 gives or_mode_forward's sum over S[i][j] x_i, 1 gives or_mode_backward's
+ * sum over S[i][j] x_j.  Outputs of other fibers are left as they are.  Used to time the
+ * oracle on a bounded part of a grid too large to transform whole within a time budget.
+ */
+void or_mode_fibers(int d, const int* n, int k, const double* S, int backward, const double* X,
+                    double* Y, long f0, long f1) {
+  long lo = 1;
+  for (int j = 0; j < k; ++j) lo *= n[j];
+  int nk = n[k];
+#pragma omp parallel for schedule(static)
+  for (long f = f0; f < f1; ++f) {
+    const long l = f % lo, h = f / lo;
+    for (int o = 0; o < nk; ++o) {
+      double acc = 0.0;
+      for (int i = 0; i < nk; ++i) {
+        const double s = backward ? S[(long)o * nk + i] : S[(long)i * nk + o];
+        acc += s * X[l + lo * (i + (long)nk * h)];
+      }
+      Y[l + lo * (o + (long)nk * h)] = acc;
+    }
+  }
+}
+
 /* Sum of the per-axis eigenvalues at the multi-index of linear index idx. */
 static double or_lambda_sum(int d, const int* n, const double* const* lam, long idx) {
   double s = 0.0;

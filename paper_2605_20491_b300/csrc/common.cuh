@@ -43,12 +43,14 @@ void count_launches(int k);
 // Live per-kernel timing (ts_profile_begin / ts_profile_end): when enabled, the launch
 // sites of the contraction kernels bracket each launch with CUDA events on its stream.
 enum ProfKind {
-  PROF_TC_PASS = 0,     // split-precision tensor-core pass, 2 or 3 bf16 planes
+  PROF_TC_PASS = 0,      // split-precision tensor-core pass writing 2 or 3 bf16 planes
   PROF_FP64_PASS = 1,
   PROF_SMALL_PASS = 2,
   PROF_RESIDUAL = 3,
-  PROF_TC_PASS_X1 = 4,  // the same kernel with one bf16 plane (BF16X1)
-  PROF_NKINDS = 5
+  PROF_TC_PASS_X1 = 4,   // the same kernel writing one bf16 plane (BF16X1)
+  PROF_TC_PASS_OUT = 5,  // the same kernel writing the FP64 / complex result (last pass, any planes)
+  PROF_TC_LIST = 6,      // the work-list form of the pass (batched applies)
+  PROF_NKINDS = 7
 };
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, void** token);

@@ -841,7 +841,8 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
     const double bytes = (double)NACC * R * n * 2.0 * NP * (ep.out_mode == 0 ? 2.0 : 1.0) +
                          (ep.out_mode == 1 ? 8.0 : ep.out_mode == 2 ? 16.0 : ep.out_mode == 3 ? 8.0
                                                  : ep.out_mode == 4 ? 16.0 : 0.0) * R * n;
-    prof_end_launch(s, tok, NP == 1 ? PROF_TC_PASS_X1 : PROF_TC_PASS, flops, bytes);
+    const int kind = ep.out_mode != 0 ? PROF_TC_PASS_OUT : (NP == 1 ? PROF_TC_PASS_X1 : PROF_TC_PASS);
+    prof_end_launch(s, tok, kind, flops, bytes);
   }
   return TS_OK;
 }
@@ -1115,8 +1116,23 @@ ts_status launch_list_t(const TcItemList& L, int smem, cudaStream_t s) {
     TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
   }
   const unsigned grid = (unsigned)(L.total < g_num_sms ? L.total : g_num_sms);
+  void* tok = nullptr;
+  if (prof_enabled()) prof_begin_launch(s, &tok);
   k_rot_tc_list<NP, NACC, BKT, PO><<<grid, TC_THREADS, smem, s>>>(L);
   TS_LAUNCHED(1);
+  if (tok) {
+    // algorithmic work of all items: products x 2 R n^2 FLOP; planes in, planes or result out
+    double flops = 0.0, bytes = 0.0;
+    for (int i = 0; i < L.count; ++i) {
+      const EpiParams& ep = L.item[i].ep;
+      const double vals = (double)ep.R * ep.n;
+      flops += 2.0 * Products<NP>::count * NACC * vals * ep.n;
+      const double out_b = ep.out_mode == 0 ? 2.0 * NP * NACC
+                         : ep.out_mode == 1 ? 8.0 : ep.out_mode == 2 ? 16.0 : ep.out_mode == 3 ? 8.0 : 16.0;
+      bytes += vals * (2.0 * NP * NACC + out_b);
+    }
+    prof_end_launch(s, tok, PROF_TC_LIST, flops, bytes);
+  }
   return TS_OK;
 }
 

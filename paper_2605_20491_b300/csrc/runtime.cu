@@ -42,6 +42,13 @@ void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed);
 bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
 
 void prof_begin_launch(cudaStream_t s, void** token) {
+  *token = nullptr;
+  // launches being captured into a graph are not timed (their events would become nodes)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEvent_t e = take_event();
   cudaEventRecord(e, s);

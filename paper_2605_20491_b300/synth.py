@@ -90,6 +90,67 @@ def complex_normal(seed: int, count: int) -> np.ndarray:
     return out
 
 
+# ------------------------------------------- the same draws on a torch device -----
+#
+# For workloads too large to generate on the host in reasonable time (the serving
+# benchmark's thousands of requests): SplitMix64 on int64 tensors, where multiplication
+# wraps modulo 2^64 and logical right shifts are arithmetic shifts with the sign bits
+# masked off.  The integer outputs equal splitmix64() bit for bit; the normals go through
+# the device's log / cos / sin, which may differ from numpy's in the last bit.
+
+def _i64(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _srl(z, s: int):
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def splitmix64_torch(seed: int, k):
+    """splitmix64() on an int64 tensor of output indices k; int64 result with the same
+    64 bits as the uint64 outputs."""
+    z = _i64(seed & _MASK) + (k + 1) * _i64(GAMMA)
+    z = (z ^ _srl(z, 30)) * _i64(_M1)
+    z = (z ^ _srl(z, 27)) * _i64(_M2)
+    return z ^ _srl(z, 31)
+
+
+def _box_muller_torch(seed: int, count: int, device):
+    import torch
+    k = torch.arange(count, dtype=torch.int64, device=device)
+    scale = 2.0 ** -53
+    u1 = 1.0 - _srl(splitmix64_torch(seed, 2 * k), 11).to(torch.float64) * scale
+    u2 = _srl(splitmix64_torch(seed, 2 * k + 1), 11).to(torch.float64) * scale
+    return torch.sqrt(-2.0 * torch.log(u1)), 2.0 * math.pi * u2
+
+
+def normal_torch(seed: int, count: int, device="cuda"):
+    """normal() generated on `device` (float64 tensor)."""
+    import torch
+    rad, th = _box_muller_torch(seed, count, device)
+    return rad * torch.cos(th)
+
+
+def complex_normal_torch(seed: int, count: int, device="cuda"):
+    """complex_normal() generated on `device`: interleaved float64 tensor of length 2 count."""
+    import torch
+    rad, th = _box_muller_torch(seed, count, device)
+    return torch.stack((rad * torch.cos(th), rad * torch.sin(th)), dim=1).reshape(-1)
+
+
+def v2_cos_bumps_torch(n, L, seed: int = 1, count: int = 8, device="cuda"):
+    """v2_cos_bumps() evaluated on `device` (the bump parameters are drawn on the host)."""
+    import torch
+    assert len(n) == 3
+    a, c = bumps_params(seed, count)
+    x = [torch.from_numpy(_axis_coords(n, L, k)).to(device) for k in range(3)]
+    v = 5.0 * torch.cos(x[0]) * torch.cos(x[1]) * torch.cos(x[2])
+    for j in range(count):
+        r2 = (x[0] - c[j][0]) ** 2 + (x[1] - c[j][1]) ** 2 + (x[2] - c[j][2]) ** 2
+        v = v + a[j] * torch.exp(-r2)
+    return v.reshape(-1).contiguous()
+
+
 # ----------------------------------------------------------------- grids -----
 
 def nodes(n: int, L: float) -> np.ndarray:

@@ -348,7 +348,7 @@ def ts_profile_begin():
     _check(lib().ts_profile_begin(), "ts_profile_begin")
 
 
-PROF_TC_PASS, PROF_FP64_PASS, PROF_SMALL_PASS, PROF_RESIDUAL, PROF_TC_PASS_X1 = range(5)
+PROF_TC_PASS, PROF_FP64_PASS, PROF_SMALL_PASS, PROF_RESIDUAL, PROF_TC_PASS_X1, PROF_TC_PASS_OUT, PROF_TC_LIST = range(7)
 
 
 def ts_profile_end(kind: int):

@@ -330,3 +330,46 @@ def test_strang_converges_to_dense_exponential_of_full_h():
     e1 = rel(O.strang(P, V2, 0.01, 10, psi), want)
     e2 = rel(O.strang(P, V2, 0.005, 20, psi), want)
     assert e1 < 1e-3 and 3.8 < e1 / e2 < 4.2
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_fiber_sample_equals_the_transforms(k):
+    """The timing sample of the oracle's transforms (a range of axis-k fibers) computes,
+    on its fibers, exactly what the full forward and backward transforms compute, and
+    leaves the other fibers alone."""
+    n = (7, 5, 6)
+    L = (2.0, 3.0, 1.5)
+    P = O.plan(n, L, S.harmonic(n, L, (1.0, 1.2, 0.8)))
+    X = S.normal(3, P.N)
+    fibers = P.N // n[k]
+    for backward, full in ((False, O.mode_forward), (True, O.mode_backward)):
+        want = full(P, k, X)
+        Y = np.full(P.N, np.nan)
+        O.mode_fibers(P, k, X, Y, backward, 0, fibers)
+        assert np.array_equal(Y, want)
+        Y = np.full(P.N, np.nan)
+        O.mode_fibers(P, k, X, Y, backward, 3, 11)
+        lo = int(np.prod(n[:k]))
+        touched = np.zeros(P.N, dtype=bool)
+        for f in range(3, 11):
+            l, h = f % lo, f // lo
+            for o in range(n[k]):
+                touched[l + lo * (o + n[k] * h)] = True
+        assert np.array_equal(Y[touched], want[touched]) and np.all(np.isnan(Y[~touched]))
+
+
+def test_device_generators_match_the_host_ones():
+    """The torch form of the seeded generators (run here on the CPU device) gives the same
+    SplitMix64 bits as the numpy form, and the same normals, complex normals and V2 up to
+    the last bit of log / cos / sin / exp."""
+    import torch
+    k = np.arange(0, 5000, dtype=np.uint64)
+    want = S.splitmix64(7, k)
+    got = S.splitmix64_torch(7, torch.arange(0, 5000, dtype=torch.int64)).numpy().view(np.uint64)
+    assert np.array_equal(got, want)
+    assert np.allclose(S.normal_torch(11, 3001, "cpu").numpy(), S.normal(11, 3001), rtol=1e-14, atol=1e-14)
+    assert np.allclose(S.complex_normal_torch(12, 999, "cpu").numpy(), S.complex_normal(12, 999),
+                       rtol=1e-14, atol=1e-14)
+    n, L = (9, 7, 5), (8.0, 8.0, 8.0)
+    assert np.allclose(S.v2_cos_bumps_torch(n, L, 1, device="cpu").numpy(), S.v2_cos_bumps(n, L, 1),
+                       rtol=1e-14, atol=1e-14)
