@@ -291,6 +291,13 @@ def run_profile_case(args):
     P = T.ts_plan_create(n, w["L"], synth.harmonic(n, w["L"], w["omega"]), (1 << T.TS_BF16X3) | (1 << T.TS_BF16X1))
     b = torch.from_numpy(synth.normal(w["seed"], P.N)).cuda()
     x = torch.empty_like(b)
+    if args.profile_fp64:
+        # the plain FP64 apply (k_rot_fp64 passes) only
+        for _ in range(args.warmup + args.steps):
+            T.ts_apply_inverse(P, w["sigma"], b, x, T.TS_FP64)
+        torch.cuda.synchronize()
+        print("profile case done", flush=True)
+        return 0
     for _ in range(args.warmup + args.steps):
         T.ts_solve_schedule(P, w["sigma"], b, x, [getattr(T, q) for q in SCHEDULE])
     torch.cuda.synchronize()
@@ -893,6 +900,8 @@ def main():
                     help="run only the refined solve (for ncu captures); prints no JSON line")
     ap.add_argument("--profile-n", type=int, default=0,
                     help="grid points per axis of the --profile-case refined solve (default: the workload's)")
+    ap.add_argument("--profile-fp64", action="store_true",
+                    help="with --profile-case: the plain FP64 inverse apply instead of the refined solve")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 6D / 9D Strang and 3D n = 256 inverse-iteration sub-runs")

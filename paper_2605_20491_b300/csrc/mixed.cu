@@ -40,6 +40,7 @@
 #include <tuple>
 #include <vector>
 
+#include "fixed.cuh"
 #include "mixed.cuh"
 #include "pointwise.cuh"
 #include "split.cuh"
@@ -72,9 +73,33 @@ constexpr int UMMA_K = 16;          // K of one tcgen05.mma kind::f16
 constexpr int MAX_STAGES = 8;
 constexpr int SMEM_LIMIT = 232448;  // 227 KB opt-in shared memory per CTA
 
+// Scales of the fixed-point iterate U = u 2^s of a refined solve (see mixed_solve_schedule):
+// fx[0] = the largest biased FP64 exponent of b (recorded by the input split), fx[1] = the
+// largest biased FP32 exponent of u_0 (recorded by the pass that stores U_0).  Scale kind 0
+// (U_0) follows from the bound max|u| <= beta max|b|, kind 1 (every later U) from max|u_0|;
+// both keep |U| < 2^(hu - 1).
+struct FixScale {
+  const int* fx;
+  int hu;   // headroom of the exact residual: |U| < 2^hu
+  int l2b;  // ceil(log2 beta) + 2
+};
+
+__device__ __forceinline__ int fix_scale(const FixScale& f, int kind) {
+  const int s0 = f.hu - (f.fx[0] - 1022) - f.l2b;
+  if (kind == 0) return s0;
+  int s1 = f.hu - (f.fx[1] - 126) - 1;
+  s1 = s1 < s0 ? s0 : s1;
+  return s1 > s0 + 60 ? s0 + 60 : s1;
+}
+
 struct EpiParams {
-  int out_mode;    // 0: bf16 planes, 1: FP64 real, 2: complex128, 3: complex64, 4: FP64 real +=
-  int* emax_out;   // out_mode 1 / 4: atomic max of the stored values' biased exponents (NULL: none)
+  int out_mode;    // 0: bf16 planes, 1: FP64 real, 2: complex128, 3: complex64, 4: FP64 real +=,
+                   // 5: U = fixed(v) (int64), 6: U = U 2^ds + fixed(v), 7: FP64 (U 2^ds + fixed(v)) 2^-s
+  int* emax_out;   // out_mode 1 / 4: atomic max of the stored values' biased exponents; 5: of the
+                   // values' biased FP32 exponents (NULL: none)
+  FixScale fxs;             // out_mode 5-7: the solve's scales
+  int fix_in, fix_out;      // scale kinds of the U read (6, 7) and of the result (5-7)
+  const long long* fix_src; // out_mode 6, 7: U before the update (may equal out for 6)
   int scale_mode;  // 0: none, 1: inverse 1/(Lambda + sigma), 2: phase e^{-i tau Lambda}
   long long R;     // rows of the pass
   int n;           // contracted (= output column) extent
@@ -143,12 +168,12 @@ __device__ __forceinline__ double f2d(float f) {
 // sigma + the row axes' eigenvalues (scale 1) or the product of their phases (scale 2) at
 // data row r of a pass, from the per-axis FP64 tables (the first row axis fastest).
 __device__ __forceinline__ void epi_row_factors(const EpiParams& ep, long long r, float* rowsum, float2* rowph) {
-  long long q = r;
+  unsigned q = (unsigned)r;  // rows of a pass are below 2^31
   double sacc = ep.sigma;
   double pr = 1.0, pi = 0.0;
   for (int k = 0; k < ep.rd; ++k) {
-    long long qq = q / ep.rn[k];
-    int i = (int)(q - qq * ep.rn[k]);
+    const unsigned qq = q / (unsigned)ep.rn[k];
+    const int i = (int)(q - qq * (unsigned)ep.rn[k]);
     q = qq;
     if (ep.scale_mode == 1) {
       sacc += ep.rlam[k][i];
@@ -176,15 +201,17 @@ __device__ __forceinline__ long long epi_out_row(const EpiParams& ep, long long 
 // (transposed: element r + R j); emx collects the largest biased exponent of FP64 stores.
 template <int NP, int NACC, bool PLANES_OUT>
 __device__ __forceinline__ void epi_chunk(const EpiParams& ep, const uint32_t (&v)[NACC][16], long long r, int jbase,
-                                          float rowsum, float2 rowph, int& emx) {
+                                          float rowsum, float2 rowph, int& emx, int fs = 0, int fds = 0,
+                                          float fsc = 0.f) {
   const int jn = ep.n - jbase < 16 ? ep.n - jbase : 16;
   long long idx = r + ep.Ro * (long long)jbase;  // r: the output row (mapped by the caller)
-  double prev[16];
-  if (!PLANES_OUT && ep.out_mode == 4) {
-    // u += delta: issue all 16 loads of the chunk before any store, so they overlap
-    const double* uo = reinterpret_cast<const double*>(ep.out);
+  // the chunk's previous values (out_mode 4: u as FP64 bits; 6, 7: the integer U), all 16
+  // loads issued before any store so that they overlap
+  long long prev[16];
+  if (!PLANES_OUT && (ep.out_mode == 4 || (NACC == 1 && ep.out_mode >= 6))) {
+    const long long* src = ep.out_mode == 4 ? reinterpret_cast<const long long*>(ep.out) : ep.fix_src;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) prev[i] = i < jn ? uo[idx + ep.Ro * (long long)i] : 0.0;
+    for (int i = 0; i < 16; ++i) prev[i] = i < jn ? src[idx + ep.Ro * (long long)i] : 0;
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i, idx += ep.Ro) {
@@ -194,7 +221,8 @@ __device__ __forceinline__ void epi_chunk(const EpiParams& ep, const uint32_t (&
 #pragma unroll
     for (int c = 0; c < NACC; ++c) val[c] = __uint_as_float(v[c][i]);
     if (ep.scale_mode == 1) {
-      val[0] = val[0] * (1.0f / (rowsum + ep.clam[j]));
+      // fast division (2 ulp of FP32, far below the rounding of the bf16 planes)
+      val[0] = __fdividef(val[0], rowsum + ep.clam[j]);
     } else if (ep.scale_mode == 2 && NACC == 2) {
       const float2 cp = ep.cph[j];
       const float cx = cp.x, cy = cp.y;
@@ -214,13 +242,25 @@ __device__ __forceinline__ void epi_chunk(const EpiParams& ep, const uint32_t (&
       reinterpret_cast<double*>(ep.out)[idx] = o;
       emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
     } else if (ep.out_mode == 4) {
-      const double o = prev[i] + f2d(val[0]);
+      const double o = __longlong_as_double(prev[i]) + f2d(val[0]);
       reinterpret_cast<double*>(ep.out)[idx] = o;
       emx = max(emx, (__double2hiint(o) >> 20) & 0x7FF);
     } else if (ep.out_mode == 2) {
       reinterpret_cast<double2*>(ep.out)[idx] = make_double2(f2d(val[0]), f2d(val[NACC - 1]));
-    } else {
+    } else if (ep.out_mode == 3 || NACC == 2) {
       reinterpret_cast<float2*>(ep.out)[idx] = make_float2(val[0], val[NACC - 1]);
+    } else if (ep.out_mode == 5) {  // the fixed-point iterate U_0 (real data only)
+      // v 2^s is exact in FP32 (fsc = 2^s, nonzero when representable) and |v 2^s| < 2^62:
+      // one conversion to int64, rounded to nearest
+      reinterpret_cast<long long*>(ep.out)[idx] = fsc != 0.f ? __float2ll_rn(val[0] * fsc) : f32_to_fixed(val[0], fs);
+      emx = max(emx, (int)((__float_as_uint(val[0]) >> 23) & 0xFFu));
+    } else {  // 6, 7: U 2^ds + fixed(delta), integer addition (exact)
+      const long long dq = fsc != 0.f ? __float2ll_rn(val[0] * fsc) : f32_to_fixed(val[0], fs);
+      const long long un = (prev[i] << fds) + dq;
+      if (ep.out_mode == 6)
+        reinterpret_cast<long long*>(ep.out)[idx] = un;
+      else
+        reinterpret_cast<double*>(ep.out)[idx] = fixed_to_f64_rz(un, fs);
     }
   }
 }
@@ -375,8 +415,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // 32 (w % 4) + 0..31 (tile rows) and the 16-column chunks (w - 2) / 4 + k EPI_WARPS / 4.
     const int g = warp & 3;
     const int part = (warp - 2) >> 2;  // which of the EPI_WARPS / 4 column interleaves
-    int emx = 0;  // largest biased exponent stored by this thread (out_mode 1 / 4)
+    int emx = 0;  // largest biased exponent stored by this thread (out_mode 1 / 4 / 5)
     int tl = 0;
+    // scale of the fixed-point result and the shift of the U read (out_mode 5-7)
+    const int fs = !PLANES_OUT && ep.out_mode >= 5 ? fix_scale(ep.fxs, ep.fix_out) : 0;
+    const int fds = !PLANES_OUT && ep.out_mode >= 6 ? fs - fix_scale(ep.fxs, ep.fix_in) : 0;
+    const float fsc = fs >= -126 && fs <= 127 ? __int_as_float((127 + fs) << 23) : 0.f;  // 2^fs
     for (int t = unit0; t < total; t += unit_step, ++tl) {
       const int ab = tl & 1, use = tl >> 1;
       const long long m0 = (long long)((t / ntiles) * CL + rank) * BM;
@@ -397,7 +441,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
         tc::tmem_ld_wait();
         if (!row_ok) continue;
-        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, ro, n0 + col0, rowsum, rowph, emx);
+        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, ro, n0 + col0, rowsum, rowph, emx, fs, fds, fsc);
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -610,11 +654,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rot_tc_list(const __grid_cons
 // ld0 = n0 rounded up to a multiple of 8); x rounded to FP32 first (the planes carry at most
 // 24 bits), then split exactly in FP32.
 // PADDED = false: rows need no padding (n0 % 8 == 0), element i goes to i.
+// emax (MODE 0, may be NULL): raised to the largest biased FP64 exponent of the input.
 template <int NP, int MODE, bool PADDED>  // MODE 0: real FP64, 1: complex128, 2: complex64
-__global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N, int n0) {
+__global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N, int n0, int* emax = nullptr) {
   const int NC = MODE == 0 ? 1 : 2;
   const int ld0 = PADDED ? (n0 + 7) & ~7 : n0;  // padded row (axis 1) of the planes
   const long long Np = PADDED ? (N / n0) * ld0 : N;  // plane stride
+  int emx = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     long long ip = i;
@@ -624,7 +670,9 @@ __global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N
     }
     float v[2];
     if (MODE == 0) {
-      v[0] = (float)reinterpret_cast<const double*>(in)[i];
+      const double x = reinterpret_cast<const double*>(in)[i];
+      emx = max(emx, (__double2hiint(x) >> 20) & 0x7FF);
+      v[0] = (float)x;
     } else if (MODE == 1) {
       double2 z = reinterpret_cast<const double2*>(in)[i];
       v[0] = (float)z.x;
@@ -635,6 +683,46 @@ __global__ void k_split_input(const void* in, __nv_bfloat16* planes, long long N
       v[1] = z.y;
     }
     for (int c = 0; c < NC; ++c) split_store<NP>(v[c], planes + (long long)c * NP * Np, Np, ip);
+  }
+  if (MODE == 0 && emax) {
+    for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(emax, emx);
+  }
+}
+
+// The same for real FP64 input on unpadded rows, four values per thread and step (two
+// 16-byte loads, one 8-byte store per plane), so that enough bytes are in flight to cover
+// HBM latency; in 16-byte aligned, planes 8-byte aligned, N a multiple of 4.
+template <int NP>
+__global__ void k_split_real4(const double* __restrict__ in, __nv_bfloat16* __restrict__ planes, long long N,
+                              int* emax) {
+  const long long n4 = N >> 2;
+  int emx = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    const double2 a = reinterpret_cast<const double2*>(in)[2 * q];
+    const double2 b = reinterpret_cast<const double2*>(in)[2 * q + 1];
+    if (emax)
+      emx = max(max(max(emx, (__double2hiint(a.x) >> 20) & 0x7FF), max((__double2hiint(a.y) >> 20) & 0x7FF,
+                                                                       (__double2hiint(b.x) >> 20) & 0x7FF)),
+                (__double2hiint(b.y) >> 20) & 0x7FF);
+    float r[4] = {(float)a.x, (float)a.y, (float)b.x, (float)b.y};
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      __nv_bfloat16 h[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        h[c] = __float2bfloat16_rn(r[c]);
+        r[c] -= __bfloat162float(h[c]);
+      }
+      uint2 w;
+      w.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+      w.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+      reinterpret_cast<uint2*>(planes + (long long)p * N)[q] = w;
+    }
+  }
+  if (emax) {
+    for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(emax, emx);
   }
 }
 
@@ -719,6 +807,112 @@ __global__ void k_phase_table(const double* lam, double tau, double2* ph, float2
   }
 }
 
+// ----------------------------------------- residual of the fixed-point iterate ----
+//
+// r = b - (-Delta_h + V1 + sigma) u for the iterate held as U = u 2^s (int64), d = 3, one
+// spacing h: the integer R = 6 U - (six neighbours) + ((Q_xy + Q_z) U >> F), with Q the
+// fixed-point tables of (sigma + V1) h^2 (F fraction bits), is exact; r = b - h^-2 2^-s R (one
+// int64 -> FP64 conversion and one FMA), split into NP bf16 planes.  A CTA marches a
+// 32 x 16 tile of axes (0, 1) along axis 2.  Every plane's U tile (with its one-cell halo)
+// and b tile arrive by TMA into a ring of shared-memory stages; the zero fill of boxes
+// reaching past the grid supplies the Dirichlet zeros, so the threads do no load address
+// arithmetic and no conversion of U.
+constexpr int FX_MX = 32, FX_MY = 16, FX_MZ = 64, FX_RD = 4;
+constexpr int FX_UW = FX_MX + 4;  // U tile row: x0 - 2 .. x0 + 33 (a TMA box starts at an even x)
+constexpr int FX_UH = FX_MY + 2;  // rows y0 - 1 .. y0 + 16
+constexpr int FX_U_BYTES = FX_UW * FX_UH * 8;
+constexpr int FX_B_BYTES = FX_MX * FX_MY * 8;
+// a tensor TMA writes shared memory at 128-byte aligned addresses: both tiles of a stage
+// start on one (the stages themselves are 128-byte multiples from a 128-byte aligned base)
+constexpr int FX_B_OFF = (FX_U_BYTES + 127) / 128 * 128;
+constexpr int FX_STAGE = (FX_B_OFF + FX_B_BYTES + 127) / 128 * 128;
+static_assert(FX_B_OFF % 128 == 0 && FX_STAGE % 128 == 0, "TMA destinations must be 128-byte aligned");
+constexpr int FX_SMEM = 128 + FX_RD * FX_STAGE + 8 * FX_RD;
+
+struct FixResidual {
+  int n0, n1, n2;
+  int F;               // fraction bits of the Q tables
+  const long long* Q;  // Q[0] = sigma h^2, then f_0 h^2 (n0), f_1 h^2 (n1), f_2 h^2 (n2)
+  double ih2;          // h^-2
+  FixScale fxs;
+  int s_kind;          // scale kind of U
+  const long long* U;  // the iterate (for the plane below a CTA's first plane)
+  __nv_bfloat16* planes;
+  long long Np;        // elements per plane
+  int ld0;             // axis-0 rows of the planes, padded to a multiple of 8
+};
+
+template <int NP>
+__global__ void __launch_bounds__(256) k_residual_fixu(const __grid_constant__ CUtensorMap tmU,
+                                                       const __grid_constant__ CUtensorMap tmB,
+                                                       const FixResidual prm) {
+  extern __shared__ uint8_t fx_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(fx_raw) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + FX_RD * FX_STAGE);
+  const int n0 = prm.n0, n1 = prm.n1, n2 = prm.n2;
+  const int tiles0 = (n0 + FX_MX - 1) / FX_MX, tiles1 = (n1 + FX_MY - 1) / FX_MY;
+  int bid = blockIdx.x;
+  const int t0 = bid % tiles0;
+  bid /= tiles0;
+  const int t1 = bid % tiles1;
+  const int z0 = (bid / tiles1) * FX_MZ, z1 = min(z0 + FX_MZ, n2);
+  const int x0 = t0 * FX_MX, y0 = t1 * FX_MY;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  const int x = x0 + lx, ya = y0 + ly, yb = ya + 8;
+  const bool va = x < n0 && ya < n1, vb = x < n0 && yb < n1;
+  const int sc = fix_scale(prm.fxs, prm.s_kind);
+  const double cs = ldexp(prm.ih2, -sc);
+  const long long qa = va ? prm.Q[0] + prm.Q[1 + x] + prm.Q[1 + n0 + ya] : 0;
+  const long long qb = vb ? prm.Q[0] + prm.Q[1 + x] + prm.Q[1 + n0 + yb] : 0;
+  const long long* q2 = prm.Q + 1 + n0 + n1;
+  const int nplanes = z1 - z0 + 1;  // planes z0 .. z1 (z1 == n2 reads the zero fill)
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < FX_RD; ++k) tc::mbar_init(&full[k], 1);
+    tc::fence_barrier_init();
+    tc::prefetch_tmap(&tmU);
+    tc::prefetch_tmap(&tmB);
+  }
+  __syncthreads();
+  auto issue = [&](int j) {  // plane z0 + j into stage j % FX_RD
+    uint8_t* st = base + (j % FX_RD) * FX_STAGE;
+    uint64_t* bar = &full[j % FX_RD];
+    tc::mbar_arrive_expect_tx(bar, FX_U_BYTES + FX_B_BYTES);
+    tc::tma_load_3d(st, &tmU, x0 - 2, y0 - 1, z0 + j, bar);
+    tc::tma_load_3d(st + FX_B_OFF, &tmB, x0, y0, z0 + j, bar);
+  };
+  if (threadIdx.x == 0)
+    for (int j = 0; j < FX_RD && j < nplanes; ++j) issue(j);
+  const long long s2 = (long long)n0 * n1;
+  long long Uda = va && z0 > 0 ? prm.U[(long long)(z0 - 1) * s2 + (long long)ya * n0 + x] : 0;
+  long long Udb = vb && z0 > 0 ? prm.U[(long long)(z0 - 1) * s2 + (long long)yb * n0 + x] : 0;
+  const long long ps2 = (long long)prm.ld0 * n1;
+  __nv_bfloat16* pa = prm.planes + (long long)z0 * ps2 + (long long)ya * prm.ld0 + x;
+  __nv_bfloat16* pb = pa + 8LL * prm.ld0;
+  const int ca = (ly + 1) * FX_UW + lx + 2, cb = ca + 8 * FX_UW;  // own cells in the U tile
+  for (int z = z0; z < z1; ++z) {
+    const int j = z - z0;
+    tc::mbar_wait(&full[j % FX_RD], (j / FX_RD) & 1, &g_tc_error, 11);
+    tc::mbar_wait(&full[(j + 1) % FX_RD], ((j + 1) / FX_RD) & 1, &g_tc_error, 11);
+    const long long* Uc = reinterpret_cast<const long long*>(base + (j % FX_RD) * FX_STAGE);
+    const long long* Uu = reinterpret_cast<const long long*>(base + ((j + 1) % FX_RD) * FX_STAGE);
+    const double* Bc = reinterpret_cast<const double*>(base + (j % FX_RD) * FX_STAGE + FX_B_OFF);
+    const long long ua = Uc[ca], ub = Uc[cb];
+    const long long qz = q2[z];
+    const long long Ra = 6 * ua - Uc[ca - 1] - Uc[ca + 1] - Uc[ca - FX_UW] - Uc[ca + FX_UW] - Uda - Uu[ca] +
+                         mul_shift(qa + qz, ua, prm.F);
+    const long long Rb = 6 * ub - Uc[cb - 1] - Uc[cb + 1] - Uc[cb - FX_UW] - Uc[cb + FX_UW] - Udb - Uu[cb] +
+                         mul_shift(qb + qz, ub, prm.F);
+    if (va) split_store<NP>(f64_to_f32(fma(-cs, __ll2double_rn(Ra), Bc[ly * FX_MX + lx])), pa, prm.Np, 0);
+    if (vb) split_store<NP>(f64_to_f32(fma(-cs, __ll2double_rn(Rb), Bc[(ly + 8) * FX_MX + lx])), pb, prm.Np, 0);
+    pa += ps2;
+    pb += ps2;
+    Uda = ua;
+    Udb = ub;
+    __syncthreads();  // every thread is done with plane z: its stage takes plane z + FX_RD
+    if (threadIdx.x == 0 && j + FX_RD < nplanes) issue(j + FX_RD);
+  }
+}
+
 // ------------------------------------------------------------ host side ----
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -762,7 +956,70 @@ ts_status make_map(CUtensorMap* m, const void* base, long long cols, long long r
   return TS_OK;
 }
 
+// 3D tensor map over an n0 x n1 x n2 array of 8-byte elements (n0 fastest, unpadded,
+// n0 * 8 a multiple of 16), box {b0, b1, 1}, no swizzle, zero fill out of bounds.
+ts_status make_map_8b(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int n0, int n1, int n2, int b0,
+                      int b1) {
+  auto enc = get_encode();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is unavailable");
+    return TS_ERR_CUDA;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)n0, (cuuint64_t)n1, (cuuint64_t)n2};
+  cuuint64_t strides[2] = {(cuuint64_t)n0 * 8, (cuuint64_t)n0 * n1 * 8};
+  cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d x %d array", (int)r, n0, n1, n2);
+    return TS_ERR_CUDA;
+  }
+  return TS_OK;
+}
+
 int g_num_sms = 0;
+
+// The residual of the fixed-point iterate into np bf16 planes (see k_residual_fixu).
+ts_status residual_fixu(const ts_plan* p, const long long* U, const double* b, const long long* Q, int F,
+                        const FixScale& fxs, int s_kind, __nv_bfloat16* planes, int np, cudaStream_t s) {
+  CUtensorMap mu, mb;
+  TS_TRY(make_map_8b(&mu, U, CU_TENSOR_MAP_DATA_TYPE_INT64, p->n[0], p->n[1], p->n[2], FX_UW, FX_UH));
+  TS_TRY(make_map_8b(&mb, b, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, p->n[0], p->n[1], p->n[2], FX_MX, FX_MY));
+  FixResidual prm{};
+  prm.n0 = p->n[0];
+  prm.n1 = p->n[1];
+  prm.n2 = p->n[2];
+  prm.F = F;
+  prm.Q = Q;
+  const double h = 2.0 * p->L[0] / (p->n[0] + 1);
+  prm.ih2 = 1.0 / (h * h);
+  prm.fxs = fxs;
+  prm.s_kind = s_kind;
+  prm.U = U;
+  prm.planes = planes;
+  prm.ld0 = (p->n[0] + 7) & ~7;
+  prm.Np = (long long)prm.ld0 * p->n[1] * p->n[2];
+  static bool attr_set[4] = {};
+  const long long blocks = (long long)((p->n[0] + FX_MX - 1) / FX_MX) * ((p->n[1] + FX_MY - 1) / FX_MY) *
+                           ((p->n[2] + FX_MZ - 1) / FX_MZ);
+  void* tok = nullptr;
+  if (prof_enabled()) prof_begin_launch(s, &tok);
+#define TS_FIXU(NP)                                                                                       \
+  if (np == NP) {                                                                                         \
+    if (!attr_set[NP]) {                                                                                  \
+      TS_CHECK_CUDA(cudaFuncSetAttribute(k_residual_fixu<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         FX_SMEM));                                                       \
+      attr_set[NP] = true;                                                                                \
+    }                                                                                                     \
+    k_residual_fixu<NP><<<(unsigned)blocks, 256, FX_SMEM, s>>>(mu, mb, prm);                              \
+  }
+  TS_FIXU(1) else TS_FIXU(2) else TS_FIXU(3)
+#undef TS_FIXU
+  TS_LAUNCHED(1);
+  if (tok) prof_end_launch(s, tok, PROF_RESIDUAL, 0.0, (16.0 + 2.0 * np) * (double)p->N);
+  return TS_OK;
+}
 
 template <int NP, int NACC, int BKT, bool PO, bool PAIR>
 ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long long R, int n, EpiParams ep,
@@ -839,8 +1096,8 @@ ts_status launch_pass_t(const __nv_bfloat16* A, const __nv_bfloat16* B, long lon
   if (tok) {
     const double flops = 2.0 * Products<NP>::count * NACC * (double)R * n * n;
     const double bytes = (double)NACC * R * n * 2.0 * NP * (ep.out_mode == 0 ? 2.0 : 1.0) +
-                         (ep.out_mode == 1 ? 8.0 : ep.out_mode == 2 ? 16.0 : ep.out_mode == 3 ? 8.0
-                                                 : ep.out_mode == 4 ? 16.0 : 0.0) * R * n;
+                         (ep.out_mode == 1 || ep.out_mode == 3 || ep.out_mode == 5 ? 8.0
+                          : ep.out_mode == 0 ? 0.0 : 16.0) * R * n;
     const int kind = ep.out_mode != 0 ? PROF_TC_PASS_OUT : (NP == 1 ? PROF_TC_PASS_X1 : PROF_TC_PASS);
     prof_end_launch(s, tok, kind, flops, bytes);
   }
@@ -1002,9 +1259,17 @@ void set_plane_output(EpiParams& ep, const ts_plan* p, int k) {
 // last pass: 1 FP64 store, 2 complex128, 3 complex64, 4 FP64 accumulate), with the
 // pointwise step fused into pass d-1.  emax_out (modes 1 / 4, may be NULL): raised to the
 // largest biased exponent of the stored values (the caller zeroes it first).
+// The epilogue of the last pass of an apply in a solve with a fixed-point iterate
+// (out_mode 5-7, see EpiParams).
+struct FixLast {
+  FixScale fxs;
+  int fix_in = 0, fix_out = 0;
+  const long long* src = nullptr;
+};
+
 ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double param, __nv_bfloat16* const buf[2],
                      const double2* tabs, const float2* tabsf, const int* tab_off, void* out, int last_mode,
-                     cudaStream_t s, int* emax_out = nullptr) {
+                     cudaStream_t s, int* emax_out = nullptr, const FixLast* fix = nullptr) {
   const int np = bf16_planes(prec);
   const int nc = op == MixedOp::Exp ? 2 : 1;
   const int d = p->d;
@@ -1031,6 +1296,12 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
       ep.cph = tabsf ? tabsf + tab_off[k] : nullptr;
     }
     if (!last) set_plane_output(ep, p, k);
+    if (last && fix) {
+      ep.fxs = fix->fxs;
+      ep.fix_in = fix->fix_in;
+      ep.fix_out = fix->fix_out;
+      ep.fix_src = fix->src;
+    }
     const __nv_bfloat16* B = fwd ? p->Bf[prec][k] : p->Bb[prec][k];
     st = pass(np, nc, buf[t & 1], B, p->N / p->n[k], p->n[k], ep, s);
   }
@@ -1038,13 +1309,21 @@ ts_status run_passes(const ts_plan* p, ts_precision prec, MixedOp op, double par
 }
 
 ts_status split_input(int np, ts_dtype dt, const void* in, __nv_bfloat16* planes, long long N, int n0,
-                      cudaStream_t s) {
-#define TS_SPLIT2(MODE, PAD)                                                        \
-  (np == 1   ? k_split_input<1, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
-   : np == 2 ? k_split_input<2, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0) \
-             : k_split_input<3, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0))
+                      cudaStream_t s, int* emax = nullptr) {
+#define TS_SPLIT2(MODE, PAD)                                                               \
+  (np == 1   ? k_split_input<1, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0, emax) \
+   : np == 2 ? k_split_input<2, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0, emax) \
+             : k_split_input<3, MODE, PAD><<<grid_1d(N), 256, 0, s>>>(in, planes, N, n0, emax))
 #define TS_SPLIT(MODE) (n0 % 8 == 0 ? TS_SPLIT2(MODE, false) : TS_SPLIT2(MODE, true))
-  if (dt == TS_R64)
+  if (dt == TS_R64 && n0 % 8 == 0 && N % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
+      reinterpret_cast<uintptr_t>(planes) % 8 == 0) {
+    if (np == 1)
+      k_split_real4<1><<<grid_1d(N / 4), 256, 0, s>>>((const double*)in, planes, N, emax);
+    else if (np == 2)
+      k_split_real4<2><<<grid_1d(N / 4), 256, 0, s>>>((const double*)in, planes, N, emax);
+    else
+      k_split_real4<3><<<grid_1d(N / 4), 256, 0, s>>>((const double*)in, planes, N, emax);
+  } else if (dt == TS_R64)
     TS_SPLIT(0);
   else if (dt == TS_C128)
     TS_SPLIT(1);
@@ -1330,6 +1609,45 @@ ts_status mixed_refine(const ts_plan* p, ts_precision prec, double sigma, const 
   return mixed_solve_schedule(p, sched, refinements + 1, sigma, b, u, s);
 }
 
+namespace {
+
+// Whether a refined solve on plan p can carry its iterate as the fixed-point integer
+// U = u 2^s (d = 3, one spacing h, the exact folded residual applies, axis-0 rows of an
+// even length and b 16-byte aligned for the residual's TMA tiles), and the factor beta of a
+// bound max|u| <= beta max|b|: 1 / (sigma + min V1) when that is positive (A is then an
+// M-matrix with A 1 >= (sigma + min V1) 1, so ||A^{-1}||_inf <= 1 / (sigma + min V1)), and
+// sqrt(N) / lambda_min(A) from the 2-norm.  The scale of U_0 follows from that bound, so it
+// may be loose by beta ||A||_inf (max|u| >= max|b| / ||A||_inf): at most 2^24 is accepted,
+// which leaves U_0 above 30 significant bits.  *l2b = ceil(log2 beta) + 2.
+bool fix_iterate_bound(const ts_plan* p, double sigma, const double* b, int* l2b) {
+  if (p->d != 3 || !isotropic_h(p) || p->n[0] % 2 != 0) return false;
+  if (reinterpret_cast<uintptr_t>(b) % 16 != 0) return false;
+  double fmin = 0.0, fmax = 0.0, lmin = sigma;
+  for (int k = 0; k < 3; ++k) {
+    const std::vector<double>& f = p->axis[k]->f;
+    const std::vector<double>& lam = p->axis[k]->lam_host;
+    if (f.empty() || lam.empty()) return false;
+    double lo = f[0], hi = std::fabs(f[0]);
+    for (double v : f) {
+      lo = v < lo ? v : lo;
+      hi = std::fabs(v) > hi ? std::fabs(v) : hi;
+    }
+    fmin += lo;
+    fmax += hi;
+    lmin += lam[0];
+  }
+  const double h = 2.0 * p->L[0] / (p->n[0] + 1);
+  const double anorm = 12.0 / (h * h) + std::fabs(sigma) + fmax;
+  double beta = HUGE_VAL;
+  if (sigma + fmin > 0.0) beta = 1.0 / (sigma + fmin);
+  if (lmin > 0.0) beta = std::fmin(beta, std::sqrt((double)p->N) / lmin);
+  if (!std::isfinite(beta) || !(std::log2(beta * anorm) <= 24.0)) return false;
+  *l2b = (int)std::ceil(std::log2(beta)) + 2;
+  return true;
+}
+
+}  // namespace
+
 ts_status mixed_solve_schedule(const ts_plan* p, const ts_precision* sched, int count, double sigma,
                                const double* b, double* u, cudaStream_t s) {
   int npmax = 0;
@@ -1340,48 +1658,85 @@ ts_status mixed_solve_schedule(const ts_plan* p, const ts_precision* sched, int 
   const int refinements = count - 1;
   const long long N = p->N;
   const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)npmax * mixed_plane_elems(p);
-  void *w0 = nullptr, *w1 = nullptr, *partial = nullptr, *qtab = nullptr;
+  int l2b = 0;
+  const bool fix_iter = refinements > 0 && fix_iterate_bound(p, sigma, b, &l2b);
+  void *w0 = nullptr, *w1 = nullptr, *partial = nullptr, *qtab = nullptr, *ubuf = nullptr;
   TS_TRY(scratch_alloc(&w0, plane_bytes, s));
   ts_status st = scratch_alloc(&w1, plane_bytes, s);
   if (st == TS_OK) st = scratch_alloc(&partial, sizeof(double) * 2 * RED_BLOCKS, s);
   if (st == TS_OK && qtable_count(p) > 0 && refinements > 0)
     st = scratch_alloc(&qtab, sizeof(long long) * qtable_count(p), s);
   __nv_bfloat16* buf[2] = {(__nv_bfloat16*)w0, (__nv_bfloat16*)w1};
-  // On isotropic grids the residual's Laplacian is summed in exact fixed point, scaled by
-  // the largest exponent of u; the pass that writes u finds it on the way out.
-  const bool fixed = isotropic_h(p);
-  int* emax = (int*)partial;
-  auto zero_emax = [&]() -> ts_status {
-    if (fixed && cudaMemsetAsync(emax, 0, sizeof(int), s) != cudaSuccess) {
+  // The fixed-point iterate: u_0 is stored as U_0 = u_0 2^s0 (int64), every refinement adds
+  // its correction to U in integer arithmetic (exact), the residuals read U directly, and
+  // the last refinement writes the FP64 u = U 2^-s.
+  FixedOperator fo;
+  if (st == TS_OK && fix_iter) st = fixed_operator_prepare(p, sigma, (long long*)qtab, &fo, s);
+  if (st == TS_OK && fix_iter && fo.ok) {
+    st = scratch_alloc(&ubuf, sizeof(long long) * (size_t)N, s);
+    int* fx = (int*)partial;  // fx[0] = emax of b, fx[1] = emax of u_0
+    if (st == TS_OK && cudaMemsetAsync(fx, 0, 2 * sizeof(int), s) != cudaSuccess) {
       set_error("memset failed");
-      return TS_ERR_CUDA;
+      st = TS_ERR_CUDA;
     }
-    return TS_OK;
-  };
-  // u_0 = P_0 b
-  if (st == TS_OK) st = split_input(bf16_planes(sched[0]), TS_R64, b, buf[0], N, p->n[0], s);
-  if (st == TS_OK && refinements > 0) st = zero_emax();
-  if (st == TS_OK)
-    st = run_passes(p, sched[0], MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s,
-                    fixed && refinements > 0 ? emax : nullptr);
-  // u_{k+1} = u_k + P_{k+1} (b - A u_k), residual in FP64, split straight into the planes
-  for (int it = 0; it < refinements && st == TS_OK; ++it) {
-    const bool more = it + 1 < refinements;
-    const ts_precision prec = sched[it + 1];
-    const int np = bf16_planes(prec);
-    if (fixed)
-      st = residual_split_fixed(p, sigma, u, b, buf[0], np, emax, (long long*)qtab, s);
-    else
-      st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
-    if (st == TS_OK && more) st = zero_emax();
+    FixLast fl;
+    fl.fxs.fx = fx;
+    fl.fxs.hu = fo.H;
+    fl.fxs.l2b = l2b;
+    long long* U = (long long*)ubuf;
+    if (st == TS_OK) st = split_input(bf16_planes(sched[0]), TS_R64, b, buf[0], N, p->n[0], s, fx);
+    fl.fix_out = 0;
     if (st == TS_OK)
-      st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 4, s,
-                      fixed && more ? emax : nullptr);
+      st = run_passes(p, sched[0], MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, U, 5, s, fx + 1, &fl);
+    for (int it = 0; it < refinements && st == TS_OK; ++it) {
+      const bool last = it + 1 == refinements;
+      const ts_precision prec = sched[it + 1];
+      st = residual_fixu(p, U, b, fo.qtab, fo.F, fl.fxs, it == 0 ? 0 : 1, buf[0], bf16_planes(prec), s);
+      fl.fix_in = it == 0 ? 0 : 1;
+      fl.fix_out = 1;
+      fl.src = U;
+      if (st == TS_OK)
+        st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, last ? (void*)u : (void*)U,
+                        last ? 7 : 6, s, nullptr, &fl);
+    }
+  } else if (st == TS_OK) {
+    // On isotropic grids the residual's Laplacian is summed in exact fixed point, scaled by
+    // the largest exponent of u; the pass that writes u finds it on the way out.
+    const bool fixed = isotropic_h(p);
+    int* emax = (int*)partial;
+    auto zero_emax = [&]() -> ts_status {
+      if (fixed && cudaMemsetAsync(emax, 0, sizeof(int), s) != cudaSuccess) {
+        set_error("memset failed");
+        return TS_ERR_CUDA;
+      }
+      return TS_OK;
+    };
+    // u_0 = P_0 b
+    st = split_input(bf16_planes(sched[0]), TS_R64, b, buf[0], N, p->n[0], s);
+    if (st == TS_OK && refinements > 0) st = zero_emax();
+    if (st == TS_OK)
+      st = run_passes(p, sched[0], MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 1, s,
+                      fixed && refinements > 0 ? emax : nullptr);
+    // u_{k+1} = u_k + P_{k+1} (b - A u_k), residual in FP64, split straight into the planes
+    for (int it = 0; it < refinements && st == TS_OK; ++it) {
+      const bool more = it + 1 < refinements;
+      const ts_precision prec = sched[it + 1];
+      const int np = bf16_planes(prec);
+      if (fixed)
+        st = residual_split_fixed(p, sigma, u, b, buf[0], np, emax, (long long*)qtab, s);
+      else
+        st = stencil_residual_split(p, nullptr, sigma, u, b, buf[0], np, (double*)partial, s);
+      if (st == TS_OK && more) st = zero_emax();
+      if (st == TS_OK)
+        st = run_passes(p, prec, MixedOp::Inverse, sigma, buf, nullptr, nullptr, nullptr, u, 4, s,
+                        fixed && more ? emax : nullptr);
+    }
   }
   scratch_free(w0, s);
   scratch_free(w1, s);
   scratch_free(partial, s);
   scratch_free(qtab, s);
+  scratch_free(ubuf, s);
   return st;
 }
 

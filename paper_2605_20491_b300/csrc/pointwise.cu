@@ -12,6 +12,7 @@
 
 #include "async_copy.cuh"
 #include "common.cuh"
+#include "fixed.cuh"
 #include "pointwise.cuh"
 #include "sem_axis.cuh"
 #include "split.cuh"
@@ -194,54 +195,6 @@ __global__ void k_stencil(AxisParams a, const double* __restrict__ V2, double si
   }
 }
 
-// x as a fixed-point integer with the scale 2^(1022 + H - emax), H = 53 + P: the mantissa
-// with its implicit bit, pre-shifted left by P, then shifted right by t = emax - e; integer
-// instructions only.  Exact when t <= P; otherwise the magnitude is truncated toward zero
-// onto the fixed-point grid.  |result| < 2^H whenever e <= emax; zero and subnormals give 0.
-__device__ __forceinline__ long long to_fixed(double x, int emax, int P) {
-  const long long bits = __double_as_longlong(x);
-  const int e = (int)((bits >> 52) & 0x7FF);
-  const long long m = ((bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52)) << P;
-  int t = emax - e;
-  t = (e == 0 || t > 63) ? 63 : t;  // m < 2^63, so a shift by 63 gives 0
-  const long long sgn = bits >> 63;  // 0 or -1
-  return ((m >> t) ^ sgn) - sgn;
-}
-
-// v -> double, rounded to nearest even, with integer instructions only (|v| < 2^63): the
-// magnitude is normalised with a count of leading zeros, its top 53 bits kept and rounded on
-// the 11 bits below them; a carry out of the mantissa bumps the exponent through the add.
-__device__ __forceinline__ double i64_to_f64(long long v) {
-  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ULL;
-  unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
-  const int lz = __clzll(a);
-  a <<= (lz & 63);
-  unsigned long long m = a >> 11;
-  const unsigned rem = (unsigned)a & 0x7FFu;
-  m += (rem > 0x400u || (rem == 0x400u && (m & 1ULL))) ? 1ULL : 0ULL;
-  const unsigned long long mag = ((unsigned long long)(1023 + 63 - 1 - lz) << 52) + m;
-  return __longlong_as_double((long long)(a == 0 ? 0ULL : (sgn | mag)));
-}
-
-// v -> float, rounded to nearest even, with 32-bit integer instructions only: the top 23
-// fraction bits rounded on the 29 below them, exponent rebased from 1023 to 127.  Results
-// below the normal float range are flushed to zero (signed), above it give infinity; NaN
-// stays NaN.
-__device__ __forceinline__ float f64_to_f32(double v) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const unsigned lo = (unsigned)bits, hi = (unsigned)(bits >> 32);
-  const unsigned sgn = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7FFu);
-  unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  const unsigned rem = lo & 0x1FFFFFFFu;
-  m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
-  unsigned f = ((unsigned)(e - 896) << 23) + m;
-  f = e <= 896 ? 0u : f;
-  f = e >= 1151 ? 0x7F800000u : f;
-  f = (e == 2047 && ((hi & 0xFFFFFu) | lo)) ? 0x7FC00000u : f;
-  return __uint_as_float(sgn | f);
-}
-
 // Residual r = b - (-Delta_h + V1 + sigma) u split into bf16 planes, for grids with the
 // same h on every axis.  The Laplacian part sum_k (2u - u_{-e_k} - u_{+e_k}) -- where all the
 // cancellation happens -- is evaluated exactly in 64-bit fixed point (one global scale from
@@ -295,14 +248,6 @@ __global__ void k_residual_fixed(AxisParams a, double sigma, const double* __res
       split_store<NP>((float)r, planes, R * ((n0 + 7) & ~7), row * ((n0 + 7) & ~7) + i0);
     }
   }
-}
-
-// (Q * U) >> F for 64-bit Q and U with the 128-bit product (floor), 0 < F < 64, for
-// results that fit in 64 bits.
-__device__ __forceinline__ long long mul_shift(long long q, long long u, int F) {
-  const unsigned long long lo = (unsigned long long)q * (unsigned long long)u;
-  const long long hi = __mul64hi(q, u);
-  return (long long)((unsigned long long)hi << (64 - F)) | (long long)(lo >> F);
 }
 
 // Q tables of the folded diagonal: Q[0] = sigma / h^-2, then f_0 / h^-2, f_1 / h^-2,

@@ -396,3 +396,29 @@ def test_noalloc_any_n(T):
     T.ts_apply_inverse(P, 0.5, dev(b), u2, T.TS_BF16X3)
     assert np.array_equal(host(u), host(u2))
     assert rel(host(u), O.apply_inverse(Po, 0.5, b)) < TOL[1]
+
+
+@pytest.mark.parametrize("n,offset", [((64, 48, 40), 0), ((40, 72, 24), 0), ((63, 64, 40), 0), ((64, 48, 40), 1)])
+def test_refined_solve_fixed_point_iterate(T, n, offset):
+    """On grids with one spacing and an even axis-0 length the refined solve keeps its
+    iterate in 64-bit fixed point (U_0 stored, corrections added in integer arithmetic,
+    residuals read U); an odd axis-0 length or a right-hand side not 16-byte aligned takes
+    the FP64 iterate.  Both reach FP64 accuracy against the oracle, for the benchmark's
+    schedule (BF16X3, BF16X3, BF16X1), two BF16X3 refinements and a single refinement."""
+    import torch
+    L = tuple((k + 1) / 4.0 for k in n)
+    f = S.harmonic(n, L, (1.0, 1.3, 0.7))
+    P, Po = plans(n, L, f, MASK | (1 << 6))
+    b = S.normal(9, Po.N)
+    want = O.apply_inverse(Po, 0.5, b)
+    storage = dev(np.concatenate([np.zeros(offset), b]))
+    bt = storage[offset:]
+    for sched, tol in (([1, 1, 6], 1e-11), ([1, 1, 1], 1e-12), ([1, 1], 5e-9)):
+        u = dev(np.full(Po.N, np.nan))
+        T.ts_solve_schedule(P, 0.5, bt, u, sched)
+        T.ts_device_status()
+        assert rel(host(u), want) < tol, (sched, rel(host(u), want))
+    # b = 0 gives u = 0 exactly on both forms
+    u = dev(np.full(Po.N, 3.0))
+    T.ts_solve_schedule(P, 0.5, torch.zeros_like(bt), u, [1, 1, 6])
+    assert not host(u).any()
