@@ -1,7 +1,15 @@
-// Fused multi-mode contraction for small axis lengths (n <= 32), complex64 data, FP32
+// Fused multi-mode propagation for small axis lengths (n <= 32), complex64 data, FP32
 // arithmetic: the exact propagator e^{-i tau (-Delta + V1)} (eq. exact_prop) of the 4D-9D
-// problems in 2 ceil(d / f) - 1 HBM passes instead of 2d, and the Strang step (Sec. 5.1)
-// with the e^{-i V2 theta} factor folded into the first and last pass.
+// problems, and the Strang step (Sec. 5.1) with the e^{-i V2 theta} factors folded into
+// the first and last pass.
+//
+// -Delta_h + V1 = sum_k H_k with H_k acting on axis k alone, so the exact propagator is the
+// tensor product of per-axis propagators: e^{-i tau (-Delta_h + V1)} = kron_k E_k with
+// E_k = T_k diag(e^{-i tau lambda_k}) T_k^{-1} (steps 2-4 of Sec. 2.1 on one axis, an n x n
+// complex matrix formed once per call in FP64).  Applying E_k directly costs the same FFMA as
+// the forward transform, the phase and the backward transform along the axis, but leaves no
+// intermediate in the eigenbasis: a step is ceil(d / f) HBM passes for groups of f axes,
+// where the forward / phase / backward form needs 2 ceil(d / f) - 1.
 //
 // Axes are cut into groups of consecutive modes.  For a group [k0, k1) with
 // lo = prod_{j<k0} n_j, G = prod_{k0<=j<k1} n_j and hi = prod_{j>=k1} n_j, a CTA owns the
@@ -9,13 +17,11 @@
 // group indices: runs of >= 8 contiguous elements in HBM, so loads and stores coalesce.
 // Input and output may be the same array: a CTA reads its whole tile before writing it.
 // CTAs are persistent over tiles and double-buffer them: while one tile is contracted the
-// next one arrives by cp.async.  In shared memory the tile is stored with every group
-// extent padded to an odd length,
-// so that the fibers of any mode start on distinct banks.  Each mode is contracted by
-// per-thread fibers held in registers (n complex values in, n out, 2 n^2 FFMA per fiber)
-// with the n x n matrix read from shared memory as broadcasts, in place.  The last group
-// runs its forward modes, multiplies every coefficient by prod_k e^{-i tau lambda_k[i_k]}
-// (per-axis FP32 phase tables), then its backward modes, in one pass.
+// next one arrives by cp.async.  In shared memory every group extent is padded to an odd
+// length, so that the fibers of any mode start on distinct banks.  Each mode is applied by
+// per-thread fibers held in registers (n complex values in, n out, 4 n^2 FFMA per fiber)
+// with the matrix read from shared memory as broadcasts, in place.  The group shape (n and
+// the number of modes) is a template parameter, so every index computation is by constants.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,24 +34,23 @@
 namespace ts {
 namespace {
 
-constexpr int SMALL_THREADS = 256;
-constexpr int MAXG = 4;  // modes per group
+constexpr int MAXG = 3;                     // modes per group
+constexpr size_t TILE_BUDGET = 48 * 1024;   // bytes of one complex64 tile buffer (two per CTA)
 
-struct GroupParams {
-  int nm;                 // modes in the group
-  int npad[MAXG];         // odd-padded extents in shared memory
-  long long lo, hi;       // extents below / above the group
-  long long G;            // product of the group's extents
-  int T;                  // tile count along lo (lo > 1) or along hi (lo == 1)
-  long long Gpad;         // product of padded extents
-  const float* fwd[MAXG]; // forward: row-major S_k   (y_j = sum_i S_k[i][j] x_i)
-  const float* bwd[MAXG]; // backward: row-major S_k^T (y_j = sum_i S_k[j][i] x_i)
-  int do_fwd, do_bwd, do_phase;
-  // phase of step 3 (middle pass): per-axis tables over all d axes
-  int d;
-  int k0;                 // first axis of the group
-  int n_all[MAXD];
-  const float2* ph[MAXD];
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Threads per CTA: the 24-point groups hold 8 x 24 fibers per mode (T = 8), so 192 threads
+// take one each with 170 registers at two CTAs per SM; the others use 256.
+template <int N>
+struct SmallCfg {
+  static constexpr int THREADS = N == 24 ? 192 : 256;
+  static constexpr int FPT = N <= 8 ? 2 : 1;  // fibers per thread sharing every matrix load
+};
+
+struct PropParams {
+  long long lo, hi;         // extents below / above the group
+  int T;                    // tile count along lo (lo > 1) or along hi (lo == 1), a power of two
+  const float2* E[MAXG];    // per mode of the group: ET[i'][i] = E_k[i][i'] (n x n, complex)
   // potential phase e^{-i theta V2}: applied on load (theta_pre) / on store (theta_post)
   const float* V2;
   float theta_pre, theta_post;
@@ -69,141 +74,156 @@ __device__ __forceinline__ float2 vphase(float2 v, float theta, float V) {
   return cmulf(v, make_float2(c, -s));
 }
 
-// Contract mode m of the tile in place along every fiber of that mode:
-// y_j = sum_i M[i][j] x_i with M row-major (M = S_k: forward, M = S_k^T: backward).
-// Tile-local indices are 32-bit; Tlo is a power of two (shift / mask) and N a constant.
-template <int N>
-__device__ void contract_mode(float2* tile, const float* M, int m, const GroupParams& p, int lgTlo, int Thi) {
+// Padded offset of the group-flattened index g (D base-N digits, fastest first) in a tile
+// whose extents are padded to N | 1.
+template <int N, int D>
+__device__ __forceinline__ int padded_offset(int g) {
+  int r = 0;
+#pragma unroll
+  for (int k = 0, mul = 1; k < D; ++k, mul *= (N | 1)) {
+    const int q = g / N;
+    r += (g - q * N) * mul;
+    g = q;
+  }
+  return r;
+}
+
+// Apply the matrix of mode M of the group, y_i = sum_i' E[i][i'] x_i' (Em holds ET[i'][i]),
+// along every fiber of that mode of the tile, in place.  FPT fibers per thread and step
+// (fibers f and f + THREADS) share every matrix load from shared memory; the output blocks
+// are a rolled loop, so that the code of a mode stays small.
+template <int N, int NM, int M, int FPT>
+__device__ __forceinline__ void prop_mode(float2* tile, const float2* Em, int lgTlo, int Thi) {
+  constexpr int THREADS = SmallCfg<N>::THREADS;
+  constexpr int NPD = N | 1;
+  constexpr int INNER_G = ipow(N, M), OUTER_G = ipow(N, NM - 1 - M);
+  constexpr int STRIDE_G = ipow(NPD, M);  // padded stride of mode M (times Tlo)
+  constexpr int GP = ipow(NPD, NM);
+  constexpr int JB = N >= 16 ? 4 : 8;     // outputs per accumulation block
+  static_assert(N % JB == 0, "axis length must be a multiple of the output block");
   const int Tlo = 1 << lgTlo;
-  int st_m = Tlo;
-  for (int j = 0; j < m; ++j) st_m *= p.npad[j];
-  int inner_cnt = Tlo;
-  for (int j = 0; j < m; ++j) inner_cnt *= N;
-  int outer_cnt = Thi;
-  for (int j = m + 1; j < p.nm; ++j) outer_cnt *= N;
-  const int fibers = inner_cnt * outer_cnt;
-  for (int f = threadIdx.x; f < fibers; f += blockDim.x) {
-    const int in_i = f % inner_cnt, out_i = f / inner_cnt;
-    int addr = in_i & (Tlo - 1);
-    int rem = in_i >> lgTlo, mul = Tlo;
-    for (int j = 0; j < m; ++j) {
-      addr += (rem % N) * mul;
-      rem /= N;
-      mul *= p.npad[j];
-    }
-    int mul2 = st_m * p.npad[m];
-    int r2 = out_i;
-    for (int j = m + 1; j < p.nm; ++j) {
-      addr += (r2 % N) * mul2;
-      r2 /= N;
-      mul2 *= p.npad[j];
-    }
-    addr += r2 * mul2;
-    float2 x[N];
+  const int st = Tlo * STRIDE_G;
+  const int fibers = Tlo * INNER_G * OUTER_G * Thi;
+  for (int f0 = threadIdx.x; f0 < fibers; f0 += FPT * THREADS) {
+    int addr[FPT];
+    float2 x[FPT][N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) x[i] = tile[addr + i * st_m];
-    // four outputs per 16-byte load of the matrix row: 8 FFMA per shared-memory load
+    for (int c = 0; c < FPT; ++c) {
+      const int f = f0 + c * THREADS < fibers ? f0 + c * THREADS : f0;  // a missing partner repeats f0
+      const int t = f & (Tlo - 1);
+      int r = f >> lgTlo;
+      const int gi = r % INNER_G;
+      r /= INNER_G;
+      const int go = r % OUTER_G;
+      const int th = r / OUTER_G;
+      addr[c] = t + Tlo * (padded_offset<N, M>(gi) + STRIDE_G * NPD * padded_offset<N, NM - 1 - M>(go) + GP * th);
 #pragma unroll
-    for (int j = 0; j < N; j += 4) {
-      float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int i = 0; i < N; ++i) x[c][i] = tile[addr[c] + i * st];
+    }
+    const bool second = FPT > 1 && f0 + THREADS < fibers;
+#pragma unroll 1
+    for (int j0 = 0; j0 < N; j0 += JB) {
+      float re[FPT][JB], im[FPT][JB];
+#pragma unroll
+      for (int c = 0; c < FPT; ++c)
+#pragma unroll
+        for (int q = 0; q < JB; ++q) re[c][q] = im[c][q] = 0.f;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const float4 w = *reinterpret_cast<const float4*>(M + i * N + j);
-        re[0] = fmaf(w.x, x[i].x, re[0]);
-        im[0] = fmaf(w.x, x[i].y, im[0]);
-        re[1] = fmaf(w.y, x[i].x, re[1]);
-        im[1] = fmaf(w.y, x[i].y, im[1]);
-        re[2] = fmaf(w.z, x[i].x, re[2]);
-        im[2] = fmaf(w.z, x[i].y, im[2]);
-        re[3] = fmaf(w.w, x[i].x, re[3]);
-        im[3] = fmaf(w.w, x[i].y, im[3]);
+#pragma unroll
+        for (int q = 0; q < JB; q += 2) {
+          const float4 e = *reinterpret_cast<const float4*>(Em + i * N + j0 + q);  // E[j0+q][i], E[j0+q+1][i]
+#pragma unroll
+          for (int c = 0; c < FPT; ++c) {
+            re[c][q] = fmaf(e.x, x[c][i].x, re[c][q]);
+            re[c][q] = fmaf(-e.y, x[c][i].y, re[c][q]);
+            im[c][q] = fmaf(e.x, x[c][i].y, im[c][q]);
+            im[c][q] = fmaf(e.y, x[c][i].x, im[c][q]);
+            re[c][q + 1] = fmaf(e.z, x[c][i].x, re[c][q + 1]);
+            re[c][q + 1] = fmaf(-e.w, x[c][i].y, re[c][q + 1]);
+            im[c][q + 1] = fmaf(e.z, x[c][i].y, im[c][q + 1]);
+            im[c][q + 1] = fmaf(e.w, x[c][i].x, im[c][q + 1]);
+          }
+        }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) tile[addr + (j + q) * st_m] = make_float2(re[q], im[q]);
+      for (int q = 0; q < JB; ++q) {
+        tile[addr[0] + (j0 + q) * st] = make_float2(re[0][q], im[0][q]);
+        if (FPT > 1 && second) tile[addr[FPT - 1] + (j0 + q) * st] = make_float2(re[FPT - 1][q], im[FPT - 1][q]);
+      }
     }
   }
 }
 
-// Shared-memory index of tile element e (global order: t fastest, group indices, th) and
-// its group-flattened index g (unpadded).
-template <int N>
-__device__ __forceinline__ int tile_index(int e, int lgTlo, const GroupParams& p, int* g_out, int* th_out) {
-  const int Tlo = 1 << lgTlo;
-  const int t = e & (Tlo - 1);
-  int r = e >> lgTlo;
-  int sidx = t, mul = Tlo, g = 0, gm = 1;
-  for (int j = 0; j < p.nm; ++j) {
-    const int ij = r % N;
-    r /= N;
-    sidx += ij * mul;
-    mul *= p.npad[j];
-    g += ij * gm;
-    gm *= N;
+template <int N, int NM, int M>
+__device__ __forceinline__ void prop_modes(float2* tile, const float2* E, int lgTlo, int Thi) {
+  if constexpr (M < NM) {
+    prop_mode<N, NM, M, SmallCfg<N>::FPT>(tile, E + M * N * N, lgTlo, Thi);
+    __syncthreads();
+    prop_modes<N, NM, M + 1>(tile, E, lgTlo, Thi);
   }
-  *g_out = g;
-  *th_out = r;
-  return sidx + r * mul;
 }
 
-// First element of tile b: (l0, h0) as in the tiling described at the top.
-__device__ __forceinline__ void tile_origin(long long b, int lgTlo, int Thi, const GroupParams& p, long long* l0,
-                                            long long* h0) {
-  if (p.lo > 1) {
-    const long long lblocks = p.lo >> lgTlo;
-    *l0 = (b % lblocks) << lgTlo;
-    *h0 = b / lblocks;
-  } else {
-    *l0 = 0;
-    *h0 = b * Thi;
-  }
+// Shared-memory offset and group-flattened index of tile element e (global order: t
+// fastest, then the group indices, then th).
+template <int N, int NM>
+__device__ __forceinline__ int tile_offset(int e, int lgTlo, int* g_out, int* th_out) {
+  constexpr int G = ipow(N, NM), GP = ipow(N | 1, NM);
+  const int t = e & ((1 << lgTlo) - 1);
+  const int r = e >> lgTlo;
+  const int g = r % G, th = r / G;
+  *g_out = g;
+  *th_out = th;
+  return t + ((padded_offset<N, NM>(g) + GP * th) << lgTlo);
 }
 
 // Persistent over tiles with two shared-memory tile buffers: the next tile's elements are
-// copied asynchronously (cp.async, one 8-byte copy per element into the padded layout)
-// while the current tile is contracted, so global-load latency overlaps arithmetic.
-template <int N>
-__global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, float2* Y, const GroupParams p,
-                                                               long long ntiles) {
+// copied asynchronously (cp.async into the padded layout) while the current tile is
+// contracted, so global-load latency overlaps arithmetic.
+template <int N, int NM>
+__global__ void __launch_bounds__(SmallCfg<N>::THREADS, 2) k_small_prop(const float2* X, float2* Y,
+                                                                     const PropParams p, long long ntiles) {
+  constexpr int SMALL_THREADS = SmallCfg<N>::THREADS;
+  constexpr int G = ipow(N, NM), GP = ipow(N | 1, NM);
   extern __shared__ __align__(16) float2 smem[];
   const int lgT = 31 - __clz(p.T);
   const int lgTlo = p.lo > 1 ? lgT : 0;
   const int Tlo = 1 << lgTlo;
   const int Thi = p.lo > 1 ? 1 : p.T;
-  const int tile_pad = Tlo * (int)p.Gpad * Thi;
-  const int tile_stride = (tile_pad + 1) & ~1;  // keep every buffer 16-byte aligned
+  const int tile_stride = (Tlo * GP * Thi + 1) & ~1;  // keep every buffer 16-byte aligned
   float2* buf[2] = {smem, smem + tile_stride};
-  float2* rowph = smem + 2 * tile_stride;                         // Tlo phase factors (middle pass)
-  float* mats = reinterpret_cast<float*>(smem + 2 * tile_stride + ((Tlo + 1) & ~1));
-  const int msz = N * N;
-  for (int e = threadIdx.x; e < p.nm * msz; e += blockDim.x) {
-    const int m = e / msz, q = e % msz;
-    if (p.do_fwd) mats[m * msz + q] = p.fwd[m][q];
-    if (p.do_bwd) mats[(p.nm + m) * msz + q] = p.bwd[m][q];
-  }
-  const int cnt = Tlo * (int)p.G * Thi;
+  float2* mats = smem + 2 * tile_stride;
+  for (int e = threadIdx.x; e < NM * N * N; e += SMALL_THREADS) mats[e] = p.E[e / (N * N)][e % (N * N)];
+  const int cnt = Tlo * G * Thi;
+  const long long loG = p.lo * G;
+  auto origin = [&](long long b) -> long long {  // HBM index of the tile's first element
+    if (p.lo > 1) {
+      const long long lblocks = p.lo >> lgTlo;
+      return ((b % lblocks) << lgTlo) + loG * (b / lblocks);
+    }
+    return loG * b * Thi;
+  };
   auto issue_load = [&](long long b, float2* dst) {
-    long long l0, h0;
-    tile_origin(b, lgTlo, Thi, p, &l0, &h0);
-    const long long gbase = l0 + p.lo * p.G * h0;
+    const long long gbase = origin(b);
     if (p.pairs == 1) {
-      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) {
+      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * SMALL_THREADS) {
         int g, th;
-        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-        cp_async16(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th));
+        const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
+        cp_async16(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th));
       }
     } else if (p.pairs == 2) {
-      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) {
+      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * SMALL_THREADS) {
         int g, th;
-        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-        const float2* src = X + gbase + p.lo * ((long long)g + p.G * th);
+        const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
+        const float2* src = X + gbase + p.lo * ((long long)g + (long long)G * th);
         cp_async8(dst + sidx, src);
         cp_async8(dst + sidx + 1, src + 1);
       }
     } else {
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      for (int e = threadIdx.x; e < cnt; e += SMALL_THREADS) {
         int g, th;
-        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-        cp_async8(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th));
+        const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
+        cp_async8(dst + sidx, X + gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th));
       }
     }
     cp_async_commit();
@@ -211,6 +231,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
   long long b = blockIdx.x;
   if (b < ntiles) issue_load(b, buf[0]);
   int cur = 0;
+  const int step_e = p.pairs ? 2 : 1;  // both pair kinds: (e, e + 1) at (sidx, sidx + 1)
   for (; b < ntiles; b += gridDim.x, cur ^= 1) {
     const long long bn = b + gridDim.x;
     if (bn < ntiles) {
@@ -221,69 +242,23 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
     }
     __syncthreads();
     float2* tile = buf[cur];
-    long long l0, h0;
-    tile_origin(b, lgTlo, Thi, p, &l0, &h0);
-    const long long gbase = l0 + p.lo * p.G * h0;
+    const long long gbase = origin(b);
     if (p.V2 && p.theta_pre != 0.f) {
-      const int step_e = p.pairs ? 2 : 1;  // both pair kinds: (e, e + 1) at (sidx, sidx + 1)
-      for (int e = step_e * threadIdx.x; e < cnt; e += step_e * blockDim.x) {
+      for (int e = step_e * threadIdx.x; e < cnt; e += step_e * SMALL_THREADS) {
         int g, th;
-        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
+        const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
+        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th);
         tile[sidx] = vphase(tile[sidx], p.theta_pre, p.V2[gidx]);
         if (p.pairs) tile[sidx + 1] = vphase(tile[sidx + 1], p.theta_pre, p.V2[gidx + 1]);
       }
       __syncthreads();
     }
-    if (p.do_fwd) {
-      for (int m = 0; m < p.nm; ++m) {
-        contract_mode<N>(tile, mats + m * msz, m, p, lgTlo, Thi);
-        __syncthreads();
-      }
-    }
-    if (p.do_phase) {
-      // phase factor of the axes below the group, one per t (the last group has no axes above)
-      for (int t = threadIdx.x; t < Tlo; t += blockDim.x) {
-        long long q = l0 + t;
-        float2 ph = make_float2(1.f, 0.f);
-        for (int k = 0; k < p.k0; ++k) {
-          const int ik = (int)(q % p.n_all[k]);
-          q /= p.n_all[k];
-          ph = cmulf(ph, p.ph[k][ik]);
-        }
-        rowph[t] = ph;
-      }
-      __syncthreads();
-      const int step_e = p.pairs == 1 ? 2 : 1;  // pairs along t share the group's phase
-      for (int e = step_e * threadIdx.x; e < cnt; e += step_e * blockDim.x) {
-        const int t = e & (Tlo - 1);
-        int r = e >> lgTlo;
-        int sidx = t, mul = Tlo;
-        float2 ph = make_float2(1.f, 0.f);
-        for (int j = 0; j < p.nm; ++j) {
-          const int ij = r % N;
-          r /= N;
-          sidx += ij * mul;
-          mul *= p.npad[j];
-          ph = cmulf(ph, p.ph[p.k0 + j][ij]);
-        }
-        sidx += r * mul;
-        tile[sidx] = cmulf(tile[sidx], cmulf(rowph[t], ph));
-        if (p.pairs == 1) tile[sidx + 1] = cmulf(tile[sidx + 1], cmulf(rowph[t + 1], ph));
-      }
-      __syncthreads();
-    }
-    if (p.do_bwd) {
-      for (int m = p.nm - 1; m >= 0; --m) {
-        contract_mode<N>(tile, mats + (p.nm + m) * msz, m, p, lgTlo, Thi);
-        __syncthreads();
-      }
-    }
+    prop_modes<N, NM, 0>(tile, mats, lgTlo, Thi);
     if (p.pairs) {
-      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) {
+      for (int e = 2 * threadIdx.x; e < cnt; e += 2 * SMALL_THREADS) {
         int g, th;
-        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
+        const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
+        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th);
         float2 v0 = tile[sidx], v1 = tile[sidx + 1];
         if (p.V2 && p.theta_post != 0.f) {
           v0 = vphase(v0, p.theta_post, p.V2[gidx]);
@@ -292,10 +267,10 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
         *reinterpret_cast<float4*>(Y + gidx) = make_float4(v0.x, v0.y, v1.x, v1.y);
       }
     } else {
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      for (int e = threadIdx.x; e < cnt; e += SMALL_THREADS) {
         int g, th;
-        const int sidx = tile_index<N>(e, lgTlo, p, &g, &th);
-        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + p.G * th);
+        const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
+        const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th);
         float2 v = tile[sidx];
         if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, p.V2[gidx]);
         Y[gidx] = v;
@@ -305,13 +280,33 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_group(const float2* X, 
   }
 }
 
-__global__ void k_small_phase_tables(const double* lam, double tau, float2* ph, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
+// ET[k][i'][i] = E_k[i][i'] with E_k[i][i'] = sum_l St[l][i] e^{-i tau lambda_l} S[i'][l]
+// (FP64, rounded to FP32): the axis propagator T diag(e^{-i tau lambda}) T^{-1} in the plan's
+// operands (forward y_l = sum_i' S[i'][l] x_i', backward y_i = sum_l St[l][i] x_l).
+struct AxisOps {
+  const double* S[MAXD];
+  const double* St[MAXD];
+  const double* lam[MAXD];
+  int n[MAXD];
+  int off[MAXD];  // offset of axis k's matrix in ET (elements)
+};
+
+__global__ void k_axis_propagators(const AxisOps a, int d, double tau, float2* ET) {
+  const int k = blockIdx.y;
+  if (k >= d) return;
+  const int n = a.n[k];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int ip = e / n, i = e - ip * n;  // ET[i'][i]
+  double re = 0.0, im = 0.0;
+  for (int l = 0; l < n; ++l) {
     double s, c;
-    sincos(tau * lam[i], &s, &c);
-    ph[i] = make_float2((float)c, (float)-s);
+    sincos(tau * a.lam[k][l], &s, &c);
+    const double w = a.St[k][(long long)l * n + i] * a.S[k][(long long)ip * n + l];
+    re += w * c;
+    im -= w * s;
   }
+  ET[a.off[k] + e] = make_float2((float)re, (float)im);
 }
 
 __global__ void k_to_f32(const double* in, float* out, long long n) {
@@ -327,49 +322,56 @@ __global__ void k_to_f32_table(const double* S, const double* St, float* Sf, flo
   }
 }
 
-constexpr size_t TILE_BUDGET = 48 * 1024;  // bytes of one complex64 tile buffer (two per CTA)
-
 int odd(int n) { return n | 1; }
 
 struct Group {
   int k0, k1, T;
 };
 
-// Greedy grouping of consecutive axes whose padded tile (times T = 8, i.e. 64-byte runs)
-// fits the budget; T then grows while it still fits (longer contiguous runs, fewer CTAs).
+// Groups of consecutive axes of equal length: each run of r axes of one length n is cut into
+// ceil(r / f) groups of balanced sizes, f = the most modes whose padded tile (with T = 8,
+// i.e. 64-byte runs) fits the budget.
 std::vector<Group> make_groups(const ts_plan* p) {
-  std::vector<Group> gs;
-  int k = 0;
-  while (k < p->d) {
-    int k1 = k + 1;
-    long long gpad = odd(p->n[k]);
-    while (k1 < p->d && (k1 - k) < MAXG && p->n[k1] == p->n[k] &&
-           (size_t)(gpad * odd(p->n[k1]) * 8 * sizeof(float2)) <= TILE_BUDGET) {
-      gpad *= odd(p->n[k1]);
-      ++k1;
+  std::vector<std::pair<int, int>> spans;  // [k, k1) of the groups
+  for (int a = 0; a < p->d;) {
+    int b = a + 1;
+    while (b < p->d && p->n[b] == p->n[a]) ++b;
+    int f = 1;
+    while (f < MAXG && f < b - a && (size_t)ipow(odd(p->n[a]), f + 1) * 8 * sizeof(float2) <= TILE_BUDGET) ++f;
+    const int r = b - a, ng = (r + f - 1) / f;
+    for (int g = 0, k = a; g < ng; ++g) {
+      const int size = r / ng + (g < r % ng ? 1 : 0);
+      spans.push_back({k, k + size});
+      k += size;
     }
-    long long lo = 1, hi = 1;
+    a = b;
+  }
+  std::vector<Group> gs;
+  for (const auto& sp : spans) {
+    const int k = sp.first, k1 = sp.second;
+    long long lo = 1, hi = 1, gpad = 1;
     for (int j = 0; j < k; ++j) lo *= p->n[j];
     for (int j = k1; j < p->d; ++j) hi *= p->n[j];
+    for (int j = k; j < k1; ++j) gpad *= odd(p->n[j]);
     const long long along = lo > 1 ? lo : hi;
     int T = 1;
     while ((size_t)(gpad * (T * 2) * sizeof(float2)) <= TILE_BUDGET && along % (T * 2) == 0 && T < 256) T *= 2;
     gs.push_back({k, k1, T});
-    k = k1;
   }
   return gs;
 }
 
 int g_small_sms = 0;
 
-template <int N>
-ts_status launch_group(const float2* X, float2* Y, const GroupParams& gp, cudaStream_t s) {
+template <int N, int NM>
+ts_status launch_prop(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+  constexpr int GP = ipow(N | 1, NM);
   const int Tlo = gp.lo > 1 ? gp.T : 1, Thi = gp.lo > 1 ? 1 : gp.T;
-  const size_t tile_stride = ((size_t)Tlo * gp.Gpad * Thi + 1) & ~size_t(1);
-  const size_t smem = sizeof(float2) * (2 * tile_stride + ((Tlo + 1) & ~1)) + sizeof(float) * 2 * gp.nm * N * N;
+  const size_t tile_stride = ((size_t)Tlo * GP * Thi + 1) & ~size_t(1);
+  const size_t smem = sizeof(float2) * (2 * tile_stride + (size_t)NM * N * N);
   static bool attr = false;
   if (!attr) {
-    TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_prop<N, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
   if (g_small_sms == 0) {
@@ -379,31 +381,37 @@ ts_status launch_group(const float2* X, float2* Y, const GroupParams& gp, cudaSt
   }
   const long long tiles = gp.lo > 1 ? (gp.lo / Tlo) * gp.hi : gp.hi / Thi;
   int per_sm = 0;
-  TS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_group<N>, SMALL_THREADS, smem));
+  constexpr int THREADS = SmallCfg<N>::THREADS;
+  TS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_prop<N, NM>, THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   const long long grid = tiles < (long long)g_small_sms * per_sm ? tiles : (long long)g_small_sms * per_sm;
   void* tok = nullptr;
   if (prof_enabled()) prof_begin_launch(s, &tok);
-  k_small_group<N><<<(unsigned)grid, SMALL_THREADS, smem, s>>>(X, Y, gp, tiles);
+  k_small_prop<N, NM><<<(unsigned)grid, THREADS, smem, s>>>(X, Y, gp, tiles);
   TS_LAUNCHED(1);
   if (tok) {
-    const long long N_all = gp.lo * gp.G * gp.hi;
-    const int modes = (gp.do_fwd ? gp.nm : 0) + (gp.do_bwd ? gp.nm : 0);
-    prof_end_launch(s, tok, PROF_SMALL_PASS, 4.0 * N * (double)N_all * modes, 16.0 * (double)N_all);
+    const long long N_all = gp.lo * (long long)ipow(N, NM) * gp.hi;
+    prof_end_launch(s, tok, PROF_SMALL_PASS, 8.0 * N * (double)N_all * NM, 16.0 * (double)N_all);
   }
   return TS_OK;
 }
 
-ts_status group_pass(int n, const float2* X, float2* Y, const GroupParams& gp, cudaStream_t s) {
+ts_status group_pass(int n, int nm, const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+#define TS_PROP_CASE(NN)                                          \
+  case NN:                                                        \
+    if (nm == 1) return launch_prop<NN, 1>(X, Y, gp, s);          \
+    if (nm == 2) return launch_prop<NN, 2>(X, Y, gp, s);          \
+    return launch_prop<NN, 3>(X, Y, gp, s);
   switch (n) {
-    case 8: return launch_group<8>(X, Y, gp, s);
-    case 16: return launch_group<16>(X, Y, gp, s);
-    case 24: return launch_group<24>(X, Y, gp, s);
-    case 32: return launch_group<32>(X, Y, gp, s);
+    TS_PROP_CASE(8)
+    TS_PROP_CASE(16)
+    TS_PROP_CASE(24)
+    TS_PROP_CASE(32)
     default:
       set_error("small-n path supports n in {8, 16, 24, 32}");
       return TS_ERR_UNSUPPORTED;
   }
+#undef TS_PROP_CASE
 }
 
 }  // namespace
@@ -435,9 +443,9 @@ ts_status build_small_tables(ts_plan* p, cudaStream_t s) {
   return TS_OK;
 }
 
-// nsteps of: [theta_pre phase on the first load] -> forward groups -> middle (fwd + phase
-// + bwd) -> backward groups -> [theta_post phase on the last store]; with V2 == NULL a
-// single exact propagator (nsteps = 1).
+// nsteps of: [theta_pre phase on the first load] -> the groups' axis propagators, one HBM
+// pass per group -> [theta_post phase on the last store]; with V2 == NULL a single exact
+// propagator (nsteps = 1).
 ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, float2* out, const double* V2, double dt,
                             int nsteps, cudaStream_t s) {
   if (!small_n_supported(p) || !p->Sf32[0]) {
@@ -446,19 +454,29 @@ ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, floa
   }
   const std::vector<Group> gs = make_groups(p);
   const long long N = p->N;
-  int tot = 0, off[MAXD];
+  AxisOps ops{};
+  int tot = 0;
   for (int k = 0; k < p->d; ++k) {
-    off[k] = tot;
-    tot += p->n[k];
+    ops.S[k] = p->S[k];
+    ops.St[k] = p->St[k];
+    ops.lam[k] = p->lam[k];
+    ops.n[k] = p->n[k];
+    ops.off[k] = tot;
+    tot += p->n[k] * p->n[k];
   }
-  void* tabs = nullptr;
+  void* mats = nullptr;
   void* v2f = nullptr;
-  TS_TRY(scratch_alloc(&tabs, sizeof(float2) * tot, s));
+  TS_TRY(scratch_alloc(&mats, sizeof(float2) * tot, s));
   ts_status st = TS_OK;
-  for (int k = 0; k < p->d && st == TS_OK; ++k) {
-    k_small_phase_tables<<<(p->n[k] + 127) / 128, 128, 0, s>>>(p->lam[k], tau, (float2*)tabs + off[k], p->n[k]);
+  {
+    int nn = 0;
+    for (int k = 0; k < p->d; ++k) nn = p->n[k] * p->n[k] > nn ? p->n[k] * p->n[k] : nn;
+    k_axis_propagators<<<dim3((nn + 127) / 128, p->d), 128, 0, s>>>(ops, p->d, tau, (float2*)mats);
     count_launches(1);
-    if (cudaGetLastError() != cudaSuccess) st = TS_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("axis propagator launch failed");
+      st = TS_ERR_CUDA;
+    }
   }
   if (st == TS_OK && V2) {
     st = scratch_alloc(&v2f, sizeof(float) * N, s);
@@ -470,48 +488,27 @@ ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, floa
   }
   const int ng = (int)gs.size();
   for (int step = 0; step < nsteps && st == TS_OK; ++step) {
-    for (int pass = 0; pass < 2 * ng - 1 && st == TS_OK; ++pass) {
-      const bool fwd_part = pass < ng - 1;
-      const bool middle = pass == ng - 1;
-      const int gi = fwd_part || middle ? pass : 2 * ng - 2 - pass;
+    for (int gi = 0; gi < ng && st == TS_OK; ++gi) {
       const Group& g = gs[gi];
-      GroupParams gp{};
-      gp.nm = g.k1 - g.k0;
+      PropParams gp{};
+      const int nm = g.k1 - g.k0;
       gp.lo = 1;
       gp.hi = 1;
-      gp.G = 1;
-      gp.Gpad = 1;
       for (int j = 0; j < g.k0; ++j) gp.lo *= p->n[j];
       for (int j = g.k1; j < p->d; ++j) gp.hi *= p->n[j];
-      for (int j = 0; j < gp.nm; ++j) {
-        const int k = g.k0 + j;
-        gp.npad[j] = odd(p->n[k]);
-        gp.G *= p->n[k];
-        gp.Gpad *= gp.npad[j];
-        gp.fwd[j] = p->Sf32[k];
-        gp.bwd[j] = p->Stf32[k];
-      }
+      for (int j = 0; j < nm; ++j) gp.E[j] = (const float2*)mats + ops.off[g.k0 + j];
       gp.T = g.T;
-      gp.do_fwd = fwd_part || middle;
-      gp.do_bwd = !fwd_part;
-      gp.do_phase = middle;
-      gp.d = p->d;
-      gp.k0 = g.k0;
-      for (int k = 0; k < p->d; ++k) {
-        gp.n_all[k] = p->n[k];
-        gp.ph[k] = (const float2*)tabs + off[k];
-      }
       gp.V2 = (const float*)v2f;
-      const bool first = pass == 0, last = pass == 2 * ng - 2;
+      const bool first = gi == 0, last = gi == ng - 1;
       gp.theta_pre = (V2 && first) ? (float)(step == 0 ? 0.5 * dt : 0.0) : 0.f;
       gp.theta_post = (V2 && last) ? (float)(step == nsteps - 1 ? 0.5 * dt : dt) : 0.f;
       const float2* src = (step == 0 && first) ? in : out;
       const bool src16 = reinterpret_cast<uintptr_t>(src) % 16 == 0, out16 = reinterpret_cast<uintptr_t>(out) % 16 == 0;
       gp.pairs = gp.lo > 1 ? (gp.T % 2 == 0 && src16 && out16 ? 1 : 0) : (p->n[g.k0] % 2 == 0 && out16 ? 2 : 0);
-      st = group_pass(p->n[g.k0], src, out, gp, s);
+      st = group_pass(p->n[g.k0], nm, src, out, gp, s);
     }
   }
-  scratch_free(tabs, s);
+  scratch_free(mats, s);
   scratch_free(v2f, s);
   return st;
 }
