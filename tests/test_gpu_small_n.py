@@ -80,3 +80,22 @@ def test_full_size_strang_fp32_vs_fp64_path(T, name):
     assert abs(b.norm().item() - 1.0) < 1e-12
     del a, b, a64
     torch.cuda.empty_cache()
+
+
+def test_full_size_6d_strang_two_steps_vs_oracle(T):
+    """The 6D workload at its full size (24^6 = 1.9e8 DoF): two complex64 Strang steps of
+    the FP32 path against the oracle's unmerged FP64 Strang steps (forward transforms,
+    phase, backward transforms and half-step potential phases, plain loops)."""
+    w = S.WORKLOADS["6d_n24_strang"]
+    n, L = w["n"], w["L"]
+    f = S.harmonic(n, L, w["omega"])
+    P, Po = plans(n, L, f, FP32_MASK)
+    V2 = S.v2_soft_coulomb(n, L)
+    psi = S.sine_state(n, L)
+    t = dev(psi.astype(np.float32))
+    T.ts_split_step(P, w["dt"], 2, dev(V2), t, T.TS_C64, T.TS_FP32)
+    got = host(t).astype(np.float64)
+    del t
+    want = O.strang(Po, V2, w["dt"], 2, psi)
+    assert rel(got, want) < 1e-5
+    assert maxrel(got, want) < MAXNORM_FACTOR * 1e-5

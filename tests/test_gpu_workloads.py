@@ -66,3 +66,11 @@ def test_n256_inverse_iteration_full_size(T):
     # Weyl: lambda_min(A) + min V2 <= lambda_1 <= lambda_min(A) + max V2
     lamA = sum(T.ts_plan_eigs(P, k)[0] for k in range(3))
     assert lamA + V2h.min() <= l1 <= lamA + V2h.max()
+    # the oracle's own FP64 operator (eq. general_system, plain loops over every point) on the
+    # GPU eigenvector: its Rayleigh quotient equals the GPU lambda and its eigen-residual is small
+    Po = O.Plan(tuple(n), tuple(L), f)
+    uh = host(u)
+    Hu_o = O.stencil(Po, uh, 0.0, V2h)
+    lam_o = float(uh @ Hu_o / (uh @ uh))
+    assert abs(lam_o - l1) / abs(l1) < 1e-11, (lam_o, l1)
+    assert np.linalg.norm(Hu_o - lam_o * uh) / (abs(lam_o) * np.linalg.norm(uh)) < 1e-5
