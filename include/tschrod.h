@@ -57,8 +57,10 @@ typedef enum {
   TS_FP64 = 0,   /* plain FP64 (FFMA64) contractions                                      */
   TS_BF16X3 = 1, /* 2-term bf16 splits of data and S_k, 3 products, FP32 accumulate (tcgen05) */
   TS_BF16X6 = 2, /* 3-term bf16 splits, 6 products, FP32 accumulate (tcgen05)              */
-  TS_TF32X3 = 3, /* 2-term tf32 splits, 3 products (reserved)                              */
-  TS_FP16X3 = 4, /* 2-term fp16 splits with scaling (reserved)                            */
+  /* values 3 and 4 are not assigned (precision_mask bits 3 and 4 are refused): with one
+     FP32 accumulator the tensor-core passes lose about 1e-5 at n = 512 to the truncating
+     accumulation whatever the split format, so tf32 or scaled fp16 splits would not give a
+     cheaper refinement schedule than the bf16 ones */
   TS_FP32 = 5,   /* plain FP32 (FFMA) fused small-n kernels: complex64 propagation with
                     every n_k in {8, 16, 24, 32} (the paper's FP32 variant)              */
   TS_BF16X1 = 6  /* one bf16 plane, one product, FP32 accumulate (tcgen05): a cheap,

@@ -44,7 +44,7 @@ struct DeviceGuard {
 };
 
 ts_status check_prec(const ts_plan* p, ts_precision prec) {
-  if ((int)prec < 0 || (int)prec >= NPREC) {
+  if ((int)prec < 0 || (int)prec >= NPREC || (int)prec == 3 || (int)prec == 4) {
     set_error("invalid precision %d", (int)prec);
     return TS_ERR_INVALID_ARG;
   }
@@ -92,7 +92,8 @@ ts_status ts_plan_create(const ts_plan_desc* desc, unsigned precision_mask, void
   TS_REQUIRE(desc->d >= 1 && desc->d <= TS_MAX_DIM, "d = %d out of range [1, %d]", desc->d, TS_MAX_DIM);
   TS_REQUIRE(desc->n && desc->L && desc->f, "desc->n, desc->L and desc->f must be non-NULL");
   TS_REQUIRE(desc->bc == 0, "only homogeneous Dirichlet (bc = 0) is supported");
-  TS_REQUIRE(precision_mask < (1u << NPREC), "precision_mask 0x%x has unknown bits", precision_mask);
+  TS_REQUIRE(precision_mask < (1u << NPREC) && !(precision_mask & 0x18u),
+             "precision_mask 0x%x has unknown bits (3 and 4 are not assigned)", precision_mask);
   long long N = 1;
   for (int k = 0; k < desc->d; ++k) {
     TS_REQUIRE(desc->n[k] >= 1 && desc->n[k] <= 4096, "n[%d] = %d out of range [1, 4096]", k, desc->n[k]);

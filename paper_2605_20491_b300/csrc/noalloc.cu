@@ -153,7 +153,7 @@ extern "C" ts_status ts_apply_inverse_noalloc(const ts_plan* plan, double sigma,
   cudaStream_t s = (cudaStream_t)stream;
   const long long N = plan->N;
   // the same precision checks, with the same statuses, as ts_apply_inverse
-  if ((int)prec < 0 || (int)prec >= NPREC) {
+  if ((int)prec < 0 || (int)prec >= NPREC || (int)prec == 3 || (int)prec == 4) {
     set_error("invalid precision %d", (int)prec);
     return TS_ERR_INVALID_ARG;
   }

@@ -21,7 +21,7 @@ TS_OK, TS_ERR_INVALID_ARG, TS_ERR_NO_MEMORY, TS_ERR_CUDA, TS_ERR_NOT_CONVERGED, 
     TS_ERR_TIMEOUT = range(7)
 STATUS_NAMES = ["TS_OK", "TS_ERR_INVALID_ARG", "TS_ERR_NO_MEMORY", "TS_ERR_CUDA", "TS_ERR_NOT_CONVERGED",
                 "TS_ERR_UNSUPPORTED", "TS_ERR_TIMEOUT"]
-TS_FP64, TS_BF16X3, TS_BF16X6, TS_TF32X3, TS_FP16X3, TS_FP32, TS_BF16X1 = range(7)
+TS_FP64, TS_BF16X3, TS_BF16X6, TS_FP32, TS_BF16X1 = 0, 1, 2, 5, 6  # 3 and 4 are not assigned
 TS_R64, TS_C128, TS_C64 = range(3)
 TS_MAX_DIM = 12
 

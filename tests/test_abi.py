@@ -125,3 +125,20 @@ def test_tile_config_refuses_clusters_other_than_single_and_pairs(built_lib):
     for cluster in (1, T.TS_TC_PAIR):
         assert L.ts_tc_config_set(0, 64, 64, 128, cluster) == T.TS_OK
         assert L.ts_tc_config_set(0, 64, 0, 0, 0) == T.TS_OK  # forget it again
+
+
+def test_unassigned_precisions_are_refused_on_host(built_lib):
+    """Precision values 3 and 4 are not assigned: a plan mask with those bits is refused
+    before any device work."""
+    import ctypes as C
+    from paper_2605_20491_b300 import tschrod as T
+    L = T.lib()
+    n = (C.c_int * 1)(8)
+    Lx = (C.c_double * 1)(1.0)
+    f0 = (C.c_double * 8)(*([0.0] * 8))
+    f = (C.POINTER(C.c_double) * 1)(C.cast(f0, C.POINTER(C.c_double)))
+    out = C.c_void_p()
+    for bit in (3, 4):
+        desc = T._Desc(1, n, Lx, f, 0, 1)
+        assert L.ts_plan_create(C.byref(desc), 1 << bit, None, C.byref(out)) == T.TS_ERR_INVALID_ARG
+        assert "not assigned" in T.ts_last_error() and out.value is None
