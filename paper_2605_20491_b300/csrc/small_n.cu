@@ -280,6 +280,163 @@ __global__ void __launch_bounds__(SmallCfg<N>::THREADS, 2) k_small_prop(const fl
   }
 }
 
+// 8-point axes in groups of three with T = 8: the tile is eight independent 8 x 8 x 8 cubes
+// (one per lo index t, or per hi index th), and warp w owns cube w.  A warp applies its
+// cube's three axis propagators alone (two fibers per lane sharing every matrix load),
+// separated by __syncwarp instead of CTA barriers; only the copies between HBM and the
+// tile are cooperative (64-byte runs along t for lo > 1).  Cube c starts at c * CUBE in
+// shared memory, element (i0, i1, i2) at i0 + 9 i1 + 81 i2 (padded extents, odd).
+constexpr int CUBE = 729;
+
+template <int M>
+__device__ __forceinline__ void cube_mode(float2* cube, const float2* Em, int lane) {
+  // fibers of mode M: 64, indexed by the two other axes (the lower one fastest)
+  constexpr int ST = M == 0 ? 1 : (M == 1 ? 9 : 81);
+  constexpr int SA = M == 0 ? 9 : 1;   // stride of the fiber index's fast axis
+  constexpr int SB = M == 2 ? 9 : 81;  // ... and of its slow axis
+  int addr[2];
+  float2 x[2][8];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int f = lane + 32 * c;
+    addr[c] = (f & 7) * SA + (f >> 3) * SB;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[c][i] = cube[addr[c] + i * ST];
+  }
+  float re[2][8], im[2][8];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) re[c][q] = im[c][q] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      const float4 e = *reinterpret_cast<const float4*>(Em + i * 8 + q);  // E[q][i], E[q+1][i]
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        re[c][q] = fmaf(e.x, x[c][i].x, re[c][q]);
+        re[c][q] = fmaf(-e.y, x[c][i].y, re[c][q]);
+        im[c][q] = fmaf(e.x, x[c][i].y, im[c][q]);
+        im[c][q] = fmaf(e.y, x[c][i].x, im[c][q]);
+        re[c][q + 1] = fmaf(e.z, x[c][i].x, re[c][q + 1]);
+        re[c][q + 1] = fmaf(-e.w, x[c][i].y, re[c][q + 1]);
+        im[c][q + 1] = fmaf(e.z, x[c][i].y, im[c][q + 1]);
+        im[c][q + 1] = fmaf(e.w, x[c][i].x, im[c][q + 1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cube[addr[c] + q * ST] = make_float2(re[c][q], im[c][q]);
+}
+
+__global__ void __launch_bounds__(256, 2) k_small_cubes(const float2* X, float2* Y, const PropParams p,
+                                                       long long ntiles) {
+  constexpr int TSZ = 8 * CUBE;  // one tile buffer
+  extern __shared__ __align__(16) float2 smem[];
+  float2* buf[2] = {smem, smem + TSZ};
+  float2* mats = smem + 2 * TSZ;
+  for (int e = threadIdx.x; e < 3 * 64; e += 256) mats[e] = p.E[e / 64][e % 64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool lo_tiles = p.lo > 1;  // cubes along lo (t = cube) or along hi (th = cube)
+  auto origin = [&](long long b) -> long long {
+    if (lo_tiles) {
+      const long long lblocks = p.lo >> 3;
+      return ((b % lblocks) << 3) + p.lo * 512 * (b / lblocks);
+    }
+    return 512LL * 8 * b;
+  };
+  // element e of a tile in HBM order (lo tiles: t fastest, then g; hi tiles: g fastest, then th)
+  auto offsets = [&](int e, long long gbase, int* sidx, long long* gidx) {
+    int c, g;
+    if (lo_tiles) {
+      c = e & 7;
+      g = e >> 3;
+      *gidx = gbase + c + p.lo * g;
+    } else {
+      c = e >> 9;
+      g = e & 511;
+      *gidx = gbase + e;
+    }
+    *sidx = c * CUBE + (g & 7) + 9 * ((g >> 3) & 7) + 81 * (g >> 6);
+  };
+  auto issue_load = [&](long long b, float2* dst) {
+    const long long gbase = origin(b);
+    if (p.pairs) {
+      for (int e = 2 * threadIdx.x; e < 4096; e += 512) {
+        int sidx;
+        long long gidx;
+        offsets(e, gbase, &sidx, &gidx);
+        // lo tiles: (t, t + 1) are cubes t and t + 1; hi tiles: (i0, i0 + 1) of one cube row
+        cp_async8(dst + sidx, X + gidx);
+        cp_async8(dst + sidx + (lo_tiles ? CUBE : 1), X + gidx + 1);
+      }
+    } else {
+      for (int e = threadIdx.x; e < 4096; e += 256) {
+        int sidx;
+        long long gidx;
+        offsets(e, gbase, &sidx, &gidx);
+        cp_async8(dst + sidx, X + gidx);
+      }
+    }
+    cp_async_commit();
+  };
+  long long b = blockIdx.x;
+  if (b < ntiles) issue_load(b, buf[0]);
+  int cur = 0;
+  for (; b < ntiles; b += gridDim.x, cur ^= 1) {
+    const long long bn = b + gridDim.x;
+    if (bn < ntiles) {
+      issue_load(bn, buf[cur ^ 1]);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // the tile has landed (copied by every thread)
+    float2* cube = buf[cur] + warp * CUBE;
+    const long long gbase = origin(b);
+    if (p.V2 && p.theta_pre != 0.f) {
+      // the warp's own cube: element g of cube `warp`
+      for (int g = lane; g < 512; g += 32) {
+        const long long gidx = lo_tiles ? gbase + warp + p.lo * g : gbase + 512LL * warp + g;
+        const int si = (g & 7) + 9 * ((g >> 3) & 7) + 81 * (g >> 6);
+        cube[si] = vphase(cube[si], p.theta_pre, p.V2[gidx]);
+      }
+      __syncwarp();
+    }
+    cube_mode<0>(cube, mats, lane);
+    __syncwarp();
+    cube_mode<1>(cube, mats + 64, lane);
+    __syncwarp();
+    cube_mode<2>(cube, mats + 128, lane);
+    __syncthreads();  // every cube is done before the cooperative store
+    float2* tile = buf[cur];
+    const int step_e = p.pairs ? 2 : 1;
+    for (int e = step_e * threadIdx.x; e < 4096; e += step_e * 256) {
+      int sidx;
+      long long gidx;
+      offsets(e, gbase, &sidx, &gidx);
+      float2 v0 = tile[sidx];
+      if (p.pairs) {
+        float2 v1 = tile[sidx + (lo_tiles ? CUBE : 1)];
+        if (p.V2 && p.theta_post != 0.f) {
+          v0 = vphase(v0, p.theta_post, p.V2[gidx]);
+          v1 = vphase(v1, p.theta_post, p.V2[gidx + 1]);
+        }
+        *reinterpret_cast<float4*>(Y + gidx) = make_float4(v0.x, v0.y, v1.x, v1.y);
+      } else {
+        if (p.V2 && p.theta_post != 0.f) v0 = vphase(v0, p.theta_post, p.V2[gidx]);
+        Y[gidx] = v0;
+      }
+    }
+    __syncthreads();  // the buffer is refilled two iterations later
+  }
+}
+
+ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s);
+
 // ET[k][i'][i] = E_k[i][i'] with E_k[i][i'] = sum_l St[l][i] e^{-i tau lambda_l} S[i'][l]
 // (FP64, rounded to FP32): the axis propagator T diag(e^{-i tau lambda}) T^{-1} in the plan's
 // operands (forward y_l = sum_i' S[i'][l] x_i', backward y_i = sum_l St[l][i] x_l).
@@ -396,7 +553,36 @@ ts_status launch_prop(const float2* X, float2* Y, const PropParams& gp, cudaStre
   return TS_OK;
 }
 
+ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (2 * 8 * CUBE + 3 * 64);
+  static bool attr = false;
+  if (!attr) {
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_cubes, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  if (g_small_sms == 0) {
+    int dev = 0;
+    TS_CHECK_CUDA(cudaGetDevice(&dev));
+    TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_small_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long long tiles = gp.lo > 1 ? (gp.lo / 8) * gp.hi : gp.hi / 8;
+  int per_sm = 0;
+  TS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_cubes, 256, smem));
+  if (per_sm < 1) per_sm = 1;
+  const long long grid = tiles < (long long)g_small_sms * per_sm ? tiles : (long long)g_small_sms * per_sm;
+  void* tok = nullptr;
+  if (prof_enabled()) prof_begin_launch(s, &tok);
+  k_small_cubes<<<(unsigned)grid, 256, smem, s>>>(X, Y, gp, tiles);
+  TS_LAUNCHED(1);
+  if (tok) {
+    const long long N_all = gp.lo * 512LL * gp.hi;
+    prof_end_launch(s, tok, PROF_SMALL_PASS, 8.0 * 8 * (double)N_all * 3, 16.0 * (double)N_all);
+  }
+  return TS_OK;
+}
+
 ts_status group_pass(int n, int nm, const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+  if (n == 8 && nm == 3 && gp.T == 8) return launch_cubes(X, Y, gp, s);  // one cube per warp
 #define TS_PROP_CASE(NN)                                          \
   case NN:                                                        \
     if (nm == 1) return launch_prop<NN, 1>(X, Y, gp, s);          \
