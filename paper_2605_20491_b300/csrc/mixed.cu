@@ -435,13 +435,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (ep.scale_mode != 0 && row_ok) epi_row_factors(ep, r, &rowsum, &rowph);
       const long long ro = row_ok ? epi_out_row(ep, r) : 0;
       const uint32_t lane_base = tmem + (uint32_t)(ab * acc_cols) + ((uint32_t)(g * 32) << 16);
-      for (int col0 = part * 16; col0 < BN; col0 += 16 * (EPI_WARPS / 4)) {
-        uint32_t v[NACC][16];
+      constexpr int CSTEP = 16 * (EPI_WARPS / 4);  // columns between a warp's chunks
+      if constexpr (NACC == 1 && PLANES_OUT) {
+        // real data, plane output: the next chunk's tensor-memory load is in flight while the
+        // current chunk is split and stored (tcgen05.wait::ld waits for all of a thread's
+        // loads, so the two register buffers alternate); the passes that write the FP64
+        // result keep one buffer, as their 16 previous values already hold the registers
+        uint32_t va[1][16], vb[1][16];
+        int col0 = part * 16;
+        if (col0 < BN) tc::tmem_ld16(lane_base + (uint32_t)col0, va[0]);
+        for (; col0 < BN; col0 += 2 * CSTEP) {
+          tc::tmem_ld_wait();
+          const int c1 = col0 + CSTEP;
+          if (c1 < BN) tc::tmem_ld16(lane_base + (uint32_t)c1, vb[0]);
+          if (row_ok) epi_chunk<NP, NACC, PLANES_OUT>(ep, va, ro, n0 + col0, rowsum, rowph, emx, fs, fds, fsc);
+          if (c1 >= BN) break;
+          tc::tmem_ld_wait();
+          const int c2 = c1 + CSTEP;
+          if (c2 < BN) tc::tmem_ld16(lane_base + (uint32_t)c2, va[0]);
+          if (row_ok) epi_chunk<NP, NACC, PLANES_OUT>(ep, vb, ro, n0 + c1, rowsum, rowph, emx, fs, fds, fsc);
+        }
+      } else {
+        for (int col0 = part * 16; col0 < BN; col0 += CSTEP) {
+          uint32_t v[NACC][16];
 #pragma unroll
-        for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
-        tc::tmem_ld_wait();
-        if (!row_ok) continue;
-        epi_chunk<NP, NACC, PLANES_OUT>(ep, v, ro, n0 + col0, rowsum, rowph, emx, fs, fds, fsc);
+          for (int c = 0; c < NACC; ++c) tc::tmem_ld16(lane_base + (uint32_t)(c * BN + col0), v[c]);
+          tc::tmem_ld_wait();
+          if (!row_ok) continue;
+          epi_chunk<NP, NACC, PLANES_OUT>(ep, v, ro, n0 + col0, rowsum, rowph, emx, fs, fds, fsc);
+        }
       }
       tc::tc_fence_before();
       __syncwarp();
