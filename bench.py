@@ -248,7 +248,8 @@ def run_profile_case(args):
     of the n = 512 workload only (with --profile-n m: on an m^3 grid of the same box and
     potential), or, with --workload 6d_n24_strang / 9d_n8_strang, the complex64 FP32 Strang
     steps only, or, with --workload 3d_n256_pcg, one BF16X3-preconditioned shifted inverse
-    iteration; warmup + steps times (not the inverse iteration), nothing else."""
+    iteration; warmup + steps times (not the inverse iteration), nothing else.  With
+    --profile-bf16x6 the Strang steps run in TS_BF16X6 (the tensor-core small-n pass)."""
     import torch
     from paper_2605_20491_b300 import tschrod as T
     if args.workload == "3d_n256_pcg":
@@ -279,10 +280,11 @@ def run_profile_case(args):
     if args.workload in ("6d_n24_strang", "9d_n8_strang"):
         w = synth.WORKLOADS[args.workload]
         n, L = w["n"], w["L"]
-        P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << T.TS_FP32)
+        prec = T.TS_BF16X6 if args.profile_bf16x6 else T.TS_FP32
+        P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << prec)
         V2 = torch.from_numpy(synth.v2_soft_coulomb(n, L)).cuda()
         x = torch.from_numpy(synth.sine_state(n, L).astype(np.float32)).cuda()
-        T.ts_split_step(P, w["dt"], args.warmup + args.steps, V2, x, T.TS_C64, T.TS_FP32)
+        T.ts_split_step(P, w["dt"], args.warmup + args.steps, V2, x, T.TS_C64, prec)
         torch.cuda.synchronize()
         print("profile case done", flush=True)
         return 0
@@ -422,35 +424,42 @@ def batched_list_kernel(T, peaks, items=40, reps=5, seed=4):
             "bound": "tensor" if f_t >= f_h else "hbm"}
 
 
-def strang_run(T, name, peaks, steps=None):
-    """complex64 Strang steps of the 6D n = 24 or 9D n = 8 workload on the FP32 fused
-    small-n path: ms per step and the HBM rate of its fused passes (algorithmic bytes per
-    device time of the pass kernels)."""
+def strang_run(T, name, peaks, steps=None, prec=None):
+    """complex64 Strang steps of the 6D n = 24 or 9D n = 8 workload on the fused small-n
+    path (TS_FP32: the FFMA kernels; TS_BF16X6: the tensor-core kernel for axes of 16 or
+    24): ms per step, the HBM rate of the fused passes (algorithmic bytes per device time
+    of the pass kernels) and, for the tensor-core kernel, its bf16 tensor rate."""
     import torch
+    prec = T.TS_FP32 if prec is None else prec
     w = synth.WORKLOADS[name]
     n, L = w["n"], w["L"]
     steps = steps or w["steps"]
-    P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << T.TS_FP32)
+    P = T.ts_plan_create(n, L, synth.harmonic(n, L, w["omega"]), 1 << prec)
     V2 = torch.from_numpy(synth.v2_soft_coulomb(n, L)).cuda()
     x = torch.from_numpy(synth.sine_state(n, L).astype(np.float32)).cuda()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    T.ts_split_step(P, w["dt"], 3, V2, x, T.TS_C64, T.TS_FP32)
+    T.ts_split_step(P, w["dt"], 3, V2, x, T.TS_C64, prec)
     torch.cuda.synchronize()
     T.ts_profile_begin()
     e0.record()
-    T.ts_split_step(P, w["dt"], steps, V2, x, T.TS_C64, T.TS_FP32)
+    T.ts_split_step(P, w["dt"], steps, V2, x, T.TS_C64, prec)
     e1.record()
     torch.cuda.synchronize()
     nl, kms, fl, by = T.ts_profile_end(T.PROF_SMALL_PASS)
     ms = e0.elapsed_time(e1) / steps
     norm = float(torch.linalg.vector_norm(x.double()).item())
     gbs = by / (kms * 1e-3) / 1e9 if kms else None
-    out = {"workload": name, "n": list(n), "dof": P.N, "dtype": "c64", "prec": "FP32 fused small-n",
+    tensor = prec == T.TS_BF16X6
+    out = {"workload": name, "n": list(n), "dof": P.N, "dtype": "c64",
+           "prec": "BF16X6 tensor-core small-n" if tensor else "FP32 fused small-n",
            "steps": steps, "ms_per_step": ms, "gdofs": P.N / (ms * 1e-3) / 1e9,
            "passes_per_step": nl / steps, "pass_ms_per_step": kms / steps, "pass_gbs": gbs,
            "pass_frac_of_hbm": gbs / peaks["hbm_gbs"] if gbs else None,
-           "hbm_floor_ms_per_step": 2.0 * 8.0 * P.N / (peaks["hbm_gbs"] * 1e9) * 1e3,
+           "hbm_floor_ms_per_pass": 2.0 * 8.0 * P.N / (peaks["hbm_gbs"] * 1e9) * 1e3,
+           "hbm_floor_ms_per_step": nl / steps * 2.0 * 8.0 * P.N / (peaks["hbm_gbs"] * 1e9) * 1e3,
            "norm_after": norm}
+    if tensor and kms:
+        out["pass_tflops"] = fl / (kms * 1e-3) / 1e12
     del x, V2
     torch.cuda.empty_cache()
     return out
@@ -902,6 +911,8 @@ def main():
                     help="grid points per axis of the --profile-case refined solve (default: the workload's)")
     ap.add_argument("--profile-fp64", action="store_true",
                     help="with --profile-case: the plain FP64 inverse apply instead of the refined solve")
+    ap.add_argument("--profile-bf16x6", action="store_true",
+                    help="with --profile-case and a Strang workload: the tensor-core small-n pass (TS_BF16X6)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 6D / 9D Strang and 3D n = 256 inverse-iteration sub-runs")

@@ -217,6 +217,13 @@ ts_status ts_solve_refined(const ts_plan* plan, double sigma, const double* b, d
  * forward transform, multiply coefficient (i_1..i_d) by e^{-i tau Lambda}, backward
  * transform.  dtype TS_C128 (2N doubles) or TS_C64 (2N floats); psi_in and psi_out may
  * alias.  prec as for ts_apply_inverse (TS_C64 data with TS_FP64 arithmetic is allowed).
+ * TS_FP32 (complex64 only, every n_k in {8, 16, 24, 32}) applies the factored form
+ * e^{-i tau A} = (x)_k E_k, E_k = T_k diag(e^{-i tau lambda_k}) T_k^{-1}, a few axes per
+ * pass through HBM on the FFMA pipes.  TS_BF16X6 on TS_C64 data with d >= 2 and every n_k
+ * in {16, 24} takes the same factored form on the tensor cores (the real 2n x 2n embedding
+ * of E_k, three bf16 planes, six products, two axes per pass); other shapes and dtypes use
+ * the transform-scale-transform passes.  The factored forms need no extra device memory
+ * beyond d small E_k tables (and an FP32 copy of V2 in the split steps).
  */
 ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void* psi_out,
                        ts_dtype dtype, ts_precision prec, void* stream);
@@ -373,7 +380,10 @@ ts_status ts_propagate(const ts_plan* plan, ts_scheme scheme, int M, double dt, 
  * i d psi/dt = (A + B) psi, A = -Delta_h + V1 (exact propagator), B = diag(V2):
  *     psi <- e^{-i V2 dt/2} e^{-i A dt} e^{-i V2 dt/2} psi.
  * The half steps of adjacent steps are merged into one e^{-i V2 dt} factor.
- * V2: N doubles (device).  psi: TS_C128 or TS_C64, updated in place.
+ * V2: N doubles (device).  psi: TS_C128 or TS_C64, updated in place.  prec as for
+ * ts_apply_exp; on the factored small-n forms (TS_FP32, and TS_BF16X6 on TS_C64 with every
+ * n_k in {16, 24}) the potential phases are applied inside the first and last pass of each
+ * step, so a step costs ceil(d / 2) or ceil(d / 3) passes over psi.
  */
 ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double* V2, void* psi,
                         ts_dtype dtype, ts_precision prec, void* stream);

@@ -114,6 +114,8 @@ ts_status apply_exp_impl(const ts_plan* p, double tau, const void* in, void* out
     }
     return small_n_propagate(p, tau, (const float2*)in, (float2*)out, nullptr, tau, 1, s);
   }
+  if (prec == TS_BF16X6 && dt == TS_C64 && small_tc_applicable(p))
+    return small_n_propagate(p, tau, (const float2*)in, (float2*)out, nullptr, tau, 1, s, true);
   if (prec != TS_FP64) return mixed_apply(p, prec, MixedOp::Exp, tau, in, out, dt, s);
   if (dt == TS_C128) return fp64_pipeline(p, (const double*)in, (double*)out, 2, 1, tau, s);
   // complex64 data, FP64 arithmetic: widen, apply, narrow.

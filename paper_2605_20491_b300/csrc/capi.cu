@@ -9,6 +9,7 @@
 #include "mixed.cuh"
 #include "pointwise.cuh"
 #include "sem_axis.cuh"
+#include "small_n.cuh"
 #include "solvers.cuh"
 
 namespace ts {
@@ -268,6 +269,7 @@ ts_status ts_device_status(void* stream) {
   clear_error();
   int flag = 0;
   TS_TRY(mixed_error_flag(&flag, true, (cudaStream_t)stream));
+  if (flag == 0) TS_TRY(small_n_error_flag(&flag, true, (cudaStream_t)stream));
   if (flag != 0) {
     set_error("a bounded device-side wait ran out (code %d)", flag);
     return TS_ERR_TIMEOUT;

@@ -30,6 +30,7 @@
 #include "common.cuh"
 #include "async_copy.cuh"
 #include "small_n.cuh"
+#include "tc_ptx.cuh"
 
 namespace ts {
 namespace {
@@ -437,6 +438,279 @@ __global__ void __launch_bounds__(256, 2) k_small_cubes(const float2* X, float2*
 
 ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s);
 
+// ------------------------------------------------ tensor-core small-n pass ----
+//
+// The same pass for groups of two axes of length N in {16, 24} on the 5th-generation tensor
+// cores (precision TS_BF16X6 on complex64 data).  Applying E_k along an axis is a real GEMM
+// per fiber: with x the 2N reals (re, im interleaved) of a fiber and R_k the real 2N x 2N
+// embedding of E_k (R[2j][2g] = Re E[j][g], R[2j][2g+1] = -Im E[j][g], R[2j+1][2g] =
+// Im E[j][g], R[2j+1][2g+1] = Re E[j][g]), y = R_k x.  A tile is T = 16 lo (or hi) indices
+// x N x N values: ROWS = 16 N fibers of the first axis, the K-major operand of one tcgen05
+// GEMM (M = ROWS in blocks of 128, N = K = 2N).  Data and R_k are split into three bf16
+// planes (the bf16x6 products of Henry, Tang & Heinecke).  The three planes of R_k are
+// stacked along N, so each data plane is read from shared memory once per K step: plane 0
+// against [R0; R1; R2] (N = 6n), plane 1 against [R0; R1] and plane 2 against R0.  The
+// accumulators are X = x0 R0 (the leading product alone, which keeps the FP32 accumulation's
+// truncation of the corrections off the large term), Y = x0 R1 + x1 R0 + x2 R0 and
+// Z = x0 R2 + x1 R1; the epilogue forms X + (Y + Z).  The first axis's epilogue writes the
+// second axis's operand (rows = fibers of the second axis) back into the same shared-memory
+// planes, transposed; the second epilogue applies the V2 phase of the last pass and stores.
+// One CTA per SM, one thread per row; every wait is bounded.
+__device__ int g_small_tc_error = 0;
+
+template <int N>
+struct SmallTc {
+  static constexpr int T = 16;
+  static constexpr int ROWS = T * N;            // 256 / 384
+  static constexpr int MB = ROWS / 128;         // M blocks
+  static constexpr int NR = 2 * N;              // reals per fiber (K and N of the GEMM)
+  static constexpr int KS = NR / 16;            // 16-wide K steps
+  static constexpr int PLANE_A = ROWS * 128;    // one bf16 plane, rows of 64 elements (128-byte swizzle)
+  static constexpr int PLANE_B = NR / 8 * 1024;  // NR rows of R_k, 8-row atoms
+  static constexpr int THREADS = ROWS;
+  static constexpr int ACC = 3 * NR;            // tensor-memory columns per M block (three accumulators)
+  static constexpr int SMEM = 1024 + 3 * PLANE_A + 6 * PLANE_B + 64;
+  static_assert(ROWS % 128 == 0 && NR % 16 == 0 && NR <= 64, "tile shape");
+  static_assert(MB * ACC <= 512, "tensor memory");
+};
+
+// Byte offset of element (row m, column k) in a K-major bf16 tile of 64-element rows with
+// the 128-byte swizzle (16-byte chunk c of row m stored at chunk c ^ (m mod 8)).
+__device__ __forceinline__ uint32_t sw128_off(int m, int k) {
+  return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((((k >> 3) ^ m) & 7) << 4) + (k & 7) * 2);
+}
+
+// The three bf16 planes of v (each the rounding of what the previous planes leave).
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 (&h)[3]) {
+  h[0] = __float2bfloat16_rn(v);
+  float r = v - __bfloat162float(h[0]);
+  h[1] = __float2bfloat16_rn(r);
+  r -= __bfloat162float(h[1]);
+  h[2] = __float2bfloat16_rn(r);
+}
+
+// Store the planes of the complex value (re, im) at columns (k, k + 1) of row m (k even).
+// (re and im converted together: the same roundings as split3 on each.)
+template <int PLANE>
+__device__ __forceinline__ void store_pair3(uint8_t* planes, int m, int k, float re, float im) {
+  const __nv_bfloat162 h0 = __floats2bfloat162_rn(re, im);
+  const float2 f0 = __bfloat1622float2(h0);
+  const float r1 = re - f0.x, i1 = im - f0.y;
+  const __nv_bfloat162 h1 = __floats2bfloat162_rn(r1, i1);
+  const float2 f1 = __bfloat1622float2(h1);
+  const __nv_bfloat162 h2 = __floats2bfloat162_rn(r1 - f1.x, i1 - f1.y);
+  const uint32_t off = sw128_off(m, k);
+  *reinterpret_cast<__nv_bfloat162*>(planes + off) = h0;
+  *reinterpret_cast<__nv_bfloat162*>(planes + PLANE + off) = h1;
+  *reinterpret_cast<__nv_bfloat162*>(planes + 2 * PLANE + off) = h2;
+}
+
+// One axis: the six bf16x6 products of A (rows mb*128..) and the stacked planes of R, as
+// three MMAs per K step and M block: columns [0, NR) X, [NR, 2 NR) Y, [2 NR, 3 NR) Z.
+template <int N>
+__device__ __forceinline__ void tc_axis_mmas(const uint8_t* A, const uint8_t* B, uint32_t tmem) {
+  using C = SmallTc<N>;
+  constexpr uint32_t id3 = tc::idesc_bf16_f32(128, 3 * C::NR), id2 = tc::idesc_bf16_f32(128, 2 * C::NR),
+                     id1 = tc::idesc_bf16_f32(128, C::NR);
+  // The descriptors are rebuilt from opaque base addresses on every call: hoisted out of the
+  // tile loop, 36 64-bit descriptors would stay live in every thread's registers.
+  uint32_t a0, b0;
+  asm volatile("mov.u32 %0, %1;" : "=r"(a0) : "r"(tc::smem_u32(A)));
+  asm volatile("mov.u32 %0, %1;" : "=r"(b0) : "r"(tc::smem_u32(B)));
+#pragma unroll
+  for (int mb = 0; mb < C::MB; ++mb) {
+    const uint32_t d = tmem + (uint32_t)(mb * C::ACC);
+#pragma unroll
+    for (int ks = 0; ks < C::KS; ++ks) {
+      const uint64_t bd = tc::desc_sw<128>(b0 + ks * 32);
+      const uint32_t a = a0 + mb * 128 * 128 + ks * 32;
+      tc::mma_bf16(d, tc::desc_sw<128>(a), bd, id3, ks == 0 ? 0u : 1u);
+      tc::mma_bf16(d + C::NR, tc::desc_sw<128>(a + C::PLANE_A), bd, id2, 1u);
+      tc::mma_bf16(d + C::NR, tc::desc_sw<128>(a + 2 * C::PLANE_A), bd, id1, 1u);
+    }
+  }
+}
+
+// Row m's accumulators in its M block (columns [0, NR) X, then Y, then Z).  Lane quadrant:
+// warp w reads lanes 32 (w mod 4) .. + 31.
+template <int N>
+__device__ __forceinline__ uint32_t tc_row_base(uint32_t tmem, int warp) {
+  return tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * SmallTc<N>::ACC);
+}
+
+// Columns [c0, c0 + 16) of the row: X + (Y + Z), 8 complex values.
+// (Y and Z first, then X: 32 registers of loads live at a time.)
+template <int N>
+__device__ __forceinline__ void tc_read16(uint32_t base, int c0, float (&v)[16]) {
+  uint32_t u[16], w[16];
+  tc::tmem_ld16(base + (uint32_t)(SmallTc<N>::NR + c0), u);
+  tc::tmem_ld16(base + (uint32_t)(2 * SmallTc<N>::NR + c0), w);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]) + __uint_as_float(w[i]);
+  tc::tmem_ld16(base + (uint32_t)c0, u);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]) + v[i];
+}
+
+// Byte offset, in one operand plane, of value j of this thread's run: row j T + tq (tiles
+// along the lower axes, LO) or tq N + j, column 2 gq.  Rows of a run differ by T = 16 (two
+// 8-row atoms) or by 1 with tq N a multiple of 8, so the offset is a thread constant plus a
+// compile-time part and one XOR of the chunk index.
+template <int N, bool LO>
+__device__ __forceinline__ uint32_t run_off(int tq, int gq, int j) {
+  constexpr int T = SmallTc<N>::T;
+  if (LO) return sw128_off(tq, 2 * gq) + (uint32_t)j * (T / 8) * 1024;
+  return (uint32_t)(tq * (N / 8)) * 1024 + (uint32_t)(j >> 3) * 1024 + (uint32_t)(j & 7) * 128 +
+         ((((uint32_t)gq >> 2) ^ (uint32_t)j) & 7) * 16 + ((uint32_t)gq & 3) * 4;
+}
+
+template <int N, bool LO>
+__global__ void __launch_bounds__(SmallTc<N>::THREADS, 1) k_small_tc(const float2* X, float2* Y,
+                                                                    const PropParams p, long long ntiles) {
+  using C = SmallTc<N>;
+  constexpr int T = C::T, G = N * N;
+  static_assert(N % 8 == 0 && T == 16, "run offsets");
+  extern __shared__ uint8_t tc_raw[];
+  uint8_t* A = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* B = A + 3 * C::PLANE_A;  // [axis][plane]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(B + 6 * C::PLANE_B);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // R_k of the group's two axes, split into planes (columns >= NR of a row are never read)
+  for (int e = tid; e < 2 * C::NR * C::NR; e += C::THREADS) {
+    const int ax = e / (C::NR * C::NR), n = (e / C::NR) % C::NR, k = e % C::NR;
+    const float2 E = p.E[ax][(k >> 1) * N + (n >> 1)];  // ET[g][j] = E[j][g]
+    const float v = (n & 1) == 0 ? ((k & 1) == 0 ? E.x : -E.y) : ((k & 1) == 0 ? E.y : E.x);
+    __nv_bfloat16 h[3];
+    split3(v, h);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) *reinterpret_cast<__nv_bfloat16*>(B + (ax * 3 + q) * C::PLANE_B + sw128_off(n, k)) = h[q];
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async();  // generic-proxy writes of B are read by the tensor cores
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t rbase = tc_row_base<N>(tmem, warp);
+  const bool pre = p.V2 && p.theta_pre != 0.f, post = p.V2 && p.theta_post != 0.f;
+  // The thread's run: fixed (t, g) = (tq, gq), the other axis's index j = 0 .. N-1.  The same
+  // pair serves the load (g = g0, j = g1: value j goes to row j T + tq or tq N + j of the
+  // first axis's operand), epilogue 1 (row (g1 = gq, t = tq) of the first axis's result:
+  // output j0 = j goes to row j T + tq or tq N + j, column gq, of the second axis's operand)
+  // and epilogue 2 (row (j0 = gq, t = tq): output (t, j0, j1 = j)).  A warp reads and
+  // writes runs of consecutive t (LO) or g (tiles along the upper axes).
+  const int tq = LO ? tid % T : tid / N, gq = LO ? tid / T : tid % N;
+  const long long lo = p.lo;
+  // element (t, g0, g1) of tile base b0 sits at b0 + t + lo (g0 + N g1) (LO) or
+  // b0 + G t + g0 + N g1
+  const long long run0 = LO ? tq + lo * gq : (long long)G * tq + gq;
+  const long long step = LO ? lo * N : (long long)N;
+  auto tile_base = [&](long long b) -> long long {
+    if (!LO) return (long long)G * T * b;
+    const long long lblocks = lo / T;
+    return (b % lblocks) * T + lo * G * (b / lblocks);
+  };
+  // the tile's values in registers: all N loads of a thread in flight at once, issued for
+  // the next tile while the current one is on the tensor cores
+  float2 xv[N];
+  float vv[N];
+  auto fetch = [&](long long b) {
+    const long long o = tile_base(b) + run0;
+    const float2* xp = X + o;
+#pragma unroll
+    for (int j = 0; j < N; ++j) xv[j] = xp[step * j];
+    if (pre) {
+      const float* vp = p.V2 + o;
+#pragma unroll
+      for (int j = 0; j < N; ++j) vv[j] = vp[step * j];
+    }
+  };
+  uint32_t phase = 0;
+  long long b = blockIdx.x;
+  if (b < ntiles) fetch(b);
+  for (; b < ntiles; b += gridDim.x) {
+    const long long o = tile_base(b) + run0;
+    // 1. the tile into the first axis's operand
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float2 x = xv[j];
+      if (pre) x = vphase(x, p.theta_pre, vv[j]);
+      store_pair3<C::PLANE_A>(A + run_off<N, LO>(tq, gq, j), 0, 0, x.x, x.y);
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    // 2. the first axis; the next tile's loads overlap it
+    if (tid == 0) {
+      tc::tc_fence_after();
+      tc_axis_mmas<N>(A, B, tmem);
+      tc::mma_commit(&bar[0]);
+    }
+    if (b + gridDim.x < ntiles) fetch(b + gridDim.x);
+    tc::mbar_wait(&bar[0], phase, &g_small_tc_error, 21);
+    phase ^= 1;
+    tc::tc_fence_after();
+    // 3. its epilogue: fiber (g1 = gq, t = tq) becomes column gq of the rows (j0, t) of the
+    //    second axis's operand
+#pragma unroll
+    for (int c0 = 0; c0 < C::NR; c0 += 16) {
+      float y[16];
+      tc_read16<N>(rbase, c0, y);
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) store_pair3<C::PLANE_A>(A + run_off<N, LO>(tq, gq, (c0 + i) >> 1), 0, 0, y[i], y[i + 1]);
+    }
+    tc::tc_fence_before();
+    tc::fence_proxy_async();
+    __syncthreads();
+    // 4. the second axis
+    if (tid == 0) {
+      tc::tc_fence_after();
+      tc_axis_mmas<N>(A, B + 3 * C::PLANE_B, tmem);
+      tc::mma_commit(&bar[0]);
+    }
+    float vp[N];
+    if (post) {
+      const float* v2 = p.V2 + o;
+#pragma unroll
+      for (int j = 0; j < N; ++j) vp[j] = v2[step * j];
+    }
+    tc::mbar_wait(&bar[0], phase, &g_small_tc_error, 22);
+    phase ^= 1;
+    tc::tc_fence_after();
+    // 5. its epilogue: row (j0 = gq, t = tq) holds the values (j1, re / im) of output
+    //    (t, j0, j1), at o + step j1
+    float2* yp = Y + o;
+#pragma unroll
+    for (int c0 = 0; c0 < C::NR; c0 += 16) {
+      float y[16];
+      tc_read16<N>(rbase, c0, y);
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        const int j1 = (c0 + i) >> 1;
+        float2 v = make_float2(y[i], y[i + 1]);
+        if (post) v = vphase(v, p.theta_post, vp[j1]);
+        yp[step * j1] = v;
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();  // A and the accumulators are reused by the next tile
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
 // ET[k][i'][i] = E_k[i][i'] with E_k[i][i'] = sum_l St[l][i] e^{-i tau lambda_l} S[i'][l]
 // (FP64, rounded to FP32): the axis propagator T diag(e^{-i tau lambda}) T^{-1} in the plan's
 // operands (forward y_l = sum_i' S[i'][l] x_i', backward y_i = sum_l St[l][i] x_l).
@@ -581,7 +855,47 @@ ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStr
   return TS_OK;
 }
 
-ts_status group_pass(int n, int nm, const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+// Whether a group can run on the tensor-core pass: two axes of length 16 or 24, tiles of
+// T = 16 along lo (lo > 1) or hi (lo == 1).
+bool tc_group_ok(int n, int nm, const PropParams& gp) {
+  if (nm != 2 || (n != 16 && n != 24)) return false;
+  return gp.lo > 1 ? gp.lo % 16 == 0 : gp.hi % 16 == 0;
+}
+
+template <int N>
+ts_status launch_small_tc(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+  using C = SmallTc<N>;
+  static bool attr = false;
+  if (!attr) {
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_tc<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_tc<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    attr = true;
+  }
+  if (g_small_sms == 0) {
+    int dev = 0;
+    TS_CHECK_CUDA(cudaGetDevice(&dev));
+    TS_CHECK_CUDA(cudaDeviceGetAttribute(&g_small_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long long tiles = gp.lo > 1 ? (gp.lo / C::T) * gp.hi : gp.hi / C::T;
+  const long long grid = tiles < g_small_sms ? tiles : g_small_sms;
+  void* tok = nullptr;
+  if (prof_enabled()) prof_begin_launch(s, &tok);
+  if (gp.lo > 1)
+    k_small_tc<N, true><<<(unsigned)grid, C::THREADS, C::SMEM, s>>>(X, Y, gp, tiles);
+  else
+    k_small_tc<N, false><<<(unsigned)grid, C::THREADS, C::SMEM, s>>>(X, Y, gp, tiles);
+  TS_LAUNCHED(1);
+  if (tok) {
+    const long long N_all = gp.lo * (long long)N * N * gp.hi;
+    // six bf16 products of a 2N x 2N real GEMM per fiber and axis, two axes
+    prof_end_launch(s, tok, PROF_SMALL_PASS, 6.0 * 2.0 * 2 * (2.0 * N) * (double)N_all * 2, 16.0 * (double)N_all);
+  }
+  return TS_OK;
+}
+
+ts_status group_pass(int n, int nm, const float2* X, float2* Y, const PropParams& gp, cudaStream_t s,
+                     bool tensor = false) {
+  if (tensor && tc_group_ok(n, nm, gp)) return n == 24 ? launch_small_tc<24>(X, Y, gp, s) : launch_small_tc<16>(X, Y, gp, s);
   if (n == 8 && nm == 3 && gp.T == 8) return launch_cubes(X, Y, gp, s);  // one cube per warp
 #define TS_PROP_CASE(NN)                                          \
   case NN:                                                        \
@@ -601,6 +915,23 @@ ts_status group_pass(int n, int nm, const float2* X, float2* Y, const PropParams
 }
 
 }  // namespace
+
+ts_status small_n_error_flag(int* host_flag, bool reset, cudaStream_t s) {
+  TS_CHECK_CUDA(cudaMemcpyFromSymbolAsync(host_flag, g_small_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  TS_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (reset && *host_flag) {
+    int zero = 0;
+    TS_CHECK_CUDA(cudaMemcpyToSymbolAsync(g_small_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+  }
+  return TS_OK;
+}
+
+bool small_tc_applicable(const ts_plan* p) {
+  if (p->d < 2) return false;
+  for (int k = 0; k < p->d; ++k)
+    if (p->n[k] != 16 && p->n[k] != 24) return false;
+  return true;
+}
 
 bool small_n_supported(const ts_plan* p) {
   for (int k = 0; k < p->d; ++k)
@@ -633,8 +964,8 @@ ts_status build_small_tables(ts_plan* p, cudaStream_t s) {
 // pass per group -> [theta_post phase on the last store]; with V2 == NULL a single exact
 // propagator (nsteps = 1).
 ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, float2* out, const double* V2, double dt,
-                            int nsteps, cudaStream_t s) {
-  if (!small_n_supported(p) || !p->Sf32[0]) {
+                            int nsteps, cudaStream_t s, bool tensor) {
+  if (!small_n_supported(p) || (!tensor && !p->Sf32[0])) {
     set_error("the FP32 small-n path needs every n_k in {8, 16, 24, 32} and TS_FP32 in the plan's mask");
     return TS_ERR_UNSUPPORTED;
   }
@@ -691,7 +1022,7 @@ ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, floa
       const float2* src = (step == 0 && first) ? in : out;
       const bool src16 = reinterpret_cast<uintptr_t>(src) % 16 == 0, out16 = reinterpret_cast<uintptr_t>(out) % 16 == 0;
       gp.pairs = gp.lo > 1 ? (gp.T % 2 == 0 && src16 && out16 ? 1 : 0) : (p->n[g.k0] % 2 == 0 && out16 ? 2 : 0);
-      st = group_pass(p->n[g.k0], nm, src, out, gp, s);
+      st = group_pass(p->n[g.k0], nm, src, out, gp, s, tensor);
     }
   }
   scratch_free(mats, s);

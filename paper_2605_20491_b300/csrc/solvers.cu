@@ -582,6 +582,8 @@ ts_status split_step_impl(const ts_plan* p, double dt, int nsteps, const double*
     }
     return small_n_propagate(p, dt, (const float2*)psi, (float2*)psi, V2, dt, nsteps, s);
   }
+  if (prec == TS_BF16X6 && dtype == TS_C64 && small_tc_applicable(p))
+    return small_n_propagate(p, dt, (const float2*)psi, (float2*)psi, V2, dt, nsteps, s, true);
   if (prec == TS_FP64 && dtype == TS_C64) {
     // FP64 arithmetic on complex64 data: widen once, run in complex128, narrow once.
     Scratch sc_mem(s);
