@@ -876,6 +876,7 @@ def run_ours(args):
     if rank == 0 and not args.no_secondary:
         # the other configurations of the workload family, each timed on its own
         line["strang_6d_n24"] = strang_run(T, "6d_n24_strang", peaks)
+        line["strang_6d_n24_bf16x6"] = strang_run(T, "6d_n24_strang", peaks, prec=T.TS_BF16X6)
         line["strang_9d_n8"] = strang_run(T, "9d_n8_strang", peaks)
         line["pcg_3d_n256"] = pcg_inverse_iteration_run(T)
     if rank == 0 and not args.no_serving:
