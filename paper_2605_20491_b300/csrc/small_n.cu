@@ -285,110 +285,134 @@ __global__ void __launch_bounds__(SmallCfg<N>::THREADS, 2) k_small_prop(const fl
 // (one per lo index t, or per hi index th), and warp w owns cube w.  A warp applies its
 // cube's three axis propagators alone (two fibers per lane sharing every matrix load),
 // separated by __syncwarp instead of CTA barriers; only the copies between HBM and the
-// tile are cooperative (64-byte runs along t for lo > 1).  Cube c starts at c * CUBE in
-// shared memory, element (i0, i1, i2) at i0 + 9 i1 + 81 i2 (padded extents, odd).
-constexpr int CUBE = 729;
+// tile are cooperative (64-byte runs along t for lo > 1).
+//
+// Cube c occupies 512 float2 at c * 512, element (i0, i1, i2) at cube_off: the row
+// i0 = 0..7 is XOR-permuted by s = (i1 >> 1) | (i2 & 1) << 2 and by c, and the low bit of
+// i1 by i2 and c >> 2.  With that swizzle every warp access of the three axis passes and of
+// the paired copies touches each 4-byte bank exactly twice (the 256-byte minimum of a warp
+// of float2), where the padded layout i0 + 9 i1 + 81 i2 met 3-4 words per bank.  The fiber
+// of a lane is then a base offset XOR a compile-time pattern of the element index.
+constexpr int CUBE = 512;
+
+__device__ __forceinline__ int cube_off(int c, int i0, int i1, int i2) {
+  const int s = (i1 >> 1) | ((i2 & 1) << 2);
+  return ((i0 ^ s ^ c) & 7) + 8 * ((i1 ^ (i2 & 1) ^ (c >> 2)) & 7) + 64 * i2;
+}
 
 template <int M>
-__device__ __forceinline__ void cube_mode(float2* cube, const float2* Em, int lane) {
-  // fibers of mode M: 64, indexed by the two other axes (the lower one fastest)
-  constexpr int ST = M == 0 ? 1 : (M == 1 ? 9 : 81);
-  constexpr int SA = M == 0 ? 9 : 1;   // stride of the fiber index's fast axis
-  constexpr int SB = M == 2 ? 9 : 81;  // ... and of its slow axis
-  int addr[2];
+__device__ __forceinline__ void cube_mode(float2* cube, int c, const float2* Em, int lane) {
+  // fibers of mode M: 64, indexed by the two other axes (a = the lower one, b = the upper);
+  // element i of a fiber sits at base ^ K(i) (+ 64 i for M = 2):
+  //   M = 0: K(i) = i;  M = 1: K(i) = (i >> 1) | (i << 3);  M = 2: K(i) = 12 (i & 1)
+  int base[2];
   float2 x[2][8];
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int f = lane + 32 * c;
-    addr[c] = (f & 7) * SA + (f >> 3) * SB;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) x[c][i] = cube[addr[c] + i * ST];
+  for (int g = 0; g < 2; ++g) {
+    const int f = lane + 32 * g, a = f & 7, b = f >> 3;
+    base[g] = M == 0 ? cube_off(c, 0, a, b) : M == 1 ? cube_off(c, a, 0, b) : cube_off(c, a, b, 0);
   }
+  auto off = [&](int g, int i) -> int {
+    if (M == 0) return base[g] ^ i;
+    if (M == 1) return base[g] ^ ((i >> 1) | (i << 3));
+    return (base[g] ^ (12 * (i & 1))) + 64 * i;
+  };
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[g][i] = cube[off(g, i)];
   float re[2][8], im[2][8];
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+  for (int g = 0; g < 2; ++g)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) re[c][q] = im[c][q] = 0.f;
+    for (int q = 0; q < 8; ++q) re[g][q] = im[g][q] = 0.f;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
       const float4 e = *reinterpret_cast<const float4*>(Em + i * 8 + q);  // E[q][i], E[q+1][i]
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        re[c][q] = fmaf(e.x, x[c][i].x, re[c][q]);
-        re[c][q] = fmaf(-e.y, x[c][i].y, re[c][q]);
-        im[c][q] = fmaf(e.x, x[c][i].y, im[c][q]);
-        im[c][q] = fmaf(e.y, x[c][i].x, im[c][q]);
-        re[c][q + 1] = fmaf(e.z, x[c][i].x, re[c][q + 1]);
-        re[c][q + 1] = fmaf(-e.w, x[c][i].y, re[c][q + 1]);
-        im[c][q + 1] = fmaf(e.z, x[c][i].y, im[c][q + 1]);
-        im[c][q + 1] = fmaf(e.w, x[c][i].x, im[c][q + 1]);
+      for (int g = 0; g < 2; ++g) {
+        re[g][q] = fmaf(e.x, x[g][i].x, re[g][q]);
+        re[g][q] = fmaf(-e.y, x[g][i].y, re[g][q]);
+        im[g][q] = fmaf(e.x, x[g][i].y, im[g][q]);
+        im[g][q] = fmaf(e.y, x[g][i].x, im[g][q]);
+        re[g][q + 1] = fmaf(e.z, x[g][i].x, re[g][q + 1]);
+        re[g][q + 1] = fmaf(-e.w, x[g][i].y, re[g][q + 1]);
+        im[g][q + 1] = fmaf(e.z, x[g][i].y, im[g][q + 1]);
+        im[g][q + 1] = fmaf(e.w, x[g][i].x, im[g][q + 1]);
       }
     }
   }
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+  for (int g = 0; g < 2; ++g)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) cube[addr[c] + q * ST] = make_float2(re[c][q], im[c][q]);
+    for (int q = 0; q < 8; ++q) cube[off(g, q)] = make_float2(re[g][q], im[g][q]);
 }
 
+// Tiles along lo (LO: t = cube, HBM runs of 8 along t) or along hi (th = cube, runs of 512);
+// PAIRS: two adjacent elements per copy (t, t + 1 or i0, i0 + 1), 16-byte global accesses.
+// The element a thread copies at step k is fixed by (tid, k), so its tile offset is a
+// thread constant plus a compile-time part.
+template <bool LO, bool PAIRS>
 __global__ void __launch_bounds__(256, 2) k_small_cubes(const float2* X, float2* Y, const PropParams p,
                                                        long long ntiles) {
   constexpr int TSZ = 8 * CUBE;  // one tile buffer
+  constexpr int EPT = PAIRS ? 2 : 1, STEPS = 4096 / (256 * EPT);
   extern __shared__ __align__(16) float2 smem[];
   float2* buf[2] = {smem, smem + TSZ};
   float2* mats = smem + 2 * TSZ;
   for (int e = threadIdx.x; e < 3 * 64; e += 256) mats[e] = p.E[e / 64][e % 64];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool lo_tiles = p.lo > 1;  // cubes along lo (t = cube) or along hi (th = cube)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long lo = p.lo;
   auto origin = [&](long long b) -> long long {
-    if (lo_tiles) {
-      const long long lblocks = p.lo >> 3;
-      return ((b % lblocks) << 3) + p.lo * 512 * (b / lblocks);
+    if (LO) {
+      const long long lblocks = lo >> 3;
+      return ((b % lblocks) << 3) + lo * 512 * (b / lblocks);
     }
     return 512LL * 8 * b;
   };
-  // element e of a tile in HBM order (lo tiles: t fastest, then g; hi tiles: g fastest, then th)
-  auto offsets = [&](int e, long long gbase, int* sidx, long long* gidx) {
-    int c, g;
-    if (lo_tiles) {
-      c = e & 7;
-      g = e >> 3;
-      *gidx = gbase + c + p.lo * g;
-    } else {
-      c = e >> 9;
-      g = e & 511;
-      *gidx = gbase + e;
-    }
-    *sidx = c * CUBE + (g & 7) + 9 * ((g >> 3) & 7) + 81 * (g >> 6);
+  // element e = EPT tid + 256 EPT k of a tile in HBM order (LO: t fastest, then g; else g
+  // fastest, then th): shared index and offset from the tile's origin
+  auto sidx_of = [&](int e) -> int {
+    const int c = LO ? (e & 7) : (e >> 9), g = LO ? (e >> 3) : (e & 511);
+    return c * CUBE + cube_off(c, g & 7, (g >> 3) & 7, g >> 6);
   };
+  auto goff_of = [&](int e) -> long long { return LO ? (long long)(e & 7) + lo * (e >> 3) : (long long)e; };
   auto issue_load = [&](long long b, float2* dst) {
-    const long long gbase = origin(b);
-    if (p.pairs) {
-      for (int e = 2 * threadIdx.x; e < 4096; e += 512) {
-        int sidx;
-        long long gidx;
-        offsets(e, gbase, &sidx, &gidx);
-        // lo tiles: (t, t + 1) are cubes t and t + 1; hi tiles: (i0, i0 + 1) of one cube row
-        cp_async8(dst + sidx, X + gidx);
-        cp_async8(dst + sidx + (lo_tiles ? CUBE : 1), X + gidx + 1);
-      }
-    } else {
-      for (int e = threadIdx.x; e < 4096; e += 256) {
-        int sidx;
-        long long gidx;
-        offsets(e, gbase, &sidx, &gidx);
-        cp_async8(dst + sidx, X + gidx);
-      }
+    const float2* src = X + origin(b);
+#pragma unroll
+    for (int k = 0; k < STEPS; ++k) {
+      const int e = EPT * tid + 256 * EPT * k;
+      const long long go = goff_of(e);
+      cp_async8(dst + sidx_of(e), src + go);
+      if (PAIRS) cp_async8(dst + sidx_of(e + 1), src + go + 1);
     }
     cp_async_commit();
   };
+  const bool pre = p.V2 && p.theta_pre != 0.f, post = p.V2 && p.theta_post != 0.f;
   long long b = blockIdx.x;
   if (b < ntiles) issue_load(b, buf[0]);
   int cur = 0;
   for (; b < ntiles; b += gridDim.x, cur ^= 1) {
     const long long bn = b + gridDim.x;
+    const long long gbase = origin(b);
+    // the tile's potential samples, loaded while the tile lands and the cubes are computed:
+    // vpre[j] for element g = lane + 32 j of the warp's cube, vpost for the thread's stores
+    float vpre[16], vpost[16];
+    if (pre) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int g = lane + 32 * j;
+        vpre[j] = p.V2[LO ? gbase + warp + lo * g : gbase + 512LL * warp + g];
+      }
+    }
+    if (post) {
+#pragma unroll
+      for (int k = 0; k < STEPS; ++k)
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) vpost[EPT * k + q] = p.V2[gbase + goff_of(EPT * tid + 256 * EPT * k) + q];
+    }
     if (bn < ntiles) {
       issue_load(bn, buf[cur ^ 1]);
       cp_async_wait<1>();
@@ -397,39 +421,38 @@ __global__ void __launch_bounds__(256, 2) k_small_cubes(const float2* X, float2*
     }
     __syncthreads();  // the tile has landed (copied by every thread)
     float2* cube = buf[cur] + warp * CUBE;
-    const long long gbase = origin(b);
-    if (p.V2 && p.theta_pre != 0.f) {
-      // the warp's own cube: element g of cube `warp`
-      for (int g = lane; g < 512; g += 32) {
-        const long long gidx = lo_tiles ? gbase + warp + p.lo * g : gbase + 512LL * warp + g;
-        const int si = (g & 7) + 9 * ((g >> 3) & 7) + 81 * (g >> 6);
-        cube[si] = vphase(cube[si], p.theta_pre, p.V2[gidx]);
+    if (pre) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int g = lane + 32 * j;
+        const int si = cube_off(warp, g & 7, (g >> 3) & 7, g >> 6);
+        cube[si] = vphase(cube[si], p.theta_pre, vpre[j]);
       }
       __syncwarp();
     }
-    cube_mode<0>(cube, mats, lane);
+    cube_mode<0>(cube, warp, mats, lane);
     __syncwarp();
-    cube_mode<1>(cube, mats + 64, lane);
+    cube_mode<1>(cube, warp, mats + 64, lane);
     __syncwarp();
-    cube_mode<2>(cube, mats + 128, lane);
+    cube_mode<2>(cube, warp, mats + 128, lane);
     __syncthreads();  // every cube is done before the cooperative store
-    float2* tile = buf[cur];
-    const int step_e = p.pairs ? 2 : 1;
-    for (int e = step_e * threadIdx.x; e < 4096; e += step_e * 256) {
-      int sidx;
-      long long gidx;
-      offsets(e, gbase, &sidx, &gidx);
-      float2 v0 = tile[sidx];
-      if (p.pairs) {
-        float2 v1 = tile[sidx + (lo_tiles ? CUBE : 1)];
-        if (p.V2 && p.theta_post != 0.f) {
-          v0 = vphase(v0, p.theta_post, p.V2[gidx]);
-          v1 = vphase(v1, p.theta_post, p.V2[gidx + 1]);
+    const float2* tile = buf[cur];
+    float2* dst = Y + gbase;
+#pragma unroll
+    for (int k = 0; k < STEPS; ++k) {
+      const int e = EPT * tid + 256 * EPT * k;
+      const long long go = goff_of(e);
+      float2 v0 = tile[sidx_of(e)];
+      if (PAIRS) {
+        float2 v1 = tile[sidx_of(e + 1)];
+        if (post) {
+          v0 = vphase(v0, p.theta_post, vpost[2 * k]);
+          v1 = vphase(v1, p.theta_post, vpost[2 * k + 1]);
         }
-        *reinterpret_cast<float4*>(Y + gidx) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        *reinterpret_cast<float4*>(dst + go) = make_float4(v0.x, v0.y, v1.x, v1.y);
       } else {
-        if (p.V2 && p.theta_post != 0.f) v0 = vphase(v0, p.theta_post, p.V2[gidx]);
-        Y[gidx] = v0;
+        if (post) v0 = vphase(v0, p.theta_post, vpost[k]);
+        dst[go] = v0;
       }
     }
     __syncthreads();  // the buffer is refilled two iterations later
@@ -827,11 +850,12 @@ ts_status launch_prop(const float2* X, float2* Y, const PropParams& gp, cudaStre
   return TS_OK;
 }
 
-ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+template <bool LO, bool PAIRS>
+ts_status launch_cubes_t(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
   const size_t smem = sizeof(float2) * (2 * 8 * CUBE + 3 * 64);
   static bool attr = false;
   if (!attr) {
-    TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_cubes, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    TS_CHECK_CUDA(cudaFuncSetAttribute(k_small_cubes<LO, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
   if (g_small_sms == 0) {
@@ -841,18 +865,23 @@ ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStr
   }
   const long long tiles = gp.lo > 1 ? (gp.lo / 8) * gp.hi : gp.hi / 8;
   int per_sm = 0;
-  TS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_cubes, 256, smem));
+  TS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_cubes<LO, PAIRS>, 256, smem));
   if (per_sm < 1) per_sm = 1;
   const long long grid = tiles < (long long)g_small_sms * per_sm ? tiles : (long long)g_small_sms * per_sm;
   void* tok = nullptr;
   if (prof_enabled()) prof_begin_launch(s, &tok);
-  k_small_cubes<<<(unsigned)grid, 256, smem, s>>>(X, Y, gp, tiles);
+  k_small_cubes<LO, PAIRS><<<(unsigned)grid, 256, smem, s>>>(X, Y, gp, tiles);
   TS_LAUNCHED(1);
   if (tok) {
     const long long N_all = gp.lo * 512LL * gp.hi;
     prof_end_launch(s, tok, PROF_SMALL_PASS, 8.0 * 8 * (double)N_all * 3, 16.0 * (double)N_all);
   }
   return TS_OK;
+}
+
+ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStream_t s) {
+  if (gp.lo > 1) return gp.pairs ? launch_cubes_t<true, true>(X, Y, gp, s) : launch_cubes_t<true, false>(X, Y, gp, s);
+  return gp.pairs ? launch_cubes_t<false, true>(X, Y, gp, s) : launch_cubes_t<false, false>(X, Y, gp, s);
 }
 
 // Whether a group can run on the tensor-core pass: two axes of length 16 or 24, tiles of
