@@ -245,35 +245,39 @@ __global__ void __launch_bounds__(SmallCfg<N>::THREADS, 2) k_small_prop(const fl
     float2* tile = buf[cur];
     const long long gbase = origin(b);
     if (p.V2 && p.theta_pre != 0.f) {
+      // V2 through the read-only path: its loads may pass the tile stores, several in flight
+#pragma unroll 4
       for (int e = step_e * threadIdx.x; e < cnt; e += step_e * SMALL_THREADS) {
         int g, th;
         const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
         const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th);
-        tile[sidx] = vphase(tile[sidx], p.theta_pre, p.V2[gidx]);
-        if (p.pairs) tile[sidx + 1] = vphase(tile[sidx + 1], p.theta_pre, p.V2[gidx + 1]);
+        tile[sidx] = vphase(tile[sidx], p.theta_pre, __ldg(p.V2 + gidx));
+        if (p.pairs) tile[sidx + 1] = vphase(tile[sidx + 1], p.theta_pre, __ldg(p.V2 + gidx + 1));
       }
       __syncthreads();
     }
     prop_modes<N, NM, 0>(tile, mats, lgTlo, Thi);
     if (p.pairs) {
+#pragma unroll 4
       for (int e = 2 * threadIdx.x; e < cnt; e += 2 * SMALL_THREADS) {
         int g, th;
         const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
         const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th);
         float2 v0 = tile[sidx], v1 = tile[sidx + 1];
         if (p.V2 && p.theta_post != 0.f) {
-          v0 = vphase(v0, p.theta_post, p.V2[gidx]);
-          v1 = vphase(v1, p.theta_post, p.V2[gidx + 1]);
+          v0 = vphase(v0, p.theta_post, __ldg(p.V2 + gidx));
+          v1 = vphase(v1, p.theta_post, __ldg(p.V2 + gidx + 1));
         }
         *reinterpret_cast<float4*>(Y + gidx) = make_float4(v0.x, v0.y, v1.x, v1.y);
       }
     } else {
+#pragma unroll 4
       for (int e = threadIdx.x; e < cnt; e += SMALL_THREADS) {
         int g, th;
         const int sidx = tile_offset<N, NM>(e, lgTlo, &g, &th);
         const long long gidx = gbase + (e & (Tlo - 1)) + p.lo * ((long long)g + (long long)G * th);
         float2 v = tile[sidx];
-        if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, p.V2[gidx]);
+        if (p.V2 && p.theta_post != 0.f) v = vphase(v, p.theta_post, __ldg(p.V2 + gidx));
         Y[gidx] = v;
       }
     }
