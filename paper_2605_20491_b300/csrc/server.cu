@@ -1,13 +1,14 @@
 // Serving runtime: continuous batching of solve, propagation and PCG requests on one GPU.
 //
 // A scheduler thread owns the device work:
-//   * admission: requests leave the FIFO queue while fewer than max_inflight are on the GPU
-//     and their scratch footprint fits the device-memory budget (requests that can never
-//     fit fail with TS_ERR_NO_MEMORY); requests that arrive while others run are admitted
-//     as slots and memory free up;
-//   * plans: four planner threads build each request's plan ahead of admission, overlapping
-//     the GPU work of earlier requests (for Q^1 axes of up to 192 nodes no step of a build
-//     synchronises the device), from a plan cache keyed by the grid and the sampled V1
+//   * admission: requests whose plan is built leave the queue, in submission order, while
+//     fewer than max_inflight are on the GPU and their scratch footprint fits the
+//     device-memory budget (requests that can never fit fail with TS_ERR_NO_MEMORY);
+//     requests that arrive while others run are admitted as slots and memory free up;
+//   * plans: planner threads (one per host core beyond four, 4 to 12) build each request's
+//     plan ahead of admission, overlapping the GPU work of earlier requests (for Q^1 axes
+//     of up to 192 nodes no step of a build synchronises the device), from a plan cache
+//     keyed by the grid and the sampled V1
 //     (n_k, L_k, f_k compared bit for bit); the per-axis eigendecompositions underneath
 //     are shared process-wide, so requests on a few distinct 1D operators rarely solve one;
 //   * batching: the inverse / exp requests admitted in one scheduling round are captured
@@ -26,6 +27,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -107,7 +109,7 @@ struct ts_server {
   int device = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<std::shared_ptr<ts::Job>> pending;
+  std::list<std::shared_ptr<ts::Job>> pending;  // submission order
   std::vector<std::shared_ptr<ts::Job>> inflight_pcg;
   std::map<long long, std::shared_ptr<ts::Job>> jobs;
   long long next_ticket = 1;
@@ -268,13 +270,19 @@ void worker_loop(ts_server* sv) {
       }
     }
     if (sv->stop && sv->pending.empty() && sv->inflight == 0) break;
-    // 2. admission
+    // 2. admission, in submission order among the requests whose plan is built: a request
+    //    still waiting for its plan does not hold back later ones.  A built request that does
+    //    not fit the memory left stops the scan, so that smaller ones cannot starve it.
     std::vector<std::shared_ptr<Job>> batch, pcg;
-    while (!sv->pending.empty() && sv->inflight < sv->cfg.max_inflight &&
-           (int)batch.size() < sv->cfg.max_batch && sv->pending.front()->plan_ready) {
-      auto jp = sv->pending.front();
+    for (auto it = sv->pending.begin(); it != sv->pending.end() && sv->inflight < sv->cfg.max_inflight &&
+                                        (int)batch.size() < sv->cfg.max_batch;) {
+      auto jp = *it;
+      if (!jp->plan_ready) {
+        ++it;
+        continue;
+      }
       if (jp->footprint > (size_t)sv->cfg.memory_budget_bytes) {
-        sv->pending.pop_front();
+        it = sv->pending.erase(it);
         snprintf(jp->msg, sizeof(jp->msg), "request needs %zu bytes of scratch, above the budget %lld",
                  jp->footprint, sv->cfg.memory_budget_bytes);
         ++sv->inflight;
@@ -291,7 +299,7 @@ void worker_loop(ts_server* sv) {
           break;
         }
       if (slot < 0) break;
-      sv->pending.pop_front();
+      it = sv->pending.erase(it);
       ts_status st = jp->plan_status;
       if (st != TS_OK) {
         ++sv->inflight;
@@ -414,7 +422,10 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   // Planners build plans on host threads (Q^1 eigendecompositions on the host, table
   // uploads and splits on their own streams); their streams take the highest priority, so
   // the few small kernels of a build are scheduled ahead of queued batch work.
-  const int nplanners = 4;
+  // One planner per host core beyond four left for the scheduler, PCG and caller threads
+  // (at least 4, at most 12): plan builds of fresh operators are the serving bound.
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int nplanners = hw - 4 < 4 ? 4 : (hw - 4 > 12 ? 12 : hw - 4);
   int prio_least = 0, prio_greatest = 0;
   TS_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
   sv->planner_streams.resize(nplanners);
