@@ -333,7 +333,8 @@ def serving_requests_on_device(T, total, seed=4, omega_set=None):
     return reqs
 
 
-def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, overload_factor=2.0, reqs=None):
+def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, overload_factor=2.0, reqs=None,
+                planner_threads=0):
     """The serving workload: `count` requests (3D grids with n_k from {32, 48, 64, 96, 128},
     30% PCG / 50% inverse / 20% exp), first submitted all at once (saturated throughput),
     then again with Poisson arrivals at rate_factor x that throughput, and once more at
@@ -349,7 +350,7 @@ def serving_run(T, count, omega_set=None, rate_factor=0.8, seed=4, prec=None, ov
         reqs = serving_requests_on_device(T, count * len(phases), seed=seed, omega_set=omega_set)
     reqs = [dict(kw, prec=prec) for kw in reqs]
     torch.cuda.synchronize()
-    server = T.Server(max_inflight=16)
+    server = T.Server(max_inflight=16, planner_threads=planner_threads)
     out = {}
     for q, phase in enumerate(phases):
         preqs = reqs[q * count:(q + 1) * count]

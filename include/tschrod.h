@@ -439,6 +439,11 @@ typedef struct {
   int max_inflight;              /* requests on the GPU at once (<= 0: 8)                */
   int max_batch;                 /* requests per captured graph (<= 0: max_inflight)     */
   int plan_cache_entries;        /* cached plans (<= 0: 1024)                            */
+  int planner_threads;           /* host threads building plans ahead of admission
+                                    (<= 0: 4); each build eigendecomposes the new axes on
+                                    the host, so more threads help while host cores are
+                                    free and hurt once they compete with the scheduler
+                                    and the PCG threads                                 */
 } ts_server_config;
 
 typedef struct {

@@ -5,8 +5,8 @@
 //     fewer than max_inflight are on the GPU and their scratch footprint fits the
 //     device-memory budget (requests that can never fit fail with TS_ERR_NO_MEMORY);
 //     requests that arrive while others run are admitted as slots and memory free up;
-//   * plans: planner threads (one per host core beyond four, 4 to 12) build each request's
-//     plan ahead of admission, overlapping the GPU work of earlier requests (for Q^1 axes
+//   * plans: planner threads (ts_server_config.planner_threads, 4 by default) build each
+//     request's plan ahead of admission, overlapping the GPU work of earlier requests (for Q^1 axes
 //     of up to 192 nodes no step of a build synchronises the device), from a plan cache
 //     keyed by the grid and the sampled V1
 //     (n_k, L_k, f_k compared bit for bit); the per-axis eigendecompositions underneath
@@ -422,10 +422,7 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   // Planners build plans on host threads (Q^1 eigendecompositions on the host, table
   // uploads and splits on their own streams); their streams take the highest priority, so
   // the few small kernels of a build are scheduled ahead of queued batch work.
-  // One planner per host core beyond four left for the scheduler, PCG and caller threads
-  // (at least 4, at most 12): plan builds of fresh operators are the serving bound.
-  const int hw = (int)std::thread::hardware_concurrency();
-  const int nplanners = hw - 4 < 4 ? 4 : (hw - 4 > 12 ? 12 : hw - 4);
+  const int nplanners = sv->cfg.planner_threads > 0 ? (sv->cfg.planner_threads > 64 ? 64 : sv->cfg.planner_threads) : 4;
   int prio_least = 0, prio_greatest = 0;
   TS_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
   sv->planner_streams.resize(nplanners);

@@ -56,7 +56,7 @@ class _Request(C.Structure):
 
 class _ServerConfig(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_longlong), ("max_inflight", C.c_int), ("max_batch", C.c_int),
-                ("plan_cache_entries", C.c_int)]
+                ("plan_cache_entries", C.c_int), ("planner_threads", C.c_int)]
 
 
 class _ServingStats(C.Structure):
@@ -421,8 +421,8 @@ class Server:
     it has been waited for."""
 
     def __init__(self, memory_budget_bytes: int = 0, max_inflight: int = 8, max_batch: int = 0,
-                 plan_cache_entries: int = 1024):
-        cfg = _ServerConfig(memory_budget_bytes, max_inflight, max_batch, plan_cache_entries)
+                 plan_cache_entries: int = 1024, planner_threads: int = 0):
+        cfg = _ServerConfig(memory_budget_bytes, max_inflight, max_batch, plan_cache_entries, planner_threads)
         h = C.c_void_p()
         _check(lib().ts_server_create(C.byref(cfg), C.byref(h)), "ts_server_create")
         self.handle = h
