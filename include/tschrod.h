@@ -220,9 +220,10 @@ ts_status ts_solve_refined(const ts_plan* plan, double sigma, const double* b, d
  * TS_FP32 (complex64 only, every n_k in {8, 16, 24, 32}) applies the factored form
  * e^{-i tau A} = (x)_k E_k, E_k = T_k diag(e^{-i tau lambda_k}) T_k^{-1}, a few axes per
  * pass through HBM on the FFMA pipes.  TS_BF16X6 on TS_C64 data with d >= 2 and every n_k
- * in {16, 24} takes the same factored form on the tensor cores (the real 2n x 2n embedding
- * of E_k, three bf16 planes, six products, two axes per pass); other shapes and dtypes use
- * the transform-scale-transform passes.  The factored forms need no extra device memory
+ * in {8, 16, 24} takes the same factored form: pairs of 16- or 24-point axes on the tensor
+ * cores (the real 2n x 2n embedding of E_k, three bf16 planes, six products, two axes per
+ * pass), 8-point axes on the FP32 kernels (at least BF16X6's accuracy); other shapes and
+ * dtypes use the transform-scale-transform passes.  The factored forms need no extra device memory
  * beyond d small E_k tables (and an FP32 copy of V2 in the split steps).
  */
 ts_status ts_apply_exp(const ts_plan* plan, double tau, const void* psi_in, void* psi_out,

@@ -962,7 +962,7 @@ ts_status small_n_error_flag(int* host_flag, bool reset, cudaStream_t s) {
 bool small_tc_applicable(const ts_plan* p) {
   if (p->d < 2) return false;
   for (int k = 0; k < p->d; ++k)
-    if (p->n[k] != 16 && p->n[k] != 24) return false;
+    if (p->n[k] != 8 && p->n[k] != 16 && p->n[k] != 24) return false;
   return true;
 }
 

@@ -5,8 +5,11 @@
 namespace ts {
 
 // True when the tensor-core small-n pass serves the plan's complex64 propagation in
-// TS_BF16X6: d >= 2 axes, each of length 16 or 24 (groups of two equal axes whose tile
-// dimension divides by 16 take the tensor-core kernel, the others the FFMA kernel).
+// TS_BF16X6: d >= 2 axes, each of length 8, 16 or 24.  Groups of two equal axes of 16 or 24
+// whose tile dimension divides by 16 take the tensor-core kernel; the others, and every
+// group of 8-point axes, take the FP32 FFMA kernels (at least as accurate; on 8-point axes
+// also the faster: a three-axis tensor-core form was latency-bound, 3.7 against 2.8 ms per
+// 9D Strang step).
 bool small_tc_applicable(const ts_plan* p);
 // True when every n_k is one of the lengths the fused kernel is instantiated for.
 bool small_n_supported(const ts_plan* p);

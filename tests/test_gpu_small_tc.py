@@ -1,11 +1,12 @@
-"""The tensor-core small-n pass (TS_BF16X6 on complex64, axes of 16 or 24 points, two axes per
-pass) against the oracle.  Each axis is a real 2n x 2n product split into three bf16 planes
-(six products: every term above 2^-24 relative kept); the leading product accumulates
-alone in FP32, so the error of one axis is the FP32 accumulation of 2n terms plus the FP32
-rounding of the result and its re-split, O(2n 2^-24) relative at worst.  With 2d axes per
-apply this stays below 5e-6 for d <= 6; 10 Strang steps below 3e-5.  The cases cover tiles
-along the lower axes (lo > 1), along the upper ones (lo = 1), groups that fall back to the
-FFMA kernel (a single axis, or a tile dimension not divisible by 16) and mixed lengths."""
+"""The small-n route of TS_BF16X6 on complex64 against the oracle: axes of 16 or 24 points
+two per pass on the tensor cores, 8-point axes on the FP32 kernels.  On the tensor cores
+each axis is a real 2n x 2n product split into three bf16 planes (six products: every
+term above 2^-24 relative kept); the leading product accumulates alone in FP32, so the
+error of one axis is the FP32 accumulation of 2n terms plus the FP32 rounding of the
+result and its re-split, O(2n 2^-24) relative at worst.  With d <= 9 axes per apply this
+stays below 5e-6; 10 Strang steps below 3e-5.  The cases cover tiles along the lower axes
+(lo > 1), along the upper ones (lo = 1), groups that go to the FFMA kernels (a single
+axis, 8-point axes, or a tile dimension 16 does not divide) and mixed lengths."""
 import functools
 
 import numpy as np
@@ -28,7 +29,8 @@ def T():
     return tschrod
 
 
-@pytest.mark.parametrize("n", [(24,) * 4, (16,) * 4, (16, 24, 24, 16), (24,) * 5, (16,) * 3, (24, 24), (16,) * 6])
+@pytest.mark.parametrize("n", [(24,) * 4, (16,) * 4, (16, 24, 24, 16), (24,) * 5, (16,) * 3, (24, 24), (16,) * 6,
+                               (8,) * 6, (8,) * 5, (8,) * 7, (8,) * 3, (8, 8, 8, 16, 16)])
 def test_bf16x6_exp_vs_oracle(T, n):
     d = len(n)
     L = (4.0,) * d
@@ -65,7 +67,8 @@ def test_bf16x6_exp_large_tau_is_unitary(T):
     assert abs(np.linalg.norm(got) / np.linalg.norm(psi.astype(np.float64)) - 1.0) < EXP_TOL
 
 
-@pytest.mark.parametrize("n,Lv,steps,dim", [((16,) * 4, 3.0, 10, 2), ((24,) * 4, 5.0, 4, 2), ((16, 16, 16), 3.0, 10, 3)])
+@pytest.mark.parametrize("n,Lv,steps,dim", [((16,) * 4, 3.0, 10, 2), ((24,) * 4, 5.0, 4, 2), ((16, 16, 16), 3.0, 10, 3),
+                                            ((8,) * 6, 5.0, 10, 3)])
 def test_bf16x6_strang_vs_oracle(T, n, Lv, steps, dim):
     """Two particles in 2D (d = 4) or one in 3D, soft-Coulomb V2: the phases folded into the
     first and last pass of each step, across tiles along the lower and upper axes."""
@@ -129,3 +132,24 @@ def test_full_size_6d_bf16x6_100_steps_vs_fp64_path(T):
     assert abs(a64.norm().item() - 1.0) < 1e-4
     del a, b, a64
     torch.cuda.empty_cache()
+
+
+def test_full_size_9d_bf16x6_two_steps_vs_oracle(T):
+    """The 9D workload at full size (8^9 = 1.3e8 DoF) requested in TS_BF16X6: two Strang
+    steps (the FP32 three-axis kernels serve 8-point axes) against the oracle's unmerged
+    FP64 Strang steps."""
+    import torch
+    w = S.WORKLOADS["9d_n8_strang"]
+    n, L = w["n"], w["L"]
+    P, Po = plans(n, L, S.harmonic(n, L, w["omega"]), X6_MASK)
+    V2 = S.v2_soft_coulomb(n, L)
+    psi = S.sine_state(n, L)
+    t = dev(psi.astype(np.float32))
+    T.ts_split_step(P, w["dt"], 2, dev(V2), t, T.TS_C64, T.TS_BF16X6)
+    T.ts_device_status()  # raises if a bounded wait gave up
+    got = host(t).astype(np.float64)
+    del t
+    torch.cuda.empty_cache()
+    want = O.strang(Po, V2, w["dt"], 2, psi)
+    assert rel(got, want) < STRANG_TOL
+    assert maxrel(got, want) < MAXNORM_FACTOR * STRANG_TOL
