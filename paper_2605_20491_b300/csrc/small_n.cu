@@ -304,8 +304,11 @@ __device__ __forceinline__ int cube_off(int c, int i0, int i1, int i2) {
   return ((i0 ^ s ^ c) & 7) + 8 * ((i1 ^ (i2 & 1) ^ (c >> 2)) & 7) + 64 * i2;
 }
 
+// With vph (mode 0 only), each loaded value is first multiplied by e^{-i theta V2}, V2 of
+// element i of the lane's fiber g in vph[g][i].
 template <int M>
-__device__ __forceinline__ void cube_mode(float2* cube, int c, const float2* Em, int lane) {
+__device__ __forceinline__ void cube_mode(float2* cube, int c, const float2* Em, int lane,
+                                          const float (*vph)[8] = nullptr, float theta = 0.f) {
   // fibers of mode M: 64, indexed by the two other axes (a = the lower one, b = the upper);
   // element i of a fiber sits at base ^ K(i) (+ 64 i for M = 2):
   //   M = 0: K(i) = i;  M = 1: K(i) = (i >> 1) | (i << 3);  M = 2: K(i) = 12 (i & 1)
@@ -325,6 +328,12 @@ __device__ __forceinline__ void cube_mode(float2* cube, int c, const float2* Em,
   for (int g = 0; g < 2; ++g)
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[g][i] = cube[off(g, i)];
+  if (M == 0 && vph) {
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[g][i] = vphase(x[g][i], theta, vph[g][i]);
+  }
   float re[2][8], im[2][8];
 #pragma unroll
   for (int g = 0; g < 2; ++g)
@@ -402,13 +411,16 @@ __global__ void __launch_bounds__(256, 2) k_small_cubes(const float2* X, float2*
     const long long bn = b + gridDim.x;
     const long long gbase = origin(b);
     // the tile's potential samples, loaded while the tile lands and the cubes are computed:
-    // vpre[j] for element g = lane + 32 j of the warp's cube, vpost for the thread's stores
-    float vpre[16], vpost[16];
+    // vpre[g][i] for element i of the lane's axis-0 fiber g of the warp's cube (applied as
+    // the first axis loads it), vpost for the thread's stores
+    float vpre[2][8], vpost[16];
     if (pre) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int g = lane + 32 * j;
-        vpre[j] = p.V2[LO ? gbase + warp + lo * g : gbase + 512LL * warp + g];
+      for (int g = 0; g < 2; ++g) {
+        const int f = lane + 32 * g, e0 = 8 * (f & 7) + 64 * (f >> 3);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          vpre[g][i] = p.V2[LO ? gbase + warp + lo * (e0 + i) : gbase + 512LL * warp + e0 + i];
       }
     }
     if (post) {
@@ -425,16 +437,10 @@ __global__ void __launch_bounds__(256, 2) k_small_cubes(const float2* X, float2*
     }
     __syncthreads();  // the tile has landed (copied by every thread)
     float2* cube = buf[cur] + warp * CUBE;
-    if (pre) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int g = lane + 32 * j;
-        const int si = cube_off(warp, g & 7, (g >> 3) & 7, g >> 6);
-        cube[si] = vphase(cube[si], p.theta_pre, vpre[j]);
-      }
-      __syncwarp();
-    }
-    cube_mode<0>(cube, warp, mats, lane);
+    if (pre)
+      cube_mode<0>(cube, warp, mats, lane, vpre, p.theta_pre);
+    else
+      cube_mode<0>(cube, warp, mats, lane);
     __syncwarp();
     cube_mode<1>(cube, warp, mats + 64, lane);
     __syncwarp();
@@ -993,9 +999,9 @@ ts_status build_small_tables(ts_plan* p, cudaStream_t s) {
   return TS_OK;
 }
 
-// nsteps of: [theta_pre phase on the first load] -> the groups' axis propagators, one HBM
-// pass per group -> [theta_post phase on the last store]; with V2 == NULL a single exact
-// propagator (nsteps = 1).
+// nsteps of: [V2 phase on the first load: dt / 2 in the first step, dt later] -> the
+// groups' axis propagators, one HBM pass per group; the closing dt / 2 phase on the last
+// store of the last step.  With V2 == NULL a single exact propagator (nsteps = 1).
 ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, float2* out, const double* V2, double dt,
                             int nsteps, cudaStream_t s, bool tensor) {
   if (!small_n_supported(p) || (!tensor && !p->Sf32[0])) {
@@ -1050,8 +1056,12 @@ ts_status small_n_propagate(const ts_plan* p, double tau, const float2* in, floa
       gp.T = g.T;
       gp.V2 = (const float*)v2f;
       const bool first = gi == 0, last = gi == ng - 1;
-      gp.theta_pre = (V2 && first) ? (float)(step == 0 ? 0.5 * dt : 0.0) : 0.f;
-      gp.theta_post = (V2 && last) ? (float)(step == nsteps - 1 ? 0.5 * dt : dt) : 0.f;
+      // The merged phase e^{-i V2 dt} between two steps is applied on the first pass's load
+      // of the later step: the first group's tiles run along the upper axes, so its
+      // potential samples are read in contiguous runs (on the last pass's store they were
+      // runs of 8 to 32 bytes).  Only the last step's closing half step is applied on a store.
+      gp.theta_pre = (V2 && first) ? (float)(step == 0 ? 0.5 * dt : dt) : 0.f;
+      gp.theta_post = (V2 && last && step == nsteps - 1) ? (float)(0.5 * dt) : 0.f;
       const float2* src = (step == 0 && first) ? in : out;
       const bool src16 = reinterpret_cast<uintptr_t>(src) % 16 == 0, out16 = reinterpret_cast<uintptr_t>(out) % 16 == 0;
       gp.pairs = gp.lo > 1 ? (gp.T % 2 == 0 && src16 && out16 ? 1 : 0) : (p->n[g.k0] % 2 == 0 && out16 ? 2 : 0);
