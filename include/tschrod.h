@@ -383,8 +383,10 @@ ts_status ts_propagate(const ts_plan* plan, ts_scheme scheme, int M, double dt, 
  * The half steps of adjacent steps are merged into one e^{-i V2 dt} factor.
  * V2: N doubles (device).  psi: TS_C128 or TS_C64, updated in place.  prec as for
  * ts_apply_exp; on the factored small-n forms (TS_FP32, and TS_BF16X6 on TS_C64 with every
- * n_k in {16, 24}) the potential phases are applied inside the first and last pass of each
- * step, so a step costs ceil(d / 2) or ceil(d / 3) passes over psi.
+ * n_k in {8, 16, 24}) the potential phases are applied inside the passes: the merged
+ * e^{-i V2 dt} (e^{-i V2 dt/2} in the first step) as each step's first pass loads psi,
+ * the closing e^{-i V2 dt/2} as the last step's last pass stores it.  A step then costs
+ * ceil(d / 2) or ceil(d / 3) passes over psi.
  */
 ts_status ts_split_step(const ts_plan* plan, double dt, int nsteps, const double* V2, void* psi,
                         ts_dtype dtype, ts_precision prec, void* stream);

@@ -1,7 +1,8 @@
-// Fused multi-mode propagation for small axis lengths (n <= 32), complex64 data, FP32
-// arithmetic: the exact propagator e^{-i tau (-Delta + V1)} (eq. exact_prop) of the 4D-9D
-// problems, and the Strang step (Sec. 5.1) with the e^{-i V2 theta} factors folded into
-// the first and last pass.
+// Fused multi-mode propagation for small axis lengths (n <= 32), complex64 data, in FP32
+// arithmetic, and for pairs of 16- or 24-point axes in BF16X6 on the tensor cores (below):
+// the exact propagator e^{-i tau (-Delta + V1)} (eq. exact_prop) of the 4D-9D problems, and
+// the Strang step (Sec. 5.1) with the e^{-i V2 theta} factors folded into the passes (the
+// merged factor on each step's first load, the closing half step on the last store).
 //
 // -Delta_h + V1 = sum_k H_k with H_k acting on axis k alone, so the exact propagator is the
 // tensor product of per-axis propagators: e^{-i tau (-Delta_h + V1)} = kron_k E_k with
@@ -487,8 +488,10 @@ ts_status launch_cubes(const float2* X, float2* Y, const PropParams& gp, cudaStr
 // truncation of the corrections off the large term), Y = x0 R1 + x1 R0 + x2 R0 and
 // Z = x0 R2 + x1 R1; the epilogue forms X + (Y + Z).  The first axis's epilogue writes the
 // second axis's operand (rows = fibers of the second axis) back into the same shared-memory
-// planes, transposed; the second epilogue applies the V2 phase of the last pass and stores.
-// One CTA per SM, one thread per row; every wait is bounded.
+// planes, transposed; the second epilogue stores.  The V2 phases of a Strang step are
+// applied as a step's first pass loads its tile and, for the last step's closing half
+// step, as the last pass stores.  One CTA per SM, one thread per row; every wait is
+// bounded.
 __device__ int g_small_tc_error = 0;
 
 template <int N>
