@@ -15,7 +15,9 @@ namespace {
 // The device's default pool serves the work buffers.  By default it hands freed memory
 // back at every synchronisation, so a solver that synchronises between calls (one PCG
 // solve per outer step of inverse iteration) maps its buffers afresh each time; keeping up
-// to 4 GiB of freed buffers in the pool avoids that.
+// to 4 GiB of freed buffers in the pool avoids that.  Setting a pool attribute is not
+// allowed while a stream captures a graph: the first allocations of a process made under
+// capture leave it for a later one (and ts_server_create sets it before any capture).
 void keep_scratch_mapped() {
   static std::mutex mu;
   static std::set<int> done;
@@ -32,10 +34,17 @@ void keep_scratch_mapped() {
 }
 }  // namespace
 
+void scratch_pool_prepare() { keep_scratch_mapped(); }
+
 ts_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t s) {
   *ptr = nullptr;
   if (bytes == 0) return TS_OK;
-  keep_scratch_mapped();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;  // unknown: leave the pool alone this time
+  }
+  if (cs == cudaStreamCaptureStatusNone) keep_scratch_mapped();
   cudaError_t e = cudaMallocAsync(ptr, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();

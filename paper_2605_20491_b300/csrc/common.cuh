@@ -170,6 +170,8 @@ AxisParams axis_params(const ts_plan* p, bool eig_tables);
 
 // Scratch allocation from the stream-ordered pool.
 ts_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t s);
+// Configure that pool for the current device now (outside any graph capture).
+void scratch_pool_prepare();
 void scratch_free(void* ptr, cudaStream_t s);
 
 // Device memory of the resident per-axis tables: stream-ordered allocations from a

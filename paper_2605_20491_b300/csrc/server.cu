@@ -419,6 +419,7 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   for (auto& s : sv->streams) TS_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   TS_CHECK_CUDA(cudaStreamCreateWithFlags(&sv->capture_stream, cudaStreamNonBlocking));
   TS_TRY(tc_prepare_kernels());
+  scratch_pool_prepare();  // its attributes cannot be set inside the rounds' graph captures
   // Planners build plans on host threads (Q^1 eigendecompositions on the host, table
   // uploads and splits on their own streams); their streams take the highest priority, so
   // the few small kernels of a build are scheduled ahead of queued batch work.

@@ -99,3 +99,29 @@ def test_server_memory_admission(T):
     st, _, _ = server.wait(server.submit(**kw))
     assert st == T.TS_ERR_NO_MEMORY
     server.close()
+
+
+def test_server_planner_threads_and_admission_order(T):
+    """Results do not depend on how many planner threads build the plans, nor on the order
+    in which built requests are admitted: one planner (requests admitted in submission
+    order) and eight (plans finishing out of order, later requests admitted first) give
+    the same bits as each request served alone."""
+    specs = S.serving_requests(16, seed=11, sizes=(16, 32, 48), mix=(0.25, 0.5, 0.25))
+    precs = [T.TS_FP64 if i % 4 == 0 else T.TS_BF16X3 for i in range(len(specs))]
+    ref_server = T.Server(max_inflight=1, planner_threads=1)
+    alone = []
+    for spec, prec in zip(specs, precs):
+        kw = build(T, spec, prec)[0]
+        assert ref_server.wait(ref_server.submit(**kw))[0] == T.TS_OK
+        alone.append(host(kw["out"]))
+    ref_server.close()
+    for threads in (1, 8):
+        server = T.Server(max_inflight=8, planner_threads=threads)
+        kws = [build(T, spec, prec)[0] for spec, prec in zip(specs, precs)]
+        tickets = [server.submit(**kw) for kw in kws]
+        for t in tickets:
+            assert server.wait(t)[0] == T.TS_OK, T.ts_last_error()
+        for a, kw in zip(alone, kws):
+            assert np.array_equal(a, host(kw["out"]))
+        assert server.stats()["completed"] == len(specs)
+        server.close()
