@@ -110,7 +110,12 @@ struct ts_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::list<std::shared_ptr<ts::Job>> pending;  // submission order
-  std::vector<std::shared_ptr<ts::Job>> inflight_pcg;
+  // PCG requests: a queue served by max_inflight persistent host threads (each keeps its
+  // pinned residual mailbox and events for its lifetime)
+  std::deque<std::shared_ptr<ts::Job>> pcg_queue;
+  std::condition_variable cv_pcg;
+  std::vector<std::thread> pcg_workers;
+  bool pcg_stop = false;
   std::map<long long, std::shared_ptr<ts::Job>> jobs;
   long long next_ticket = 1;
   size_t mem_used = 0, mem_peak = 0;
@@ -250,9 +255,23 @@ void run_pcg(ts_server* sv, std::shared_ptr<Job> jp) {
   sv->cv_work.notify_all();
 }
 
+void pcg_worker_loop(ts_server* sv) {
+  cudaSetDevice(sv->device);
+  while (true) {
+    std::shared_ptr<Job> jp;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv_pcg.wait(lk, [&] { return sv->pcg_stop || !sv->pcg_queue.empty(); });
+      if (sv->pcg_queue.empty()) return;
+      jp = sv->pcg_queue.front();
+      sv->pcg_queue.pop_front();
+    }
+    run_pcg(sv, jp);
+  }
+}
+
 void worker_loop(ts_server* sv) {
   cudaSetDevice(sv->device);
-  std::vector<std::thread> pcg_threads;
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
     // 1. completions of launched graphs
@@ -315,8 +334,9 @@ void worker_loop(ts_server* sv) {
       ++sv->inflight;
       (jp->req.kind == TS_REQ_PCG ? pcg : batch).push_back(jp);
     }
-    // 3. launch: PCG on pooled host threads, the rest as one captured graph
-    for (auto& jp : pcg) pcg_threads.emplace_back(run_pcg, sv, jp);
+    // 3. launch: PCG on the pooled host threads, the rest as one captured graph
+    for (auto& jp : pcg) sv->pcg_queue.push_back(jp);
+    if (!pcg.empty()) sv->cv_pcg.notify_all();
     if (!batch.empty()) {
       ts_server::Batch bt;
       bt.jobs = batch;
@@ -389,7 +409,6 @@ void worker_loop(ts_server* sv) {
     }
   }
   lk.unlock();
-  for (auto& t : pcg_threads) t.join();
 }
 
 }  // namespace
@@ -430,6 +449,7 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   for (auto& s : sv->planner_streams)
     TS_CHECK_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio_greatest));
   for (int i = 0; i < nplanners; ++i) sv->planners.emplace_back(planner_loop, sv, i);
+  for (int i = 0; i < sv->cfg.max_inflight; ++i) sv->pcg_workers.emplace_back(pcg_worker_loop, sv);
   sv->worker = std::thread(worker_loop, sv);
   *out = sv;
   return TS_OK;
@@ -553,7 +573,13 @@ ts_status ts_server_destroy(ts_server* sv) {
   }
   sv->cv_work.notify_all();
   sv->cv_plan.notify_all();
-  if (sv->worker.joinable()) sv->worker.join();
+  if (sv->worker.joinable()) sv->worker.join();  // returns once every request has finished
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->pcg_stop = true;
+  }
+  sv->cv_pcg.notify_all();
+  for (auto& t : sv->pcg_workers) t.join();
   for (auto& t : sv->planners) t.join();
   sv->plans.clear();
   for (auto s : sv->streams) cudaStreamDestroy(s);
