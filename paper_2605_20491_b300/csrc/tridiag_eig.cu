@@ -84,9 +84,8 @@ void qr_step(int n, int lo, int hi, double* a, double* b, double* Z, RotateFn ro
   }
 }
 
-}  // namespace
-
-bool tridiag_eig_host(int n, const double* diag, const double* offdiag, double* lam, double* Zout) {
+// The QR iteration above on the whole matrix.
+bool tridiag_qr(int n, const double* diag, const double* offdiag, double* lam, double* Zout) {
   if (n <= 0) return true;
   static const RotateFn rotate = pick_rotate();
   std::vector<double> a(diag, diag + n), b(n > 1 ? n - 1 : 1, 0.0);
@@ -117,6 +116,75 @@ bool tridiag_eig_host(int n, const double* diag, const double* offdiag, double* 
     std::copy(Z.begin() + (size_t)perm[j] * n, Z.begin() + (size_t)perm[j] * n + n, Zout + (size_t)j * n);
   }
   return true;
+}
+
+// A persymmetric matrix (a_i = a_{n-1-i}, b_i = b_{n-2-i}: a potential symmetric about the
+// middle of a uniform grid, as x^2 on [-L, L]) commutes with the exchange J, so its
+// eigenvectors are even or odd under J and it splits into two tridiagonal problems of half
+// the size; the accumulated rotations, O(n^3), then cost a quarter.  With m = n / 2 and the
+// entries of the first half:
+//   n = 2m:     even: a_{m-1} + b_{m-1} in the last diagonal entry, v = [u; J u] / sqrt 2;
+//               odd:  a_{m-1} - b_{m-1},                             v = [u; -J u] / sqrt 2;
+//   n = 2m + 1: even: size m + 1 with the middle entry a_m coupled by sqrt 2 b_{m-1}
+//               (unknown y_m = v_m / sqrt 2), v = [y_0 .. y_{m-1}, sqrt 2 y_m, mirror] / sqrt 2;
+//               odd:  size m (v_m = 0), v = [u; 0; -J u] / sqrt 2.
+// Node grids computed in floating point are symmetric only to rounding, so the test allows
+// 16 ulp of the matrix's scale and the halves are formed from the mirrored pairs' means:
+// the decomposition is that of a matrix within that distance of the input, the order of
+// the QR iteration's own backward error.  Even and odd vectors are orthogonal exactly.
+bool split_persymmetric(int n, const double* a, const double* b, double* lam, double* Zout) {
+  double amax = 0.0, bmax = 0.0;
+  for (int i = 0; i < n; ++i) amax = std::fmax(amax, std::fabs(a[i]));
+  for (int i = 0; i + 1 < n; ++i) bmax = std::fmax(bmax, std::fabs(b[i]));
+  const double tol = 16.0 * std::ldexp(1.0, -52) * (amax + 2.0 * bmax);
+  for (int i = 0; i < n / 2; ++i)
+    if (std::fabs(a[i] - a[n - 1 - i]) > tol) return false;
+  for (int i = 0; i + 1 < n - 1 - i; ++i)
+    if (std::fabs(b[i] - b[n - 2 - i]) > tol) return false;
+  const int m = n / 2;
+  const bool odd_n = n & 1;
+  const int ne = odd_n ? m + 1 : m, no = m;
+  std::vector<double> ea(ne), eb(ne), oa(no), ob(no > 1 ? no : 1);
+  for (int i = 0; i < m; ++i) ea[i] = oa[i] = 0.5 * (a[i] + a[n - 1 - i]);
+  for (int i = 0; i + 1 < m; ++i) eb[i] = ob[i] = 0.5 * (b[i] + b[n - 2 - i]);
+  const double sq2 = std::sqrt(2.0), is2 = 1.0 / sq2;
+  if (odd_n) {
+    ea[m] = a[m];
+    eb[m - 1] = sq2 * 0.5 * (b[m - 1] + b[m]);
+  } else {
+    ea[m - 1] += b[m - 1];
+    oa[m - 1] -= b[m - 1];
+  }
+  std::vector<double> el(ne), ol(no), EZ((size_t)ne * ne), OZ((size_t)no * no);
+  if (!tridiag_qr(ne, ea.data(), eb.data(), el.data(), EZ.data())) return false;
+  if (!tridiag_qr(no, oa.data(), ob.data(), ol.data(), OZ.data())) return false;
+  // merge the two ascending spectra; column j of Zout is the eigenvector of lam[j]
+  int ie = 0, io = 0;
+  for (int j = 0; j < n; ++j) {
+    double* z = Zout + (size_t)j * n;
+    if (io >= no || (ie < ne && el[ie] <= ol[io])) {
+      const double* u = EZ.data() + (size_t)ie * ne;
+      for (int i = 0; i < m; ++i) z[i] = z[n - 1 - i] = u[i] * is2;
+      if (odd_n) z[m] = u[m];  // sqrt 2 y_m / sqrt 2
+      lam[j] = el[ie++];
+    } else {
+      const double* u = OZ.data() + (size_t)io * no;
+      for (int i = 0; i < m; ++i) {
+        z[i] = u[i] * is2;
+        z[n - 1 - i] = -u[i] * is2;
+      }
+      if (odd_n) z[m] = 0.0;
+      lam[j] = ol[io++];
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+bool tridiag_eig_host(int n, const double* diag, const double* offdiag, double* lam, double* Zout) {
+  if (n >= 16 && split_persymmetric(n, diag, offdiag, lam, Zout)) return true;
+  return tridiag_qr(n, diag, offdiag, lam, Zout);
 }
 
 }  // namespace ts

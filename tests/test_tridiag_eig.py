@@ -96,3 +96,44 @@ def test_invalid_arguments(T):
     with pytest.raises(T.TsError) as e:
         T.ts_tridiag_eig(np.zeros(0), np.zeros(0))
     assert e.value.status == T.TS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n", [16, 17, 64, 97, 128, 191])
+def test_persymmetric_split(T, n):
+    """A matrix symmetric about its middle (a potential symmetric on a symmetric grid) is
+    solved as two half-size problems of even and odd eigenvectors: the same spectrum as
+    LAPACK, orthonormal eigenvectors of the right parity, for even and odd n, random
+    entries and a double-well potential whose lowest pairs are nearly degenerate."""
+    rng = np.random.default_rng(n)
+    half_a, half_b = rng.standard_normal((n + 1) // 2) * 5, rng.standard_normal(n // 2)
+    a = np.concatenate([half_a, half_a[: n // 2][::-1]])
+    b = np.concatenate([half_b, half_b[: (n - 1) // 2][::-1]])
+    h = 10.0 / (n + 1)
+    x = -5.0 + h * np.arange(1, n + 1)
+    well_a = 2 / h ** 2 + 4.0 * (x ** 2 - 4.0) ** 2
+    for aa, bb in ((a, b), (well_a, np.full(n - 1, -1 / h ** 2))):
+        lam, Z = T.ts_tridiag_eig(aa, bb)
+        ref = np.linalg.eigvalsh(np.diag(aa) + np.diag(bb, 1) + np.diag(bb, -1))
+        assert np.abs(lam - ref).max() < 1e-14 * n * np.abs(ref).max()
+        check_decomposition(lam, Z, aa, bb)
+        parity = np.sum(Z * Z[::-1, :], axis=0)  # +1 even, -1 odd
+        assert np.abs(np.abs(parity) - 1).max() < 1e-12
+
+
+def test_nearly_persymmetric_inputs(T):
+    """Entries symmetric only to rounding (a grid computed in floating point) take the split
+    with the mirrored pairs averaged: the decomposition still satisfies the input to
+    rounding.  An asymmetry well above rounding takes the plain QR."""
+    n = 80
+    h = 16.0 / (n + 1)
+    x = -8.0 + h * np.arange(1, n + 1)
+    a = 2 / h ** 2 + (1.3 * x) ** 2
+    b = np.full(n - 1, -1 / h ** 2)
+    assert not np.array_equal(a, a[::-1])  # the float grid is not exactly symmetric
+    lam, Z = T.ts_tridiag_eig(a, b)
+    check_decomposition(lam, Z, a, b)
+    skew = a + 1e-6 * x  # an odd term: no symmetry
+    lam2, Z2 = T.ts_tridiag_eig(skew, b)
+    ref = np.linalg.eigvalsh(np.diag(skew) + np.diag(b, 1) + np.diag(b, -1))
+    assert np.abs(lam2 - ref).max() < 1e-14 * n * np.abs(ref).max()
+    check_decomposition(lam2, Z2, skew, b)
