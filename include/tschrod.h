@@ -437,13 +437,17 @@ typedef struct {
   ts_precision prec;   /* contraction precision (PCG: of the preconditioner)              */
 } ts_request;
 
+#define TS_SERVER_MAX_INFLIGHT 1024
 typedef struct {
   long long memory_budget_bytes; /* scratch budget (<= 0: half the free device memory)   */
-  int max_inflight;              /* requests on the GPU at once (<= 0: 8)                */
+  int max_inflight;              /* requests on the GPU at once (<= 0: 8); each is one
+                                    stream and one pooled PCG thread, so values above
+                                    TS_SERVER_MAX_INFLIGHT are refused with
+                                    TS_ERR_INVALID_ARG before any CUDA call             */
   int max_batch;                 /* requests per captured graph (<= 0: max_inflight)     */
   int plan_cache_entries;        /* cached plans (<= 0: 1024)                            */
   int planner_threads;           /* host threads building plans ahead of admission
-                                    (<= 0: 4); each build eigendecomposes the new axes on
+                                    (<= 0: 4; above 64: 64); each build eigendecomposes the new axes on
                                     the host, so more threads help while host cores are
                                     free and hurt once they compete with the scheduler
                                     and the PCG threads                                 */

@@ -418,12 +418,13 @@ using namespace ts;
 
 extern "C" {
 
-ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
-  clear_error();
-  TS_REQUIRE(out, "out is NULL");
-  *out = nullptr;
-  ts_server* sv = new ts_server();
-  if (cfg) sv->cfg = *cfg;
+namespace {
+
+// Streams, kernels and threads of a new server; the threads start only after every CUDA
+// call has succeeded, so a failure leaves only streams for the caller to release.
+ts_status server_init(ts_server* sv) {
+  TS_REQUIRE(sv->cfg.max_inflight <= TS_SERVER_MAX_INFLIGHT, "max_inflight %d is above %d", sv->cfg.max_inflight,
+             TS_SERVER_MAX_INFLIGHT);
   if (sv->cfg.max_inflight <= 0) sv->cfg.max_inflight = 8;
   if (sv->cfg.max_batch <= 0) sv->cfg.max_batch = sv->cfg.max_inflight;
   if (sv->cfg.plan_cache_entries <= 0) sv->cfg.plan_cache_entries = 1024;
@@ -451,6 +452,27 @@ ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
   for (int i = 0; i < nplanners; ++i) sv->planners.emplace_back(planner_loop, sv, i);
   for (int i = 0; i < sv->cfg.max_inflight; ++i) sv->pcg_workers.emplace_back(pcg_worker_loop, sv);
   sv->worker = std::thread(worker_loop, sv);
+  return TS_OK;
+}
+
+}  // namespace
+
+ts_status ts_server_create(const ts_server_config* cfg, ts_server** out) {
+  clear_error();
+  TS_REQUIRE(out, "out is NULL");
+  *out = nullptr;
+  ts_server* sv = new ts_server();
+  if (cfg) sv->cfg = *cfg;
+  const ts_status st = server_init(sv);
+  if (st != TS_OK) {
+    for (auto s : sv->streams)
+      if (s) cudaStreamDestroy(s);
+    for (auto s : sv->planner_streams)
+      if (s) cudaStreamDestroy(s);
+    if (sv->capture_stream) cudaStreamDestroy(sv->capture_stream);
+    delete sv;
+    return st;
+  }
   *out = sv;
   return TS_OK;
 }

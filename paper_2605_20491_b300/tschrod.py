@@ -67,6 +67,7 @@ class _ServingStats(C.Structure):
 
 
 TS_TC_PAIR = -2  # ts_tc_config_set cluster value: CTA pairs sharing each MMA
+TS_SERVER_MAX_INFLIGHT = 1024  # largest ts_server_config.max_inflight
 TS_REQ_INVERSE, TS_REQ_EXP, TS_REQ_PCG = range(3)
 
 

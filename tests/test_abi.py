@@ -142,3 +142,21 @@ def test_unassigned_precisions_are_refused_on_host(built_lib):
         desc = T._Desc(1, n, Lx, f, 0, 1)
         assert L.ts_plan_create(C.byref(desc), 1 << bit, None, C.byref(out)) == T.TS_ERR_INVALID_ARG
         assert "not assigned" in T.ts_last_error() and out.value is None
+
+
+def test_server_config_checked_before_device_work(built_lib):
+    """max_inflight above TS_SERVER_MAX_INFLIGHT is refused before any CUDA call; on a
+    host without a device a valid config fails in its first CUDA call instead, and both
+    return no handle (the half-built server is released)."""
+    import ctypes as C
+    from paper_2605_20491_b300 import tschrod as T
+    L = T.lib()
+    out = C.c_void_p()
+    cfg = T._ServerConfig(0, T.TS_SERVER_MAX_INFLIGHT + 1, 0, 0, 0)
+    assert L.ts_server_create(C.byref(cfg), C.byref(out)) == T.TS_ERR_INVALID_ARG
+    assert "max_inflight" in T.ts_last_error() and out.value is None
+    import torch
+    if not torch.cuda.is_available():
+        cfg = T._ServerConfig(0, 4, 0, 0, 0)
+        assert L.ts_server_create(C.byref(cfg), C.byref(out)) != T.TS_OK
+        assert out.value is None
