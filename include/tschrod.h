@@ -179,10 +179,9 @@ ts_status ts_apply_inverse(const ts_plan* plan, double sigma, const double* b, d
  * above it returns TS_ERR_INVALID_ARG with its own requirement in the message.  Set-up: the
  * first call in each CUDA context of a device looks up the array's device address
  * (cudaGetSymbolAddress) and keeps it for that context; a device whose context has been
- * replaced (e.g. after cudaDeviceReset) is looked up again.  Make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's contents
- * (nothing needs to start at zero); calls that overlap on the GPU (other streams or
- * threads) race on it, so serialise them.
+ * replaced (e.g. after cudaDeviceReset) is looked up again.  All calls share the array
+ * and it keeps the last call's contents (nothing needs to start at zero); calls that
+ * overlap on the GPU (other streams or threads) race on it, so serialise them.
  */
 ts_status ts_apply_inverse_noalloc(const ts_plan* plan, double sigma, const double* b, double* u,
                                    ts_precision prec, void* stream);
